@@ -1,0 +1,194 @@
+"""Oracle: the filter equations and their conjugate-gradient solution.  Test infrastructure only.
+
+For a wavenumber k (l = 1/k, Sect. 2.1) and order n the system matrix is
+    S = M + (1/2) l^(2n) K (M^-1 K)^(n-1)
+with M = diag(A) the lumped mass and K the l-free operator of the placement
+(Sect. 2.1.1: n = 1 and n = 2 written out, "can be generalized").  Right-hand
+sides and initial guesses per placement:
+  vertex_scalar : b = M phi,           x0 = phi            (Sect. 2.1.1)
+  vertex_vector : b = R u_c (2 comps), x0 = M^-1 b, unknowns (u block, v block)
+                  coupled by T                              (Sect. 2.1.2)
+  cell          : b = A_c u_c,         x0 = u_c, each component on its own (Eq. 6)
+The solve follows Sect. 2.2.2: S x0 is subtracted first (residual form), then
+conjugate gradients run on the remainder.  The result is the unique solution
+of the SPD system; CG is only the means, so the oracle drives the true
+residual as low as FP64 allows, and `filter_dense` re-solves tiny systems with
+a dense LU as a second opinion.
+
+Entries that are not unknowns (land) pass through unchanged for the vertex
+scalar and cell placements; the vertex-vector output is zero there.
+
+`residual_certificate` bounds the error of any candidate solution without
+solving: S >= M (K is symmetric positive semidefinite for n = 1, and
+K M^-1 K is for n = 2), hence ||x - x*||_M <= ||b - S x||_{M^-1}.
+Parity: pinned (Fourier closed forms on periodic grids, dense solves, tests).
+"""
+
+from dataclasses import dataclass, field as dc_field
+
+import numpy as np
+import scipy.sparse as sp
+
+from .operators import scalar_vertex_operators, vector_vertex_operators, cell_operators
+
+
+@dataclass
+class Problem:
+    placement: str
+    K: sp.csr_matrix           # l-free operator of the unknowns, symmetric
+    A: np.ndarray              # lumped mass of the unknowns
+    n_in: int                  # entries per input component
+    n_out: int                 # entries per output component
+    n_comp: int
+    out_ids: np.ndarray        # output index of each output unknown
+    parts: dict = dc_field(default_factory=dict)
+
+    def apply_S(self, x, ell, order):
+        """S x = M x + (1/2) l^(2n) K (M^-1 K)^(n-1) x."""
+        y = self.K @ x
+        for _ in range(order - 1):
+            y = self.K @ (y / self.A)
+        return self.A * x + 0.5 * ell ** (2 * order) * y
+
+    def systems(self, fld):
+        """[(b, x0)] of the independent systems of one field [n_comp][n_in]."""
+        if self.placement == "vertex_scalar":
+            phi = fld[0][self.parts["vert_ids"]]
+            return [(self.A * phi, phi.copy())]
+        if self.placement == "vertex_vector":
+            kc = self.parts["kept_tri"]
+            R = self.parts["R"]
+            b = np.concatenate([R @ fld[0][kc], R @ fld[1][kc]])
+            return [(b, b / self.A)]
+        if self.placement == "cell":
+            ids = self.parts["cell_ids"]
+            return [(self.A * fld[c][ids], fld[c][ids].copy()) for c in range(self.n_comp)]
+        raise ValueError(self.placement)
+
+    def output(self, fld, sols):
+        """Assemble [n_comp][n_out] from the system solutions."""
+        if self.placement == "vertex_scalar":
+            out = np.array(fld, dtype=np.float64, copy=True)
+            out[0][self.out_ids] = sols[0]
+            return out
+        if self.placement == "vertex_vector":
+            n = self.out_ids.size
+            out = np.zeros((2, self.n_out))
+            out[0][self.out_ids] = sols[0][:n]
+            out[1][self.out_ids] = sols[0][n:]
+            return out
+        out = np.array(fld, dtype=np.float64, copy=True)
+        for c in range(self.n_comp):
+            out[c][self.out_ids] = sols[c]
+        return out
+
+    def weights(self):
+        """Area of each output unknown (A_v or A_c)."""
+        if self.placement == "vertex_vector":
+            return self.A[: self.out_ids.size]
+        return self.A
+
+
+def build_problem(mesh, placement, cell_A=None):
+    V = mesh["coords"].shape[0]
+    T = np.asarray(mesh["tri"]).shape[0]
+    if placement == "vertex_scalar":
+        o = scalar_vertex_operators(mesh)
+        return Problem(placement, o["K"], o["A"], V, V, 1, o["vert_ids"], parts=o)
+    if placement == "vertex_vector":
+        o = vector_vertex_operators(mesh)
+        K2 = sp.bmat([[o["Kt"], o["Tm"]], [-o["Tm"], o["Kt"]]]).tocsr()
+        A2 = np.concatenate([o["A"], o["A"]])
+        return Problem(placement, K2, A2, T, V, 2, o["vert_ids"], parts=o)
+    if placement == "cell":
+        o = cell_operators(mesh, cell_A)
+        return Problem(placement, o["K"], o["A"], T, T, 2, o["cell_ids"], parts=o)
+    raise ValueError(placement)
+
+
+def cg(apply_A, b, x0, rtol, max_iter=200000, max_restarts=8):
+    """Conjugate gradients (Hestenes-Stiefel) from x0 for SPD A.
+
+    Stops when the TRUE residual ||b - A x|| <= rtol * ||b - A x0||; the
+    recursive residual is trusted only until it reaches the target, then CG
+    restarts from the current iterate (at most max_restarts times, and only
+    while the true residual keeps falling).
+    Returns (x, iterations, achieved true relative residual)."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = b - apply_A(x)
+    r0 = np.linalg.norm(r)
+    if r0 == 0.0:
+        return x, 0, 0.0
+    target = rtol * r0
+    its = 0
+    best = r0
+    for _ in range(max_restarts + 1):
+        p = r.copy()
+        rr = r @ r
+        while np.sqrt(rr) > target and its < max_iter:
+            q = apply_A(p)
+            alpha = rr / (p @ q)
+            x += alpha * p
+            r -= alpha * q
+            rr_new = r @ r
+            p = r + (rr_new / rr) * p
+            rr = rr_new
+            its += 1
+        r = b - apply_A(x)
+        true = np.linalg.norm(r)
+        if true <= target or its >= max_iter or true >= 0.5 * best:
+            best = min(best, true)
+            break
+        best = true
+    return x, its, best / r0
+
+
+def filter_field(problem, fld, ks, order, rtol=1e-14, max_iter=200000):
+    """Filtered fields [K][n_comp][n_out] and per-(k, system) stats."""
+    out = []
+    stats = []
+    for k in ks:
+        ell = 1.0 / k
+        sols = []
+        for b, x0 in problem.systems(fld):
+            x, its, rel = cg(lambda v: problem.apply_S(v, ell, order), b, x0, rtol, max_iter)
+            sols.append(x)
+            stats.append((k, its, rel))
+        out.append(problem.output(fld, sols))
+    return np.stack(out), stats
+
+
+def dense_S(problem, ell, order):
+    K = problem.K.toarray()
+    G = K.copy()
+    for _ in range(order - 1):
+        G = K @ (G / problem.A[:, None])
+    return np.diag(problem.A) + 0.5 * ell ** (2 * order) * G
+
+
+def filter_dense(problem, fld, ks, order):
+    """Same result as filter_field by a dense LU solve of S (small meshes only)."""
+    out = []
+    for k in ks:
+        S = dense_S(problem, 1.0 / k, order)
+        sols = [np.linalg.solve(S, b) for b, _ in problem.systems(fld)]
+        out.append(problem.output(fld, sols))
+    return np.stack(out)
+
+
+def residual_certificate(problem, fld, filtered_k, k, order):
+    """For one wavenumber: per system (||b - S x||_{M^-1}, ||x||_M) where x is the
+    candidate solution read back from `filtered_k` [n_comp][n_out].  The first
+    number bounds ||x - x*||_M."""
+    ell = 1.0 / k
+    res = []
+    syst = problem.systems(fld)
+    ids = problem.out_ids
+    if problem.placement == "vertex_vector":
+        xs = [np.concatenate([filtered_k[0][ids], filtered_k[1][ids]])]
+    else:
+        xs = [filtered_k[c][ids] for c in range(len(syst))]
+    for (b, _), x in zip(syst, xs):
+        r = b - problem.apply_S(x, ell, order)
+        res.append((np.sqrt(np.sum(r * r / problem.A)), np.sqrt(np.sum(problem.A * x * x))))
+    return res

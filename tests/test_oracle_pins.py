@@ -1,0 +1,361 @@
+"""Pins of the oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: a Fourier
+closed form, a brute-force re-derivation by another formula, an exact
+invariant, or a dense direct solve.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+import synth
+from oracle.mesh import edge_vectors
+from oracle.operators import scalar_vertex_operators, vector_vertex_operators, cell_operators
+
+
+def _fft_filter_split_square(f, n, ell, order):
+    """Sect. 2.1.1 with the split-square weights: M^-1 K is the 5-point
+    Laplacian, whose Fourier symbol is 4 sin^2(pi p/n) + 4 sin^2(pi q/n);
+    the filter multiplies each mode by 1 / (1 + (1/2) (l^2 mu)^n)  (Eq. 1)."""
+    p = np.fft.fftfreq(n) * n
+    mu = 4 * np.sin(np.pi * p / n)[None, :] ** 2 + 4 * np.sin(np.pi * p / n)[:, None] ** 2
+    H = 1.0 / (1.0 + 0.5 * (ell ** 2 * mu) ** order)
+    return np.real(np.fft.ifft2(np.fft.fft2(f.reshape(n, n)) * H)).ravel()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_split_square_matches_fourier_closed_form(order):
+    w = synth.workload("periodic32")
+    P = oracle.build_problem(w["mesh"], "vertex_scalar")
+    f = w["fields"][0]
+    out, st = oracle.filter_field(P, f, w["k"], order)
+    ref = _fft_filter_split_square(f[0], 32, 1.0 / w["k"][0], order)
+    assert np.max(np.abs(out[0, 0] - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_split_square_weights_exact():
+    """Diagonal edges of the split square have two right angles opposite them,
+    so their weight is exactly zero; axis edges get -1 (two 45-degree angles);
+    A_v = 6 * (1/2) / 3 = 1 (the Fig. 2 mesh)."""
+    m = synth.periodic_split_square(8, 8)
+    o = scalar_vertex_operators(m)
+    K = o["K"].tocoo()
+    assert np.allclose(o["A"], 1.0, rtol=1e-15)
+    x = m["coords"]
+    for i, j, v in zip(K.row, K.col, K.data):
+        if i == j:
+            assert v == 4.0
+            continue
+        d = x[j] - x[i]
+        d -= 8 * np.round(d / 8)
+        if abs(d[0]) + abs(d[1]) == 1:
+            assert v == -1.0
+        else:
+            assert abs(d[0]) == 1 and abs(d[1]) == 1 and v == 0.0
+    assert K.nnz == 64 * 7      # six mesh edges per vertex plus the diagonal
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_equilateral_plane_waves_are_eigenvectors(order):
+    """Equilateral lattice (side a): cot 60 deg = 1/sqrt(3), A_v = sqrt(3)/2 a^2, so
+    M^-1 K has the symbol (4 / (3 a^2)) sum_{3 edge directions} (1 - cos kappa.e).
+    Every allowed plane wave is filtered by 1 / (1 + (1/2)(l^2 mu)^n)."""
+    nx, ny, a = 12, 8, 2.0
+    m = synth.periodic_equilateral(nx, ny, a)
+    P = oracle.build_problem(m, "vertex_scalar")
+    x = m["coords"]
+    dirs = np.array([[a, 0], [a / 2, a * np.sqrt(3) / 2], [-a / 2, a * np.sqrt(3) / 2]])
+    ell = 1.7
+    for p, q in [(1, 0), (0, 1), (2, 3), (5, 7), (6, 4)]:
+        kap = np.array([2 * np.pi * p / m["period_x"], 2 * np.pi * q / m["period_y"]])
+        f = np.cos(x @ kap + 0.3)
+        mu = 4.0 / (3 * a * a) * np.sum(1 - np.cos(dirs @ kap))
+        H = 1.0 / (1.0 + 0.5 * (ell ** 2 * mu) ** order)
+        out, _ = oracle.filter_field(P, f[None, :], [1.0 / ell], order)
+        assert np.max(np.abs(out[0, 0] - H * f)) < 1e-12
+
+
+def test_equilateral_symbol_is_laplacian_at_long_waves():
+    """The weights reproduce -Lap: mu(kappa) / |kappa|^2 -> 1 as kappa -> 0."""
+    nx, ny, a = 64, 64, 1.0
+    m = synth.periodic_equilateral(nx, ny, a)
+    o = scalar_vertex_operators(m)
+    x = m["coords"]
+    kap = np.array([2 * np.pi / m["period_x"], 2 * np.pi / m["period_y"]])
+    f = np.cos(x @ kap)
+    Lf = (o["K"] @ f) / o["A"]
+    ratio = Lf[f > 0.5] / f[f > 0.5] / (kap @ kap)
+    assert np.allclose(ratio, 1.0, atol=2e-3)
+
+
+def _frame_gradients(P0, P1, P2):
+    """Brute force: gradients of the barycentric basis by solving the 2x2
+    system of a local orthonormal frame of the triangle's plane."""
+    e1 = P1 - P0
+    e2 = P2 - P0
+    u = e1 / np.linalg.norm(e1)
+    n = np.cross(e1, e2)
+    n /= np.linalg.norm(n)
+    v = np.cross(n, u)
+    J = np.array([[e1 @ u, e1 @ v], [e2 @ u, e2 @ v]])
+    # N1, N2 take values (1,0) and (0,1) at P1, P2 and 0 at P0
+    G = np.linalg.solve(J, np.eye(2))          # columns: gradients of N1, N2 in (u, v)
+    g1 = G[0, 0] * u + G[1, 0] * v
+    g2 = G[0, 1] * u + G[1, 1] * v
+    return [-(g1 + g2), g1, g2], 0.5 * np.linalg.norm(np.cross(e1, e2))
+
+
+def test_stiffness_matches_bruteforce_gradients_on_sphere():
+    m = synth.icosphere(2, radius=10.0, jitter=0.2, seed=5)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=6)
+    o = scalar_vertex_operators(m)
+    t = np.asarray(m["tri"])[o["kept_tri"]]
+    tl = o["tri_local"]
+    n = o["vert_ids"].size
+    K = np.zeros((n, n))
+    A = np.zeros(n)
+    x = m["coords"]
+    for c in range(t.shape[0]):
+        g, ar = _frame_gradients(x[t[c, 0]], x[t[c, 1]], x[t[c, 2]])
+        for a in range(3):
+            A[tl[c, a]] += ar / 3
+            for b in range(3):
+                K[tl[c, a], tl[c, b]] += ar * (g[a] @ g[b])
+    assert np.max(np.abs(o["K"].toarray() - K)) < 1e-12 * np.max(np.abs(K))
+    assert np.allclose(o["A"], A, rtol=1e-13)
+
+
+def test_invariants_scalar_operator():
+    m = synth.icosphere(3, radius=6371.0, jitter=0.2, seed=7)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=8)
+    o = scalar_vertex_operators(m)
+    K = o["K"]
+    assert np.max(np.abs(K @ np.ones(K.shape[0]))) < 1e-13 * np.max(np.abs(K.diagonal()))
+    assert abs(K - K.T).max() == 0.0
+    # Median-dual areas partition the kept triangles exactly
+    assert np.isclose(o["A"].sum(), o["tri_area"].sum(), rtol=1e-13)
+
+
+def test_sphere_area_converges_to_4_pi_r2():
+    errs = []
+    for lev in (2, 3, 4, 5):
+        m = synth.icosphere(lev, radius=1.0, jitter=0.0)
+        o = scalar_vertex_operators(m)
+        errs.append(abs(o["A"].sum() - 4 * np.pi))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.5 < r < 4.5 for r in ratios)      # second order: chordal area deficit ~ h^2
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "cell"])
+def test_constant_field_passes_unchanged(placement):
+    m = synth.icosphere(3, radius=6371.0, jitter=0.2, seed=9)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=10)
+    P = oracle.build_problem(m, placement)
+    n_in = P.n_in
+    f = np.full((P.n_comp, n_in), 2.5)
+    out, _ = oracle.filter_field(P, f, [2 * np.pi / 3000.0, 2 * np.pi / 300.0], 2)
+    assert np.max(np.abs(out - 2.5)) < 1e-12
+
+
+def test_mean_is_conserved():
+    m = synth.icosphere(3, radius=6371.0, jitter=0.2, seed=9)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=10)
+    P = oracle.build_problem(m, "vertex_scalar")
+    f = synth.grf_sphere(m["coords"], seed=3, n_features=64)[None, :]
+    for order in (1, 2):
+        out, _ = oracle.filter_field(P, f, [2 * np.pi / 2000.0], order)
+        ids = P.out_ids
+        assert np.isclose(P.A @ out[0, 0][ids], P.A @ f[0][ids], rtol=1e-11)
+
+
+def test_long_scale_limit_is_area_weighted_mean():
+    """n = 1, l -> infinity on a connected domain: the filter returns the
+    area-weighted mean (the kernel of K is the constants)."""
+    m = synth.icosphere(2, radius=1.0, jitter=0.2, seed=4)
+    P = oracle.build_problem(m, "vertex_scalar")
+    f = synth.grf_sphere(m["coords"], seed=2, n_features=32)[None, :]
+    # l = 1e4 on the unit sphere damps every non-constant mode (-Lap >= 2 there)
+    # below 1e-8, while keeping the system well enough conditioned for LU.
+    out = oracle.filter_dense(P, f, [1e-4], 1)
+    mean = (P.A @ f[0]) / P.A.sum()
+    assert np.max(np.abs(out[0, 0] - mean)) < 1e-5
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_cg_matches_dense_solve_on_tiny_meshes(placement, order):
+    m = synth.icosphere(2, radius=6371.0, jitter=0.2, seed=21)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=22, polar_cap_deg=10.0)
+    P = oracle.build_problem(m, placement)
+    rng = np.random.default_rng(0)
+    f = rng.normal(size=(P.n_comp, P.n_in))
+    ks = 2 * np.pi / np.array([5000.0, 2000.0, 800.0])
+    a, _ = oracle.filter_field(P, f, ks, order)
+    b = oracle.filter_dense(P, f, ks, order)
+    assert np.max(np.abs(a - b)) < 1e-11 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+def test_system_matrix_is_spd(placement):
+    m = synth.icosphere(1, radius=6371.0, jitter=0.2, seed=2)
+    P = oracle.build_problem(m, placement)
+    for order in (1, 2):
+        S = oracle.solve.dense_S(P, 3000.0, order)
+        assert np.max(np.abs(S - S.T)) <= 1e-12 * np.max(np.abs(S))
+        assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() > 0
+
+
+def test_vector_operator_reduces_to_scalar_on_plane():
+    """No metric terms on a plane: the vertex-vector filter is the scalar filter
+    of each component, with the cell-to-vertex projection as right-hand side."""
+    m = synth.periodic_split_square(12, 12)
+    Pv = oracle.build_problem(m, "vertex_vector")
+    Ps = oracle.build_problem(m, "vertex_scalar")
+    rng = np.random.default_rng(1)
+    f = rng.normal(size=(2, m["tri"].shape[0]))
+    ks = [0.7]
+    outv = oracle.filter_dense(Pv, f, ks, 2)
+    R = Pv.parts["R"]
+    S = oracle.solve.dense_S(Ps, 1 / 0.7, 2)
+    for c in range(2):
+        ref = np.linalg.solve(S, R @ f[c])
+        assert np.max(np.abs(outv[0, c] - ref)) < 1e-12
+
+
+def test_vector_metric_terms_by_quadrature():
+    """T and the metric mass term re-derived with a quadrature rule exact for
+    quadratics (edge midpoints) and brute-force frame gradients; T is
+    antisymmetric and [[K~, T], [-T, K~]] is symmetric."""
+    m = synth.icosphere(1, radius=6371.0, jitter=0.2, seed=3)
+    o = vector_vertex_operators(m)
+    x = m["coords"]
+    t = np.asarray(m["tri"])[o["kept_tri"]]
+    n = o["vert_ids"].size
+    Tq = np.zeros((n, n))
+    Mq = np.zeros((n, n))
+    R = m["radius"]
+    for c in range(t.shape[0]):
+        P = [x[t[c, i]] for i in range(3)]
+        g, ar = _frame_gradients(*P)
+        cen = (P[0] + P[1] + P[2]) / 3
+        cen /= np.linalg.norm(cen)
+        lat = np.arcsin(cen[2])
+        mc = np.tan(lat) / R
+        east = np.array([-cen[1], cen[0], 0.0]) / np.hypot(cen[0], cen[1])
+        dx = [gi @ east for gi in g]
+        # edge-midpoint rule: N values at the midpoints are 1/2 on the two ends
+        mids = [(0, 1), (1, 2), (2, 0)]
+        for a in range(3):
+            for b in range(3):
+                s_nn = 0.0
+                s_t = 0.0
+                for (i, j) in mids:
+                    Na = 0.5 * ((a == i) + (a == j))
+                    Nb = 0.5 * ((b == i) + (b == j))
+                    s_nn += Na * Nb * ar / 3
+                    s_t += mc * (-Nb * dx[a] + Na * dx[b]) * ar / 3
+                Mq[t[c, a], t[c, b]] += (R ** -2 + mc ** 2) * s_nn
+                Tq[t[c, a], t[c, b]] += s_t
+    Kt = o["Kt"].toarray() - o["K"].toarray()
+    assert np.max(np.abs(Kt - Mq)) < 1e-12 * np.max(np.abs(Mq))
+    assert np.max(np.abs(o["Tm"].toarray() - Tq)) < 1e-12 * np.max(np.abs(Tq))
+    T = o["Tm"].toarray()
+    assert np.max(np.abs(T + T.T)) < 1e-15 * np.max(np.abs(T))
+
+
+def _bloch_cells_split_square(u1, u2, n, ell, A_c, Aconst, order):
+    """Eq. 6 on the split square.  Lower triangle t1(i,j) neighbours
+    t2(i,j), t2(i,j-1), t2(i+1,j); upper t2(i,j) neighbours t1(i,j), t1(i,j+1),
+    t1(i-1,j).  With u_t(R) = sum alpha e^{i kappa.R} the graph Laplacian is
+    [[3, -g], [-conj g, 3]], g = 1 + e^{-i ky} + e^{i kx}, per mode."""
+    a1 = np.fft.fft2(u1.reshape(n, n))
+    a2 = np.fft.fft2(u2.reshape(n, n))
+    kk = 2 * np.pi * np.fft.fftfreq(n)
+    KX, KY = np.meshgrid(kk, kk, indexing="xy")
+    g = 1 + np.exp(-1j * KY) + np.exp(1j * KX)
+    o1 = np.empty_like(a1)
+    o2 = np.empty_like(a2)
+    c = Aconst * ell ** 2
+    for jj in range(n):
+        for ii in range(n):
+            L = np.array([[3, -g[jj, ii]], [-np.conj(g[jj, ii]), 3]])
+            G = L if order == 1 else L @ L / A_c
+            S = A_c * np.eye(2) + 0.5 * (c if order == 1 else c * c) * G
+            r = np.linalg.solve(S, A_c * np.array([a1[jj, ii], a2[jj, ii]]))
+            o1[jj, ii], o2[jj, ii] = r
+    return np.real(np.fft.ifft2(o1)).ravel(), np.real(np.fft.ifft2(o2)).ravel()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_cells_on_split_square_match_bloch_closed_form(order):
+    n = 16
+    m = synth.periodic_split_square(n, n)
+    P = oracle.build_problem(m, "cell", cell_A=1.5)
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=(2, 2 * n * n))
+    ell = 1.3
+    out, _ = oracle.filter_field(P, f, [1 / ell], order)
+    for c in range(2):
+        r1, r2 = _bloch_cells_split_square(f[c][0::2], f[c][1::2], n, ell, 0.5, 1.5, order)
+        assert np.max(np.abs(out[0, c][0::2] - r1)) < 1e-12
+        assert np.max(np.abs(out[0, c][1::2] - r2)) < 1e-12
+
+
+def test_cell_constant_reproduces_laplacian_with_mixed_term():
+    """A = 3/2 on the split square: -l^2(d_xx + d_yy + d_xy) at long waves
+    (the paper's Sect. 2.1.2 statement, sign set by the split direction)."""
+    n = 64
+    m = synth.periodic_split_square(n, n)
+    o = cell_operators(m, 1.5)
+    c = synth.triangle_centroids(m)
+    for kap in (np.array([2 * np.pi / n, 0]), np.array([0, 2 * np.pi / n]),
+                np.array([2 * np.pi / n, 2 * np.pi / n])):
+        f = np.cos(c @ kap)
+        rq = (f @ (o["K"] @ f)) / (f @ (o["A"] * f))     # Rayleigh quotient
+        sym = kap[0] ** 2 + kap[1] ** 2 + kap[0] * kap[1]
+        assert abs(rq / sym - 1.0) < 5e-3
+
+
+def test_cell_constant_sqrt3_on_equilateral_mesh():
+    nx, ny = 64, 64
+    m = synth.periodic_equilateral(nx, ny, 1.0)
+    o = cell_operators(m, np.sqrt(3.0))
+    c = synth.triangle_centroids(m)
+    kap = np.array([2 * np.pi / m["period_x"], 0.0])
+    f = np.cos(c @ kap)
+    rq = (f @ (o["K"] @ f)) / (f @ (o["A"] * f))         # Rayleigh quotient
+    assert abs(rq / (kap @ kap) - 1.0) < 5e-3
+
+
+def test_spectrum_matches_parseval_on_periodic_grid():
+    """E(k) on the periodic grid equals (1/2) sum |phi_hat H_k|^2 / N^2 (Parseval)."""
+    n = 32
+    m = synth.periodic_split_square(n, n)
+    P = oracle.build_problem(m, "vertex_scalar")
+    f = synth.grf_periodic(n, n, seed=4)[None, :]
+    ks = np.array([0.2, 0.4, 0.9, 2.0])
+    out, _ = oracle.filter_field(P, f, ks, 1)
+    E = oracle.filtered_energy(out, P.out_ids, P.weights())
+    Eref = []
+    for k in ks:
+        g = _fft_filter_split_square(f[0], n, 1 / k, 1)
+        Eref.append(0.5 * np.sum(np.abs(np.fft.fft2(g.reshape(n, n))) ** 2) / n ** 4)
+    assert np.allclose(E, Eref, rtol=1e-12)
+    kmid, spec = oracle.spectrum(ks, E)
+    assert np.all(spec >= 0)
+    assert np.allclose(kmid, np.sqrt(ks[1:] * ks[:-1]))
+
+
+def test_certificate_bounds_error():
+    m = synth.icosphere(2, radius=6371.0, jitter=0.2, seed=21)
+    P = oracle.build_problem(m, "vertex_scalar")
+    rng = np.random.default_rng(3)
+    f = rng.normal(size=(1, P.n_in))
+    k = 2 * np.pi / 3000.0
+    exact = oracle.filter_dense(P, f, [k], 2)[0]
+    cand = exact + 1e-6 * rng.normal(size=exact.shape)
+    (bound, _), = oracle.residual_certificate(P, f, cand, k, 2)
+    err = np.sqrt(np.sum(P.A * (cand[0][P.out_ids] - exact[0][P.out_ids]) ** 2))
+    assert err <= bound * (1 + 1e-9)
