@@ -1,0 +1,248 @@
+/*
+ * ifilt.h -- C ABI of the GB300 implicit-filter library (libifilt.so).
+ *
+ * The implicit filter of Nowak, Danilov, Mueller and Liu ("Implementation of
+ * implicit filter for spatial spectra extraction") coarse-grains a field phi
+ * on an unstructured triangular mesh by solving
+ *
+ *     (1 + 1/2 (-l^2 Lap)^n) phi_l = phi,      k = 1/l        (Eq. 1 and 2)
+ *
+ * with a discrete Laplacian built for the data placement (Sect. 2.1).  The
+ * work is split in two phases (Sect. 2.2): a mesh-only preparation whose
+ * arrays are reused for every scale, and a solving phase of sparse matrix
+ * products inside a conjugate-gradient iteration (Sect. 2.2.2).  Spectra are
+ * differences of filtered energies over k (Sect. 1, 4, 5).
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented "host" are CPU memory; "device" are CUDA device
+ *     memory of the current device (e.g. torch tensors' data_ptr()).
+ *   - The caller owns every buffer it passes; the library never frees them
+ *     and keeps no reference to them after the call returns.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; calls that return host results synchronise it.
+ *   - A negative ifilt_status is an error: outputs are left untouched and
+ *     ifilt_last_error() returns a message (thread-local).  IFILT_NOT_CONVERGED
+ *     is a warning: outputs are written, per-column stats say which columns
+ *     missed the tolerance.  No call aborts the process or waits without bound.
+ */
+#ifndef IFILT_H
+#define IFILT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ifilt_mesh_s* ifilt_mesh;
+
+typedef enum {
+  IFILT_OK = 0,
+  IFILT_NOT_CONVERGED = 1,   /* warning: some column stopped at max_iter or broke down */
+  IFILT_EINVAL = -1,         /* bad argument */
+  IFILT_ENOMEM = -2,         /* device or host allocation failed */
+  IFILT_ECUDA = -3,          /* a CUDA call failed */
+  IFILT_EMESH = -4,          /* malformed mesh (index out of range, degenerate triangle, ...) */
+  IFILT_DEVICE_TIMEOUT = -5  /* a bounded device-side wait expired */
+} ifilt_status;
+
+/* Data placements (Sect. 2.1, Fig. 1). */
+enum {
+  IFILT_VERTEX_SCALAR = 0,   /* scalar at vertices, median-dual volumes, P1 FE (Sect. 2.1.1)     */
+  IFILT_VERTEX_VECTOR = 1,   /* (u, v) from cells filtered at vertices with metric terms (Sect. 2.1.2) */
+  IFILT_CELL = 2             /* (u, v) at triangles, simplified Laplacian of Eq. 6, per component */
+};
+
+/* Mesh geometry. */
+enum {
+  IFILT_GEOM_PLANAR_PERIODIC = 0,  /* coords [V][2]; edge vectors taken as minimum images */
+  IFILT_GEOM_PLANAR = 1,           /* coords [V][2] */
+  IFILT_GEOM_SPHERE = 2            /* coords [V][3] on a sphere of `radius`; flat chordal triangles */
+};
+
+enum { IFILT_REORDER_NONE = 0, IFILT_REORDER_RCM = 1 };
+
+/* Arithmetic of the solve. */
+enum {
+  IFILT_PREC_FP64 = 0,       /* FP64 matrix, vectors and dots */
+  IFILT_PREC_FP32_IR = 1,    /* FP32 matrix and Krylov vectors, FP64 dots, FP64 true residual
+                                and iterative-refinement correction */
+  IFILT_PREC_BF16_IR = 2     /* as FP32_IR with BF16-stored matrix values */
+};
+
+enum {
+  IFILT_METHOD_PLAIN = 0,    /* one right-hand side at a time: S assembled per scale in FP64 CSR,
+                                separate SpMV / dot / axpy kernels, host convergence test every
+                                iteration (the paper's CG, Sect. 2.2.2) */
+  IFILT_METHOD_BATCHED = 1   /* every (field, component, scale) column of the call solved together:
+                                one shared operator, per-column shift, fused kernels, CUDA graphs */
+};
+
+/* How order n = 2 is solved by the batched method (ignored for n = 1). */
+enum {
+  IFILT_N2_AUTO = 0,         /* complex factorisation */
+  IFILT_N2_REAL = 1,         /* CG on S = M + 1/2 l^4 K M^-1 K with the product assembled */
+  IFILT_N2_COMPLEX = 2       /* S = M (1 + i a)(1 - i a), a = l^2 M^-1 K / sqrt(2):
+                                phi_l = Re[(M + i l^2/sqrt(2) K)^-1 M phi], solved by
+                                conjugate orthogonal CG (a CG-type method for complex
+                                symmetric systems).  Same solution, condition ~ l^2 instead of l^4. */
+};
+
+typedef struct {
+  int32_t n_vert;            /* V > 0 */
+  int32_t n_tri;             /* T > 0 */
+  const double* coords;      /* host [V][2] or [V][3] (geometry), any length unit */
+  const int32_t* tri;        /* host [T][3] vertex ids, counter-clockwise seen from outside */
+  const uint8_t* ocean;      /* host [V], nonzero = ocean; NULL = everything is ocean.
+                                A triangle is in the domain iff its 3 vertices are ocean;
+                                coast edges get the no-flux condition of Sect. 2.1 */
+  int32_t geometry;          /* IFILT_GEOM_* */
+  double period_x, period_y; /* periodic plane only */
+  double radius;             /* sphere only (metric factor m = tan(lat)/radius, Sect. 2.1.2) */
+  int32_t placement;         /* IFILT_VERTEX_SCALAR / _VECTOR / IFILT_CELL */
+  int32_t max_order;         /* highest filter order n the mesh must serve: 1 or 2 */
+  int32_t reorder;           /* IFILT_REORDER_* : device row order */
+  double cell_A;             /* constant A of Eq. 6 (cell placement); 0 selects sqrt(3) */
+  int32_t ell_slice;         /* rows per sliced-ELL slice; 0 = library default */
+} ifilt_mesh_desc;
+
+typedef struct {
+  int32_t order;             /* filter order n, 1 <= n <= mesh max_order */
+  double tol;                /* stop when ||r|| <= tol * ||r0|| (r0 = b - S phi, Sect. 2.2.2); the paper uses 1e-9 */
+  int32_t max_iter;          /* cap on Krylov iterations per column (all refinement rounds); 0 = 100000 */
+  int32_t precision;         /* IFILT_PREC_* */
+  int32_t method;            /* IFILT_METHOD_* */
+  int32_t n2_solver;         /* IFILT_N2_* */
+  int32_t precond;           /* 0 none, 1 Jacobi (diagonal of the shifted operator) */
+  int32_t check_every;       /* batched: iterations per CUDA graph between host checks; 0 = 32 */
+  double inner_tol;          /* FP32 inner solves: relative reduction per refinement round; 0 = 1e-4 */
+  int32_t max_lanes;         /* batched: widest column tile in 32-bit lanes; 0 = library default */
+} ifilt_solve_opts;
+
+typedef struct {
+  int32_t iters;             /* Krylov iterations (all rounds) */
+  int32_t refinements;       /* FP64 true-residual rounds */
+  int32_t status;            /* IFILT_OK or IFILT_NOT_CONVERGED */
+  int32_t pad;
+  double rel_residual;       /* final true ||b - S x|| / ||b - S x0|| in FP64 (of the system solved) */
+} ifilt_col_stats;
+
+typedef struct {
+  int32_t placement, geometry, max_order, reorder;
+  int32_t n_rows;            /* unknown rows on the device (vertices or cells of the ocean domain) */
+  int32_t n_in;              /* entries per input component (V, or T for vector/cell) */
+  int32_t n_out;             /* entries per output component (V, or T for cell) */
+  int32_t n_comp;            /* components per field: 1 scalar, 2 vector or cell */
+  int64_t nnz_k;             /* stored entries of the n = 1 operator (blocks for the vector placement) */
+  int64_t nnz_g2;            /* stored entries of K M^-1 K (0 if max_order < 2) */
+  int32_t ell_slice, ell_width_k, ell_width_g2, pad;
+  int64_t device_bytes;      /* device memory held by the handle */
+} ifilt_mesh_info_t;
+
+/* Export selectors for ifilt_mesh_export (host copies of the prepared arrays). */
+enum {
+  IFILT_EXPORT_PERM = 0,       /* int32 [n_rows]: original input index of each device row */
+  IFILT_EXPORT_K_ROWPTR = 1,   /* int64 [n_rows+1]: CSR of the n = 1 operator in device order */
+  IFILT_EXPORT_K_COL = 2,      /* int32 [nnz_k] */
+  IFILT_EXPORT_K_VAL = 3,      /* double [nnz_k] (vector placement: [nnz_k][2] = (K~, Tm)) */
+  IFILT_EXPORT_MASS = 4,       /* double [n_rows]: lumped mass A_v or A_c */
+  IFILT_EXPORT_G2_ROWPTR = 5,  /* int64 [n_rows+1] */
+  IFILT_EXPORT_G2_COL = 6,     /* int32 [nnz_g2] */
+  IFILT_EXPORT_G2_VAL = 7      /* double [nnz_g2] (vector: [nnz_g2][2]) */
+};
+
+/* Build and cache the mesh-only arrays on the current device (Sect. 2.2.1):
+ * ocean subset, device row order, the l-free operator K of the placement
+ * (P1 stiffness for vertices, Sect. 2.1.1; stiffness plus metric terms and the
+ * metric operator T for vectors, Sect. 2.1.2; A * graph Laplacian for cells,
+ * Eq. 6), the lumped mass, K M^-1 K when max_order >= 2, FP64 CSR and
+ * FP64/FP32/BF16 sliced-ELL copies.  Host inputs are read during the call only.
+ * On success *out owns device memory until ifilt_release_mesh.  Errors:
+ * EINVAL (null or inconsistent arguments), EMESH (index out of range, repeated
+ * vertex in a triangle, zero-area triangle, an edge shared by more than two
+ * ocean triangles, empty ocean), ENOMEM, ECUDA. */
+ifilt_status ifilt_prepare_mesh(const ifilt_mesh_desc* desc, void* stream, ifilt_mesh* out);
+
+/* The host half of ifilt_prepare_mesh: ocean subset, row order, operators
+ * and packing on the CPU, no device memory touched (needs no GPU).  The
+ * handle answers ifilt_mesh_info / ifilt_mesh_export; ifilt_mesh_upload makes
+ * it usable by ifilt_solve.  Errors as ifilt_prepare_mesh. */
+ifilt_status ifilt_prepare_mesh_host(const ifilt_mesh_desc* desc, ifilt_mesh* out);
+
+/* Copy a host-prepared mesh to the current device (no-op if already there).
+ * Errors: ENOMEM, ECUDA. */
+ifilt_status ifilt_mesh_upload(ifilt_mesh mesh, void* stream);
+
+/* Release a prepared mesh (NULL is ignored).  Waits for the device. */
+void ifilt_release_mesh(ifilt_mesh mesh);
+
+ifilt_status ifilt_mesh_info(ifilt_mesh mesh, ifilt_mesh_info_t* out);
+
+/* Copy one prepared array to host memory `dst` of `bytes` bytes (EINVAL if
+ * too small).  For tests of the integer layout against an independent
+ * reference. */
+ifilt_status ifilt_mesh_export(ifilt_mesh mesh, int32_t what, void* dst, size_t bytes);
+
+/* Filter a batch of fields at a list of wavenumbers (Eq. 1-2 solved as in
+ * Sect. 2.2.2).
+ *   fields  : device double [n_fields][n_comp][n_in]  (original mesh order)
+ *   k       : host double [n_k], k = 1/l > 0 in radians per coordinate unit
+ *   out     : device double [n_fields][n_k][n_comp][n_out]
+ *   stats   : host [n_fields][n_k][n_sys] or NULL, n_sys = 2 for the cell
+ *             placement (u and v solved separately) and 1 otherwise
+ * Land entries (not unknowns) of scalar-vertex and cell outputs copy the input;
+ * vertex-vector outputs are zero there.  Synchronises `stream` before
+ * returning.  Device scratch is taken from the stream-ordered allocator and
+ * returned before the call ends. */
+ifilt_status ifilt_solve(ifilt_mesh mesh, const ifilt_solve_opts* opts,
+                         int32_t n_fields, const double* fields, int32_t n_k,
+                         const double* k, double* out, ifilt_col_stats* stats,
+                         void* stream);
+
+/* Coarse-grained energy spectrum of filtered fields (Sect. 1, 4, 5; the paper
+ * gives no formula, the reading is):
+ *   energy[f][j] = sum_i w_i 1/2 sum_c out[f][j][c][i]^2 / sum_i w_i over unknowns i
+ *   spec[f][j]   = (energy[f][j+1] - energy[f][j]) / (k[j+1] - k[j]), k ascending,
+ *   kmid[j]      = sqrt(k[j] k[j+1])
+ * with w the lumped mass (A_v or A_c).  `filtered` is device memory in the
+ * layout ifilt_solve writes; k must be strictly ascending.  energy [F][n_k],
+ * spec [F][n_k-1] and kmid [n_k-1] are host memory (spec/kmid may be NULL).
+ * Synchronises `stream`. */
+ifilt_status ifilt_spectrum(ifilt_mesh mesh, int32_t n_fields, int32_t n_k,
+                            const double* k, const double* filtered,
+                            double* energy, double* spec, double* kmid, void* stream);
+
+/* Device memory an ifilt_solve call with these options would take from the
+ * stream-ordered allocator (upper bound), for admission control. */
+size_t ifilt_solve_scratch_bytes(ifilt_mesh mesh, const ifilt_solve_opts* opts,
+                                 int32_t n_fields, int32_t n_k);
+
+/* Per-kernel timing sampled with CUDA events on the launching stream while
+ * profiling is on (off by default).  Each record: kernel name, launches,
+ * sampled launches, summed sampled milliseconds, algorithmic bytes per launch
+ * (averaged over the sampled launches). */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  int64_t samples;
+  double sampled_ms;
+  double bytes_per_launch;
+} ifilt_kernel_profile;
+
+void ifilt_profile_enable(int32_t on);
+/* Writes up to `max` records, returns how many kernels have records. */
+int32_t ifilt_profile_read(ifilt_kernel_profile* out, int32_t max);
+void ifilt_profile_reset(void);
+
+/* Thread-local message for the last non-OK status of this thread. */
+const char* ifilt_last_error(void);
+
+/* Library version string. */
+const char* ifilt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFILT_H */

@@ -1,0 +1,277 @@
+"""Python binding of libifilt (include/ifilt.h): argument marshalling only.
+
+Every computation runs inside the compiled library; this module converts numpy
+arrays and torch CUDA tensors to pointers, checks shapes and dtypes, and raises
+IfiltError for a negative status.  There is no fallback: if the library is not
+built, `load()` raises.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libifilt.so")
+
+VERTEX_SCALAR, VERTEX_VECTOR, CELL = 0, 1, 2
+GEOM_PLANAR_PERIODIC, GEOM_PLANAR, GEOM_SPHERE = 0, 1, 2
+PREC_FP64, PREC_FP32_IR, PREC_BF16_IR = 0, 1, 2
+METHOD_PLAIN, METHOD_BATCHED = 0, 1
+N2_AUTO, N2_REAL, N2_COMPLEX = 0, 1, 2
+OK, NOT_CONVERGED = 0, 1
+EXPORT = dict(perm=0, k_rowptr=1, k_col=2, k_val=3, mass=4, g2_rowptr=5, g2_col=6, g2_val=7)
+PLACEMENTS = {"vertex_scalar": VERTEX_SCALAR, "vertex_vector": VERTEX_VECTOR, "cell": CELL}
+GEOMS = {"planar_periodic": GEOM_PLANAR_PERIODIC, "planar": GEOM_PLANAR, "sphere": GEOM_SPHERE}
+
+
+class IfiltError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ifilt status {status}: {msg}")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_vert", C.c_int32), ("n_tri", C.c_int32), ("coords", C.c_void_p), ("tri", C.c_void_p),
+                ("ocean", C.c_void_p), ("geometry", C.c_int32), ("period_x", C.c_double),
+                ("period_y", C.c_double), ("radius", C.c_double), ("placement", C.c_int32),
+                ("max_order", C.c_int32), ("reorder", C.c_int32), ("cell_A", C.c_double),
+                ("ell_slice", C.c_int32)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("order", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
+                ("method", C.c_int32), ("n2_solver", C.c_int32), ("precond", C.c_int32),
+                ("check_every", C.c_int32), ("inner_tol", C.c_double), ("max_lanes", C.c_int32)]
+
+
+class ColStats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("status", C.c_int32), ("pad", C.c_int32),
+                ("rel_residual", C.c_double)]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("placement", C.c_int32), ("geometry", C.c_int32), ("max_order", C.c_int32),
+                ("reorder", C.c_int32), ("n_rows", C.c_int32), ("n_in", C.c_int32), ("n_out", C.c_int32),
+                ("n_comp", C.c_int32), ("nnz_k", C.c_int64), ("nnz_g2", C.c_int64), ("ell_slice", C.c_int32),
+                ("ell_width_k", C.c_int32), ("ell_width_g2", C.c_int32), ("pad", C.c_int32),
+                ("device_bytes", C.c_int64)]
+
+
+class KernelProfile(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("samples", C.c_int64),
+                ("sampled_ms", C.c_double), ("bytes_per_launch", C.c_double)]
+
+
+COL_STATS_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("status", np.int32),
+                            ("pad", np.int32), ("rel_residual", np.float64)])
+
+# every symbol include/ifilt.h declares
+SYMBOLS = ["ifilt_prepare_mesh", "ifilt_prepare_mesh_host", "ifilt_mesh_upload", "ifilt_release_mesh", "ifilt_mesh_info", "ifilt_mesh_export", "ifilt_solve",
+           "ifilt_spectrum", "ifilt_solve_scratch_bytes", "ifilt_profile_enable", "ifilt_profile_read",
+           "ifilt_profile_reset", "ifilt_last_error", "ifilt_version"]
+
+_lib = None
+
+
+def load(path=None):
+    """Load libifilt.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with `python -m paper_2404_07398_gb300.build`")
+    lib = C.CDLL(p)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    lib.ifilt_prepare_mesh.argtypes = [C.POINTER(MeshDesc), vp, C.POINTER(vp)]
+    lib.ifilt_prepare_mesh.restype = i32
+    lib.ifilt_prepare_mesh_host.argtypes = [C.POINTER(MeshDesc), C.POINTER(vp)]
+    lib.ifilt_prepare_mesh_host.restype = i32
+    lib.ifilt_mesh_upload.argtypes = [vp, vp]
+    lib.ifilt_mesh_upload.restype = i32
+    lib.ifilt_release_mesh.argtypes = [vp]
+    lib.ifilt_release_mesh.restype = None
+    lib.ifilt_mesh_info.argtypes = [vp, C.POINTER(MeshInfo)]
+    lib.ifilt_mesh_info.restype = i32
+    lib.ifilt_mesh_export.argtypes = [vp, i32, vp, C.c_size_t]
+    lib.ifilt_mesh_export.restype = i32
+    lib.ifilt_solve.argtypes = [vp, C.POINTER(SolveOpts), i32, vp, i32, vp, vp, vp, vp]
+    lib.ifilt_solve.restype = i32
+    lib.ifilt_spectrum.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.ifilt_spectrum.restype = i32
+    lib.ifilt_solve_scratch_bytes.argtypes = [vp, C.POINTER(SolveOpts), i32, i32]
+    lib.ifilt_solve_scratch_bytes.restype = C.c_size_t
+    lib.ifilt_profile_enable.argtypes = [i32]
+    lib.ifilt_profile_enable.restype = None
+    lib.ifilt_profile_read.argtypes = [C.POINTER(KernelProfile), i32]
+    lib.ifilt_profile_read.restype = i32
+    lib.ifilt_profile_reset.argtypes = []
+    lib.ifilt_profile_reset.restype = None
+    lib.ifilt_last_error.argtypes = []
+    lib.ifilt_last_error.restype = C.c_char_p
+    lib.ifilt_version.argtypes = []
+    lib.ifilt_version.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st < 0:
+        raise IfiltError(st, load().ifilt_last_error().decode())
+    return st
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(a):
+    """Pointer of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return C.c_void_p(a.ctypes.data)
+    assert a.is_contiguous()
+    return C.c_void_p(a.data_ptr())
+
+
+class Mesh:
+    """A prepared mesh (device-resident handle)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        info = MeshInfo()
+        _check(load().ifilt_mesh_info(handle, C.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in MeshInfo._fields_ if f != "pad"}
+
+    def upload(self, stream=None):
+        _check(load().ifilt_mesh_upload(self.handle, _stream_ptr(stream)))
+
+    def release(self):
+        if self.handle:
+            load().ifilt_release_mesh(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+    def export(self, what):
+        key = EXPORT[what]
+        n = self.info["n_rows"]
+        nv = 2 if self.info["placement"] == VERTEX_VECTOR else 1
+        sizes = {"perm": (n, np.int32), "k_rowptr": (n + 1, np.int64), "k_col": (self.info["nnz_k"], np.int32),
+                 "k_val": (self.info["nnz_k"] * nv, np.float64), "mass": (n, np.float64),
+                 "g2_rowptr": (n + 1 if self.info["nnz_g2"] else 0, np.int64),
+                 "g2_col": (self.info["nnz_g2"], np.int32), "g2_val": (self.info["nnz_g2"] * nv, np.float64)}
+        cnt, dt = sizes[what]
+        out = np.zeros(max(int(cnt), 1), dtype=dt)
+        _check(load().ifilt_mesh_export(self.handle, key, _ptr(out), out.nbytes))
+        return out[:cnt]
+
+
+def _desc(mesh, placement, max_order, reorder, cell_A, ell_slice):
+    coords = np.ascontiguousarray(mesh["coords"], dtype=np.float64)
+    tri = np.ascontiguousarray(mesh["tri"], dtype=np.int32)
+    ocean = mesh.get("ocean")
+    ocean = None if ocean is None else np.ascontiguousarray(ocean, dtype=np.uint8)
+    d = MeshDesc(n_vert=coords.shape[0], n_tri=tri.shape[0], coords=coords.ctypes.data, tri=tri.ctypes.data,
+                 ocean=None if ocean is None else ocean.ctypes.data, geometry=GEOMS[mesh["geom"]],
+                 period_x=float(mesh.get("period_x", 0.0)), period_y=float(mesh.get("period_y", 0.0)),
+                 radius=float(mesh.get("radius", 0.0)), placement=PLACEMENTS.get(placement, placement),
+                 max_order=max_order, reorder=reorder, cell_A=float(cell_A), ell_slice=ell_slice)
+    return d, (coords, tri, ocean)   # keep the arrays alive with the descriptor
+
+
+def prepare_mesh(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_slice=0, stream=None):
+    """`mesh` is a dict with coords [V][2|3], tri [T][3], geom, period_x, period_y,
+    radius and optional ocean [V] (uint8).  Returns a device-resident Mesh."""
+    d, keep = _desc(mesh, placement, max_order, reorder, cell_A, ell_slice)
+    h = C.c_void_p()
+    _check(load().ifilt_prepare_mesh(C.byref(d), _stream_ptr(stream), C.byref(h)))
+    return Mesh(h)
+
+
+def prepare_mesh_host(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_slice=0):
+    """Host half of the preparation (no GPU needed): the Mesh answers info and
+    export; `upload()` makes it solvable."""
+    d, keep = _desc(mesh, placement, max_order, reorder, cell_A, ell_slice)
+    h = C.c_void_p()
+    _check(load().ifilt_prepare_mesh_host(C.byref(d), C.byref(h)))
+    return Mesh(h)
+
+
+def solve_opts(order=1, tol=1e-9, precision=PREC_FP64, method=METHOD_BATCHED, n2_solver=N2_AUTO, max_iter=0,
+               precond=0, check_every=0, inner_tol=0.0, max_lanes=0):
+    return SolveOpts(order=order, tol=tol, max_iter=max_iter, precision=precision, method=method,
+                     n2_solver=n2_solver, precond=precond, check_every=check_every, inner_tol=inner_tol,
+                     max_lanes=max_lanes)
+
+
+def solve(mesh, fields, k, out=None, stream=None, **opts):
+    """fields: torch CUDA float64 [F][n_comp][n_in]; k: 1-D array of wavenumbers.
+    Returns (out [F][K][n_comp][n_out] float64 CUDA tensor, stats structured array, status)."""
+    import torch
+    lib = load()
+    info = mesh.info
+    assert fields.is_cuda and fields.dtype == torch.float64 and fields.is_contiguous()
+    F = fields.shape[0]
+    assert tuple(fields.shape[1:]) == (info["n_comp"], info["n_in"]), (fields.shape, info)
+    kk = np.ascontiguousarray(k, dtype=np.float64).ravel()
+    K = kk.size
+    if out is None:
+        out = torch.empty((F, K, info["n_comp"], info["n_out"]), dtype=torch.float64, device=fields.device)
+    assert out.is_contiguous() and out.dtype == torch.float64
+    nsys = 2 if info["placement"] == CELL else 1
+    stats = np.zeros(F * K * nsys, dtype=COL_STATS_DTYPE)
+    o = solve_opts(**opts)
+    st = lib.ifilt_solve(mesh.handle, C.byref(o), F, _ptr(fields), K, _ptr(kk), _ptr(out), _ptr(stats),
+                         _stream_ptr(stream))
+    _check(st)
+    return out, stats.reshape(F, K, nsys), st
+
+
+def spectrum(mesh, filtered, k, stream=None):
+    """filtered: CUDA float64 [F][K][n_comp][n_out] (as `solve` returns); k ascending.
+    Returns (energy [F][K], spec [F][K-1], kmid [K-1]) as numpy arrays."""
+    lib = load()
+    kk = np.ascontiguousarray(k, dtype=np.float64).ravel()
+    F, K = filtered.shape[0], kk.size
+    energy = np.zeros((F, K))
+    spec = np.zeros((F, max(K - 1, 1)))
+    kmid = np.zeros(max(K - 1, 1))
+    _check(lib.ifilt_spectrum(mesh.handle, F, K, _ptr(kk), _ptr(filtered), _ptr(energy), _ptr(spec),
+                              _ptr(kmid), _stream_ptr(stream)))
+    return energy, spec[:, :K - 1], kmid[:K - 1]
+
+
+def scratch_bytes(mesh, F, K, **opts):
+    o = solve_opts(**opts)
+    return load().ifilt_solve_scratch_bytes(mesh.handle, C.byref(o), F, K)
+
+
+def profile_enable(on=True):
+    load().ifilt_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load().ifilt_profile_reset()
+
+
+def profile_read():
+    lib = load()
+    n = lib.ifilt_profile_read(None, 0)
+    arr = (KernelProfile * max(n, 1))()
+    lib.ifilt_profile_read(arr, n)
+    return [dict(name=a.name.decode(), launches=a.launches, samples=a.samples, sampled_ms=a.sampled_ms,
+                 bytes_per_launch=a.bytes_per_launch) for a in arr[:n]]
+
+
+def version():
+    return load().ifilt_version().decode()

@@ -1,0 +1,146 @@
+// Internal declarations of libifilt (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "../../include/ifilt.h"
+
+namespace ifilt {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  ifilt_status status;
+  std::string msg;
+};
+[[noreturn]] void fail(ifilt_status st, const char* fmt, ...);
+void set_last_error(const std::string& msg);
+
+#define IFILT_CUDA(call)                                                          \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      ::ifilt::fail(e_ == cudaErrorMemoryAllocation ? IFILT_ENOMEM : IFILT_ECUDA, \
+                    "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+                    __FILE__, __LINE__);                                          \
+  } while (0)
+
+// ---------------------------------------------------------------- host side
+// Compressed sparse rows; `nval` doubles per entry (1 = scalar, 2 = block
+// [[a, b], [-b, a]] stored as (a, b)).
+struct HostCSR {
+  int32_t n = 0;
+  int32_t nval = 1;
+  std::vector<int64_t> row_ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  int64_t nnz() const { return row_ptr.empty() ? 0 : row_ptr.back(); }
+};
+
+struct HostPrepared {
+  int32_t placement = 0, geometry = 0, max_order = 1, reorder = 1;
+  int32_t n_rows = 0, n_in = 0, n_out = 0, n_comp = 1;
+  std::vector<int32_t> perm;      // device row -> original index (vertex or triangle)
+  std::vector<double> mass;       // lumped mass per row
+  HostCSR K;                      // n = 1 operator, l-free, device order, sorted columns
+  HostCSR G2;                     // K M^-1 K (max_order >= 2)
+  // vertex-vector right-hand side: b_i = sum over incident ocean triangles c of (A_c / 3) u_c
+  std::vector<int64_t> proj_ptr;
+  std::vector<int32_t> proj_cell;
+  std::vector<double> proj_w;
+};
+
+HostPrepared prepare_host(const ifilt_mesh_desc& d);
+
+// ---------------------------------------------------------------- device side
+// Sliced ELL: rows are cut into slices of `slice_h`; slice s holds its rows
+// row-major with width slice_w[s] (a multiple of 4) starting at slice_off[s].
+// Padding entries point at their own row with value 0.
+struct DevEll {
+  int32_t n = 0, slice_h = 0, n_slices = 0, nval = 1, max_width = 0;
+  int64_t entries = 0;
+  int64_t* slice_off = nullptr;
+  int32_t* slice_w = nullptr;
+  int32_t* col = nullptr;
+  double* val64 = nullptr;
+  float* val32 = nullptr;
+  __nv_bfloat16* val16 = nullptr;
+};
+
+struct DevCSR {
+  int32_t n = 0;          // rows of the real (expanded) matrix
+  int64_t nnz = 0;
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+};
+
+}  // namespace ifilt
+
+struct ifilt_mesh_s {
+  ifilt::HostPrepared host;
+  int device = -1;               // -1 until uploaded
+  int32_t slice_h = 0;
+  int64_t bytes = 0;
+  std::vector<void*> allocations;
+  // device arrays
+  int32_t* perm = nullptr;       // [n_rows]
+  double* mass = nullptr;        // [n_rows]
+  double* diag_k = nullptr;      // [n_rows] diagonal of K (K~ for vectors)
+  double* diag_g2 = nullptr;     // [n_rows]
+  int64_t* proj_ptr = nullptr;
+  int32_t* proj_cell = nullptr;
+  double* proj_w = nullptr;
+  double* w_out = nullptr;       // [n_out] lumped mass of each output entry (0 where not an unknown)
+  int32_t* inv_perm = nullptr;   // [n_out] device row of each output entry, -1 where not an unknown
+  ifilt::DevEll ell_k, ell_g2;
+  ifilt::DevCSR csr_k, csr_g2;   // real expanded CSR in FP64 (vector placement: interleaved u,v rows)
+};
+
+namespace ifilt {
+
+// device upload (device_mesh.cu)
+void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st);
+void free_mesh(ifilt_mesh_s* m);
+
+// solvers (solve_plain.cu, solve_batched.cu)
+ifilt_status solve_plain(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, const double* fields,
+                         int32_t nk, const double* k, double* out, ifilt_col_stats* stats,
+                         cudaStream_t st);
+ifilt_status solve_batched(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F,
+                           const double* fields, int32_t nk, const double* k, double* out,
+                           ifilt_col_stats* stats, cudaStream_t st);
+size_t batched_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, int32_t nk);
+size_t plain_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o);
+
+// right-hand side and output maps (io.cu)
+// b and x0 of one system in device order, layout [n_rows][nsub] (nsub = 2 for
+// the vertex-vector placement, else 1).  `field` is one field [n_comp][n_in];
+// `comp` selects the component for the cell placement.
+void launch_rhs(ifilt_mesh_s* m, const double* field, int comp, double* b, double* x0, cudaStream_t st);
+// out[c][o] for every output entry o of one system: the solution where o is an
+// unknown, the input (scalar, cell) or 0 (vector) elsewhere.  x is [n_rows][nsub]
+// with stride `ld` doubles between consecutive sub-values (1 for a packed system).
+void launch_output_plain(ifilt_mesh_s* m, const double* x, const double* field, int comp,
+                         double* out_sys, cudaStream_t st);
+
+// spectrum (spectrum.cu)
+// energy [F][nk], spec [F][nk-1], kmid [nk-1] written to device buffers;
+// `partial` holds F*nk*nb doubles.
+void spectrum_device(ifilt_mesh_s* m, int32_t F, int32_t nk, const double* k_dev, const double* filtered,
+                     double* energy, double* spec, double* kmid, double* partial, int nb, cudaStream_t st);
+
+// profiling (abi.cpp): per-kernel launch counts and CUDA-event samples
+bool profiling_on();
+void profile_add(const char* name, int64_t launches, int64_t samples, double sampled_ms,
+                 double bytes_per_launch);
+
+// stream-ordered scratch
+void* scratch_alloc(size_t bytes, cudaStream_t st);
+void scratch_free(void* p, cudaStream_t st);
+
+}  // namespace ifilt

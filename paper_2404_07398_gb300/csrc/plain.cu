@@ -1,0 +1,265 @@
+// Plain path: one right-hand side at a time in FP64, the way the paper's
+// CuPy implementation proceeds (Sect. 2.2.2): for every scale the system
+// matrix S = M + 1/2 l^(2n) K (M^-1 K)^(n-1) is assembled explicitly as CSR,
+// S x0 is subtracted from the right-hand side, and conjugate gradients run
+// with one sparse matrix-vector product, separate dot and axpy kernels and a
+// host-side convergence test per iteration.  This is the baseline the
+// batched path is measured against.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace ifilt {
+namespace {
+
+constexpr int kBlock = 256;
+
+__global__ void assemble_s_kernel(int32_t n, int nsub, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                  const double* __restrict__ gval, const double* __restrict__ mass, double c,
+                                  double* __restrict__ sval) {
+  for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const double mr = mass[r / nsub];
+    for (int64_t e = rp[r]; e < rp[r + 1]; e++) sval[e] = c * gval[e] + (col[e] == r ? mr : 0.0);
+  }
+}
+
+// y = A x, TPR threads per row, shuffle reduction within the row group.
+template <int TPR>
+__global__ void spmv_csr_kernel(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ x,
+                                double* __restrict__ y) {
+  // The loop runs the same number of times in every lane of a warp (rows are
+  // taken a warp's worth at a time), so the shuffles below see all 32 lanes.
+  const int lane = threadIdx.x % TPR;
+  constexpr int RPW = 32 / TPR;  // rows per warp step
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+  const int sub = (threadIdx.x % 32) / TPR;
+  for (int64_t r0 = warp * RPW; r0 < n; r0 += nwarps * RPW) {
+    const int64_t r = r0 + sub;
+    double s = 0.0;
+    if (r < n)
+      for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += TPR) s += val[e] * x[col[e]];
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o /= 2) s += __shfl_down_sync(0xffffffffu, s, o, TPR);
+    if (lane == 0 && r < n) y[r] = s;
+  }
+}
+
+__global__ void dot_partial_kernel(int32_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                   double* __restrict__ partial) {
+  __shared__ double sm[kBlock / 32];
+  double s = 0.0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += a[i] * b[i];
+#pragma unroll
+  for (int o = 16; o > 0; o /= 2) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x % 32 == 0) sm[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBlock / 32; w++) t += sm[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void dot_final_kernel(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sm[kBlock];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o /= 2) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
+// Device scalars of the CG recurrence.
+struct Scalars {
+  double rho, rho_new, pq;
+};
+
+__global__ void sub_kernel(int32_t n, const double* __restrict__ b, const double* __restrict__ y,
+                           double* __restrict__ r, double* __restrict__ p) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double v = b[i] - y[i];
+    r[i] = v;
+    if (p) p[i] = v;
+  }
+}
+
+// x += alpha p  with alpha = rho / pq
+__global__ void axpy_x_kernel(int32_t n, const Scalars* __restrict__ s, const double* __restrict__ p,
+                              double* __restrict__ x) {
+  const double alpha = s->rho / s->pq;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += alpha * p[i];
+}
+
+// r -= alpha q
+__global__ void axpy_r_kernel(int32_t n, const Scalars* __restrict__ s, const double* __restrict__ q,
+                              double* __restrict__ r) {
+  const double alpha = s->rho / s->pq;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] -= alpha * q[i];
+}
+
+// p = r + beta p with beta = rho_new / rho; then rho <- rho_new (one thread, after the sweep it reads)
+__global__ void xpay_kernel(int32_t n, const Scalars* __restrict__ s, const double* __restrict__ r,
+                            double* __restrict__ p) {
+  const double beta = s->rho_new / s->rho;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = r[i] + beta * p[i];
+}
+
+__global__ void roll_rho_kernel(Scalars* s) { s->rho = s->rho_new; }
+
+struct PlainWork {
+  double *sval, *x, *b, *r, *p, *q, *partial;
+  Scalars* sc;
+  double* host;  // pinned [1]
+};
+
+}  // namespace
+
+size_t plain_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o) {
+  const DevCSR& G = o.order >= 2 ? m->csr_g2 : m->csr_k;
+  size_t n = (size_t)G.n;
+  return (size_t)G.nnz * 8 + 6 * n * 8 + 4096 * 8 + 1024;
+}
+
+ifilt_status solve_plain(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, const double* fields, int32_t nk,
+                         const double* k, double* out, ifilt_col_stats* stats, cudaStream_t st) {
+  const HostPrepared& h = m->host;
+  const DevCSR& G = o.order >= 2 ? m->csr_g2 : m->csr_k;
+  const int32_t n = G.n;  // real unknowns
+  const int nsub = h.placement == IFILT_VERTEX_VECTOR ? 2 : 1;
+  const int nsys = h.placement == IFILT_CELL ? 2 : 1;
+  const int max_iter = o.max_iter > 0 ? o.max_iter : 100000;
+  const int grid = (int)std::min<long long>((n + kBlock - 1) / kBlock, 152LL * 8);
+  const int nb = grid;
+
+  PlainWork w{};
+  char* base = (char*)scratch_alloc(plain_scratch_bytes(m, o), st);
+  char* cur = base;
+  auto take = [&](size_t bytes) {
+    char* p = cur;
+    cur += (bytes + 255) / 256 * 256;
+    return p;
+  };
+  w.sval = (double*)take((size_t)G.nnz * 8);
+  w.x = (double*)take((size_t)n * 8);
+  w.b = (double*)take((size_t)n * 8);
+  w.r = (double*)take((size_t)n * 8);
+  w.p = (double*)take((size_t)n * 8);
+  w.q = (double*)take((size_t)n * 8);
+  w.partial = (double*)take(4096 * 8);
+  w.sc = (Scalars*)take(sizeof(Scalars));
+  IFILT_CUDA(cudaMallocHost(&w.host, sizeof(double) * 2));
+
+  const double avg = (double)G.nnz / std::max(1, n);
+  auto spmv = [&](const double* x, double* y) {
+    if (avg <= 8) spmv_csr_kernel<4><<<grid * 2, kBlock, 0, st>>>(n, G.row_ptr, G.col, w.sval, x, y);
+    else if (avg <= 24) spmv_csr_kernel<8><<<grid * 2, kBlock, 0, st>>>(n, G.row_ptr, G.col, w.sval, x, y);
+    else spmv_csr_kernel<16><<<grid * 2, kBlock, 0, st>>>(n, G.row_ptr, G.col, w.sval, x, y);
+  };
+  auto dot = [&](const double* a, const double* b, double* dst) {
+    dot_partial_kernel<<<nb, kBlock, 0, st>>>(n, a, b, w.partial);
+    dot_final_kernel<<<1, kBlock, 0, st>>>(nb, w.partial, dst);
+  };
+  auto fetch = [&](const double* dev) {
+    IFILT_CUDA(cudaMemcpyAsync(w.host, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    IFILT_CUDA(cudaStreamSynchronize(st));
+    return w.host[0];
+  };
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  const bool prof = profiling_on();
+  if (prof) {
+    IFILT_CUDA(cudaEventCreate(&ev0));
+    IFILT_CUDA(cudaEventCreate(&ev1));
+  }
+  double spmv_ms = 0.0;
+  int64_t spmv_samples = 0, spmv_launches = 0;
+  // algorithmic bytes of one CSR SpMV: values + column indices + row pointers,
+  // one read of x per stored entry's column is counted once per row (x fits L2),
+  // plus x read and y written once.
+  const double spmv_bytes = (double)G.nnz * 12.0 + (double)(n + 1) * 8.0 + 2.0 * n * 8.0;
+
+  ifilt_status result = IFILT_OK;
+  const int64_t out_sys_stride = (int64_t)h.n_out;
+  for (int32_t f = 0; f < F; f++) {
+    const double* field = fields + (int64_t)f * h.n_comp * h.n_in;
+    for (int sys = 0; sys < nsys; sys++) {
+      for (int32_t j = 0; j < nk; j++) {
+        const double ell = 1.0 / k[j];
+        const double c = 0.5 * std::pow(ell, 2.0 * o.order);
+        assemble_s_kernel<<<grid, kBlock, 0, st>>>(n, nsub, G.row_ptr, G.col, G.val, m->mass, c, w.sval);
+        launch_rhs(m, field, sys, w.b, w.x, st);
+        spmv(w.x, w.q);
+        sub_kernel<<<grid, kBlock, 0, st>>>(n, w.b, w.q, w.r, w.p);
+        dot(w.r, w.r, &w.sc->rho);
+        const double rho0 = fetch(&w.sc->rho);
+        const double target = o.tol * std::sqrt(rho0);
+        double rho = rho0;
+        int it = 0;
+        bool broke = false;
+        while (std::sqrt(rho) > target && it < max_iter) {
+          if (prof && (it % 16) == 0) IFILT_CUDA(cudaEventRecord(ev0, st));
+          spmv(w.p, w.q);
+          if (prof && (it % 16) == 0) {
+            IFILT_CUDA(cudaEventRecord(ev1, st));
+          }
+          dot(w.p, w.q, &w.sc->pq);
+          axpy_x_kernel<<<grid, kBlock, 0, st>>>(n, w.sc, w.p, w.x);
+          axpy_r_kernel<<<grid, kBlock, 0, st>>>(n, w.sc, w.q, w.r);
+          dot(w.r, w.r, &w.sc->rho_new);
+          const double rn = fetch(&w.sc->rho_new);
+          if (prof && (it % 16) == 0) {
+            float ms = 0.f;
+            IFILT_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+            spmv_ms += ms;
+            spmv_samples++;
+          }
+          spmv_launches++;
+          it++;
+          if (!std::isfinite(rn)) {
+            broke = true;
+            break;
+          }
+          xpay_kernel<<<grid, kBlock, 0, st>>>(n, w.sc, w.r, w.p);
+          roll_rho_kernel<<<1, 1, 0, st>>>(w.sc);
+          rho = rn;
+        }
+        // true residual in FP64
+        spmv(w.x, w.q);
+        sub_kernel<<<grid, kBlock, 0, st>>>(n, w.b, w.q, w.r, nullptr);
+        dot(w.r, w.r, &w.sc->rho_new);
+        const double rt = std::sqrt(fetch(&w.sc->rho_new));
+        const double rel = rho0 > 0 ? rt / std::sqrt(rho0) : 0.0;
+        const bool ok = !broke && (rho0 == 0.0 || std::sqrt(rho) <= target);
+        if (!ok) result = IFILT_NOT_CONVERGED;
+        double* out_sys = out + (((int64_t)f * nk + j) * h.n_comp + sys) * out_sys_stride;
+        launch_output_plain(m, w.x, field, sys, out_sys, st);
+        if (stats) {
+          ifilt_col_stats& s = stats[((int64_t)f * nk + j) * nsys + sys];
+          s.iters = it;
+          s.refinements = 1;
+          s.status = ok ? IFILT_OK : IFILT_NOT_CONVERGED;
+          s.pad = 0;
+          s.rel_residual = rel;
+        }
+      }
+    }
+  }
+  IFILT_CUDA(cudaStreamSynchronize(st));
+  if (prof) {
+    profile_add("plain_spmv_csr_fp64", spmv_launches, spmv_samples, spmv_ms, spmv_bytes);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
+  cudaFreeHost(w.host);
+  scratch_free(base, st);
+  return result;
+}
+
+}  // namespace ifilt

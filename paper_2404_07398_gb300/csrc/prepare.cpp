@@ -1,0 +1,463 @@
+// Host side of the preparation phase (Sect. 2.2.1 of the paper): everything
+// that depends on the mesh only and is reused for every scale and field.
+//
+//   1. ocean subset: a triangle is in the domain iff its three vertices are
+//      ocean; coast edges carry the no-flux condition of Sect. 2.1 by simply
+//      having no neighbour across them;
+//   2. device row order: reverse Cuthill-McKee on the graph of the n = 1
+//      operator (least (degree, id) start per component, children by
+//      (degree, id), sequence reversed) so that gathered neighbour rows of a
+//      sparse product sit close together in memory;
+//   3. the l-free operator K of the placement and the lumped mass:
+//        vertex scalar: K_ab = int grad N_a . grad N_b = -1/2 cot(opposite angle)
+//                       summed over the two triangles of edge ab, A_v = sum A_c/3
+//                       (Sect. 2.1.1);
+//        vertex vector: blocks [[K~, Tm], [-Tm, K~]], K~ = stiffness + (R^-2 + m^2)
+//                       x consistent P1 mass, Tm_ab = int m (-N_b d_x N_a + N_a d_x N_b),
+//                       m = tan(lat)/R per triangle (Sect. 2.1.2);
+//        cell:          A * graph Laplacian of edge-adjacent triangles, A_c (Eq. 6);
+//   4. G2 = K M^-1 K for order n = 2 (Sect. 2.1.1).
+// Everything is FP64 here; device copies are cast once at upload.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace ifilt {
+namespace {
+
+struct V3 {
+  double x, y, z;
+};
+inline V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 add(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline V3 scale(V3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
+
+struct Geometry {
+  const double* xy;
+  int geom;
+  double px, py, radius;
+  V3 pos(int v) const {
+    if (geom == IFILT_GEOM_SPHERE) return {xy[3 * (int64_t)v], xy[3 * (int64_t)v + 1], xy[3 * (int64_t)v + 2]};
+    return {xy[2 * (int64_t)v], xy[2 * (int64_t)v + 1], 0.0};
+  }
+  // x_b - x_a, minimum image on the periodic plane
+  V3 edge(int a, int b) const {
+    V3 d = sub(pos(b), pos(a));
+    if (geom == IFILT_GEOM_PLANAR_PERIODIC) {
+      d.x -= px * std::nearbyint(d.x / px);
+      d.y -= py * std::nearbyint(d.y / py);
+    }
+    return d;
+  }
+};
+
+// Compressed adjacency (no self loops), rows sorted ascending.
+struct Graph {
+  int32_t n = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> adj;
+};
+
+// counting-sort based CSR "item -> list" builder
+void bucket(int32_t n, const std::vector<int32_t>& key, std::vector<int64_t>& ptr,
+            std::vector<int32_t>& idx) {
+  ptr.assign((size_t)n + 1, 0);
+  for (int32_t k : key) ptr[(size_t)k + 1]++;
+  for (int32_t i = 0; i < n; i++) ptr[i + 1] += ptr[i];
+  idx.resize(key.size());
+  std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+  for (size_t i = 0; i < key.size(); i++) idx[fill[key[i]]++] = (int32_t)i;
+}
+
+std::vector<int32_t> reverse_cuthill_mckee(const Graph& g) {
+  const int32_t n = g.n;
+  std::vector<int32_t> deg(n);
+  int32_t maxdeg = 0;
+  for (int32_t v = 0; v < n; v++) {
+    deg[v] = (int32_t)(g.ptr[v + 1] - g.ptr[v]);
+    maxdeg = std::max(maxdeg, deg[v]);
+  }
+  // vertices by (degree, id): counting sort on degree, stable in id
+  std::vector<int64_t> cnt((size_t)maxdeg + 2, 0);
+  for (int32_t v = 0; v < n; v++) cnt[deg[v] + 1]++;
+  for (int32_t d = 0; d <= maxdeg; d++) cnt[d + 1] += cnt[d];
+  std::vector<int32_t> by_key(n);
+  for (int32_t v = 0; v < n; v++) by_key[cnt[deg[v]]++] = v;
+
+  std::vector<uint8_t> seen(n, 0);
+  std::vector<int32_t> seq;
+  seq.reserve(n);
+  std::vector<int32_t> fresh;
+  size_t scan = 0, head = 0;
+  while ((int32_t)seq.size() < n) {
+    while (seen[by_key[scan]]) scan++;
+    int32_t s = by_key[scan];
+    seen[s] = 1;
+    seq.push_back(s);
+    while (head < seq.size()) {
+      int32_t u = seq[head++];
+      fresh.clear();
+      for (int64_t e = g.ptr[u]; e < g.ptr[u + 1]; e++) {
+        int32_t w = g.adj[e];
+        if (!seen[w]) {
+          seen[w] = 1;
+          fresh.push_back(w);
+        }
+      }
+      std::sort(fresh.begin(), fresh.end(), [&](int32_t a, int32_t b) {
+        return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
+      });
+      seq.insert(seq.end(), fresh.begin(), fresh.end());
+    }
+  }
+  std::reverse(seq.begin(), seq.end());
+  return seq;
+}
+
+// Position of column c in row r of a CSR with sorted columns.
+inline int64_t find_entry(const HostCSR& a, int32_t r, int32_t c) {
+  const int32_t* b = a.col.data() + a.row_ptr[r];
+  const int32_t* e = a.col.data() + a.row_ptr[r + 1];
+  const int32_t* p = std::lower_bound(b, e, c);
+  return (p != e && *p == c) ? (int64_t)(p - a.col.data()) : -1;
+}
+
+// CSR pattern in device order from a compact-id graph and the permutation.
+HostCSR pattern_from_graph(const Graph& g, const std::vector<int32_t>& order,
+                           const std::vector<int32_t>& rank, int nval) {
+  HostCSR a;
+  a.n = g.n;
+  a.nval = nval;
+  a.row_ptr.assign((size_t)g.n + 1, 0);
+  for (int32_t r = 0; r < g.n; r++) {
+    int32_t c = order[r];
+    a.row_ptr[r + 1] = a.row_ptr[r] + (g.ptr[c + 1] - g.ptr[c]) + 1;
+  }
+  a.col.resize(a.row_ptr.back());
+  for (int32_t r = 0; r < g.n; r++) {
+    int32_t c = order[r];
+    int32_t* out = a.col.data() + a.row_ptr[r];
+    int k = 0;
+    out[k++] = r;
+    for (int64_t e = g.ptr[c]; e < g.ptr[c + 1]; e++) out[k++] = rank[g.adj[e]];
+    std::sort(out, out + k);
+  }
+  a.val.assign((size_t)a.col.size() * nval, 0.0);
+  return a;
+}
+
+// G = K M^-1 K with the structural product pattern (explicit zeros kept).
+HostCSR product_kmk(const HostCSR& K, const std::vector<double>& mass) {
+  const int32_t n = K.n;
+  const int nv = K.nval;
+  HostCSR G;
+  G.n = n;
+  G.nval = nv;
+  G.row_ptr.assign((size_t)n + 1, 0);
+  std::vector<int32_t> mark(n, -1);
+  std::vector<double> acc((size_t)n * nv, 0.0);
+  std::vector<int32_t> cols;
+  // pass 1: pattern sizes
+  for (int32_t i = 0; i < n; i++) {
+    int64_t cnt = 0;
+    for (int64_t e = K.row_ptr[i]; e < K.row_ptr[i + 1]; e++) {
+      int32_t j = K.col[e];
+      for (int64_t f = K.row_ptr[j]; f < K.row_ptr[j + 1]; f++) {
+        int32_t k = K.col[f];
+        if (mark[k] != i) {
+          mark[k] = i;
+          cnt++;
+        }
+      }
+    }
+    G.row_ptr[i + 1] = G.row_ptr[i] + cnt;
+  }
+  G.col.resize(G.row_ptr.back());
+  G.val.resize((size_t)G.row_ptr.back() * nv);
+  std::fill(mark.begin(), mark.end(), -1);
+  for (int32_t i = 0; i < n; i++) {
+    cols.clear();
+    for (int64_t e = K.row_ptr[i]; e < K.row_ptr[i + 1]; e++) {
+      int32_t j = K.col[e];
+      const double inv = 1.0 / mass[j];
+      for (int64_t f = K.row_ptr[j]; f < K.row_ptr[j + 1]; f++) {
+        int32_t k = K.col[f];
+        if (mark[k] != i) {
+          mark[k] = i;
+          cols.push_back(k);
+          for (int q = 0; q < nv; q++) acc[(size_t)k * nv + q] = 0.0;
+        }
+        if (nv == 1) {
+          acc[k] += K.val[e] * inv * K.val[f];
+        } else {
+          // blocks [[a, b], [-b, a]] multiply like a + i b
+          double a1 = K.val[2 * e] * inv, b1 = K.val[2 * e + 1] * inv;
+          double a2 = K.val[2 * f], b2 = K.val[2 * f + 1];
+          acc[2 * (size_t)k] += a1 * a2 - b1 * b2;
+          acc[2 * (size_t)k + 1] += a1 * b2 + b1 * a2;
+        }
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    int64_t o = G.row_ptr[i];
+    for (size_t t = 0; t < cols.size(); t++) {
+      G.col[o + t] = cols[t];
+      for (int q = 0; q < nv; q++) G.val[(size_t)(o + t) * nv + q] = acc[(size_t)cols[t] * nv + q];
+    }
+  }
+  return G;
+}
+
+}  // namespace
+
+HostPrepared prepare_host(const ifilt_mesh_desc& d) {
+  if (d.n_vert <= 0 || d.n_tri <= 0 || !d.coords || !d.tri)
+    fail(IFILT_EINVAL, "mesh needs n_vert > 0, n_tri > 0, coords and tri");
+  if (d.placement < IFILT_VERTEX_SCALAR || d.placement > IFILT_CELL) fail(IFILT_EINVAL, "unknown placement %d", d.placement);
+  if (d.geometry < IFILT_GEOM_PLANAR_PERIODIC || d.geometry > IFILT_GEOM_SPHERE) fail(IFILT_EINVAL, "unknown geometry %d", d.geometry);
+  if (d.max_order < 1 || d.max_order > 2) fail(IFILT_EINVAL, "max_order must be 1 or 2");
+  if (d.geometry == IFILT_GEOM_PLANAR_PERIODIC && !(d.period_x > 0 && d.period_y > 0))
+    fail(IFILT_EINVAL, "periodic geometry needs positive periods");
+  if (d.geometry == IFILT_GEOM_SPHERE && !(d.radius > 0)) fail(IFILT_EINVAL, "sphere needs radius > 0");
+  if (d.reorder != IFILT_REORDER_NONE && d.reorder != IFILT_REORDER_RCM) fail(IFILT_EINVAL, "unknown reorder %d", d.reorder);
+
+  const int32_t V = d.n_vert, T = d.n_tri;
+  const int32_t* tri = d.tri;
+  const int dim = d.geometry == IFILT_GEOM_SPHERE ? 3 : 2;
+  for (int64_t i = 0; i < (int64_t)V * dim; i++)
+    if (!std::isfinite(d.coords[i])) fail(IFILT_EMESH, "coordinate %lld is not finite", (long long)i);
+  for (int32_t t = 0; t < T; t++) {
+    int a = tri[3 * (int64_t)t], b = tri[3 * (int64_t)t + 1], c = tri[3 * (int64_t)t + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= V || b >= V || c >= V)
+      fail(IFILT_EMESH, "triangle %d has a vertex index out of range", t);
+    if (a == b || b == c || a == c) fail(IFILT_EMESH, "triangle %d repeats a vertex", t);
+  }
+  Geometry geo{d.coords, d.geometry, d.period_x, d.period_y, d.radius};
+
+  HostPrepared hp;
+  hp.placement = d.placement;
+  hp.geometry = d.geometry;
+  hp.max_order = d.max_order;
+  hp.reorder = d.reorder;
+
+  // ---- 1. ocean subset
+  std::vector<int32_t> kept;  // original ids of kept triangles, ascending
+  kept.reserve(T);
+  for (int32_t t = 0; t < T; t++) {
+    bool k = true;
+    if (d.ocean)
+      k = d.ocean[tri[3 * (int64_t)t]] && d.ocean[tri[3 * (int64_t)t + 1]] && d.ocean[tri[3 * (int64_t)t + 2]];
+    if (k) kept.push_back(t);
+  }
+  if (kept.empty()) fail(IFILT_EMESH, "no ocean triangle");
+  const int32_t Tk = (int32_t)kept.size();
+  std::vector<double> area(Tk);
+  for (int32_t c = 0; c < Tk; c++) {
+    const int32_t* tv = tri + 3 * (int64_t)kept[c];
+    V3 e1 = geo.edge(tv[0], tv[1]), e2 = geo.edge(tv[0], tv[2]);
+    area[c] = 0.5 * norm(cross(e1, e2));
+    if (!(area[c] > 0.0)) fail(IFILT_EMESH, "triangle %d has zero area", kept[c]);
+  }
+  // vertex compaction (ascending original id)
+  std::vector<int32_t> vid(V, -1), verts;
+  for (int32_t c = 0; c < Tk; c++)
+    for (int q = 0; q < 3; q++) vid[tri[3 * (int64_t)kept[c] + q]] = 0;
+  for (int32_t v = 0; v < V; v++)
+    if (vid[v] == 0) {
+      vid[v] = (int32_t)verts.size();
+      verts.push_back(v);
+    }
+  const int32_t Nv = (int32_t)verts.size();
+  // incidence: compact vertex -> kept triangles (compact triangle ids)
+  std::vector<int32_t> inc_key((size_t)Tk * 3);
+  for (int32_t c = 0; c < Tk; c++)
+    for (int q = 0; q < 3; q++) inc_key[3 * (size_t)c + q] = vid[tri[3 * (int64_t)kept[c] + q]];
+  std::vector<int64_t> inc_ptr;
+  std::vector<int32_t> inc_idx;  // -> 3*c + corner
+  bucket(Nv, inc_key, inc_ptr, inc_idx);
+  auto corner_v = [&](int32_t c, int q) { return vid[tri[3 * (int64_t)kept[c] + q]]; };
+
+  // ---- graph of the n = 1 operator (compact ids)
+  Graph g;
+  const bool cells = d.placement == IFILT_CELL;
+  if (!cells) {
+    g.n = Nv;
+    g.ptr.assign((size_t)Nv + 1, 0);
+    std::vector<int32_t> tmp;
+    std::vector<std::vector<int32_t>> rows;  // built row by row
+    g.adj.reserve((size_t)Nv * 7);
+    for (int32_t v = 0; v < Nv; v++) {
+      tmp.clear();
+      for (int64_t e = inc_ptr[v]; e < inc_ptr[v + 1]; e++) {
+        int32_t c = inc_idx[e] / 3;
+        for (int q = 0; q < 3; q++) {
+          int32_t w = corner_v(c, q);
+          if (w != v) tmp.push_back(w);
+        }
+      }
+      std::sort(tmp.begin(), tmp.end());
+      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+      g.adj.insert(g.adj.end(), tmp.begin(), tmp.end());
+      g.ptr[v + 1] = (int64_t)g.adj.size();
+    }
+  } else {
+    g.n = Tk;
+    g.ptr.assign((size_t)Tk + 1, 0);
+    g.adj.reserve((size_t)Tk * 3);
+    std::vector<int32_t> tmp;
+    for (int32_t c = 0; c < Tk; c++) {
+      tmp.clear();
+      for (int q = 0; q < 3; q++) {
+        int32_t a = corner_v(c, q), b = corner_v(c, (q + 1) % 3);
+        int found = 0;
+        // triangles incident to a that also contain b
+        for (int64_t e = inc_ptr[a]; e < inc_ptr[a + 1]; e++) {
+          int32_t c2 = inc_idx[e] / 3;
+          if (c2 == c) continue;
+          if (corner_v(c2, 0) == b || corner_v(c2, 1) == b || corner_v(c2, 2) == b) {
+            tmp.push_back(c2);
+            found++;
+          }
+        }
+        if (found > 1) fail(IFILT_EMESH, "an edge of triangle %d is shared by more than two ocean triangles", kept[c]);
+      }
+      std::sort(tmp.begin(), tmp.end());
+      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+      g.adj.insert(g.adj.end(), tmp.begin(), tmp.end());
+      g.ptr[c + 1] = (int64_t)g.adj.size();
+    }
+  }
+  const int32_t N = g.n;
+
+  // ---- 2. device order
+  std::vector<int32_t> order(N), rank(N);
+  if (d.reorder == IFILT_REORDER_RCM) order = reverse_cuthill_mckee(g);
+  else std::iota(order.begin(), order.end(), 0);
+  for (int32_t r = 0; r < N; r++) rank[order[r]] = r;
+
+  hp.n_rows = N;
+  hp.perm.resize(N);
+  for (int32_t r = 0; r < N; r++) hp.perm[r] = cells ? kept[order[r]] : verts[order[r]];
+  hp.n_comp = d.placement == IFILT_VERTEX_SCALAR ? 1 : 2;
+  hp.n_in = d.placement == IFILT_VERTEX_SCALAR ? V : T;
+  hp.n_out = cells ? T : V;
+
+  // ---- 3. operator and mass in device order
+  const int nval = d.placement == IFILT_VERTEX_VECTOR ? 2 : 1;
+  hp.K = pattern_from_graph(g, order, rank, nval);
+  HostCSR& K = hp.K;
+  hp.mass.assign(N, 0.0);
+  if (cells) {
+    const double Ac = d.cell_A > 0 ? d.cell_A : std::sqrt(3.0);
+    for (int32_t r = 0; r < N; r++) {
+      int64_t b = K.row_ptr[r], e = K.row_ptr[r + 1];
+      for (int64_t q = b; q < e; q++) K.val[q] = (K.col[q] == r) ? Ac * (double)(e - b - 1) : -Ac;
+      hp.mass[r] = area[order[r]];
+    }
+  } else {
+    const bool vec = d.placement == IFILT_VERTEX_VECTOR;
+    const bool sphere = d.geometry == IFILT_GEOM_SPHERE;
+    const double inv_r2 = sphere ? 1.0 / (d.radius * d.radius) : 0.0;
+    const size_t nnz = K.col.size();
+    std::vector<double> stiff(nnz, 0.0), mmass, tm;
+    if (vec) {
+      mmass.assign(nnz, 0.0);
+      tm.assign(nnz, 0.0);
+    }
+    for (int32_t c = 0; c < Tk; c++) {
+      const int32_t* tv = tri + 3 * (int64_t)kept[c];
+      int32_t rr[3] = {rank[vid[tv[0]]], rank[vid[tv[1]]], rank[vid[tv[2]]]};
+      const double A = area[c];
+      for (int q = 0; q < 3; q++) hp.mass[rr[q]] += A / 3.0;
+      // stiffness: corner k receives nothing, its opposite edge (a, b) gets -1/2 cot
+      for (int k = 0; k < 3; k++) {
+        int a = (k + 1) % 3, b = (k + 2) % 3;
+        V3 u = geo.edge(tv[k], tv[a]), v = geo.edge(tv[k], tv[b]);
+        double w = -0.5 * dot(u, v) / norm(cross(u, v));
+        stiff[find_entry(K, rr[a], rr[b])] += w;
+        stiff[find_entry(K, rr[b], rr[a])] += w;
+      }
+      if (vec) {
+        // metric factor m = tan(lat)/R and zonal unit vector at the centroid direction
+        double m = 0.0;
+        V3 east{1.0, 0.0, 0.0};
+        if (sphere) {
+          V3 cdir = add(add(geo.pos(tv[0]), geo.pos(tv[1])), geo.pos(tv[2]));
+          cdir = scale(cdir, 1.0 / norm(cdir));
+          double lat = std::asin(std::max(-1.0, std::min(1.0, cdir.z)));
+          m = std::tan(lat) / d.radius;
+          double h = std::sqrt(cdir.x * cdir.x + cdir.y * cdir.y);
+          east = {-cdir.y / h, cdir.x / h, 0.0};
+        }
+        // P1 gradients on the flat triangle: grad N_k = n x (x_{k+2} - x_{k+1}) / (2A)
+        V3 e1 = geo.edge(tv[0], tv[1]), e2 = geo.edge(tv[0], tv[2]);
+        V3 nrm = cross(e1, e2);
+        double twoA = norm(nrm);
+        nrm = scale(nrm, 1.0 / twoA);
+        double dx[3];
+        for (int k = 0; k < 3; k++) {
+          V3 eab = geo.edge(tv[(k + 1) % 3], tv[(k + 2) % 3]);
+          dx[k] = dot(scale(cross(nrm, eab), 1.0 / twoA), east);
+        }
+        const double coef = inv_r2 + m * m;
+        for (int a = 0; a < 3; a++)
+          for (int b = 0; b < 3; b++) {
+            int64_t p = find_entry(K, rr[a], rr[b]);
+            // consistent P1 mass: A/6 on the diagonal, A/12 off it
+            mmass[p] += coef * (a == b ? A / 6.0 : A / 12.0);
+            // int N = A/3; m and d_x N are constant on the triangle
+            if (a != b) tm[p] += m * (A / 3.0) * (dx[b] - dx[a]);
+          }
+      }
+    }
+    // diagonal stiffness: minus the off-diagonal row sum (basis functions sum to one)
+    for (int32_t r = 0; r < N; r++) {
+      double s = 0.0;
+      int64_t pd = -1;
+      for (int64_t q = K.row_ptr[r]; q < K.row_ptr[r + 1]; q++) {
+        if (K.col[q] == r) pd = q;
+        else s += stiff[q];
+      }
+      stiff[pd] = -s;
+    }
+    for (size_t q = 0; q < nnz; q++) {
+      if (vec) {
+        K.val[2 * q] = stiff[q] + mmass[q];
+        K.val[2 * q + 1] = tm[q];
+      } else {
+        K.val[q] = stiff[q];
+      }
+    }
+  }
+  if (d.placement == IFILT_VERTEX_VECTOR) {
+    // Projection of cell velocities to vertices: R_vc = A_c / 3 (Sect. 2.1.2)
+    hp.proj_ptr.assign((size_t)N + 1, 0);
+    for (int32_t r = 0; r < N; r++) {
+      int32_t v = order[r];
+      hp.proj_ptr[r + 1] = hp.proj_ptr[r] + (inc_ptr[v + 1] - inc_ptr[v]);
+    }
+    hp.proj_cell.resize(hp.proj_ptr.back());
+    hp.proj_w.resize(hp.proj_ptr.back());
+    for (int32_t r = 0; r < N; r++) {
+      int32_t v = order[r];
+      int64_t o = hp.proj_ptr[r];
+      for (int64_t e = inc_ptr[v]; e < inc_ptr[v + 1]; e++, o++) {
+        int32_t c = inc_idx[e] / 3;
+        hp.proj_cell[o] = kept[c];
+        hp.proj_w[o] = area[c] / 3.0;
+      }
+    }
+  }
+  // ---- 4. order-2 product
+  if (d.max_order >= 2) hp.G2 = product_kmk(K, hp.mass);
+  return hp;
+}
+
+}  // namespace ifilt
