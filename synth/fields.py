@@ -53,13 +53,14 @@ def grf_sphere(points, seed=13, n_features=512, k_min=None, k_max=None, slope=-3
     kap = d * kmag[:, None]
     theta = rng.uniform(0, 2 * np.pi, size=n_features)
     amp = kmag ** ((slope + 1.0) / 2.0) * rng.normal(size=n_features)
-    kap_t = torch.from_numpy(kap)
-    th_t = torch.from_numpy(theta)
-    amp_t = torch.from_numpy(amp)
+    dev = "cuda" if (pts.shape[0] > 2_000_000 and torch.cuda.is_available()) else "cpu"
+    kap_t = torch.tensor(kap, device=dev)
+    th_t = torch.tensor(theta, device=dev)
+    amp_t = torch.tensor(amp, device=dev)
     out = np.empty(pts.shape[0], dtype=np.float64)
     for s in range(0, pts.shape[0], chunk):
-        x = torch.from_numpy(pts[s:s + chunk])
+        x = torch.tensor(pts[s:s + chunk], device=dev)
         ph = (x[:, 0:1] * kap_t[:, 0] + x[:, 1:2] * kap_t[:, 1] + x[:, 2:3] * kap_t[:, 2]) + th_t
-        out[s:s + chunk] = (torch.cos(ph) * amp_t).sum(dim=1).numpy()
+        out[s:s + chunk] = (torch.cos(ph) * amp_t).sum(dim=1).cpu().numpy()
     out /= np.sqrt(np.mean(out ** 2))
     return out

@@ -84,40 +84,46 @@ _ICO_F = np.array([
 ], dtype=np.int64)
 
 
+def _device(n):
+    """Generator device: the GPU for big meshes when one is present."""
+    import torch
+    return "cuda" if (n > 2_000_000 and torch.cuda.is_available()) else "cpu"
+
+
 def _subdivide(xyz, faces):
-    """One 1-to-4 split of every face; midpoints projected to the unit sphere.
-    New vertices are appended in the order of their sorted edge key."""
+    """One 1-to-4 split of every face (torch tensors); midpoints projected to
+    the unit sphere.  New vertices are appended in the order of their sorted
+    edge key."""
+    import torch
     nv = xyz.shape[0]
     a, b, c = faces[:, 0], faces[:, 1], faces[:, 2]
-    e = np.stack([np.stack([a, b], 1), np.stack([b, c], 1), np.stack([c, a], 1)], 0)  # [3, F, 2]
-    lo = np.minimum(e[..., 0], e[..., 1])
-    hi = np.maximum(e[..., 0], e[..., 1])
-    key = lo * nv + hi
-    ukey, inv = np.unique(key.ravel(), return_inverse=True)
+    lo = torch.stack([torch.minimum(a, b), torch.minimum(b, c), torch.minimum(c, a)])
+    hi = torch.stack([torch.maximum(a, b), torch.maximum(b, c), torch.maximum(c, a)])
+    key = (lo * nv + hi).reshape(-1)
+    ukey, inv = torch.unique(key, sorted=True, return_inverse=True)
     inv = inv.reshape(3, -1)
-    ulo = ukey // nv
-    uhi = ukey % nv
-    mid = xyz[ulo] + xyz[uhi]
-    mid /= np.linalg.norm(mid, axis=1, keepdims=True)
-    new_xyz = np.concatenate([xyz, mid], 0)
+    mid = xyz[ukey // nv] + xyz[ukey % nv]
+    mid = mid / torch.linalg.norm(mid, dim=1, keepdim=True)
+    new_xyz = torch.cat([xyz, mid], 0)
     mab, mbc, mca = inv[0] + nv, inv[1] + nv, inv[2] + nv
-    f = np.empty((faces.shape[0] * 4, 3), dtype=np.int64)
-    f[0::4] = np.stack([a, mab, mca], 1)
-    f[1::4] = np.stack([mab, b, mbc], 1)
-    f[2::4] = np.stack([mca, mbc, c], 1)
-    f[3::4] = np.stack([mab, mbc, mca], 1)
+    f = torch.empty((faces.shape[0] * 4, 3), dtype=torch.int64, device=faces.device)
+    f[0::4] = torch.stack([a, mab, mca], 1)
+    f[1::4] = torch.stack([mab, b, mbc], 1)
+    f[2::4] = torch.stack([mca, mbc, c], 1)
+    f[3::4] = torch.stack([mab, mbc, mca], 1)
     return new_xyz, f
 
 
 def _tangent_basis(n):
-    """Orthonormal tangent vectors (e1, e2) at unit normals n (rows)."""
-    ref = np.zeros_like(n)
+    """Orthonormal tangent vectors (e1, e2) at unit normals n (rows, torch)."""
+    import torch
+    ref = torch.zeros_like(n)
     ref[:, 2] = 1.0
-    near_pole = np.abs(n[:, 2]) > 0.9
-    ref[near_pole] = np.array([1.0, 0.0, 0.0])
-    e1 = np.cross(ref, n)
-    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
-    e2 = np.cross(n, e1)
+    near_pole = n[:, 2].abs() > 0.9
+    ref[near_pole] = torch.tensor([1.0, 0.0, 0.0], dtype=n.dtype, device=n.device)
+    e1 = torch.linalg.cross(ref, n)
+    e1 = e1 / torch.linalg.norm(e1, dim=1, keepdim=True)
+    e2 = torch.linalg.cross(n, e1)
     return e1, e2
 
 
@@ -126,25 +132,34 @@ def icosphere(level, radius=6371.0, jitter=0.2, seed=11):
     20*4^level triangles.  Each vertex is displaced tangentially, uniformly in
     a disc of radius `jitter` times the mean length of its edges, then put back
     on the sphere (seeded)."""
-    xyz = _ICO_V / np.linalg.norm(_ICO_V, axis=1, keepdims=True)
-    faces = _ICO_F.copy()
+    import torch
+    dev = _device(10 * 4 ** level + 2)
+    xyz = torch.tensor(_ICO_V / np.linalg.norm(_ICO_V, axis=1, keepdims=True), device=dev)
+    faces = torch.tensor(_ICO_F, device=dev)
     for _ in range(level):
         xyz, faces = _subdivide(xyz, faces)
     if jitter > 0:
         nv = xyz.shape[0]
-        # mean incident edge length
-        e = np.concatenate([faces[:, [0, 1]], faces[:, [1, 2]], faces[:, [2, 0]]], 0)
-        ln = np.linalg.norm(xyz[e[:, 0]] - xyz[e[:, 1]], axis=1)
-        acc = np.bincount(e[:, 0], weights=ln, minlength=nv) + np.bincount(e[:, 1], weights=ln, minlength=nv)
-        cnt = np.bincount(e[:, 0], minlength=nv) + np.bincount(e[:, 1], minlength=nv)
+        e = torch.cat([faces[:, [0, 1]], faces[:, [1, 2]], faces[:, [2, 0]]], 0)
+        ln = torch.linalg.norm(xyz[e[:, 0]] - xyz[e[:, 1]], dim=1)
+        acc = torch.zeros(nv, dtype=xyz.dtype, device=dev)
+        cnt = torch.zeros(nv, dtype=xyz.dtype, device=dev)
+        acc.index_add_(0, e[:, 0], ln)
+        acc.index_add_(0, e[:, 1], ln)
+        one = torch.ones_like(ln)
+        cnt.index_add_(0, e[:, 0], one)
+        cnt.index_add_(0, e[:, 1], one)
         hloc = acc / cnt
         rng = np.random.default_rng(seed)
-        rad = jitter * hloc * np.sqrt(rng.random(nv))
-        ang = 2.0 * np.pi * rng.random(nv)
+        u1 = torch.tensor(rng.random(nv), device=dev)
+        u2 = torch.tensor(rng.random(nv), device=dev)
+        rad = jitter * hloc * torch.sqrt(u1)
+        ang = 2.0 * np.pi * u2
         e1, e2 = _tangent_basis(xyz)
-        xyz = xyz + (rad * np.cos(ang))[:, None] * e1 + (rad * np.sin(ang))[:, None] * e2
-        xyz /= np.linalg.norm(xyz, axis=1, keepdims=True)
-    return dict(coords=(xyz * radius).astype(np.float64), tri=faces.astype(np.int32),
+        xyz = xyz + (rad * torch.cos(ang))[:, None] * e1 + (rad * torch.sin(ang))[:, None] * e2
+        xyz = xyz / torch.linalg.norm(xyz, dim=1, keepdim=True)
+    coords = (xyz * radius).cpu().numpy().astype(np.float64)
+    return dict(coords=coords, tri=faces.cpu().numpy().astype(np.int32),
                 geom="sphere", period_x=0.0, period_y=0.0, radius=float(radius))
 
 
@@ -153,20 +168,26 @@ def land_mask(coords, frac_land=0.3, n_blobs=64, seed=12, polar_cap_deg=0.0):
     the unit sphere, thresholded so that a fraction `frac_land` of the points is
     land.  With polar_cap_deg > 0 every point within that many degrees of a
     geographic pole is also land."""
-    x = coords / np.linalg.norm(coords, axis=1, keepdims=True)
+    import torch
+    dev = _device(coords.shape[0])
+    x = torch.tensor(coords, device=dev)
+    x = x / torch.linalg.norm(x, dim=1, keepdim=True)
     rng = np.random.default_rng(seed)
     c = rng.normal(size=(n_blobs, 3))
     c /= np.linalg.norm(c, axis=1, keepdims=True)
     sig = rng.uniform(0.15, 0.5, size=n_blobs)
     w = rng.uniform(0.5, 1.5, size=n_blobs)
-    s = np.zeros(x.shape[0])
+    s = torch.zeros(x.shape[0], dtype=x.dtype, device=dev)
+    ct = torch.tensor(c, device=dev)
     for b in range(n_blobs):
-        d2 = 2.0 * (1.0 - x @ c[b])
-        s += w[b] * np.exp(-d2 / (2.0 * sig[b] ** 2))
+        d2 = 2.0 * (1.0 - x @ ct[b])
+        s += w[b] * torch.exp(-d2 / (2.0 * sig[b] ** 2))
+    s = s.cpu().numpy()
     thr = np.quantile(s, 1.0 - frac_land)
     land = s >= thr
     if polar_cap_deg > 0:
-        lat = np.degrees(np.arcsin(np.clip(x[:, 2], -1, 1)))
+        z = x[:, 2].clamp(-1, 1).cpu().numpy()
+        lat = np.degrees(np.arcsin(z))
         land |= np.abs(lat) >= 90.0 - polar_cap_deg
     return (~land).astype(np.uint8)
 
