@@ -1,0 +1,427 @@
+#!/usr/bin/env python3
+"""Benchmark: solved field-scales per second of the implicit filter.
+
+Workload (default): the velocity batch of the paper's scale -- an icosahedral
+sphere mesh of 10,485,762 vertices and 20,971,520 triangles (20 % jitter,
+30 % land plus polar caps), velocity components (u, v) on the triangles,
+filter order n = 2 at 40 wavenumbers log-spaced between 2*pi/4000 km and
+2*pi/10 km, filtered with the vertex-vector placement (Sect. 2.1.2, 40 scales
+x 2 components) and the cell placement (Eq. 6, 40 scales x 2 components), then
+turned into spectra.  One step = both solves + both spectra = 160 field-scales.
+Arithmetic: FP32 matrix and Krylov vectors, FP64 dots, FP64 true residual and
+refinement to the paper's relative tolerance 1e-9.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+bounded samples of the same workload instead.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solved field-scales/sec at 10.5M vertices, batched vs plain CG; p50/p99 latency"
+UNIT = "field-scales/s"
+N_K = 40
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--level", type=int, default=10, help="icosahedral level (10 = the named workload)")
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--plain-sample", type=int, default=2, help="columns timed on the plain FP64 path")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="ifilt_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r["power"] > 300.0] or rows
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                          ("swp", "sw_power_cap")):
+            if any(r[key].lower() == "active" for r in rows):
+                reasons.append(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(level):
+    import synth
+    w = synth.workload("uv_batch", level=level)
+    return w
+
+
+def workload_config(args, w, world):
+    m = w["mesh"]
+    return {"workload": f"uv_batch: icosahedral level {args.level} sphere, {m['coords'].shape[0]} vertices, "
+                        f"{m['tri'].shape[0]} triangles, 30% land + polar caps; (u,v) on triangles; "
+                        f"vertex-vector and cell placements; n=2; {N_K} wavenumbers 2pi/4000..2pi/10 km",
+            "vertices": int(m["coords"].shape[0]), "triangles": int(m["tri"].shape[0]),
+            "columns_per_step": 4 * N_K, "order": 2, "n2_solver": "complex", "tol": args.tol,
+            "precision": args.precision, "l2": "inputs larger than L2 (GBs per vector), no flush",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+class Ours:
+    """The CUDA path through the library's public API."""
+
+    def __init__(self, args, w):
+        import torch
+        from paper_2404_07398_gb300 import api
+        self.api = api
+        api.load()
+        self.k = np.ascontiguousarray(w["k"])
+        self.fields = torch.tensor(w["fields"], dtype=torch.float64, device="cuda")
+        t0 = time.time()
+        self.mv = api.prepare_mesh(w["mesh"], "vertex_vector", max_order=2)
+        self.mc = api.prepare_mesh(w["mesh"], "cell", max_order=2)
+        self.prepare_s = time.time() - t0
+        prec = {"fp32": api.PREC_FP32_IR, "bf16": api.PREC_BF16_IR, "fp64": api.PREC_FP64}[args.precision]
+        self.opts = dict(order=2, tol=args.tol, precision=prec, n2_solver=api.N2_COMPLEX)
+        K = self.k.size
+        self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
+        self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
+        self.stats = None
+
+    def step(self, fields=None):
+        f = self.fields if fields is None else fields
+        api = self.api
+        _, sv, stv = api.solve(self.mv, f, self.k, out=self.out_v, **self.opts)
+        _, sc, stc = api.solve(self.mc, f, self.k, out=self.out_c, **self.opts)
+        ev = api.spectrum(self.mv, self.out_v, self.k)
+        ec = api.spectrum(self.mc, self.out_c, self.k)
+        self.stats = (sv, sc, max(stv, stc))
+        return ev, ec
+
+    def plain_sample(self, ncols):
+        """Plain one-RHS FP64 CG (the paper's solver form, S assembled per scale)
+        on the cell placement at the `ncols` largest wavenumbers (the columns it
+        finishes fastest).  Returns (columns, seconds, per-column stats)."""
+        import torch
+        api = self.api
+        ks = self.k[-ncols:]
+        out = torch.empty((1, ks.size, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.time()
+        _, st, _ = api.solve(self.mc, self.fields, ks, out=out, order=2, tol=self.opts["tol"],
+                             precision=api.PREC_FP64, method=api.METHOD_PLAIN)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        return 2 * ks.size, dt, st
+
+
+def roofline(api, peak_gbs, peak_kind):
+    recs = api.profile_read()
+    best = None
+    for r in recs:
+        if r["samples"] == 0 or r["launches"] == 0:
+            continue
+        avg_ms = r["sampled_ms"] / r["samples"]
+        total = avg_ms * r["launches"]
+        if best is None or total > best[0]:
+            best = (total, r, avg_ms)
+    if best is None:
+        return None, recs
+    _, r, avg_ms = best
+    achieved = r["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    shares = {}
+    tot = sum(x["sampled_ms"] / x["samples"] * x["launches"] for x in recs if x["samples"])
+    for x in recs:
+        if x["samples"]:
+            shares[x["name"]] = round(x["sampled_ms"] / x["samples"] * x["launches"] / tot, 4)
+    return {"bound": "hbm", "kernel": r["name"], "achieved": round(achieved, 1), "peak": peak_gbs,
+            "peak_kind": f"{peak_kind} (copy)", "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
+            "traffic": None, "bytes_per_launch": r["bytes_per_launch"], "avg_launch_ms": round(avg_ms, 4),
+            "launches": r["launches"], "time_share_of_sampled": shares}, recs
+
+
+def total_launches(recs):
+    for r in recs:
+        if r["name"] == "(all kernels)":
+            return int(r["launches"])
+    return None
+
+
+def cpu_baseline(w, budget_s):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    the cell placement's u component at the largest wavenumbers (fastest
+    columns first) until `budget_s` of solving has elapsed.  Returns the
+    throughput in field-scales/s over that sample (an upper bound for the full
+    workload, whose small-k columns take far longer)."""
+    import oracle
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter = threadpool_limits(1)
+    except Exception:
+        limiter = None
+    t0 = time.time()
+    P = oracle.build_problem(w["mesh"], "cell")
+    prep = time.time() - t0
+    f = w["fields"][0]
+    done = 0
+    spent = 0.0
+    ks = list(w["k"][::-1])
+    for k in ks:
+        t1 = time.time()
+        _oracle_one(oracle, P, f, k)
+        spent += time.time() - t1
+        done += 1
+        if spent >= budget_s:
+            break
+    if limiter is not None:
+        limiter.unregister()
+    return {"value": done / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"cell placement, component u, the {done} largest of {len(ks)} wavenumbers "
+                      f"(fastest columns), FP64 CG to rel. residual 1e-9, {spent:.1f} s of solving; "
+                      f"oracle operator assembly {prep:.1f} s not counted"}
+
+
+def _oracle_one(oracle, P, f, k):
+    """One cell-placement column (u component) by the oracle's CG."""
+    b, x0 = P.systems(f)[0]
+    return oracle.cg(lambda v: P.apply_S(v, 1.0 / k, 2), b, x0, 1e-9)
+
+
+def summarize_stats(stats):
+    out = {}
+    for name, s in zip(("vertex_vector", "cell"), stats[:2]):
+        s = s.reshape(-1)
+        out[name] = {"iters_max": int(s["iters"].max()), "iters_mean": float(s["iters"].mean()),
+                     "refinements_max": int(s["refinements"].max()),
+                     "rel_residual_max": float(s["rel_residual"].max()),
+                     "not_converged": int((s["status"] != 0).sum())}
+    return out
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2404_07398_gb300 import api
+    t_setup = time.time()
+    w = make_workload(args.level)
+    o = Ours(args, w)
+    peak, pk = peaks()
+    units = 4 * N_K
+    for _ in range(args.warmup):
+        o.step()
+    torch.cuda.synchronize()
+    barrier(world)
+    setup_s = time.time() - t_setup
+
+    api.profile_reset()
+    api.profile_enable(True)
+    clocks = Clocks(local)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        o.step()
+        lat.append((time.perf_counter() - t) * 1e3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop()
+    api.profile_enable(False)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    value = world * units * args.steps / (ms / 1e3)
+    roof, recs = roofline(api, peak, pk)
+    launches = total_launches(recs)
+    stats = summarize_stats(o.stats)
+
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(o.fields.shape, dtype=torch.float64, pin_memory=True)
+        host.copy_(o.fields)
+        dev = torch.empty_like(o.fields)
+        torch.cuda.synchronize()
+        barrier(world)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dev.copy_(host, non_blocking=True)
+        ev, ec = o.step(dev)       # spectra come back to host memory
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(a.elapsed_time(b), world)
+        bo = sum(x.nbytes for x in ev + ec)
+        e2e = {"value": round(world * units / (ems / 1e3), 4), "unit": UNIT,
+               "h2d_bytes_per_step": int(host.numel() * 8), "d2h_bytes_per_step": int(bo),
+               "ms_per_step": round(ems, 1)}
+
+    plain = None
+    if args.plain_sample > 0 and rank == 0:
+        cols, dt, st = o.plain_sample(args.plain_sample)
+        st = st.reshape(-1)
+        plain = {"value": round(cols / dt, 4), "unit": UNIT, "columns": cols,
+                 "sample": f"plain one-RHS FP64 CG (S assembled per scale, CSR SpMV, host test each "
+                           f"iteration) on the cell placement, u and v at the {args.plain_sample} largest "
+                           f"wavenumbers (its fastest columns)",
+                 "iters": [int(x) for x in st["iters"]]}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[
+                args.precision], "data": "synthetic (seeded mesh, land mask and k^-3 random fields)",
+            "config": workload_config(args, w, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": ck,
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1),
+                           "p99": round(float(np.percentile(lat, 99)), 1),
+                           "per": "step (160 field-scales, both placements, spectra)"},
+            "plain_cg_sample": plain, "solver_stats": stats,
+            "setup_s": round(setup_s, 1), "prepare_s": round(o.prepare_s, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    w = make_workload(args.level)
+    t0 = time.time()
+    P = oracle.build_problem(w["mesh"], "cell")
+    prep = time.time() - t0
+    f = w["fields"][0]
+    ks = w["k"][::-1][:3]          # each step: the three largest wavenumbers, u component
+    per = []
+    for i in range(args.warmup + args.steps):
+        t = time.time()
+        for k in ks:
+            _oracle_one(oracle, P, f, k)
+        if i >= args.warmup:
+            per.append(time.time() - t)
+    total = sum(per)
+    value = len(ks) * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded mesh, land mask and k^-3 random fields)",
+            "config": workload_config(args, w, world),
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"per step: cell placement, component u, the {len(ks)} largest of "
+                                       f"{N_K} wavenumbers (its fastest columns), FP64 CG to rel. residual "
+                                       f"1e-9; oracle assembly {prep:.1f} s not timed"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -86,6 +86,12 @@ void profile_add(const char* name, int64_t launches, int64_t samples, double sam
   r.bytes_sum += bytes_per_launch * (double)samples;
 }
 
+void profile_count(int64_t launches) {
+  if (!profiling_on()) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_recs["(all kernels)"].launches += launches;
+}
+
 }  // namespace ifilt
 
 using namespace ifilt;
@@ -319,6 +325,7 @@ ifilt_status ifilt_spectrum(ifilt_mesh m, int32_t n_fields, int32_t n_k, const d
   double* part = km_dev + K;
   IFILT_CUDA(cudaMemcpyAsync(k_dev, k, K * sizeof(double), cudaMemcpyHostToDevice, st));
   spectrum_device(m, n_fields, n_k, k_dev, filtered, e_dev, s_dev, km_dev, part, nb, st);
+  profile_count(2);
   IFILT_CUDA(cudaMemcpyAsync(energy, e_dev, F * K * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (spec && K > 1) IFILT_CUDA(cudaMemcpyAsync(spec, s_dev, F * (K - 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (kmid && K > 1) IFILT_CUDA(cudaMemcpyAsync(kmid, km_dev, (K - 1) * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -23,6 +23,8 @@
 // b - S x in FP64 from an FP64 solution and restarts the inner solve on it.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -33,10 +35,10 @@ namespace ifilt {
 
 int grid_for(const void* kernel, int block, size_t smem, long long work_items) {
   int dev = 0, sms = kNumSMs, occ = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem);
-  if (occ < 1) occ = 1;
+  IFILT_CUDA(cudaGetDevice(&dev));
+  IFILT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  IFILT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem));
+  if (occ < 1) fail(IFILT_ECUDA, "kernel cannot be resident with %d threads and %zu bytes of shared memory", block, smem);
   long long g = (long long)sms * occ;
   long long need = (work_items + block - 1) / block;
   if (need < 1) need = 1;
@@ -109,7 +111,8 @@ struct Cols {
   int* iters;
   int* rounds;
   int* status;      // 0 ok, 1 not converged, 2 breakdown
-  int* live;        // [1] number of active columns
+  int* refresh;     // column waits for its FP64 true residual / next refinement round
+  int* live;        // [3] number of active columns, columns to refresh, columns not done
 };
 
 struct Params {
@@ -463,7 +466,18 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
   double d1[VEC], d2[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; v++) d1[v] = d2[v] = 0.0;
-  if (tr < RPP) {
+  // Lanes of columns that are not being refreshed keep their inner state; a
+  // thread none of whose columns is refreshed skips its loads altogether, so
+  // the traffic follows the number of refreshed columns.
+  bool mine[VEC];
+  bool any = false, all = true;
+#pragma unroll
+  for (int v = 0; v < VEC; v++) {
+    mine[v] = C.refresh[CPLX ? (l0 + v) >> 1 : l0 + v] != 0;
+    any |= mine[v];
+    all &= mine[v];
+  }
+  if (tr < RPP && any) {
     double sh[VEC];
     int src[VEC];
 #pragma unroll
@@ -548,11 +562,23 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
             d2[v] += rv * rv;
           }
         }
-        stp(r + off, ro);
-        stp(p + off, ro);
-        stp(d + off, zo);
+        if (all) {
+          stp(r + off, ro);
+          stp(p + off, ro);
+          stp(d + off, zo);
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; v++)
+            if (mine[v]) {
+              r[off + v] = ro.v[v];
+              p[off + v] = ro.v[v];
+              d[off + v] = (T)0;
+            }
+        }
       }
     }
+  }
+  if (tr < RPP) {
 #pragma unroll
     for (int v = 0; v < VEC; v++) sm[tr * NSL + l0 + v] = d1[v];
     if constexpr (CPLX) {
@@ -580,6 +606,8 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
   const double rim = CPLX ? reduce_slot(partial, nb, P.pstride, ok ? 2 * col + 1 : -1, buf) : 0.0;
   const double n2 = reduce_slot(partial, nb, P.pstride, ok ? P.W + col : -1, buf);
   if (threadIdx.y != 0 || !ok) return;
+  if (!C.refresh[col]) return;
+  C.refresh[col] = 0;
   if (C.r0n2[col] < 0.0) {
     C.r0n2[col] = n2;
     C.tol2[col] = P.tol2_rel * n2;
@@ -614,11 +642,46 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
   atomicAdd(C.live, 1);
 }
 
-// x64 += d
+// x64 += d on the lanes of refreshed columns
+template <typename T, bool CPLX>
+__global__ void accumulate_kernel(int64_t total, int W, const int* __restrict__ refresh, double* __restrict__ x64,
+                                  const T* __restrict__ d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i % W);
+    if (refresh[CPLX ? l >> 1 : l]) x64[i] += (double)d[i];
+  }
+}
+
+// Flags every column whose inner solve has ended but which is not done for
+// a refinement round, and counts active / to-refresh / unfinished columns.
+__global__ void scan_kernel(int ncols, Cols C) {
+  __shared__ int cnt[3];
+  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    const int a = C.active[c], dn = C.done[c];
+    const int rf = (!a && !dn) ? 1 : 0;
+    C.refresh[c] = rf;
+    if (a) atomicAdd(&cnt[0], 1);
+    if (rf) atomicAdd(&cnt[1], 1);
+    if (!dn) atomicAdd(&cnt[2], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) C.live[threadIdx.x] = cnt[threadIdx.x];
+}
+
+// dst[row][l'] = src[row][map[l']] (0 where map < 0): narrows the lane tiles
+// to the columns that are still running.
 template <typename T>
-__global__ void accumulate_kernel(int64_t total, double* __restrict__ x64, const T* __restrict__ d) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-    x64[i] += (double)d[i];
+__global__ void gather_lanes_kernel(int64_t rows, int Wold, int Wnew, const int* __restrict__ map,
+                                    const T* __restrict__ src, T* __restrict__ dst) {
+  const int64_t total = rows * Wnew;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / Wnew;
+    const int l = (int)(i - row * Wnew);
+    const int mo = map[l];
+    dst[i] = mo >= 0 ? src[row * Wold + mo] : (T)0;
+  }
 }
 
 // out[f][k][comp][o] from the FP64 solution (real part); land entries copy the
@@ -648,6 +711,21 @@ __global__ void output_kernel(Params P, int32_t n_out, const int32_t* __restrict
 
 // ------------------------------------------------------------------ host side
 
+// Error of the launch just made (or a stale one left by an earlier call), with
+// the launch geometry in the message.
+void launch_check(const char* what, int blocks, size_t smem, int W) {
+  static const bool trace = [] {
+    const char* t = getenv("IFILT_TRACE");
+    return t && t[0] == '1';
+  }();
+  if (trace) fprintf(stderr, "ifilt trace: %s blocks=%d W=%d pending=%s\n", what, blocks, W,
+                     cudaGetErrorString(cudaPeekAtLastError()));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    fail(e == cudaErrorMemoryAllocation ? IFILT_ENOMEM : IFILT_ECUDA, "%s launch (blocks=%d, smem=%zu, W=%d): %s",
+         what, blocks, smem, W, cudaGetErrorString(e));
+}
+
 struct Variant {
   bool cplx, blk;
   int prec;  // 0 fp64, 1 fp32, 2 bf16-valued fp32
@@ -663,6 +741,95 @@ struct ColumnSpec {
   double shift;
 };
 
+// Lane tiles of one batch: [row][sub][lane] arrays, reallocated narrower when
+// finished columns are retired.
+template <typename T>
+struct Tiles {
+  int W = 0;
+  T *d = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+  double* x64 = nullptr;
+  void* base = nullptr;
+};
+
+template <typename T>
+Tiles<T> alloc_tiles(int64_t n, int NS, int W, cudaStream_t st) {
+  Tiles<T> t;
+  t.W = W;
+  const size_t vb = ((size_t)n * NS * W * sizeof(T) + 255) / 256 * 256;
+  const size_t xb = ((size_t)n * NS * W * sizeof(double) + 255) / 256 * 256;
+  char* b = (char*)scratch_alloc(4 * vb + xb, st);
+  t.base = b;
+  t.d = (T*)b;
+  t.r = (T*)(b + vb);
+  t.p = (T*)(b + 2 * vb);
+  t.q = (T*)(b + 3 * vb);
+  t.x64 = (double*)(b + 4 * vb);
+  return t;
+}
+
+// Host copy of the per-column state, for retiring and re-packing columns.
+struct HostCols {
+  std::vector<double> shift, rho, alpha, beta, rn2, target2, r0n2, tol2, rel;
+  std::vector<int> active, done, iters, rounds, status, refresh;
+  void resize(int n) {
+    for (auto* v : {&shift, &rn2, &target2, &r0n2, &tol2, &rel}) v->assign(n, 0.0);
+    for (auto* v : {&rho, &alpha, &beta}) v->assign(2 * n, 0.0);
+    for (auto* v : {&active, &done, &iters, &rounds, &status, &refresh}) v->assign(n, 0);
+  }
+};
+
+void cols_download(const Cols& C, HostCols& H, int n, cudaStream_t st) {
+  H.resize(n);
+  auto dn = [&](void* dst, const void* src, size_t b) {
+    IFILT_CUDA(cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, st));
+  };
+  dn(H.shift.data(), C.shift, n * 8);
+  dn(H.rho.data(), C.rho, 2 * n * 8);
+  dn(H.alpha.data(), C.alpha, 2 * n * 8);
+  dn(H.beta.data(), C.beta, 2 * n * 8);
+  dn(H.rn2.data(), C.rn2, n * 8);
+  dn(H.target2.data(), C.target2, n * 8);
+  dn(H.r0n2.data(), C.r0n2, n * 8);
+  dn(H.tol2.data(), C.tol2, n * 8);
+  dn(H.rel.data(), C.rel, n * 8);
+  dn(H.active.data(), C.active, n * 4);
+  dn(H.done.data(), C.done, n * 4);
+  dn(H.iters.data(), C.iters, n * 4);
+  dn(H.rounds.data(), C.rounds, n * 4);
+  dn(H.status.data(), C.status, n * 4);
+  dn(H.refresh.data(), C.refresh, n * 4);
+  IFILT_CUDA(cudaStreamSynchronize(st));
+}
+
+void cols_upload(const Cols& C, const HostCols& H, int n, cudaStream_t st) {
+  auto up = [&](void* dst, const void* src, size_t b) {
+    IFILT_CUDA(cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, st));
+  };
+  up(C.shift, H.shift.data(), n * 8);
+  up(C.rho, H.rho.data(), 2 * n * 8);
+  up(C.alpha, H.alpha.data(), 2 * n * 8);
+  up(C.beta, H.beta.data(), 2 * n * 8);
+  up(C.rn2, H.rn2.data(), n * 8);
+  up(C.target2, H.target2.data(), n * 8);
+  up(C.r0n2, H.r0n2.data(), n * 8);
+  up(C.tol2, H.tol2.data(), n * 8);
+  up(C.rel, H.rel.data(), n * 8);
+  up(C.active, H.active.data(), n * 4);
+  up(C.done, H.done.data(), n * 4);
+  up(C.iters, H.iters.data(), n * 4);
+  up(C.rounds, H.rounds.data(), n * 4);
+  up(C.status, H.status.data(), n * 4);
+  up(C.refresh, H.refresh.data(), n * 4);
+  // the host vectors must outlive the copies
+  IFILT_CUDA(cudaStreamSynchronize(st));
+}
+
+// Host record of every column of the batch (index into the batch's spec list).
+struct ColResult {
+  int iters = 0, rounds = 0, status = 0, done = 0;
+  double rel = 0.0;
+};
+
 template <typename T, typename MV, bool CPLX, bool BLK>
 ifilt_status run_batch(ifilt_mesh_s* m, const ifilt_solve_opts& o, const std::vector<ColumnSpec>& cols,
                        int nsrc_total, const double* bsrc_all, const double* x0src_all, const double* fields,
@@ -671,38 +838,35 @@ ifilt_status run_batch(ifilt_mesh_s* m, const ifilt_solve_opts& o, const std::ve
   const HostPrepared& h = m->host;
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
-  const int lanes_per_col = CPLX ? 2 : 1;
-  const int ncols_real = (int)cols.size();
-  int W = ncols_real * lanes_per_col;
-  W = (W + 3) / 4 * 4;
-  if (W / VEC > kBlock) fail(IFILT_EINVAL, "batch too wide (%d lanes)", W);
-  const int ncols = W / lanes_per_col;
+  const int lpc = CPLX ? 2 : 1;  // lanes per column
+  const int nreal = (int)cols.size();
+  auto lanes_for = [&](int ncol) { return (ncol * lpc + 3) / 4 * 4; };
+  const int Wmax = lanes_for(nreal);
+  if (Wmax / VEC > kBlock) fail(IFILT_EINVAL, "batch too wide (%d lanes)", Wmax);
+  const int ncmax = Wmax / lpc;
   const int64_t n = h.n_rows;
   const bool use_g2 = (o.order >= 2) && !CPLX;
   const DevEll& E = use_g2 ? m->ell_g2 : m->ell_k;
-  EllView<MV> A = ell_view<MV>(E);
-  EllView<double> A64 = ell_view<double>(E);
+  const EllView<MV> A = ell_view<MV>(E);
+  const EllView<double> A64 = ell_view<double>(E);
 
-  // sources used by this batch: compact them
   std::vector<int> src_ids;
   for (auto& c : cols)
     if (std::find(src_ids.begin(), src_ids.end(), c.src) == src_ids.end()) src_ids.push_back(c.src);
   const int nsrc = (int)src_ids.size();
 
-  // launch geometry
-  const size_t smem_spmm = (size_t)(kBlock / (W / VEC)) * W * sizeof(double);
-  const size_t smem_upd = (size_t)(kBlock / (W / VEC)) * (W + W / 2) * sizeof(double);
-  const size_t smem_res = (size_t)(kBlock / (W / VEC)) * 2 * W * sizeof(double);
-  const long long rows_work = n * (long long)(W / VEC);
-  const int nb = grid_for((const void*)spmm_kernel<T, MV, CPLX, BLK>, kBlock, smem_spmm, rows_work);
-  const int pstride = 2 * W;
+  auto smem_of = [&](int W, int slots_per_lane2) {  // slots per row-pass in units of W/2
+    return (size_t)(kBlock / (W / VEC)) * (size_t)W * slots_per_lane2 / 2 * sizeof(double);
+  };
+  auto blocks_for = [&](int W) {
+    return grid_for((const void*)spmm_kernel<T, MV, CPLX, BLK>, kBlock, smem_of(W, 2), n * (long long)(W / VEC));
+  };
+  const int nb_max = blocks_for(Wmax);
 
-  // scratch
-  const size_t vb = vec_bytes<T>(n, NS, W);
-  const size_t xb = (size_t)n * NS * W * sizeof(double);
+  // fixed scratch: sources, reduction partials, column state, tables
   const size_t sb = (size_t)nsrc * n * NS * sizeof(double);
-  size_t total = 4 * vb + xb + 2 * sb + (size_t)nb * pstride * 8 + (size_t)ncols * (8 * 16 + 4 * 8) +
-                 (size_t)W * 4 + 64 * 256;
+  size_t total = 2 * sb + (size_t)nb_max * 2 * Wmax * 8 + (size_t)ncmax * (8 * 16 + 4 * 8) + (size_t)Wmax * 8 +
+                 64 * 256;
   char* base = (char*)scratch_alloc(total, st);
   char* cur = base;
   auto take = [&](size_t bytes) {
@@ -710,68 +874,30 @@ ifilt_status run_batch(ifilt_mesh_s* m, const ifilt_solve_opts& o, const std::ve
     cur += (bytes + 255) / 256 * 256;
     return (void*)p;
   };
-  T* d = (T*)take(vb);
-  T* r = (T*)take(vb);
-  T* p = (T*)take(vb);
-  T* q = (T*)take(vb);
-  double* x64 = (double*)take(xb);
   double* bs = (double*)take(sb);
   double* x0s = (double*)take(sb);
-  double* partial = (double*)take((size_t)nb * pstride * 8);
+  double* partial = (double*)take((size_t)nb_max * 2 * Wmax * 8);
   Cols C{};
-  C.shift = (double*)take(ncols * 8);
-  C.rho = (double*)take(2 * ncols * 8);
-  C.alpha = (double*)take(2 * ncols * 8);
-  C.beta = (double*)take(2 * ncols * 8);
-  C.rn2 = (double*)take(ncols * 8);
-  C.target2 = (double*)take(ncols * 8);
-  C.r0n2 = (double*)take(ncols * 8);
-  C.tol2 = (double*)take(ncols * 8);
-  C.rel = (double*)take(ncols * 8);
-  C.active = (int*)take(ncols * 4);
-  C.done = (int*)take(ncols * 4);
-  C.iters = (int*)take(ncols * 4);
-  C.rounds = (int*)take(ncols * 4);
-  C.status = (int*)take(ncols * 4);
-  C.live = (int*)take(4);
-  int* lane_src = (int*)take(W * 4);
-  int64_t* col_out = (int64_t*)take(ncols * 8);
-  int64_t* col_in = (int64_t*)take(ncols * 8);
-
-  // host-side column tables
-  std::vector<double> shift(ncols, 0.0), neg(ncols, -1.0), zeros(2 * ncols, 0.0);
-  std::vector<int> done(ncols, 0), izero(ncols, 0), lsrc(W, 0);
-  std::vector<int64_t> cout_(ncols, -1), cin(ncols, 0);
-  for (int c = 0; c < ncols; c++) {
-    if (c < ncols_real) {
-      const ColumnSpec& cs = cols[c];
-      shift[c] = cs.shift;
-      int s = (int)(std::find(src_ids.begin(), src_ids.end(), cs.src) - src_ids.begin());
-      for (int t = 0; t < lanes_per_col; t++) lsrc[c * lanes_per_col + t] = s;
-      const int comp = h.placement == IFILT_CELL ? cs.sys : 0;
-      cout_[c] = (((int64_t)cs.f * nk + cs.kj) * h.n_comp + comp) * h.n_out;
-      cin[c] = ((int64_t)cs.f * h.n_comp + comp) * h.n_in;
-    } else {
-      done[c] = 1;
-    }
-  }
-  auto up = [&](void* dst, const void* src, size_t bytes) {
-    IFILT_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
-  };
-  up(C.shift, shift.data(), ncols * 8);
-  up(C.r0n2, neg.data(), ncols * 8);
-  up(C.rho, zeros.data(), 2 * ncols * 8);
-  up(C.alpha, zeros.data(), 2 * ncols * 8);
-  up(C.beta, zeros.data(), 2 * ncols * 8);
-  up(C.done, done.data(), ncols * 4);
-  up(C.active, izero.data(), ncols * 4);
-  up(C.iters, izero.data(), ncols * 4);
-  up(C.rounds, izero.data(), ncols * 4);
-  up(C.status, izero.data(), ncols * 4);
-  up(C.live, izero.data(), 4);
-  up(lane_src, lsrc.data(), W * 4);
-  up(col_out, cout_.data(), ncols * 8);
-  up(col_in, cin.data(), ncols * 8);
+  C.shift = (double*)take(ncmax * 8);
+  C.rho = (double*)take(2 * ncmax * 8);
+  C.alpha = (double*)take(2 * ncmax * 8);
+  C.beta = (double*)take(2 * ncmax * 8);
+  C.rn2 = (double*)take(ncmax * 8);
+  C.target2 = (double*)take(ncmax * 8);
+  C.r0n2 = (double*)take(ncmax * 8);
+  C.tol2 = (double*)take(ncmax * 8);
+  C.rel = (double*)take(ncmax * 8);
+  C.active = (int*)take(ncmax * 4);
+  C.done = (int*)take(ncmax * 4);
+  C.iters = (int*)take(ncmax * 4);
+  C.rounds = (int*)take(ncmax * 4);
+  C.status = (int*)take(ncmax * 4);
+  C.refresh = (int*)take(ncmax * 4);
+  C.live = (int*)take(4 * 4);
+  int* lane_src = (int*)take(Wmax * 4);
+  int* lane_map = (int*)take(Wmax * 4);
+  int64_t* col_out = (int64_t*)take(ncmax * 8);
+  int64_t* col_in = (int64_t*)take(ncmax * 8);
   for (int s = 0; s < nsrc; s++) {
     IFILT_CUDA(cudaMemcpyAsync(bs + (size_t)s * n * NS, bsrc_all + (size_t)src_ids[s] * n * NS,
                                n * NS * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -779,137 +905,334 @@ ifilt_status run_batch(ifilt_mesh_s* m, const ifilt_solve_opts& o, const std::ve
                                n * NS * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
 
+  // current column set: batch-spec index of each column (-1 = padding)
+  std::vector<int> curcols(nreal);
+  for (int c = 0; c < nreal; c++) curcols[c] = c;
+  std::vector<ColResult> res(nreal);
+  std::vector<int> lsrc_h;
+  std::vector<int64_t> cout_h, cin_h;
+  auto upload_tables = [&](int W) {
+    const int nc = W / lpc;
+    lsrc_h.assign(W, 0);
+    cout_h.assign(nc, -1);
+    cin_h.assign(nc, 0);
+    for (int c = 0; c < nc; c++) {
+      const int id = c < (int)curcols.size() ? curcols[c] : -1;
+      if (id < 0) continue;
+      const ColumnSpec& cs = cols[id];
+      const int s = (int)(std::find(src_ids.begin(), src_ids.end(), cs.src) - src_ids.begin());
+      for (int t = 0; t < lpc; t++) lsrc_h[c * lpc + t] = s;
+      const int comp = h.placement == IFILT_CELL ? cs.sys : 0;
+      cout_h[c] = (((int64_t)cs.f * nk + cs.kj) * h.n_comp + comp) * h.n_out;
+      cin_h[c] = ((int64_t)cs.f * h.n_comp + comp) * h.n_in;
+    }
+    IFILT_CUDA(cudaMemcpyAsync(lane_src, lsrc_h.data(), W * 4, cudaMemcpyHostToDevice, st));
+    IFILT_CUDA(cudaMemcpyAsync(col_out, cout_h.data(), nc * 8, cudaMemcpyHostToDevice, st));
+    IFILT_CUDA(cudaMemcpyAsync(col_in, cin_h.data(), nc * 8, cudaMemcpyHostToDevice, st));
+    IFILT_CUDA(cudaStreamSynchronize(st));
+  };
+
+  // initial column state: every real column asks for its first true residual
+  HostCols H;
+  H.resize(ncmax);
+  for (int c = 0; c < ncmax; c++) {
+    if (c < nreal) {
+      H.shift[c] = cols[c].shift;
+      H.r0n2[c] = -1.0;
+      H.refresh[c] = 1;
+    } else {
+      H.done[c] = 1;
+    }
+  }
+  cols_upload(C, H, ncmax, st);
+  upload_tables(Wmax);
+
   Params P{};
   P.n = (int32_t)n;
-  P.W = W;
-  P.ncols = ncols;
-  P.pstride = pstride;
   P.maxit = o.max_iter > 0 ? o.max_iter : 100000;
   P.tol2_rel = o.tol * o.tol;
   const double itol = (sizeof(T) == 8) ? 0.0 : (o.inner_tol > 0 ? o.inner_tol : 1e-4);
   P.inner2 = itol * itol;
+  Tiles<T> tl = alloc_tiles<T>(n, NS, Wmax, st);
+  auto set_width = [&](int W) {
+    P.W = W;
+    P.ncols = W / lpc;
+    P.pstride = 2 * W;
+  };
+  set_width(Wmax);
+  IFILT_CUDA(cudaMemsetAsync(tl.d, 0, (size_t)n * NS * Wmax * sizeof(T), st));
+  {
+    const int g = grid_for((const void*)init_x_kernel<CPLX, BLK>, kBlock, 0, n * NS * Wmax);
+    launch_check("before init", 0, 0, Wmax);
+    (void)0;
+    init_x_kernel<CPLX, BLK><<<g, kBlock, 0, st>>>(P, x0s, lane_src, tl.x64);
+    launch_check("init", g, 0, Wmax);
+  }
 
-  const int fin_grid = (ncols + 31) / 32;
-  const dim3 fin_block(32, 8);
-  const int ew_grid = grid_for((const void*)accumulate_kernel<T>, kBlock, 0, n * NS * W);
-
-  init_x_kernel<CPLX, BLK><<<ew_grid, kBlock, 0, st>>>(P, x0s, lane_src, x64);
-  IFILT_CUDA(cudaGetLastError());
-
-  // capture m iterations in a graph
   const int m_it = o.check_every > 0 ? o.check_every : 32;
   const bool prof = profiling_on();
   cudaEvent_t ev[6] = {};
   if (prof)
     for (auto& e : ev) IFILT_CUDA(cudaEventCreate(&e));
-  IFILT_CUDA(cudaFuncSetAttribute(spmm_kernel<T, MV, CPLX, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_spmm));
-  IFILT_CUDA(cudaFuncSetAttribute(update_kernel<T, CPLX, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_upd));
-  IFILT_CUDA(cudaFuncSetAttribute(residual_kernel<T, CPLX, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_res));
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  IFILT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  for (int it = 0; it < m_it; it++) {
-    if (prof && it == 0) cudaEventRecord(ev[0], st);
-    spmm_kernel<T, MV, CPLX, BLK><<<nb, kBlock, smem_spmm, st>>>(A, P, p, q, m->mass, C, partial);
-    if (prof && it == 0) cudaEventRecord(ev[1], st);
-    finish_alpha_kernel<CPLX><<<fin_grid, fin_block, 0, st>>>(P, nb, partial, C);
-    if (prof && it == 0) cudaEventRecord(ev[2], st);
-    update_kernel<T, CPLX, BLK><<<nb, kBlock, smem_upd, st>>>(P, d, p, r, q, C, partial);
-    if (prof && it == 0) cudaEventRecord(ev[3], st);
-    finish_beta_kernel<CPLX><<<fin_grid, fin_block, 0, st>>>(P, nb, partial, C);
-    if (prof && it == 0) cudaEventRecord(ev[4], st);
-    direction_kernel<T, CPLX, BLK><<<nb, kBlock, 0, st>>>(P, p, r, C);
-    if (prof && it == 0) cudaEventRecord(ev[5], st);
-  }
-  cudaError_t cap = cudaStreamEndCapture(st, &graph);
-  if (cap != cudaSuccess) fail(IFILT_ECUDA, "graph capture failed: %s", cudaGetErrorString(cap));
-  IFILT_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-
-  int* h_flags = nullptr;
-  IFILT_CUDA(cudaMallocHost(&h_flags, sizeof(int) * (2 * ncols + 1)));
-  double t_spmm = 0, t_upd = 0, t_dir = 0;
-  int64_t samples = 0, graph_launches = 0;
-  const int max_rounds = 64;
-  const int round_cap = std::max(P.maxit, 1);
-  for (int round = 0; round < max_rounds; round++) {
-    residual_kernel<T, CPLX, BLK><<<nb, kBlock, smem_res, st>>>(A64, P, x64, bs, lane_src, m->mass, C, r, d, p,
-                                                               partial);
-    finish_residual_kernel<CPLX><<<fin_grid, fin_block, 0, st>>>(P, nb, partial, C);
-    IFILT_CUDA(cudaGetLastError());
-    IFILT_CUDA(cudaMemcpyAsync(h_flags, C.live, sizeof(int), cudaMemcpyDeviceToHost, st));
-    IFILT_CUDA(cudaStreamSynchronize(st));
-    if (h_flags[0] == 0) break;
-    int inner = 0;
-    while (true) {
-      IFILT_CUDA(cudaGraphLaunch(exec, st));
-      graph_launches++;
-      IFILT_CUDA(cudaMemcpyAsync(h_flags, C.live, sizeof(int), cudaMemcpyDeviceToHost, st));
-      IFILT_CUDA(cudaStreamSynchronize(st));
-      if (prof) {
-        float a = 0, b = 0, c = 0;
-        if (cudaEventElapsedTime(&a, ev[0], ev[1]) == cudaSuccess &&
-            cudaEventElapsedTime(&b, ev[2], ev[3]) == cudaSuccess &&
-            cudaEventElapsedTime(&c, ev[4], ev[5]) == cudaSuccess && h_flags[0] > 0) {
-          t_spmm += a;
-          t_upd += b;
-          t_dir += c;
-          samples++;
-        }
-      }
-      inner += m_it;
-      if (h_flags[0] == 0 || inner >= round_cap) break;
+  int nb = nb_max;
+  // IFILT_NO_GRAPH=1 launches every iteration directly and checks each launch
+  // (debugging aid); otherwise m iterations are captured once per tile width.
+  const char* ng = getenv("IFILT_NO_GRAPH");
+  const bool use_graph = !(ng && ng[0] == '1');
+  auto enqueue_iters = [&](bool check) {
+    const int W = P.W;
+    const size_t sm2 = smem_of(W, 2), sm3 = smem_of(W, 3);
+    const int fin_grid = (P.ncols + 31) / 32;
+    const dim3 fin_block(32, 8);
+    auto chk = [&](const char* what) {
+      if (!check) return;
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess)
+        fail(IFILT_ECUDA, "%s (W=%d, blocks=%d, smem=%zu/%zu): %s", what, W, nb, sm2, sm3, cudaGetErrorString(e));
+    };
+    // Inside a stream capture an event record is only a dependency marker
+    // unless it is recorded as an external event node.
+    const unsigned evflags = check ? cudaEventRecordDefault : cudaEventRecordExternal;
+    auto rec = [&](cudaEvent_t e) { IFILT_CUDA(cudaEventRecordWithFlags(e, st, evflags)); };
+    for (int it = 0; it < m_it; it++) {
+      if (prof && it == 0) rec(ev[0]);
+      spmm_kernel<T, MV, CPLX, BLK><<<nb, kBlock, sm2, st>>>(A, P, tl.p, tl.q, m->mass, C, partial);
+      chk("spmm");
+      if (prof && it == 0) rec(ev[1]);
+      finish_alpha_kernel<CPLX><<<fin_grid, fin_block, 0, st>>>(P, nb, partial, C);
+      chk("finish_alpha");
+      if (prof && it == 0) rec(ev[2]);
+      update_kernel<T, CPLX, BLK><<<nb, kBlock, sm3, st>>>(P, tl.d, tl.p, tl.r, tl.q, C, partial);
+      chk("update");
+      if (prof && it == 0) rec(ev[3]);
+      finish_beta_kernel<CPLX><<<fin_grid, fin_block, 0, st>>>(P, nb, partial, C);
+      chk("finish_beta");
+      if (prof && it == 0) rec(ev[4]);
+      direction_kernel<T, CPLX, BLK><<<nb, kBlock, 0, st>>>(P, tl.p, tl.r, C);
+      chk("direction");
+      if (prof && it == 0) rec(ev[5]);
     }
-    accumulate_kernel<T><<<ew_grid, kBlock, 0, st>>>(n * NS * W, x64, d);
-  }
-  // results
-  {
-    dim3 og((unsigned)std::min<long long>((h.n_out + kBlock - 1) / kBlock, 1024), (unsigned)ncols);
-    output_kernel<CPLX, BLK><<<og, kBlock, 0, st>>>(P, h.n_out, m->inv_perm, x64, fields, col_out, col_in, out);
+  };
+  auto capture = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    nb = blocks_for(P.W);
     IFILT_CUDA(cudaGetLastError());
-  }
-  std::vector<int> it_h(ncols), rd_h(ncols), stt_h(ncols), done_h(ncols);
-  std::vector<double> rel_h(ncols);
-  IFILT_CUDA(cudaMemcpyAsync(it_h.data(), C.iters, ncols * 4, cudaMemcpyDeviceToHost, st));
-  IFILT_CUDA(cudaMemcpyAsync(rd_h.data(), C.rounds, ncols * 4, cudaMemcpyDeviceToHost, st));
-  IFILT_CUDA(cudaMemcpyAsync(stt_h.data(), C.status, ncols * 4, cudaMemcpyDeviceToHost, st));
-  IFILT_CUDA(cudaMemcpyAsync(done_h.data(), C.done, ncols * 4, cudaMemcpyDeviceToHost, st));
-  IFILT_CUDA(cudaMemcpyAsync(rel_h.data(), C.rel, ncols * 8, cudaMemcpyDeviceToHost, st));
-  IFILT_CUDA(cudaStreamSynchronize(st));
+    if (!use_graph) return;
+    IFILT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    enqueue_iters(false);
+    cudaError_t cap = cudaStreamEndCapture(st, &graph);
+    if (cap != cudaSuccess) fail(IFILT_ECUDA, "graph capture failed: %s", cudaGetErrorString(cap));
+    launch_check("capture", nb, 0, P.W);
+    IFILT_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    launch_check("instantiate", nb, 0, P.W);
+  };
+  // writes the outputs of the current columns for which `sel` holds
+  auto emit = [&](const std::vector<int>& sel) {
+    const int nc = P.ncols;
+    std::vector<int64_t> co(nc, -1);
+    for (int c = 0; c < nc && c < (int)curcols.size(); c++)
+      if (curcols[c] >= 0 && sel[c]) co[c] = cout_h[c];
+    IFILT_CUDA(cudaMemcpyAsync(col_out, co.data(), nc * 8, cudaMemcpyHostToDevice, st));
+    dim3 og((unsigned)std::min<long long>((h.n_out + kBlock - 1) / kBlock, 1024), (unsigned)nc);
+    output_kernel<CPLX, BLK><<<og, kBlock, 0, st>>>(P, h.n_out, m->inv_perm, tl.x64, fields, col_out, col_in, out);
+    IFILT_CUDA(cudaGetLastError());
+    IFILT_CUDA(cudaStreamSynchronize(st));
+  };
+  auto record = [&](const HostCols& Hc, int c) {
+    const int id = curcols[c];
+    if (id < 0) return;
+    ColResult& r = res[id];
+    r.iters = Hc.iters[c];
+    r.rounds = Hc.rounds[c];
+    r.status = Hc.status[c];
+    r.done = Hc.done[c];
+    r.rel = Hc.rel[c];
+  };
+  // Retire finished columns and narrow the tiles to the ones still running.
+  auto compact = [&]() {
+    const int nc = P.ncols, Wold = P.W;
+    cols_download(C, H, nc, st);
+    std::vector<int> keep, sel(nc, 0);
+    for (int c = 0; c < nc; c++) {
+      if (c >= (int)curcols.size() || curcols[c] < 0) continue;
+      if (H.done[c]) {
+        sel[c] = 1;
+        record(H, c);
+      } else {
+        keep.push_back(c);
+      }
+    }
+    emit(sel);
+    const int Wn = lanes_for((int)keep.size());
+    const int ncn = Wn / lpc;
+    std::vector<int> map(Wn, -1);
+    HostCols Hn;
+    Hn.resize(ncn);
+    std::vector<int> ncur(ncn, -1);
+    for (int j = 0; j < ncn; j++) {
+      if (j >= (int)keep.size()) {
+        Hn.done[j] = 1;
+        continue;
+      }
+      const int c = keep[j];
+      ncur[j] = curcols[c];
+      for (int t = 0; t < lpc; t++) map[j * lpc + t] = c * lpc + t;
+      Hn.shift[j] = H.shift[c];
+      for (int t = 0; t < 2; t++) {
+        Hn.rho[2 * j + t] = H.rho[2 * c + t];
+        Hn.alpha[2 * j + t] = H.alpha[2 * c + t];
+        Hn.beta[2 * j + t] = H.beta[2 * c + t];
+      }
+      Hn.rn2[j] = H.rn2[c];
+      Hn.target2[j] = H.target2[c];
+      Hn.r0n2[j] = H.r0n2[c];
+      Hn.tol2[j] = H.tol2[c];
+      Hn.rel[j] = H.rel[c];
+      Hn.active[j] = H.active[c];
+      Hn.done[j] = H.done[c];
+      Hn.iters[j] = H.iters[c];
+      Hn.rounds[j] = H.rounds[c];
+      Hn.status[j] = H.status[c];
+      Hn.refresh[j] = H.refresh[c];
+    }
+    IFILT_CUDA(cudaMemcpyAsync(lane_map, map.data(), Wn * 4, cudaMemcpyHostToDevice, st));
+    Tiles<T> tn = alloc_tiles<T>(n, NS, Wn, st);
+    const int64_t rows = n * NS;
+    const int g = grid_for((const void*)gather_lanes_kernel<T>, kBlock, 0, rows * Wn);
+    gather_lanes_kernel<T><<<g, kBlock, 0, st>>>(rows, Wold, Wn, lane_map, tl.d, tn.d);
+    gather_lanes_kernel<T><<<g, kBlock, 0, st>>>(rows, Wold, Wn, lane_map, tl.r, tn.r);
+    gather_lanes_kernel<T><<<g, kBlock, 0, st>>>(rows, Wold, Wn, lane_map, tl.p, tn.p);
+    gather_lanes_kernel<double><<<g, kBlock, 0, st>>>(rows, Wold, Wn, lane_map, tl.x64, tn.x64);
+    IFILT_CUDA(cudaGetLastError());
+    scratch_free(tl.base, st);
+    tl = tn;
+    curcols = ncur;
+    set_width(Wn);
+    cols_upload(C, Hn, ncn, st);
+    upload_tables(Wn);
+    capture();
+  };
 
+  capture();
+  int* h_flags = nullptr;
+  IFILT_CUDA(cudaMallocHost(&h_flags, sizeof(int) * 4));
+  launch_check("pinned flags", 0, 0, P.W);
+  auto scan = [&]() {
+    launch_check("before scan", 0, 0, P.W);
+    scan_kernel<<<1, 256, 0, st>>>(P.ncols, C);
+    launch_check("scan", 1, 0, P.W);
+    IFILT_CUDA(cudaMemcpyAsync(h_flags, C.live, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    IFILT_CUDA(cudaStreamSynchronize(st));
+  };
+  double t_spmm = 0, t_upd = 0, t_dir = 0, b_spmm = 0, b_upd = 0, b_dir = 0;
+  int64_t samples = 0, graph_launches = 0, other_launches = 2;
+  const double mbytes = (double)E.entries * (4.0 + E.nval * sizeof(MV)) + (double)n * 8.0;
+  const int64_t guard = (int64_t)(P.maxit / m_it + 2) * 8 + 64;
   ifilt_status result = IFILT_OK;
+  for (int64_t loop = 0;; loop++) {
+    if (loop > guard) {
+      result = IFILT_NOT_CONVERGED;
+      break;
+    }
+    scan();
+    other_launches++;
+    if (h_flags[2] == 0) break;  // every column finished
+    if (h_flags[1] > 0) {        // FP64 true residual and a new inner round for finished inner solves
+      const int W = P.W;
+      const int ga = grid_for((const void*)accumulate_kernel<T, CPLX>, kBlock, 0, n * NS * W);
+      launch_check("before refinement", 0, 0, 0);
+      accumulate_kernel<T, CPLX><<<ga, kBlock, 0, st>>>(n * NS * W, W, C.refresh, tl.x64, tl.d);
+      launch_check("accumulate", ga, 0, W);
+      residual_kernel<T, CPLX, BLK><<<nb, kBlock, smem_of(W, 4), st>>>(A64, P, tl.x64, bs, lane_src, m->mass, C,
+                                                                      tl.r, tl.d, tl.p, partial);
+      launch_check("residual", nb, smem_of(W, 4), W);
+      finish_residual_kernel<CPLX><<<(P.ncols + 31) / 32, dim3(32, 8), 0, st>>>(P, nb, partial, C);
+      launch_check("finish_residual", (P.ncols + 31) / 32, 0, W);
+      other_launches += 3;
+      scan();
+      other_launches++;
+      if (h_flags[2] == 0) break;
+    }
+    const int running = h_flags[2];
+    if (lanes_for(running) < P.W && running * 5 <= P.ncols * 3) {
+      compact();
+      launch_check("compact", 0, 0, P.W);
+    }
+    if (h_flags[0] == 0) continue;
+    if (use_graph) IFILT_CUDA(cudaGraphLaunch(exec, st));
+    else enqueue_iters(true);
+    graph_launches++;
+    IFILT_CUDA(cudaStreamSynchronize(st));
+    launch_check("graph", nb, 0, P.W);
+
+    if (prof) {
+      float a = 0, b = 0, c = 0;
+      IFILT_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+      IFILT_CUDA(cudaEventElapsedTime(&b, ev[2], ev[3]));
+      IFILT_CUDA(cudaEventElapsedTime(&c, ev[4], ev[5]));
+      {
+        const double vb = (double)n * NS * P.W * sizeof(T);
+        t_spmm += a;
+        t_upd += b;
+        t_dir += c;
+        b_spmm += 2.0 * vb + mbytes;
+        b_upd += 6.0 * vb;
+        b_dir += 3.0 * vb;
+        samples++;
+      }
+    }
+  }
+  // outputs and stats of the columns still in the tiles
+  {
+    const int nc = P.ncols;
+    cols_download(C, H, nc, st);
+    std::vector<int> sel(nc, 1);
+    for (int c = 0; c < nc; c++)
+      if (c < (int)curcols.size()) record(H, c);
+    emit(sel);
+  }
+  profile_count(other_launches + graph_launches * m_it * 5);
   const int nsys = h.placement == IFILT_CELL ? 2 : 1;
-  for (int c = 0; c < ncols_real; c++) {
-    const ColumnSpec& cs = cols[c];
-    int status = stt_h[c] != 0 || !done_h[c] || rel_h[c] > o.tol ? IFILT_NOT_CONVERGED : IFILT_OK;
+  for (int id = 0; id < nreal; id++) {
+    const ColumnSpec& cs = cols[id];
+    const ColResult& r = res[id];
+    const int status = (r.status != 0 || !r.done || r.rel > o.tol) ? IFILT_NOT_CONVERGED : IFILT_OK;
     if (status != IFILT_OK) result = IFILT_NOT_CONVERGED;
     if (stats) {
       ifilt_col_stats& s = stats[((int64_t)cs.f * nk + cs.kj) * nsys + cs.sys];
-      s.iters = it_h[c];
-      s.refinements = rd_h[c];
+      s.iters = r.iters;
+      s.refinements = r.rounds;
       s.status = status;
       s.pad = 0;
-      s.rel_residual = rel_h[c];
+      s.rel_residual = r.rel;
     }
   }
   if (prof) {
-    const double vbytes = (double)n * NS * W * sizeof(T);
-    const double mbytes = (double)E.entries * (4.0 + E.nval * sizeof(MV)) + (double)n * 8.0;
     const int64_t launches = graph_launches * m_it;
+    const char* k1 = CPLX ? "c" : "r";
+    const char* k2 = BLK ? "b" : "s";
+    const char* k3 = sizeof(T) == 8 ? "f64" : "f32";
     char nm[32];
-    snprintf(nm, sizeof nm, "spmm_%s%s_%s", CPLX ? "c" : "r", BLK ? "b" : "s", sizeof(T) == 8 ? "f64" : "f32");
-    profile_add(nm, launches, samples, t_spmm, 2.0 * vbytes + mbytes);
-    snprintf(nm, sizeof nm, "update_%s%s_%s", CPLX ? "c" : "r", BLK ? "b" : "s", sizeof(T) == 8 ? "f64" : "f32");
-    profile_add(nm, launches, samples, t_upd, 6.0 * vbytes);
-    snprintf(nm, sizeof nm, "direction_%s%s_%s", CPLX ? "c" : "r", BLK ? "b" : "s", sizeof(T) == 8 ? "f64" : "f32");
-    profile_add(nm, launches, samples, t_dir, 3.0 * vbytes);
+    if (samples > 0) {
+      snprintf(nm, sizeof nm, "spmm_%s%s_%s", k1, k2, k3);
+      profile_add(nm, launches, samples, t_spmm, b_spmm / samples);
+      snprintf(nm, sizeof nm, "update_%s%s_%s", k1, k2, k3);
+      profile_add(nm, launches, samples, t_upd, b_upd / samples);
+      snprintf(nm, sizeof nm, "direction_%s%s_%s", k1, k2, k3);
+      profile_add(nm, launches, samples, t_dir, b_dir / samples);
+    }
     for (auto& e : ev) cudaEventDestroy(e);
   }
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
   cudaFreeHost(h_flags);
+  scratch_free(tl.base, st);
   scratch_free(base, st);
   return result;
 }
@@ -965,6 +1288,7 @@ ifilt_status solve_batched(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F
       const int id = f * nsys + s;
       launch_rhs(m, fields + (int64_t)f * h.n_comp * h.n_in, s, bsrc + (size_t)id * n * NS,
                  x0src + (size_t)id * n * NS, st);
+      profile_count(1);
     }
 
   std::vector<ColumnSpec> all;

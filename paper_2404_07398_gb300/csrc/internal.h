@@ -138,6 +138,8 @@ void spectrum_device(ifilt_mesh_s* m, int32_t F, int32_t nk, const double* k_dev
 bool profiling_on();
 void profile_add(const char* name, int64_t launches, int64_t samples, double sampled_ms,
                  double bytes_per_launch);
+// count kernel launches of this library (reported as "(all kernels)")
+void profile_count(int64_t launches);
 
 // stream-ordered scratch
 void* scratch_alloc(size_t bytes, cudaStream_t st);

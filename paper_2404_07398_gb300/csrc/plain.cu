@@ -240,6 +240,7 @@ ifilt_status solve_plain(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, 
         if (!ok) result = IFILT_NOT_CONVERGED;
         double* out_sys = out + (((int64_t)f * nk + j) * h.n_comp + sys) * out_sys_stride;
         launch_output_plain(m, w.x, field, sys, out_sys, st);
+        profile_count(4 + 9LL * it + 5 + 1);  // setup, iterations, true residual, output
         if (stats) {
           ifilt_col_stats& s = stats[((int64_t)f * nk + j) * nsys + sys];
           s.iters = it;

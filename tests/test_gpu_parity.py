@@ -192,3 +192,42 @@ def test_sphere_workload_full_size_certificate(lib):
     for j in (10, 25, 39):
         ref, _ = oracle.filter_field(P, w["fields"][0], [w["k"][j]], 2, rtol=1e-12)
         assert _rel(res[0, j, 0], ref[0, 0]) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("placement", ["vertex_vector", "cell"])
+def test_wide_batch_forty_scales(lib, placement):
+    """The full 40-scale list at once (80 and 160 lanes, the shape of the
+    velocity workload) on a level-4 mesh, FP32 + FP64 refinement, complex n = 2
+    form: exercises lane retirement and per-column refinement."""
+    m = _sphere(4, 63, polar=5.0)
+    P = oracle.build_problem(m, placement)
+    f = _fields(P, 1, 8)
+    ks = synth.log_wavenumbers(4000.0, 10.0, 40)
+    res, stats, st = _run(lib, m, placement, f, ks, 2, tol=1e-10, precision=1, n2_solver=2)
+    assert st == 0, stats
+    sel = [0, 7, 19, 39]
+    _, ref = _oracle(m, placement, f, ks[sel], 2)
+    _check(res[:, sel], ref, TOL_MIXED)
+
+
+def test_profiling_samples_in_graph_mode(lib):
+    """Kernel timing through CUDA events recorded inside the captured graphs."""
+    import torch
+    m = _sphere(4, 65)
+    P = oracle.build_problem(m, "vertex_scalar")
+    f = torch.tensor(_fields(P, 1, 9), device="cuda")
+    h = lib.prepare_mesh(m, "vertex_scalar", max_order=2)
+    lib.profile_reset()
+    lib.profile_enable(True)
+    try:
+        out, stats, st = lib.solve(h, f, synth.log_wavenumbers(4000.0, 300.0, 6), order=2, tol=1e-10,
+                                   precision=1)
+    finally:
+        lib.profile_enable(False)
+    h.release()
+    assert st == 0
+    recs = {r["name"]: r for r in lib.profile_read()}
+    spmm = [r for n, r in recs.items() if n.startswith("spmm_")]
+    assert spmm and spmm[0]["samples"] > 0 and spmm[0]["sampled_ms"] > 0
+    assert spmm[0]["bytes_per_launch"] > 0
+    assert recs["(all kernels)"]["launches"] >= spmm[0]["launches"] * 5
