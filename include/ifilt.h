@@ -104,7 +104,7 @@ typedef struct {
   int32_t max_order;         /* highest filter order n the mesh must serve: 1 or 2 */
   int32_t reorder;           /* IFILT_REORDER_* : device row order */
   double cell_A;             /* constant A of Eq. 6 (cell placement); 0 selects sqrt(3) */
-  int32_t ell_slice;         /* rows per sliced-ELL slice; 0 = library default */
+  int32_t ell_slice;         /* rows per sliced-ELL slice, 4..1024; 0 = library default (64) */
 } ifilt_mesh_desc;
 
 typedef struct {

@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <vector>
 
@@ -72,6 +73,52 @@ __device__ __forceinline__ void stp(T* p, const Pack<T>& v) {
   *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(&v);
 }
 
+// Per-thread dot-product accumulator.  For FP32 vectors the FP64 unit of
+// GB300 is far too slow to take one operation per element, so partial sums
+// are carried as an unevaluated pair (s, c) on the FP32 pipes: each product
+// a*b is split exactly into p + e by an FMA, p is added to s with a two-sum,
+// and every rounding error goes into c (the compensated dot product of Ogita,
+// Rump and Oishi, 2005).  Its error is about u|sum| + (m u)^2 sum|terms| for a
+// chain of m terms, so chains are kept short: `flush` moves the pair into an
+// FP64 sum every few rows, which costs one FP64 add per lane and flush.
+// Explicit _rn intrinsics keep the compiler from contracting the error terms.
+template <typename T>
+struct DotAcc {
+  double d = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { d = fma((double)a, (double)b, d); }
+  __device__ __forceinline__ void add_sum(T x) { d += (double)x; }
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ double get() const { return d; }
+};
+template <>
+struct DotAcc<float> {
+  float s = 0.f, c = 0.f;
+  double d = 0.0;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+  }
+  // x is a row's few terms already summed in FP32: a two-sum only
+  __device__ __forceinline__ void add_sum(float x) {
+    const float t = __fadd_rn(s, x);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+    s = t;
+  }
+  __device__ __forceinline__ void flush() {
+    d += (double)s + (double)c;
+    s = 0.f;
+    c = 0.f;
+  }
+  __device__ __forceinline__ double get() const { return d + ((double)s + (double)c); }
+};
+constexpr int kFlushRows = 16;  // rows per compensated chain (lanes x 2 terms each)
+
 // 4 consecutive ELL entries' values (NV per entry) converted to AT.
 template <typename MV, int NV, typename AT>
 __device__ __forceinline__ void load_vals(const MV* __restrict__ p, AT* out) {
@@ -112,6 +159,8 @@ struct Cols {
   int* rounds;
   int* status;      // 0 ok, 1 not converged, 2 breakdown
   int* refresh;     // column waits for its FP64 true residual / next refinement round
+  int* round_it0;   // iteration count when the current inner round started
+  int* round_cap;   // iterations allowed in the current inner round
   int* live;        // [3] number of active columns, columns to refresh, columns not done
 };
 
@@ -123,100 +172,175 @@ struct Params {
   int maxit;
   double tol2_rel;  // tol^2
   double inner2;    // inner_tol^2 (0: run to the outer tolerance)
+  int spt;          // ELL slices per SpMM tile
+  int wmax;         // widest ELL slice
 };
 
 // ------------------------------------------------------------------ kernels
 
+template <typename T, typename MV>
+__device__ __forceinline__ T cvt(MV v) {
+  if constexpr (sizeof(MV) == 2) return (T)__bfloat162float(v);
+  else return (T)v;
+}
+
+// q = M p + shift * acc for one row (all sub-rows), and the row's share of
+// <p, q>: the row's few terms are summed in FP32, then added to the
+// compensated per-thread accumulator.
+template <typename T, bool CPLX, bool BLK>
+__device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, int l0, const double* __restrict__ mass,
+                                              const T* sh, T (*acc)[Pack<T>::N], const T* __restrict__ p,
+                                              T* __restrict__ q, DotAcc<T>* dacc) {
+  constexpr int VEC = Pack<T>::N;
+  constexpr int NS = BLK ? 2 : 1;
+  const T mr = (T)mass[r];
+  T rowdot[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; v++) rowdot[v] = (T)0;
+#pragma unroll
+  for (int b = 0; b < NS; b++) {
+    const int64_t off = r * rowW + (int64_t)b * W + l0;
+    const Pack<T> pr = ldp(p + off);
+    Pack<T> qo;
+    if constexpr (CPLX) {
+#pragma unroll
+      for (int v = 0; v < VEC; v += 2) {
+        const T pre = pr.v[v], pim = pr.v[v + 1];
+        const T qre = mr * pre - sh[v] * acc[b][v + 1];
+        const T qim = mr * pim + sh[v] * acc[b][v];
+        qo.v[v] = qre;
+        qo.v[v + 1] = qim;
+        rowdot[v] = fma(pre, qre, fma(-pim, qim, rowdot[v]));
+        rowdot[v + 1] = fma(pre, qim, fma(pim, qre, rowdot[v + 1]));
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < VEC; v++) {
+        const T qv = mr * pr.v[v] + sh[v] * acc[b][v];
+        qo.v[v] = qv;
+        if constexpr (NS == 1) dacc[v].add(pr.v[v], qv);  // a single exact product
+        else rowdot[v] = fma(pr.v[v], qv, rowdot[v]);
+      }
+    }
+    stp(q + off, qo);
+  }
+  if constexpr (CPLX || NS > 1) {
+#pragma unroll
+    for (int v = 0; v < VEC; v++) dacc[v].add_sum(rowdot[v]);
+  }
+}
+
+constexpr int kMaxSpt = 64;       // sliced-ELL slices staged per tile
+constexpr int kStageBytes = 48 * 1024;
+
+// q = M p + shift * (G p) for every lane, with the per-block partials of <p, q>.
+// Work is cut into tiles of `spt` ELL slices: the tile's column indices and
+// values are first copied cooperatively (coalesced 16-byte loads) into shared
+// memory, so a row then waits on one dependent global access (the gathered
+// neighbour rows of p) instead of three (slice descriptor, indices, values).
 template <typename T, typename MV, bool CPLX, bool BLK>
-__global__ void __launch_bounds__(kBlock) spmm_kernel(EllView<MV> A, Params P, const T* __restrict__ p,
+__global__ void __launch_bounds__(kBlock, 4) spmm_kernel(EllView<MV> A, Params P, int n_slices, const T* __restrict__ p,
                                                       T* __restrict__ q, const double* __restrict__ mass,
                                                       Cols C, double* __restrict__ partial) {
   if (*C.live == 0) return;
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
   constexpr int NV = BLK ? 2 : 1;
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_w[kMaxSpt], s_o[kMaxSpt];
   const int W = P.W;
   const int TPR = W / VEC;
   const int RPP = kBlock / TPR;
+  const int H = A.slice_h;
+  const int spt = P.spt;
+  const int TR = spt * H;
+  double* sred = reinterpret_cast<double*>(smraw);
+  int* scol = reinterpret_cast<int*>(smraw + (size_t)RPP * W * sizeof(double));
+  MV* sval = reinterpret_cast<MV*>(scol + (size_t)TR * P.wmax);
   const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
   const int l0 = g * VEC;
-  double dacc[VEC];
+  const bool on = tr < RPP && tr < TR;
+  DotAcc<T> dacc[VEC];
+  T sh[VEC];
 #pragma unroll
-  for (int v = 0; v < VEC; v++) dacc[v] = 0.0;
-  if (tr < RPP) {
-    T sh[VEC];
+  for (int v = 0; v < VEC; v++) sh[v] = on ? (T)C.shift[CPLX ? (l0 + v) >> 1 : l0 + v] : (T)0;
+  const int64_t rowW = (int64_t)NS * W;
+  int chain = 0;
+  const int ntiles = (n_slices + spt - 1) / spt;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int s0 = tile * spt, s1 = min(s0 + spt, n_slices);
+    const int64_t ob = A.slice_off[s0], oe = A.slice_off[s1];
+    if ((int)threadIdx.x < s1 - s0) {
+      s_w[threadIdx.x] = A.slice_w[s0 + threadIdx.x];
+      s_o[threadIdx.x] = (int)(A.slice_off[s0 + threadIdx.x] - ob);
+    }
+    const int ne = (int)(oe - ob);  // a multiple of 4 entries
+    for (int i = threadIdx.x; i < ne / 4; i += kBlock)
+      reinterpret_cast<int4*>(scol)[i] = __ldg(reinterpret_cast<const int4*>(A.col + ob) + i);
+    if constexpr ((4 * NV * sizeof(MV)) % 16 == 0) {
+      const int n16 = ne * NV * (int)sizeof(MV) / 16;
+      for (int i = threadIdx.x; i < n16; i += kBlock)
+        reinterpret_cast<uint4*>(sval)[i] = __ldg(reinterpret_cast<const uint4*>(A.val + ob * NV) + i);
+    } else {
+      const int n8 = ne * NV * (int)sizeof(MV) / 8;
+      for (int i = threadIdx.x; i < n8; i += kBlock)
+        reinterpret_cast<uint2*>(sval)[i] = __ldg(reinterpret_cast<const uint2*>(A.val + ob * NV) + i);
+    }
+    __syncthreads();
+    const int64_t r0 = (int64_t)s0 * H;
+    const int rows = (int)min((int64_t)TR, (int64_t)P.n - r0);
+    if (on) {
+      for (int lr = tr; lr < rows; lr += RPP) {
+        const int64_t r = r0 + lr;
+        const int sl = lr / H;
+        const int w = s_w[sl];
+        const int eb = s_o[sl] + (lr - sl * H) * w;
+        T acc[NS][VEC];
 #pragma unroll
-    for (int v = 0; v < VEC; v++) sh[v] = (T)C.shift[CPLX ? (l0 + v) >> 1 : l0 + v];
-    const int64_t rowW = (int64_t)NS * W;
-    for (int64_t r = (int64_t)blockIdx.x * RPP + tr; r < P.n; r += (int64_t)gridDim.x * RPP) {
-      const int s = (int)(r / A.slice_h);
-      const int w = A.slice_w[s];
-      const int64_t base = A.slice_off[s] + (r - (int64_t)s * A.slice_h) * w;
-      T acc[NS][VEC];
+        for (int b = 0; b < NS; b++)
 #pragma unroll
-      for (int b = 0; b < NS; b++)
+          for (int v = 0; v < VEC; v++) acc[b][v] = (T)0;
+        for (int e = 0; e < w; e += 4) {
+          const int4 c4 = *reinterpret_cast<const int4*>(scol + eb + e);
+          const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+          const MV* vv = sval + (size_t)(eb + e) * NV;
 #pragma unroll
-        for (int v = 0; v < VEC; v++) acc[b][v] = (T)0;
-      for (int e = 0; e < w; e += 4) {
-        const int4 c4 = __ldg(reinterpret_cast<const int4*>(A.col + base + e));
-        T vals[4 * NV];
-        load_vals<MV, NV, T>(A.val + (base + e) * NV, vals);
-        const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+          for (int t = 0; t < 4; t++) {
+            const T* src = p + (int64_t)cc[t] * rowW + l0;
+            const Pack<T> pu = ldp(src);
+            if constexpr (BLK) {
+              const Pack<T> pv = ldp(src + W);
+              const T a = cvt<T>(vv[2 * t]), bb = cvt<T>(vv[2 * t + 1]);
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
-          const T* src = p + (int64_t)cc[t] * rowW + l0;
-          Pack<T> pu = ldp(src);
-          if constexpr (BLK) {
-            Pack<T> pv = ldp(src + W);
-            const T a = vals[2 * t], bb = vals[2 * t + 1];
+              for (int v = 0; v < VEC; v++) {
+                acc[0][v] = fma(a, pu.v[v], fma(bb, pv.v[v], acc[0][v]));
+                acc[1][v] = fma(a, pv.v[v], fma(-bb, pu.v[v], acc[1][v]));
+              }
+            } else {
+              const T a = cvt<T>(vv[t]);
 #pragma unroll
-            for (int v = 0; v < VEC; v++) {
-              acc[0][v] = fma(a, pu.v[v], fma(bb, pv.v[v], acc[0][v]));
-              acc[1][v] = fma(a, pv.v[v], fma(-bb, pu.v[v], acc[1][v]));
+              for (int v = 0; v < VEC; v++) acc[0][v] = fma(a, pu.v[v], acc[0][v]);
             }
-          } else {
-            const T a = vals[t];
-#pragma unroll
-            for (int v = 0; v < VEC; v++) acc[0][v] = fma(a, pu.v[v], acc[0][v]);
           }
         }
-      }
-      const T mr = (T)mass[r];
+        if (++chain == kFlushRows) {
+          chain = 0;
 #pragma unroll
-      for (int b = 0; b < NS; b++) {
-        const int64_t off = r * rowW + (int64_t)b * W + l0;
-        const Pack<T> pr = ldp(p + off);
-        Pack<T> qo;
-        if constexpr (CPLX) {
-#pragma unroll
-          for (int v = 0; v < VEC; v += 2) {
-            const T pre = pr.v[v], pim = pr.v[v + 1];
-            const T qre = mr * pre - sh[v] * acc[b][v + 1];
-            const T qim = mr * pim + sh[v] * acc[b][v];
-            qo.v[v] = qre;
-            qo.v[v + 1] = qim;
-            dacc[v] += (double)pre * qre - (double)pim * qim;
-            dacc[v + 1] += (double)pre * qim + (double)pim * qre;
-          }
-        } else {
-#pragma unroll
-          for (int v = 0; v < VEC; v++) {
-            const T qv = mr * pr.v[v] + sh[v] * acc[b][v];
-            qo.v[v] = qv;
-            dacc[v] += (double)pr.v[v] * qv;
-          }
+          for (int v = 0; v < VEC; v++) dacc[v].flush();
         }
-        stp(q + off, qo);
+        spmm_epilogue<T, CPLX, BLK>(r, rowW, W, l0, mass, sh, acc, p, q, dacc);
       }
     }
+    __syncthreads();  // the next tile overwrites the stage
+  }
+  if (tr < RPP) {
 #pragma unroll
-    for (int v = 0; v < VEC; v++) sm[tr * W + l0 + v] = dacc[v];
+    for (int v = 0; v < VEC; v++) sred[tr * W + l0 + v] = dacc[v].get();
   }
   __syncthreads();
   for (int l = threadIdx.x; l < W; l += kBlock) {
     double s = 0.0;
-    for (int t = 0; t < RPP; t++) s += sm[t * W + l];
+    for (int t = 0; t < RPP; t++) s += sred[t * W + l];
     partial[(int64_t)blockIdx.x * P.pstride + l] = s;
   }
 }
@@ -224,7 +348,7 @@ __global__ void __launch_bounds__(kBlock) spmm_kernel(EllView<MV> A, Params P, c
 // x += alpha p ; r -= alpha q ; partial <r, r> (slots [0, W): lane-wise for real,
 // (re, im) pairs for complex) and ||r||^2 (complex only, slots W + column).
 template <typename T, bool CPLX, bool BLK>
-__global__ void __launch_bounds__(kBlock) update_kernel(Params P, T* __restrict__ x, const T* __restrict__ p,
+__global__ void __launch_bounds__(kBlock, 4) update_kernel(Params P, T* __restrict__ x, const T* __restrict__ p,
                                                         T* __restrict__ r, const T* __restrict__ q, Cols C,
                                                         double* __restrict__ partial) {
   if (*C.live == 0) return;
@@ -237,11 +361,7 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Params P, T* __restrict_
   const int RPP = kBlock / TPR;
   const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
   const int l0 = g * VEC;
-  double d1[VEC], d2[VEC / 2 > 0 ? VEC / 2 : 1];
-#pragma unroll
-  for (int v = 0; v < VEC; v++) d1[v] = 0.0;
-#pragma unroll
-  for (int v = 0; v < (VEC / 2 > 0 ? VEC / 2 : 1); v++) d2[v] = 0.0;
+  DotAcc<T> d1[VEC], d2[VEC / 2 > 0 ? VEC / 2 : 1];
   if (tr < RPP) {
     T a[VEC];
 #pragma unroll
@@ -250,7 +370,15 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Params P, T* __restrict_
       else a[v] = (T)C.alpha[2 * (l0 + v)];
     }
     const int64_t rowW = (int64_t)NS * W;
+    int chain = 0;
     for (int64_t row = (int64_t)blockIdx.x * RPP + tr; row < P.n; row += (int64_t)gridDim.x * RPP) {
+      if (++chain == kFlushRows) {
+        chain = 0;
+#pragma unroll
+        for (int v = 0; v < VEC; v++) d1[v].flush();
+#pragma unroll
+        for (int v = 0; v < (VEC / 2 > 0 ? VEC / 2 : 1); v++) d2[v].flush();
+      }
 #pragma unroll
       for (int b = 0; b < NS; b++) {
         const int64_t off = row * rowW + (int64_t)b * W + l0;
@@ -264,17 +392,17 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Params P, T* __restrict_
             xv.v[v + 1] += are * pv.v[v + 1] + aim * pv.v[v];
             rv.v[v] -= are * qv.v[v] - aim * qv.v[v + 1];
             rv.v[v + 1] -= are * qv.v[v + 1] + aim * qv.v[v];
-            const double rre = rv.v[v], rim = rv.v[v + 1];
-            d1[v] += rre * rre - rim * rim;
-            d1[v + 1] += 2.0 * rre * rim;
-            d2[v / 2] += rre * rre + rim * rim;
+            const T rre = rv.v[v], rim = rv.v[v + 1];
+            d1[v].add_sum(fma(rre, rre, -rim * rim));
+            d1[v + 1].add((T)2 * rre, rim);
+            d2[v / 2].add_sum(fma(rre, rre, rim * rim));
           }
         } else {
 #pragma unroll
           for (int v = 0; v < VEC; v++) {
             xv.v[v] = fma(a[v], pv.v[v], xv.v[v]);
             rv.v[v] = fma(-a[v], qv.v[v], rv.v[v]);
-            d1[v] += (double)rv.v[v] * rv.v[v];
+            d1[v].add(rv.v[v], rv.v[v]);
           }
         }
         stp(x + off, xv);
@@ -282,10 +410,10 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Params P, T* __restrict_
       }
     }
 #pragma unroll
-    for (int v = 0; v < VEC; v++) sm[tr * NSL + l0 + v] = d1[v];
+    for (int v = 0; v < VEC; v++) sm[tr * NSL + l0 + v] = d1[v].get();
     if constexpr (CPLX) {
 #pragma unroll
-      for (int v = 0; v < VEC / 2; v++) sm[tr * NSL + W + l0 / 2 + v] = d2[v];
+      for (int v = 0; v < VEC / 2; v++) sm[tr * NSL + W + l0 / 2 + v] = d2[v].get();
     }
   }
   __syncthreads();
@@ -412,7 +540,9 @@ __global__ void finish_beta_kernel(Params P, int nb, const double* __restrict__ 
       stop = true;
     } else if (n2 <= C.target2[col]) {
       stop = true;
-    } else if (it >= P.maxit) {
+    } else if (it >= P.maxit || it - C.round_it0[col] >= C.round_cap[col]) {
+      // iteration cap, or an inner round that stalls: end the round so that a
+      // fresh FP64 residual restarts it
       stop = true;
     }
     if (stop) {
@@ -425,18 +555,17 @@ __global__ void finish_beta_kernel(Params P, int nb, const double* __restrict__ 
   C.beta[2 * col + 1] = bi;
 }
 
-// x64 = x0 (real lanes; imaginary lanes 0)
+// x64 = x0 on the lanes of newly admitted columns (real lanes; imaginary lanes 0)
 template <bool CPLX, bool BLK>
-__global__ void init_x_kernel(Params P, const double* __restrict__ x0src, const int* __restrict__ lane_src,
-                              double* __restrict__ x64) {
+__global__ void init_lanes_kernel(Params P, const double* const* __restrict__ xptr, const int* __restrict__ lane_src,
+                                  const int* __restrict__ fresh, double* __restrict__ x64) {
   constexpr int NS = BLK ? 2 : 1;
   const int64_t total = (int64_t)P.n * NS * P.W;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int l = (int)(i % P.W);
+    if (!fresh[CPLX ? l >> 1 : l]) continue;
     const int64_t rs = i / P.W;  // row * NS + sub
-    double v = 0.0;
-    if (!(CPLX && (l & 1))) v = x0src[(int64_t)lane_src[l] * P.n * NS + rs];
-    x64[i] = v;
+    x64[i] = (CPLX && (l & 1)) ? 0.0 : xptr[lane_src[l]][rs];
   }
 }
 
@@ -446,7 +575,7 @@ __global__ void init_x_kernel(Params P, const double* __restrict__ x0src, const 
 template <typename T, bool CPLX, bool BLK>
 __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Params P,
                                                           const double* __restrict__ x64,
-                                                          const double* __restrict__ bsrc,
+                                                          const double* const* __restrict__ bptr,
                                                           const int* __restrict__ lane_src,
                                                           const double* __restrict__ mass, Cols C,
                                                           T* __restrict__ r, T* __restrict__ d, T* __restrict__ p,
@@ -455,6 +584,7 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
   constexpr int NS = BLK ? 2 : 1;
   constexpr int NV = BLK ? 2 : 1;
   constexpr int DP = VEC / 2;  // double packs per thread
+  if (C.live[1] == 0) return;   // no column waits for a refinement round
   extern __shared__ double sm[];
   const int W = P.W;
   const int ncolsW = CPLX ? W / 2 : W;
@@ -541,7 +671,7 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
         if constexpr (CPLX) {
 #pragma unroll
           for (int v = 0; v < VEC; v += 2) {
-            const double bre = bsrc[(int64_t)src[v] * P.n * NS + row * NS + b];
+            const double bre = bptr[src[v]][row * NS + b];
             const double r_re = bre - (mr * xo[v] - sh[v] * acc[b][v + 1]);
             const double r_im = -(mr * xo[v + 1] + sh[v] * acc[b][v]);
             const T tre = (T)r_re, tim = (T)r_im;
@@ -554,7 +684,7 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
         } else {
 #pragma unroll
           for (int v = 0; v < VEC; v++) {
-            const double bv = bsrc[(int64_t)src[v] * P.n * NS + row * NS + b];
+            const double bv = bptr[src[v]][row * NS + b];
             const double rv = bv - (mr * xo[v] + sh[v] * acc[b][v]);
             const T t = (T)rv;
             ro.v[v] = t;
@@ -599,6 +729,7 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
 
 template <bool CPLX>
 __global__ void finish_residual_kernel(Params P, int nb, const double* __restrict__ partial, Cols C) {
+  if (C.live[1] == 0) return;
   __shared__ double buf[8][33];
   const int col = blockIdx.x * 32 + threadIdx.x;
   const bool ok = col < P.ncols;
@@ -637,6 +768,10 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
   C.rho[2 * col + 1] = rim;
   C.rn2[col] = n2;
   C.target2[col] = fmax(P.inner2 * n2, 0.25 * C.tol2[col]);
+  // later rounds get twice the length of the first (at least 256 iterations)
+  if (C.rounds[col] == 1) C.round_cap[col] = max(256, 2 * (C.iters[col] - C.round_it0[col]));
+  else if (C.rounds[col] == 0) C.round_cap[col] = P.maxit;
+  C.round_it0[col] = C.iters[col];
   C.rounds[col]++;
   C.active[col] = 1;
   atomicAdd(C.live, 1);
@@ -645,7 +780,8 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
 // x64 += d on the lanes of refreshed columns
 template <typename T, bool CPLX>
 __global__ void accumulate_kernel(int64_t total, int W, const int* __restrict__ refresh, double* __restrict__ x64,
-                                  const T* __restrict__ d) {
+                                  const T* __restrict__ d, const int* __restrict__ live) {
+  if (live[1] == 0) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int l = (int)(i % W);
     if (refresh[CPLX ? l >> 1 : l]) x64[i] += (double)d[i];
@@ -684,18 +820,18 @@ __global__ void gather_lanes_kernel(int64_t rows, int Wold, int Wnew, const int*
   }
 }
 
-// out[f][k][comp][o] from the FP64 solution (real part); land entries copy the
+// The FP64 solution (real part) of every column flagged in `emit`, written to
+// its caller block out[comp][o] in original mesh order; land entries copy the
 // input (scalar, cell) or are zero (vector).
 template <bool CPLX, bool BLK>
 __global__ void output_kernel(Params P, int32_t n_out, const int32_t* __restrict__ inv,
-                              const double* __restrict__ x64, const double* __restrict__ fields,
-                              const int64_t* __restrict__ col_out, const int64_t* __restrict__ col_in,
-                              double* __restrict__ out) {
+                              const double* __restrict__ x64, double* const* __restrict__ col_out,
+                              const double* const* __restrict__ col_in, const int* __restrict__ emit) {
   constexpr int NS = BLK ? 2 : 1;
   const int col = blockIdx.y;
-  const int64_t obase = col_out[col];
-  if (obase < 0) return;
-  const int64_t ibase = col_in[col];
+  if (!emit[col]) return;
+  double* out = col_out[col];
+  const double* in = col_in[col];
   const int lane = CPLX ? 2 * col : col;
   for (int32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
     const int32_t r = inv[o];
@@ -703,8 +839,8 @@ __global__ void output_kernel(Params P, int32_t n_out, const int32_t* __restrict
     for (int b = 0; b < NS; b++) {
       double v;
       if (r >= 0) v = x64[((int64_t)r * NS + b) * P.W + lane];
-      else v = BLK ? 0.0 : fields[ibase + o];
-      out[obase * 1 + (int64_t)b * n_out + o] = v;
+      else v = BLK ? 0.0 : in[o];
+      out[(int64_t)b * n_out + o] = v;
     }
   }
 }
@@ -726,29 +862,15 @@ void launch_check(const char* what, int blocks, size_t smem, int W) {
          what, blocks, smem, W, cudaGetErrorString(e));
 }
 
-struct Variant {
-  bool cplx, blk;
-  int prec;  // 0 fp64, 1 fp32, 2 bf16-valued fp32
-};
-
-template <typename T>
-size_t vec_bytes(int64_t n, int ns, int W) {
-  return (size_t)n * ns * W * sizeof(T);
-}
-
-struct ColumnSpec {
-  int f, sys, kj, src;
-  double shift;
-};
-
-// Lane tiles of one batch: [row][sub][lane] arrays, reallocated narrower when
-// finished columns are retired.
+// Lane tiles of an engine: [row][sub][lane] arrays, reallocated when columns
+// are admitted or retired.
 template <typename T>
 struct Tiles {
   int W = 0;
   T *d = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   double* x64 = nullptr;
   void* base = nullptr;
+  int64_t bytes = 0;
 };
 
 template <typename T>
@@ -757,6 +879,7 @@ Tiles<T> alloc_tiles(int64_t n, int NS, int W, cudaStream_t st) {
   t.W = W;
   const size_t vb = ((size_t)n * NS * W * sizeof(T) + 255) / 256 * 256;
   const size_t xb = ((size_t)n * NS * W * sizeof(double) + 255) / 256 * 256;
+  t.bytes = (int64_t)(4 * vb + xb);
   char* b = (char*)scratch_alloc(4 * vb + xb, st);
   t.base = b;
   t.d = (T*)b;
@@ -770,11 +893,33 @@ Tiles<T> alloc_tiles(int64_t n, int NS, int W, cudaStream_t st) {
 // Host copy of the per-column state, for retiring and re-packing columns.
 struct HostCols {
   std::vector<double> shift, rho, alpha, beta, rn2, target2, r0n2, tol2, rel;
-  std::vector<int> active, done, iters, rounds, status, refresh;
+  std::vector<int> active, done, iters, rounds, status, refresh, round_it0, round_cap;
   void resize(int n) {
     for (auto* v : {&shift, &rn2, &target2, &r0n2, &tol2, &rel}) v->assign(n, 0.0);
     for (auto* v : {&rho, &alpha, &beta}) v->assign(2 * n, 0.0);
-    for (auto* v : {&active, &done, &iters, &rounds, &status, &refresh}) v->assign(n, 0);
+    for (auto* v : {&active, &done, &iters, &rounds, &status, &refresh, &round_it0, &round_cap}) v->assign(n, 0);
+  }
+  // entry j of this <- entry c of h
+  void take(int j, const HostCols& h, int c) {
+    shift[j] = h.shift[c];
+    for (int t = 0; t < 2; t++) {
+      rho[2 * j + t] = h.rho[2 * c + t];
+      alpha[2 * j + t] = h.alpha[2 * c + t];
+      beta[2 * j + t] = h.beta[2 * c + t];
+    }
+    rn2[j] = h.rn2[c];
+    target2[j] = h.target2[c];
+    r0n2[j] = h.r0n2[c];
+    tol2[j] = h.tol2[c];
+    rel[j] = h.rel[c];
+    active[j] = h.active[c];
+    done[j] = h.done[c];
+    iters[j] = h.iters[c];
+    rounds[j] = h.rounds[c];
+    status[j] = h.status[c];
+    refresh[j] = h.refresh[c];
+    round_it0[j] = h.round_it0[c];
+    round_cap[j] = h.round_cap[c];
   }
 };
 
@@ -798,6 +943,8 @@ void cols_download(const Cols& C, HostCols& H, int n, cudaStream_t st) {
   dn(H.rounds.data(), C.rounds, n * 4);
   dn(H.status.data(), C.status, n * 4);
   dn(H.refresh.data(), C.refresh, n * 4);
+  dn(H.round_it0.data(), C.round_it0, n * 4);
+  dn(H.round_cap.data(), C.round_cap, n * 4);
   IFILT_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -820,510 +967,627 @@ void cols_upload(const Cols& C, const HostCols& H, int n, cudaStream_t st) {
   up(C.rounds, H.rounds.data(), n * 4);
   up(C.status, H.status.data(), n * 4);
   up(C.refresh, H.refresh.data(), n * 4);
-  // the host vectors must outlive the copies
-  IFILT_CUDA(cudaStreamSynchronize(st));
+  up(C.round_it0, H.round_it0.data(), n * 4);
+  up(C.round_cap, H.round_cap.data(), n * 4);
+  IFILT_CUDA(cudaStreamSynchronize(st));  // the host vectors must outlive the copies
 }
 
-// Host record of every column of the batch (index into the batch's spec list).
-struct ColResult {
-  int iters = 0, rounds = 0, status = 0, done = 0;
-  double rel = 0.0;
-};
-
 template <typename T, typename MV, bool CPLX, bool BLK>
-ifilt_status run_batch(ifilt_mesh_s* m, const ifilt_solve_opts& o, const std::vector<ColumnSpec>& cols,
-                       int nsrc_total, const double* bsrc_all, const double* x0src_all, const double* fields,
-                       int32_t nk, double* out, ifilt_col_stats* stats, cudaStream_t st) {
-  (void)nsrc_total;
-  const HostPrepared& h = m->host;
-  constexpr int VEC = Pack<T>::N;
-  constexpr int NS = BLK ? 2 : 1;
-  const int lpc = CPLX ? 2 : 1;  // lanes per column
-  const int nreal = (int)cols.size();
-  auto lanes_for = [&](int ncol) { return (ncol * lpc + 3) / 4 * 4; };
-  const int Wmax = lanes_for(nreal);
-  if (Wmax / VEC > kBlock) fail(IFILT_EINVAL, "batch too wide (%d lanes)", Wmax);
-  const int ncmax = Wmax / lpc;
-  const int64_t n = h.n_rows;
-  const bool use_g2 = (o.order >= 2) && !CPLX;
-  const DevEll& E = use_g2 ? m->ell_g2 : m->ell_k;
-  const EllView<MV> A = ell_view<MV>(E);
-  const EllView<double> A64 = ell_view<double>(E);
+class EngineT final : public Engine {
+  static constexpr int VEC = Pack<T>::N;
+  static constexpr int NS = BLK ? 2 : 1;
+  static constexpr int LPC = CPLX ? 2 : 1;  // lanes per column
+  static constexpr int NVAL = BLK ? 2 : 1;
 
-  std::vector<int> src_ids;
-  for (auto& c : cols)
-    if (std::find(src_ids.begin(), src_ids.end(), c.src) == src_ids.end()) src_ids.push_back(c.src);
-  const int nsrc = (int)src_ids.size();
+  struct Source {
+    const double* field = nullptr;
+    int sys = 0;
+    double* buf = nullptr;  // b [n][NS] then x0 [n][NS]
+    int refs = 0;
+  };
+  struct Slot {
+    ColumnJob job;
+    int src = -1;
+    bool retired = false;
+  };
 
-  auto smem_of = [&](int W, int slots_per_lane2) {  // slots per row-pass in units of W/2
-    return (size_t)(kBlock / (W / VEC)) * (size_t)W * slots_per_lane2 / 2 * sizeof(double);
-  };
-  auto blocks_for = [&](int W) {
-    return grid_for((const void*)spmm_kernel<T, MV, CPLX, BLK>, kBlock, smem_of(W, 2), n * (long long)(W / VEC));
-  };
-  const int nb_max = blocks_for(Wmax);
-
-  // fixed scratch: sources, reduction partials, column state, tables
-  const size_t sb = (size_t)nsrc * n * NS * sizeof(double);
-  size_t total = 2 * sb + (size_t)nb_max * 2 * Wmax * 8 + (size_t)ncmax * (8 * 16 + 4 * 8) + (size_t)Wmax * 8 +
-                 64 * 256;
-  char* base = (char*)scratch_alloc(total, st);
-  char* cur = base;
-  auto take = [&](size_t bytes) {
-    char* p = cur;
-    cur += (bytes + 255) / 256 * 256;
-    return (void*)p;
-  };
-  double* bs = (double*)take(sb);
-  double* x0s = (double*)take(sb);
-  double* partial = (double*)take((size_t)nb_max * 2 * Wmax * 8);
-  Cols C{};
-  C.shift = (double*)take(ncmax * 8);
-  C.rho = (double*)take(2 * ncmax * 8);
-  C.alpha = (double*)take(2 * ncmax * 8);
-  C.beta = (double*)take(2 * ncmax * 8);
-  C.rn2 = (double*)take(ncmax * 8);
-  C.target2 = (double*)take(ncmax * 8);
-  C.r0n2 = (double*)take(ncmax * 8);
-  C.tol2 = (double*)take(ncmax * 8);
-  C.rel = (double*)take(ncmax * 8);
-  C.active = (int*)take(ncmax * 4);
-  C.done = (int*)take(ncmax * 4);
-  C.iters = (int*)take(ncmax * 4);
-  C.rounds = (int*)take(ncmax * 4);
-  C.status = (int*)take(ncmax * 4);
-  C.refresh = (int*)take(ncmax * 4);
-  C.live = (int*)take(4 * 4);
-  int* lane_src = (int*)take(Wmax * 4);
-  int* lane_map = (int*)take(Wmax * 4);
-  int64_t* col_out = (int64_t*)take(ncmax * 8);
-  int64_t* col_in = (int64_t*)take(ncmax * 8);
-  for (int s = 0; s < nsrc; s++) {
-    IFILT_CUDA(cudaMemcpyAsync(bs + (size_t)s * n * NS, bsrc_all + (size_t)src_ids[s] * n * NS,
-                               n * NS * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    IFILT_CUDA(cudaMemcpyAsync(x0s + (size_t)s * n * NS, x0src_all + (size_t)src_ids[s] * n * NS,
-                               n * NS * sizeof(double), cudaMemcpyDeviceToDevice, st));
+ public:
+  EngineT(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st, int64_t budget)
+      : m_(m), o_(o), st_(st), budget_(budget) {
+    const HostPrepared& h = m->host;
+    n_ = h.n_rows;
+    E_ = (o.order >= 2 && !CPLX) ? &m->ell_g2 : &m->ell_k;
+    A_ = ell_view<MV>(*E_);
+    A64_ = ell_view<double>(*E_);
+    int lanes = o.max_lanes > 0 ? o.max_lanes : 256;
+    lanes = std::min(lanes, kBlock * VEC) / 4 * 4;
+    if (lanes < 4) fail(IFILT_EINVAL, "max_lanes must allow at least 4 lanes");
+    wcap_ = lanes;
+    ncap_ = wcap_ / LPC;
+    entry_bytes_ = 4 + NVAL * sizeof(MV);
+    if ((size_t)E_->slice_h * E_->max_width * entry_bytes_ > (size_t)kStageBytes)
+      fail(IFILT_EINVAL, "ELL slice of %d rows x %d entries exceeds the shared-memory stage", E_->slice_h,
+           E_->max_width);
+    int dev = 0;
+    IFILT_CUDA(cudaGetDevice(&dev));
+    IFILT_CUDA(cudaDeviceGetAttribute(&n_sms_, cudaDevAttrMultiProcessorCount, dev));
+    nb_max_ = n_sms_ * (2048 / kBlock);
+    IFILT_CUDA(cudaFuncSetAttribute(spmm_kernel<T, MV, CPLX, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kBlock * VEC * sizeof(double) + kStageBytes)));
+    // fixed part: partial sums, column state, tables
+    size_t total = (size_t)nb_max_ * 2 * wcap_ * 8 + (size_t)ncap_ * (8 * 16 + 4 * 10 + 4 * 8) +
+                   (size_t)wcap_ * 8 + 64 * 256;
+    char* cur = (char*)scratch_alloc(total, st_);
+    fixed_ = cur;
+    fixed_bytes_ = (int64_t)total;
+    auto take = [&](size_t bytes) {
+      char* p = cur;
+      cur += (bytes + 255) / 256 * 256;
+      return (void*)p;
+    };
+    partial_ = (double*)take((size_t)nb_max_ * 2 * wcap_ * 8);
+    C_.shift = (double*)take(ncap_ * 8);
+    C_.rho = (double*)take(2 * ncap_ * 8);
+    C_.alpha = (double*)take(2 * ncap_ * 8);
+    C_.beta = (double*)take(2 * ncap_ * 8);
+    C_.rn2 = (double*)take(ncap_ * 8);
+    C_.target2 = (double*)take(ncap_ * 8);
+    C_.r0n2 = (double*)take(ncap_ * 8);
+    C_.tol2 = (double*)take(ncap_ * 8);
+    C_.rel = (double*)take(ncap_ * 8);
+    C_.active = (int*)take(ncap_ * 4);
+    C_.done = (int*)take(ncap_ * 4);
+    C_.iters = (int*)take(ncap_ * 4);
+    C_.rounds = (int*)take(ncap_ * 4);
+    C_.status = (int*)take(ncap_ * 4);
+    C_.refresh = (int*)take(ncap_ * 4);
+    C_.round_it0 = (int*)take(ncap_ * 4);
+    C_.round_cap = (int*)take(ncap_ * 4);
+    C_.live = (int*)take(4 * 4);
+    lane_src_ = (int*)take(wcap_ * 4);
+    lane_map_ = (int*)take(wcap_ * 4);
+    flags_ = (int*)take(ncap_ * 4);
+    bptr_ = (const double**)take(ncap_ * 8);
+    xptr_ = (const double**)take(ncap_ * 8);
+    col_out_ = (double**)take(ncap_ * 8);
+    col_in_ = (const double**)take(ncap_ * 8);
+    IFILT_CUDA(cudaMemsetAsync(C_.live, 0, 16, st_));
+    IFILT_CUDA(cudaMallocHost(&h_cnt_, 4 * sizeof(int)));
+    P_.n = (int32_t)n_;
+    P_.maxit = o.max_iter > 0 ? o.max_iter : 100000;
+    P_.tol2_rel = o.tol * o.tol;
+    const double itol = (sizeof(T) == 8) ? 0.0 : (o.inner_tol > 0 ? o.inner_tol : 1e-4);
+    P_.inner2 = itol * itol;
+    P_.wmax = E_->max_width;
+    m_it_ = o.check_every > 0 ? o.check_every : 32;
+    const char* ng = getenv("IFILT_NO_GRAPH");
+    use_graph_ = !(ng && ng[0] == '1');
+    prof_ = profiling_on();
+    if (prof_)
+      for (auto& e : ev_) IFILT_CUDA(cudaEventCreate(&e));
   }
 
-  // current column set: batch-spec index of each column (-1 = padding)
-  std::vector<int> curcols(nreal);
-  for (int c = 0; c < nreal; c++) curcols[c] = c;
-  std::vector<ColResult> res(nreal);
-  std::vector<int> lsrc_h;
-  std::vector<int64_t> cout_h, cin_h;
-  auto upload_tables = [&](int W) {
-    const int nc = W / lpc;
-    lsrc_h.assign(W, 0);
-    cout_h.assign(nc, -1);
-    cin_h.assign(nc, 0);
-    for (int c = 0; c < nc; c++) {
-      const int id = c < (int)curcols.size() ? curcols[c] : -1;
-      if (id < 0) continue;
-      const ColumnSpec& cs = cols[id];
-      const int s = (int)(std::find(src_ids.begin(), src_ids.end(), cs.src) - src_ids.begin());
-      for (int t = 0; t < lpc; t++) lsrc_h[c * lpc + t] = s;
-      const int comp = h.placement == IFILT_CELL ? cs.sys : 0;
-      cout_h[c] = (((int64_t)cs.f * nk + cs.kj) * h.n_comp + comp) * h.n_out;
-      cin_h[c] = ((int64_t)cs.f * h.n_comp + comp) * h.n_in;
+  ~EngineT() override {
+    cudaStreamSynchronize(st_);
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    for (auto& s : src_)
+      if (s.buf) scratch_free(s.buf, st_);
+    if (tl_.base) scratch_free(tl_.base, st_);
+    if (fixed_) scratch_free(fixed_, st_);
+    if (h_cnt_) cudaFreeHost(h_cnt_);
+    for (auto& e : ev_)
+      if (e) cudaEventDestroy(e);
+    cudaStreamSynchronize(st_);
+  }
+
+  void submit(const std::vector<ColumnJob>& jobs) override {
+    for (const auto& j : jobs) pend_.push_back(j);
+  }
+  bool idle() const override { return live_columns() == 0 && pend_.empty(); }
+  int64_t bytes_held() const override {
+    int64_t b = fixed_bytes_ + tl_.bytes;
+    for (auto& s : src_)
+      if (s.buf) b += src_bytes();
+    return b;
+  }
+  int running() const override { return live_columns(); }
+  int pending() const override { return (int)pend_.size(); }
+  cudaStream_t stream() const override { return st_; }
+
+ private:
+  int live_columns() const {
+    int c = 0;
+    for (auto& s : cur_)
+      if (s.src >= 0 && !s.retired) c++;
+    return c;
+  }
+  int lanes_for(int ncol) const { return (ncol * LPC + 3) / 4 * 4; }
+  size_t smem_of(int W, int slots2) const {
+    return (size_t)(kBlock / (W / VEC)) * (size_t)W * slots2 / 2 * sizeof(double);
+  }
+  int spmm_spt(int W) const {
+    const int RPP = kBlock / (W / VEC);
+    int spt = std::max(1, (RPP + E_->slice_h - 1) / E_->slice_h);
+    while (spt > 1 && (size_t)spt * E_->slice_h * E_->max_width * entry_bytes_ > (size_t)kStageBytes) spt--;
+    return std::min(spt, kMaxSpt);
+  }
+  size_t spmm_smem(int W) const {
+    return smem_of(W, 2) + (size_t)spmm_spt(W) * E_->slice_h * E_->max_width * entry_bytes_;
+  }
+  int blocks_for(int W) const {
+    const long long ntiles = (E_->n_slices + spmm_spt(W) - 1) / spmm_spt(W);
+    return std::min(nb_max_, grid_for((const void*)spmm_kernel<T, MV, CPLX, BLK>, kBlock, spmm_smem(W),
+                                      ntiles * kBlock));
+  }
+  size_t src_bytes() const { return (size_t)2 * n_ * NS * sizeof(double); }
+  int64_t tile_bytes(int W) const { return (int64_t)n_ * NS * W * (4 * sizeof(T) + sizeof(double)); }
+  double shift_of(double k) const {
+    const double ell = 1.0 / k;
+    if (o_.order == 1) return 0.5 * ell * ell;
+    if (CPLX) return ell * ell / std::sqrt(2.0);
+    return 0.5 * ell * ell * ell * ell;
+  }
+
+  // source slot (b, x0) of a (field, system), built on first use
+  int source_for(const ColumnJob& j) {
+    for (int s = 0; s < (int)src_.size(); s++)
+      if (src_[s].buf && src_[s].field == j.field && src_[s].sys == j.sys) {
+        src_[s].refs++;
+        return s;
+      }
+    int s = -1;
+    for (int t = 0; t < (int)src_.size(); t++)
+      if (!src_[t].buf) s = t;
+    if (s < 0) {
+      if ((int)src_.size() >= ncap_) fail(IFILT_ECUDA, "source table full");
+      src_.emplace_back();
+      s = (int)src_.size() - 1;
     }
-    IFILT_CUDA(cudaMemcpyAsync(lane_src, lsrc_h.data(), W * 4, cudaMemcpyHostToDevice, st));
-    IFILT_CUDA(cudaMemcpyAsync(col_out, cout_h.data(), nc * 8, cudaMemcpyHostToDevice, st));
-    IFILT_CUDA(cudaMemcpyAsync(col_in, cin_h.data(), nc * 8, cudaMemcpyHostToDevice, st));
-    IFILT_CUDA(cudaStreamSynchronize(st));
-  };
-
-  // initial column state: every real column asks for its first true residual
-  HostCols H;
-  H.resize(ncmax);
-  for (int c = 0; c < ncmax; c++) {
-    if (c < nreal) {
-      H.shift[c] = cols[c].shift;
-      H.r0n2[c] = -1.0;
-      H.refresh[c] = 1;
-    } else {
-      H.done[c] = 1;
+    Source& q = src_[s];
+    q.field = j.field;
+    q.sys = j.sys;
+    q.buf = (double*)scratch_alloc(src_bytes(), st_);
+    q.refs = 1;
+    launch_rhs(m_, j.field, j.sys, q.buf, q.buf + (size_t)n_ * NS, st_);
+    other_launches_++;
+    return s;
+  }
+  void release_source(int s) {
+    if (s < 0) return;
+    if (--src_[s].refs == 0) {
+      scratch_free(src_[s].buf, st_);
+      src_[s].buf = nullptr;
+      src_[s].field = nullptr;
     }
   }
-  cols_upload(C, H, ncmax, st);
-  upload_tables(Wmax);
 
-  Params P{};
-  P.n = (int32_t)n;
-  P.maxit = o.max_iter > 0 ? o.max_iter : 100000;
-  P.tol2_rel = o.tol * o.tol;
-  const double itol = (sizeof(T) == 8) ? 0.0 : (o.inner_tol > 0 ? o.inner_tol : 1e-4);
-  P.inner2 = itol * itol;
-  Tiles<T> tl = alloc_tiles<T>(n, NS, Wmax, st);
-  auto set_width = [&](int W) {
-    P.W = W;
-    P.ncols = W / lpc;
-    P.pstride = 2 * W;
-  };
-  set_width(Wmax);
-  IFILT_CUDA(cudaMemsetAsync(tl.d, 0, (size_t)n * NS * Wmax * sizeof(T), st));
-  {
-    const int g = grid_for((const void*)init_x_kernel<CPLX, BLK>, kBlock, 0, n * NS * Wmax);
-    launch_check("before init", 0, 0, Wmax);
-    (void)0;
-    init_x_kernel<CPLX, BLK><<<g, kBlock, 0, st>>>(P, x0s, lane_src, tl.x64);
-    launch_check("init", g, 0, Wmax);
-  }
-
-  const int m_it = o.check_every > 0 ? o.check_every : 32;
-  const bool prof = profiling_on();
-  cudaEvent_t ev[6] = {};
-  if (prof)
-    for (auto& e : ev) IFILT_CUDA(cudaEventCreate(&e));
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int nb = nb_max;
-  // IFILT_NO_GRAPH=1 launches every iteration directly and checks each launch
-  // (debugging aid); otherwise m iterations are captured once per tile width.
-  const char* ng = getenv("IFILT_NO_GRAPH");
-  const bool use_graph = !(ng && ng[0] == '1');
-  auto enqueue_iters = [&](bool check) {
-    const int W = P.W;
-    const size_t sm2 = smem_of(W, 2), sm3 = smem_of(W, 3);
-    const int fin_grid = (P.ncols + 31) / 32;
-    const dim3 fin_block(32, 8);
+  // one step: refinement prologue, m iterations, counters to the host
+  void enqueue_step(bool check) {
+    const int W = P_.W;
+    const size_t sm2 = spmm_smem(W), sm3 = smem_of(W, 3), sm4 = smem_of(W, 4);
+    const int fg = (P_.ncols + 31) / 32;
+    const dim3 fb(32, 8);
+    const unsigned evf = check ? cudaEventRecordDefault : cudaEventRecordExternal;
+    auto rec = [&](int i) {
+      if (prof_) IFILT_CUDA(cudaEventRecordWithFlags(ev_[i], st_, evf));
+    };
     auto chk = [&](const char* what) {
       if (!check) return;
       cudaError_t e = cudaGetLastError();
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess)
-        fail(IFILT_ECUDA, "%s (W=%d, blocks=%d, smem=%zu/%zu): %s", what, W, nb, sm2, sm3, cudaGetErrorString(e));
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
+      if (e != cudaSuccess) fail(IFILT_ECUDA, "%s (W=%d, blocks=%d): %s", what, W, nb_, cudaGetErrorString(e));
     };
-    // Inside a stream capture an event record is only a dependency marker
-    // unless it is recorded as an external event node.
-    const unsigned evflags = check ? cudaEventRecordDefault : cudaEventRecordExternal;
-    auto rec = [&](cudaEvent_t e) { IFILT_CUDA(cudaEventRecordWithFlags(e, st, evflags)); };
-    for (int it = 0; it < m_it; it++) {
-      if (prof && it == 0) rec(ev[0]);
-      spmm_kernel<T, MV, CPLX, BLK><<<nb, kBlock, sm2, st>>>(A, P, tl.p, tl.q, m->mass, C, partial);
+    const int ga = grid_for((const void*)accumulate_kernel<T, CPLX>, kBlock, 0, n_ * NS * W);
+    scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
+    chk("scan");
+    accumulate_kernel<T, CPLX><<<ga, kBlock, 0, st_>>>(n_ * NS * W, W, C_.refresh, tl_.x64, tl_.d, C_.live);
+    chk("accumulate");
+    residual_kernel<T, CPLX, BLK><<<nb_, kBlock, sm4, st_>>>(A64_, P_, tl_.x64, bptr_, lane_src_, m_->mass, C_,
+                                                            tl_.r, tl_.d, tl_.p, partial_);
+    chk("residual");
+    finish_residual_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
+    chk("finish_residual");
+    scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
+    for (int it = 0; it < m_it_; it++) {
+      if (it == 0) rec(0);
+      spmm_kernel<T, MV, CPLX, BLK><<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, m_->mass, C_,
+                                                                partial_);
       chk("spmm");
-      if (prof && it == 0) rec(ev[1]);
-      finish_alpha_kernel<CPLX><<<fin_grid, fin_block, 0, st>>>(P, nb, partial, C);
+      if (it == 0) rec(1);
+      finish_alpha_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
       chk("finish_alpha");
-      if (prof && it == 0) rec(ev[2]);
-      update_kernel<T, CPLX, BLK><<<nb, kBlock, sm3, st>>>(P, tl.d, tl.p, tl.r, tl.q, C, partial);
+      if (it == 0) rec(2);
+      update_kernel<T, CPLX, BLK><<<nb_, kBlock, sm3, st_>>>(P_, tl_.d, tl_.p, tl_.r, tl_.q, C_, partial_);
       chk("update");
-      if (prof && it == 0) rec(ev[3]);
-      finish_beta_kernel<CPLX><<<fin_grid, fin_block, 0, st>>>(P, nb, partial, C);
+      if (it == 0) rec(3);
+      finish_beta_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
       chk("finish_beta");
-      if (prof && it == 0) rec(ev[4]);
-      direction_kernel<T, CPLX, BLK><<<nb, kBlock, 0, st>>>(P, tl.p, tl.r, C);
+      if (it == 0) rec(4);
+      direction_kernel<T, CPLX, BLK><<<nb_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_);
       chk("direction");
-      if (prof && it == 0) rec(ev[5]);
+      if (it == 0) rec(5);
     }
-  };
-  auto capture = [&]() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    exec = nullptr;
-    graph = nullptr;
-    nb = blocks_for(P.W);
-    IFILT_CUDA(cudaGetLastError());
-    if (!use_graph) return;
-    IFILT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    enqueue_iters(false);
-    cudaError_t cap = cudaStreamEndCapture(st, &graph);
+    scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
+    IFILT_CUDA(cudaMemcpyAsync(h_cnt_, C_.live, 3 * sizeof(int), cudaMemcpyDeviceToHost, st_));
+  }
+  int launches_per_step() const { return 7 + 5 * m_it_; }
+
+  void capture() {
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    exec_ = nullptr;
+    graph_ = nullptr;
+    nb_ = blocks_for(P_.W);
+    launch_check("before capture", nb_, 0, P_.W);
+    if (!use_graph_) return;
+    IFILT_CUDA(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(false);
+    cudaError_t cap = cudaStreamEndCapture(st_, &graph_);
     if (cap != cudaSuccess) fail(IFILT_ECUDA, "graph capture failed: %s", cudaGetErrorString(cap));
-    launch_check("capture", nb, 0, P.W);
-    IFILT_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-    launch_check("instantiate", nb, 0, P.W);
-  };
-  // writes the outputs of the current columns for which `sel` holds
-  auto emit = [&](const std::vector<int>& sel) {
-    const int nc = P.ncols;
-    std::vector<int64_t> co(nc, -1);
-    for (int c = 0; c < nc && c < (int)curcols.size(); c++)
-      if (curcols[c] >= 0 && sel[c]) co[c] = cout_h[c];
-    IFILT_CUDA(cudaMemcpyAsync(col_out, co.data(), nc * 8, cudaMemcpyHostToDevice, st));
-    dim3 og((unsigned)std::min<long long>((h.n_out + kBlock - 1) / kBlock, 1024), (unsigned)nc);
-    output_kernel<CPLX, BLK><<<og, kBlock, 0, st>>>(P, h.n_out, m->inv_perm, tl.x64, fields, col_out, col_in, out);
-    IFILT_CUDA(cudaGetLastError());
-    IFILT_CUDA(cudaStreamSynchronize(st));
-  };
-  auto record = [&](const HostCols& Hc, int c) {
-    const int id = curcols[c];
-    if (id < 0) return;
-    ColResult& r = res[id];
-    r.iters = Hc.iters[c];
-    r.rounds = Hc.rounds[c];
-    r.status = Hc.status[c];
-    r.done = Hc.done[c];
-    r.rel = Hc.rel[c];
-  };
-  // Retire finished columns and narrow the tiles to the ones still running.
-  auto compact = [&]() {
-    const int nc = P.ncols, Wold = P.W;
-    cols_download(C, H, nc, st);
-    std::vector<int> keep, sel(nc, 0);
-    for (int c = 0; c < nc; c++) {
-      if (c >= (int)curcols.size() || curcols[c] < 0) continue;
-      if (H.done[c]) {
-        sel[c] = 1;
-        record(H, c);
-      } else {
-        keep.push_back(c);
-      }
+    launch_check("capture", nb_, 0, P_.W);
+    IFILT_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
+  }
+
+  void set_width(int W) {
+    P_.W = W;
+    P_.ncols = W / LPC;
+    P_.pstride = 2 * W;
+    P_.spt = W > 0 ? spmm_spt(W) : 1;
+  }
+
+  void release_tiles() {
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    exec_ = nullptr;
+    graph_ = nullptr;
+    if (tl_.base) scratch_free(tl_.base, st_);
+    tl_ = Tiles<T>{};
+    cur_.clear();
+    set_width(0);
+  }
+
+  // Keep the running columns, admit queued ones into the free lanes (within
+  // the lane capacity and the memory budget) and re-pack the tiles.
+  void relayout() {
+    const int nc_old = P_.ncols;
+    HostCols Hold;
+    if (nc_old > 0) cols_download(C_, Hold, nc_old, st_);
+    std::vector<int> keep;
+    for (int c = 0; c < (int)cur_.size(); c++)
+      if (cur_[c].src >= 0 && !cur_[c].retired) keep.push_back(c);
+    std::vector<ColumnJob> adm;
+    int64_t held = bytes_held();
+    int64_t new_src = 0;
+    while ((int)(keep.size() + adm.size()) < ncap_ && !pend_.empty()) {
+      const int Wtry = lanes_for((int)(keep.size() + adm.size()) + 1);
+      const int64_t need = held + tile_bytes(Wtry) + new_src + (int64_t)src_bytes();
+      if (budget_ > 0 && need > budget_ && !(keep.empty() && adm.empty())) break;
+      adm.push_back(pend_.front());
+      pend_.pop_front();
+      new_src += (int64_t)src_bytes();
     }
-    emit(sel);
-    const int Wn = lanes_for((int)keep.size());
-    const int ncn = Wn / lpc;
-    std::vector<int> map(Wn, -1);
+    const int nreal = (int)(keep.size() + adm.size());
+    if (nreal == 0) {
+      release_tiles();
+      return;
+    }
+    const int Wn = lanes_for(nreal);
+    const int ncn = Wn / LPC;
     HostCols Hn;
     Hn.resize(ncn);
-    std::vector<int> ncur(ncn, -1);
-    for (int j = 0; j < ncn; j++) {
-      if (j >= (int)keep.size()) {
-        Hn.done[j] = 1;
-        continue;
-      }
+    std::vector<Slot> ncur(ncn);
+    std::vector<int> map(Wn, -1), fresh(ncn, 0);
+    for (int j = 0; j < (int)keep.size(); j++) {
       const int c = keep[j];
-      ncur[j] = curcols[c];
-      for (int t = 0; t < lpc; t++) map[j * lpc + t] = c * lpc + t;
-      Hn.shift[j] = H.shift[c];
-      for (int t = 0; t < 2; t++) {
-        Hn.rho[2 * j + t] = H.rho[2 * c + t];
-        Hn.alpha[2 * j + t] = H.alpha[2 * c + t];
-        Hn.beta[2 * j + t] = H.beta[2 * c + t];
-      }
-      Hn.rn2[j] = H.rn2[c];
-      Hn.target2[j] = H.target2[c];
-      Hn.r0n2[j] = H.r0n2[c];
-      Hn.tol2[j] = H.tol2[c];
-      Hn.rel[j] = H.rel[c];
-      Hn.active[j] = H.active[c];
-      Hn.done[j] = H.done[c];
-      Hn.iters[j] = H.iters[c];
-      Hn.rounds[j] = H.rounds[c];
-      Hn.status[j] = H.status[c];
-      Hn.refresh[j] = H.refresh[c];
+      ncur[j] = cur_[c];
+      Hn.take(j, Hold, c);
+      for (int t = 0; t < LPC; t++) map[j * LPC + t] = c * LPC + t;
     }
-    IFILT_CUDA(cudaMemcpyAsync(lane_map, map.data(), Wn * 4, cudaMemcpyHostToDevice, st));
-    Tiles<T> tn = alloc_tiles<T>(n, NS, Wn, st);
-    const int64_t rows = n * NS;
-    const int g = grid_for((const void*)gather_lanes_kernel<T>, kBlock, 0, rows * Wn);
-    gather_lanes_kernel<T><<<g, kBlock, 0, st>>>(rows, Wold, Wn, lane_map, tl.d, tn.d);
-    gather_lanes_kernel<T><<<g, kBlock, 0, st>>>(rows, Wold, Wn, lane_map, tl.r, tn.r);
-    gather_lanes_kernel<T><<<g, kBlock, 0, st>>>(rows, Wold, Wn, lane_map, tl.p, tn.p);
-    gather_lanes_kernel<double><<<g, kBlock, 0, st>>>(rows, Wold, Wn, lane_map, tl.x64, tn.x64);
-    IFILT_CUDA(cudaGetLastError());
-    scratch_free(tl.base, st);
-    tl = tn;
-    curcols = ncur;
+    for (int i = 0; i < (int)adm.size(); i++) {
+      const int j = (int)keep.size() + i;
+      ncur[j].job = adm[i];
+      ncur[j].src = source_for(adm[i]);
+      Hn.shift[j] = shift_of(adm[i].k);
+      Hn.r0n2[j] = -1.0;
+      fresh[j] = 1;
+    }
+    for (int j = nreal; j < ncn; j++) Hn.done[j] = 1;
+    Tiles<T> tn = alloc_tiles<T>(n_, NS, Wn, st_);
+    const int64_t rows = n_ * NS;
+    if (tl_.base && !keep.empty()) {
+      IFILT_CUDA(cudaMemcpyAsync(lane_map_, map.data(), Wn * 4, cudaMemcpyHostToDevice, st_));
+      const int g = grid_for((const void*)gather_lanes_kernel<T>, kBlock, 0, rows * Wn);
+      gather_lanes_kernel<T><<<g, kBlock, 0, st_>>>(rows, P_.W, Wn, lane_map_, tl_.d, tn.d);
+      gather_lanes_kernel<T><<<g, kBlock, 0, st_>>>(rows, P_.W, Wn, lane_map_, tl_.r, tn.r);
+      gather_lanes_kernel<T><<<g, kBlock, 0, st_>>>(rows, P_.W, Wn, lane_map_, tl_.p, tn.p);
+      gather_lanes_kernel<double><<<g, kBlock, 0, st_>>>(rows, P_.W, Wn, lane_map_, tl_.x64, tn.x64);
+      other_launches_ += 4;
+      launch_check("gather", g, 0, Wn);
+      IFILT_CUDA(cudaStreamSynchronize(st_));  // lane_map_ is rewritten below
+    } else {
+      IFILT_CUDA(cudaMemsetAsync(tn.d, 0, (size_t)rows * Wn * sizeof(T), st_));
+    }
+    if (tl_.base) scratch_free(tl_.base, st_);
+    tl_ = tn;
+    cur_ = ncur;
     set_width(Wn);
-    cols_upload(C, Hn, ncn, st);
-    upload_tables(Wn);
+    upload_tables();
+    cols_upload(C_, Hn, ncn, st_);
+    IFILT_CUDA(cudaMemcpyAsync(flags_, fresh.data(), ncn * 4, cudaMemcpyHostToDevice, st_));
+    const int g = grid_for((const void*)init_lanes_kernel<CPLX, BLK>, kBlock, 0, rows * Wn);
+    init_lanes_kernel<CPLX, BLK><<<g, kBlock, 0, st_>>>(P_, xptr_, lane_src_, flags_, tl_.x64);
+    other_launches_++;
+    launch_check("init lanes", g, 0, Wn);
+    IFILT_CUDA(cudaStreamSynchronize(st_));
     capture();
-  };
+  }
 
-  capture();
-  int* h_flags = nullptr;
-  IFILT_CUDA(cudaMallocHost(&h_flags, sizeof(int) * 4));
-  launch_check("pinned flags", 0, 0, P.W);
-  auto scan = [&]() {
-    launch_check("before scan", 0, 0, P.W);
-    scan_kernel<<<1, 256, 0, st>>>(P.ncols, C);
-    launch_check("scan", 1, 0, P.W);
-    IFILT_CUDA(cudaMemcpyAsync(h_flags, C.live, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    IFILT_CUDA(cudaStreamSynchronize(st));
-  };
-  double t_spmm = 0, t_upd = 0, t_dir = 0, b_spmm = 0, b_upd = 0, b_dir = 0;
-  int64_t samples = 0, graph_launches = 0, other_launches = 2;
-  const double mbytes = (double)E.entries * (4.0 + E.nval * sizeof(MV)) + (double)n * 8.0;
-  const int64_t guard = (int64_t)(P.maxit / m_it + 2) * 8 + 64;
-  ifilt_status result = IFILT_OK;
-  for (int64_t loop = 0;; loop++) {
-    if (loop > guard) {
-      result = IFILT_NOT_CONVERGED;
-      break;
+  void upload_tables() {
+    const HostPrepared& h = m_->host;
+    const int W = P_.W, nc = P_.ncols;
+    const double* any_b = nullptr;
+    const double* any_x = nullptr;
+    for (auto& s : src_)
+      if (s.buf) {
+        any_b = s.buf;
+        any_x = s.buf + (size_t)n_ * NS;
+        break;
+      }
+    std::vector<const double*> bp(ncap_, any_b), xp(ncap_, any_x), ci(ncap_, nullptr);
+    std::vector<double*> co(ncap_, nullptr);
+    for (int s = 0; s < (int)src_.size(); s++)
+      if (src_[s].buf) {
+        bp[s] = src_[s].buf;
+        xp[s] = src_[s].buf + (size_t)n_ * NS;
+      }
+    std::vector<int> ls(W, 0);
+    for (int c = 0; c < nc; c++) {
+      const Slot& sl = cur_[c];
+      if (sl.src < 0) continue;
+      for (int t = 0; t < LPC; t++) ls[c * LPC + t] = sl.src;
+      const int comp = h.placement == IFILT_CELL ? sl.job.sys : 0;
+      co[c] = sl.job.out + (int64_t)comp * h.n_out;
+      ci[c] = BLK ? nullptr : sl.job.field + (int64_t)comp * h.n_in;
     }
-    scan();
-    other_launches++;
-    if (h_flags[2] == 0) break;  // every column finished
-    if (h_flags[1] > 0) {        // FP64 true residual and a new inner round for finished inner solves
-      const int W = P.W;
-      const int ga = grid_for((const void*)accumulate_kernel<T, CPLX>, kBlock, 0, n * NS * W);
-      launch_check("before refinement", 0, 0, 0);
-      accumulate_kernel<T, CPLX><<<ga, kBlock, 0, st>>>(n * NS * W, W, C.refresh, tl.x64, tl.d);
-      launch_check("accumulate", ga, 0, W);
-      residual_kernel<T, CPLX, BLK><<<nb, kBlock, smem_of(W, 4), st>>>(A64, P, tl.x64, bs, lane_src, m->mass, C,
-                                                                      tl.r, tl.d, tl.p, partial);
-      launch_check("residual", nb, smem_of(W, 4), W);
-      finish_residual_kernel<CPLX><<<(P.ncols + 31) / 32, dim3(32, 8), 0, st>>>(P, nb, partial, C);
-      launch_check("finish_residual", (P.ncols + 31) / 32, 0, W);
-      other_launches += 3;
-      scan();
-      other_launches++;
-      if (h_flags[2] == 0) break;
-    }
-    const int running = h_flags[2];
-    if (lanes_for(running) < P.W && running * 5 <= P.ncols * 3) {
-      compact();
-      launch_check("compact", 0, 0, P.W);
-    }
-    if (h_flags[0] == 0) continue;
-    if (use_graph) IFILT_CUDA(cudaGraphLaunch(exec, st));
-    else enqueue_iters(true);
-    graph_launches++;
-    IFILT_CUDA(cudaStreamSynchronize(st));
-    launch_check("graph", nb, 0, P.W);
+    IFILT_CUDA(cudaMemcpyAsync(lane_src_, ls.data(), W * 4, cudaMemcpyHostToDevice, st_));
+    IFILT_CUDA(cudaMemcpyAsync(bptr_, bp.data(), ncap_ * 8, cudaMemcpyHostToDevice, st_));
+    IFILT_CUDA(cudaMemcpyAsync(xptr_, xp.data(), ncap_ * 8, cudaMemcpyHostToDevice, st_));
+    IFILT_CUDA(cudaMemcpyAsync(col_out_, co.data(), ncap_ * 8, cudaMemcpyHostToDevice, st_));
+    IFILT_CUDA(cudaMemcpyAsync(col_in_, ci.data(), ncap_ * 8, cudaMemcpyHostToDevice, st_));
+    IFILT_CUDA(cudaStreamSynchronize(st_));
+  }
 
-    if (prof) {
+  // write outputs and stats of finished columns, free their lanes' sources
+  void retire(const HostCols& H, std::vector<ColumnDone>& done) {
+    const HostPrepared& h = m_->host;
+    const int nc = P_.ncols;
+    std::vector<int> emit(nc, 0);
+    bool any = false;
+    for (int c = 0; c < nc; c++) {
+      Slot& sl = cur_[c];
+      if (sl.src < 0 || sl.retired || !H.done[c]) continue;
+      emit[c] = 1;
+      any = true;
+    }
+    if (!any) return;
+    IFILT_CUDA(cudaMemcpyAsync(flags_, emit.data(), nc * 4, cudaMemcpyHostToDevice, st_));
+    dim3 og((unsigned)std::min<long long>((h.n_out + kBlock - 1) / kBlock, 1024), (unsigned)nc);
+    output_kernel<CPLX, BLK><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, col_out_, col_in_, flags_);
+    other_launches_++;
+    launch_check("output", (int)og.x, 0, P_.W);
+    IFILT_CUDA(cudaStreamSynchronize(st_));
+    for (int c = 0; c < nc; c++) {
+      if (!emit[c]) continue;
+      Slot& sl = cur_[c];
+      const int status = (H.status[c] != 0 || H.rel[c] > o_.tol) ? IFILT_NOT_CONVERGED : IFILT_OK;
+      if (sl.job.stat) {
+        sl.job.stat->iters = H.iters[c];
+        sl.job.stat->refinements = H.rounds[c];
+        sl.job.stat->status = status;
+        sl.job.stat->pad = 0;
+        sl.job.stat->rel_residual = H.rel[c];
+      }
+      done.push_back({sl.job.request, status});
+      sl.retired = true;
+      release_source(sl.src);
+    }
+  }
+
+ public:
+  void launch() override {
+    if (launched_) return;
+    if (live_columns() == 0) {
+      if (pend_.empty()) return;
+      relayout();
+      if (P_.W == 0) return;
+    }
+    if (use_graph_) IFILT_CUDA(cudaGraphLaunch(exec_, st_));
+    else enqueue_step(true);
+    steps_++;
+    launched_ = true;
+  }
+
+  void settle(std::vector<ColumnDone>& done) override {
+    if (!launched_) return;
+    IFILT_CUDA(cudaStreamSynchronize(st_));
+    launched_ = false;
+    const int live = h_cnt_[0], notdone = h_cnt_[2];
+    (void)live;
+    if (prof_) {
       float a = 0, b = 0, c = 0;
-      IFILT_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
-      IFILT_CUDA(cudaEventElapsedTime(&b, ev[2], ev[3]));
-      IFILT_CUDA(cudaEventElapsedTime(&c, ev[4], ev[5]));
-      {
-        const double vb = (double)n * NS * P.W * sizeof(T);
-        t_spmm += a;
-        t_upd += b;
-        t_dir += c;
-        b_spmm += 2.0 * vb + mbytes;
-        b_upd += 6.0 * vb;
-        b_dir += 3.0 * vb;
-        samples++;
+      IFILT_CUDA(cudaEventElapsedTime(&a, ev_[0], ev_[1]));
+      IFILT_CUDA(cudaEventElapsedTime(&b, ev_[2], ev_[3]));
+      IFILT_CUDA(cudaEventElapsedTime(&c, ev_[4], ev_[5]));
+      if (a > 0.01f) {  // the first iteration did work (kernels exit early when no column runs)
+        const double vb = (double)n_ * NS * P_.W * sizeof(T);
+        const double mb = (double)E_->entries * (4.0 + E_->nval * sizeof(MV)) + (double)n_ * 8.0;
+        t_[0] += a;
+        t_[1] += b;
+        t_[2] += c;
+        by_[0] += 2.0 * vb + mb;
+        by_[1] += 6.0 * vb;
+        by_[2] += 3.0 * vb;
+        samples_++;
       }
     }
-  }
-  // outputs and stats of the columns still in the tiles
-  {
-    const int nc = P.ncols;
-    cols_download(C, H, nc, st);
-    std::vector<int> sel(nc, 1);
-    for (int c = 0; c < nc; c++)
-      if (c < (int)curcols.size()) record(H, c);
-    emit(sel);
-  }
-  profile_count(other_launches + graph_launches * m_it * 5);
-  const int nsys = h.placement == IFILT_CELL ? 2 : 1;
-  for (int id = 0; id < nreal; id++) {
-    const ColumnSpec& cs = cols[id];
-    const ColResult& r = res[id];
-    const int status = (r.status != 0 || !r.done || r.rel > o.tol) ? IFILT_NOT_CONVERGED : IFILT_OK;
-    if (status != IFILT_OK) result = IFILT_NOT_CONVERGED;
-    if (stats) {
-      ifilt_col_stats& s = stats[((int64_t)cs.f * nk + cs.kj) * nsys + cs.sys];
-      s.iters = r.iters;
-      s.refinements = r.rounds;
-      s.status = status;
-      s.pad = 0;
-      s.rel_residual = r.rel;
+    const int lc = live_columns();
+    if (notdone < lc) {
+      HostCols H;
+      cols_download(C_, H, P_.ncols, st_);
+      retire(H, done);
     }
-  }
-  if (prof) {
-    const int64_t launches = graph_launches * m_it;
-    const char* k1 = CPLX ? "c" : "r";
-    const char* k2 = BLK ? "b" : "s";
-    const char* k3 = sizeof(T) == 8 ? "f64" : "f32";
-    char nm[32];
-    if (samples > 0) {
-      snprintf(nm, sizeof nm, "spmm_%s%s_%s", k1, k2, k3);
-      profile_add(nm, launches, samples, t_spmm, b_spmm / samples);
-      snprintf(nm, sizeof nm, "update_%s%s_%s", k1, k2, k3);
-      profile_add(nm, launches, samples, t_upd, b_upd / samples);
-      snprintf(nm, sizeof nm, "direction_%s%s_%s", k1, k2, k3);
-      profile_add(nm, launches, samples, t_dir, b_dir / samples);
+    const int run = live_columns();
+    bool want = false;
+    if (run < lc && run * 5 <= P_.ncols * 3) want = true;                      // narrow the tiles
+    if (!pend_.empty() && ncap_ - run >= std::max(1, ncap_ / 4)) want = true;  // room for queued columns
+    if (!pend_.empty() && run == 0) want = true;
+    if (run == 0 && pend_.empty()) {
+      release_tiles();
+      return;
     }
-    for (auto& e : ev) cudaEventDestroy(e);
+    if (want) relayout();
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  cudaFreeHost(h_flags);
-  scratch_free(tl.base, st);
-  scratch_free(base, st);
-  return result;
-}
 
-using BatchFn = ifilt_status (*)(ifilt_mesh_s*, const ifilt_solve_opts&, const std::vector<ColumnSpec>&, int,
-                                 const double*, const double*, const double*, int32_t, double*, ifilt_col_stats*,
-                                 cudaStream_t);
+  void report_profile() override {
+    profile_count(other_launches_ + steps_ * launches_per_step());
+    other_launches_ = 0;
+    if (prof_ && samples_ > 0) {
+      const int64_t launches = steps_ * m_it_;
+      const char* k1 = CPLX ? "c" : "r";
+      const char* k2 = BLK ? "b" : "s";
+      const char* k3 = sizeof(T) == 8 ? "f64" : "f32";
+      char nm[32];
+      snprintf(nm, sizeof nm, "spmm_%s%s_%s", k1, k2, k3);
+      profile_add(nm, launches, samples_, t_[0], by_[0] / samples_);
+      snprintf(nm, sizeof nm, "update_%s%s_%s", k1, k2, k3);
+      profile_add(nm, launches, samples_, t_[1], by_[1] / samples_);
+      snprintf(nm, sizeof nm, "direction_%s%s_%s", k1, k2, k3);
+      profile_add(nm, launches, samples_, t_[2], by_[2] / samples_);
+    }
+    steps_ = 0;
+    samples_ = 0;
+    t_[0] = t_[1] = t_[2] = by_[0] = by_[1] = by_[2] = 0;
+  }
+
+ private:
+  ifilt_mesh_s* m_;
+  ifilt_solve_opts o_;
+  cudaStream_t st_;
+  int64_t budget_;
+  const DevEll* E_ = nullptr;
+  EllView<MV> A_{};
+  EllView<double> A64_{};
+  int64_t n_ = 0;
+  int wcap_ = 0, ncap_ = 0, nb_max_ = 0, n_sms_ = kNumSMs, nb_ = 1;
+  size_t entry_bytes_ = 0;
+  Params P_{};
+  Cols C_{};
+  void* fixed_ = nullptr;
+  int64_t fixed_bytes_ = 0;
+  double* partial_ = nullptr;
+  int* lane_src_ = nullptr;
+  int* lane_map_ = nullptr;
+  int* flags_ = nullptr;
+  const double** bptr_ = nullptr;
+  const double** xptr_ = nullptr;
+  double** col_out_ = nullptr;
+  const double** col_in_ = nullptr;
+  int* h_cnt_ = nullptr;
+  Tiles<T> tl_{};
+  std::vector<Slot> cur_;
+  std::deque<ColumnJob> pend_;
+  std::vector<Source> src_;
+  cudaGraph_t graph_ = nullptr;
+  cudaGraphExec_t exec_ = nullptr;
+  int m_it_ = 32;
+  bool use_graph_ = true, launched_ = false, prof_ = false;
+  cudaEvent_t ev_[6] = {};
+  double t_[3] = {0, 0, 0}, by_[3] = {0, 0, 0};
+  int64_t samples_ = 0, steps_ = 0, other_launches_ = 0;
+};
 
 template <typename T, typename MV>
-BatchFn pick_kind(bool cplx, bool blk) {
-  if (cplx) return blk ? run_batch<T, MV, true, true> : run_batch<T, MV, true, false>;
-  return blk ? run_batch<T, MV, false, true> : run_batch<T, MV, false, false>;
-}
-
-BatchFn pick(int prec, bool cplx, bool blk) {
-  if (prec == IFILT_PREC_FP64) return pick_kind<double, double>(cplx, blk);
-  if (prec == IFILT_PREC_BF16_IR) return pick_kind<float, __nv_bfloat16>(cplx, blk);
-  return pick_kind<float, float>(cplx, blk);
+Engine* make_kind(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st, int64_t budget, bool cplx, bool blk) {
+  if (cplx) {
+    if (blk) return new EngineT<T, MV, true, true>(m, o, st, budget);
+    return new EngineT<T, MV, true, false>(m, o, st, budget);
+  }
+  if (blk) return new EngineT<T, MV, false, true>(m, o, st, budget);
+  return new EngineT<T, MV, false, false>(m, o, st, budget);
 }
 
 }  // namespace
+
+Engine* make_engine(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st, int64_t budget) {
+  const bool cplx = o.order >= 2 && o.n2_solver != IFILT_N2_REAL;
+  const bool blk = m->host.placement == IFILT_VERTEX_VECTOR;
+  if (o.precision == IFILT_PREC_FP64) return make_kind<double, double>(m, o, st, budget, cplx, blk);
+  if (o.precision == IFILT_PREC_BF16_IR) return make_kind<float, __nv_bfloat16>(m, o, st, budget, cplx, blk);
+  return make_kind<float, float>(m, o, st, budget, cplx, blk);
+}
 
 size_t batched_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, int32_t nk) {
   const HostPrepared& h = m->host;
   const bool cplx = o.order >= 2 && o.n2_solver != IFILT_N2_REAL;
   const int nsys = h.placement == IFILT_CELL ? 2 : 1;
   const int ns = h.placement == IFILT_VERTEX_VECTOR ? 2 : 1;
-  const int lanes = (int)std::min<long long>((long long)F * nsys * nk * (cplx ? 2 : 1),
-                                             o.max_lanes > 0 ? o.max_lanes : 256);
+  const int vec = o.precision == IFILT_PREC_FP64 ? 2 : 4;
+  const int cap = std::min(o.max_lanes > 0 ? o.max_lanes : 256, kBlock * vec) / 4 * 4;
+  const int lanes = (int)std::min<long long>((long long)F * nsys * nk * (cplx ? 2 : 1), cap);
   const int W = (lanes + 3) / 4 * 4;
   const size_t tb = o.precision == IFILT_PREC_FP64 ? 8 : 4;
   const size_t n = (size_t)h.n_rows;
-  size_t srcs = (size_t)F * nsys * n * ns * 8 * 2;
-  return 4 * n * ns * W * tb + n * ns * W * 8 + 2 * srcs + (size_t)152 * 16 * 2 * W * 8 + (1 << 20);
+  const size_t cols = (size_t)W / (cplx ? 2 : 1);
+  const size_t srcs = std::min<size_t>((size_t)F * nsys, cols) * n * ns * 16;
+  // tiles twice (old and new during a re-pack), sources, partial sums and tables
+  return 2 * n * ns * W * (4 * tb + 8) + srcs + (size_t)152 * 8 * 2 * W * 8 + (1 << 20);
 }
 
 ifilt_status solve_batched(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, const double* fields, int32_t nk,
                            const double* k, double* out, ifilt_col_stats* stats, cudaStream_t st) {
   const HostPrepared& h = m->host;
-  const bool cplx = o.order >= 2 && o.n2_solver != IFILT_N2_REAL;
-  const bool blk = h.placement == IFILT_VERTEX_VECTOR;
   const int nsys = h.placement == IFILT_CELL ? 2 : 1;
-  const int NS = blk ? 2 : 1;
-  const int64_t n = h.n_rows;
-  const int nsrc = F * nsys;
-
-  // right-hand sides and initial guesses of every (field, system), device order
-  double* srcbuf = (double*)scratch_alloc((size_t)2 * nsrc * n * NS * sizeof(double) + 512, st);
-  double* bsrc = srcbuf;
-  double* x0src = srcbuf + (size_t)nsrc * n * NS;
-  for (int f = 0; f < F; f++)
-    for (int s = 0; s < nsys; s++) {
-      const int id = f * nsys + s;
-      launch_rhs(m, fields + (int64_t)f * h.n_comp * h.n_in, s, bsrc + (size_t)id * n * NS,
-                 x0src + (size_t)id * n * NS, st);
-      profile_count(1);
-    }
-
-  std::vector<ColumnSpec> all;
+  // every (field, system, scale) column; the largest scales (slowest columns) are admitted first
+  std::vector<ColumnJob> jobs;
+  jobs.reserve((size_t)F * nsys * nk);
   for (int f = 0; f < F; f++)
     for (int s = 0; s < nsys; s++)
       for (int j = 0; j < nk; j++) {
-        const double ell = 1.0 / k[j];
-        double shift;
-        if (o.order == 1) shift = 0.5 * ell * ell;
-        else if (cplx) shift = ell * ell / std::sqrt(2.0);
-        else shift = 0.5 * ell * ell * ell * ell;
-        all.push_back({f, s, j, f * nsys + s, shift});
+        ColumnJob c;
+        c.field = fields + (int64_t)f * h.n_comp * h.n_in;
+        c.sys = s;
+        c.k = k[j];
+        c.out = out + ((int64_t)f * nk + j) * h.n_comp * h.n_out;
+        c.stat = stats ? &stats[((int64_t)f * nk + j) * nsys + s] : nullptr;
+        jobs.push_back(c);
       }
-  const int lanes_per_col = cplx ? 2 : 1;
-  int max_lanes = o.max_lanes > 0 ? o.max_lanes : 256;
-  const int vecw = o.precision == IFILT_PREC_FP64 ? 2 : 4;
-  max_lanes = std::min(max_lanes, kBlock * vecw);
-  const int per_batch = std::max(1, max_lanes / lanes_per_col);
-  BatchFn fn = pick(o.precision, cplx, blk);
-  ifilt_status result = IFILT_OK;
+  std::stable_sort(jobs.begin(), jobs.end(), [](const ColumnJob& a, const ColumnJob& b) { return a.k < b.k; });
   // CUDA graphs cannot be captured on the legacy default stream, so the
-  // iterations run on a private stream ordered after the caller's work.
+  // engine runs on a private stream ordered after the caller's work.
   cudaStream_t ws = nullptr;
   cudaEvent_t ev = nullptr;
   IFILT_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
   IFILT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   IFILT_CUDA(cudaEventRecord(ev, st));
   IFILT_CUDA(cudaStreamWaitEvent(ws, ev, 0));
+  ifilt_status result = IFILT_OK;
+  Engine* e = nullptr;
   try {
-    for (size_t b0 = 0; b0 < all.size(); b0 += per_batch) {
-      std::vector<ColumnSpec> part(all.begin() + b0, all.begin() + std::min(all.size(), b0 + per_batch));
-      ifilt_status s = fn(m, o, part, nsrc, bsrc, x0src, fields, nk, out, stats, ws);
-      if (s != IFILT_OK) result = s;
+    e = make_engine(m, o, ws, 0);
+    e->submit(jobs);
+    std::vector<ColumnDone> done;
+    while (!e->idle()) {
+      e->launch();
+      e->settle(done);
     }
+    for (auto& d : done)
+      if (d.status != IFILT_OK) result = IFILT_NOT_CONVERGED;
+    e->report_profile();
+    delete e;
+    e = nullptr;
   } catch (...) {
+    delete e;
     cudaStreamSynchronize(ws);
     cudaStreamDestroy(ws);
     cudaEventDestroy(ev);
@@ -1333,7 +1597,6 @@ ifilt_status solve_batched(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F
   IFILT_CUDA(cudaStreamWaitEvent(st, ev, 0));
   cudaStreamDestroy(ws);
   cudaEventDestroy(ev);
-  scratch_free(srcbuf, st);
   return result;
 }
 

@@ -131,6 +131,7 @@ std::vector<double> diagonal(const HostCSR& a) {
 void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
   const HostPrepared& h = m->host;
   if (slice_h <= 0) slice_h = 64;
+  if (slice_h < 4 || slice_h > 1024) fail(IFILT_EINVAL, "ell_slice must be between 4 and 1024 rows");
   m->perm = dev_copy(m, h.perm.data(), h.perm.size(), st);
   m->mass = dev_copy(m, h.mass.data(), h.mass.size(), st);
   std::vector<double> dk = diagonal(h.K);

@@ -128,6 +128,47 @@ void launch_rhs(ifilt_mesh_s* m, const double* field, int comp, double* b, doubl
 void launch_output_plain(ifilt_mesh_s* m, const double* x, const double* field, int comp,
                          double* out_sys, cudaStream_t st);
 
+// ---------------------------------------------------------------- engines
+// One column of work: a (field, system, wavenumber) solve.  `field` is the
+// caller's device field [n_comp][n_in]; `out` the caller's device block
+// [n_comp][n_out] of that (field, wavenumber); `stat` a host record or null.
+struct ColumnJob {
+  int64_t request = 0;
+  const double* field = nullptr;
+  int sys = 0;
+  double k = 0.0;
+  double* out = nullptr;
+  ifilt_col_stats* stat = nullptr;
+};
+
+struct ColumnDone {
+  int64_t request;
+  int status;  // IFILT_OK or IFILT_NOT_CONVERGED
+};
+
+// A persistent batched solver for one mesh and one (order, precision, n = 2
+// form): columns queue up, are admitted into free lanes of the tiles at step
+// boundaries, iterate together, and retire (outputs written) when done.
+// launch() enqueues one step on the engine's stream; settle() waits for it
+// and retires finished columns.  Not thread-safe: one owner drives it.
+class Engine {
+ public:
+  virtual ~Engine() = default;
+  virtual void submit(const std::vector<ColumnJob>& jobs) = 0;
+  virtual bool idle() const = 0;
+  virtual void launch() = 0;
+  virtual void settle(std::vector<ColumnDone>& done) = 0;
+  virtual int64_t bytes_held() const = 0;   // device memory held now
+  virtual int running() const = 0;          // columns in the tiles
+  virtual int pending() const = 0;          // columns waiting for lanes
+  virtual cudaStream_t stream() const = 0;
+  // kernels launched so far and sampled kernel timings (profiling)
+  virtual void report_profile() = 0;
+};
+
+// `budget` bounds the device memory the engine may take (0 = no bound).
+Engine* make_engine(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st, int64_t budget);
+
 // spectrum (spectrum.cu)
 // energy [F][nk], spec [F][nk-1], kmid [nk-1] written to device buffers;
 // `partial` holds F*nk*nb doubles.
