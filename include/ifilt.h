@@ -213,6 +213,27 @@ ifilt_status ifilt_spectrum(ifilt_mesh mesh, int32_t n_fields, int32_t n_k,
                             const double* k, const double* filtered,
                             double* energy, double* spec, double* kmid, void* stream);
 
+/* The spectrum of ifilt_spectrum for callers that cannot allocate device
+ * memory during a call: for instance a service that reserves all of HBM up
+ * front for resident meshes and request buffers, or a process held to a
+ * fixed device-memory budget, where taking scratch from an allocator would
+ * fail or stall.  This entry point calls no allocator (no cudaMalloc,
+ * cudaFree, memory pool or torch allocation).  Its scratch is one fixed array
+ * of 532 KB inside the library, resident on every device that loads the
+ * library until the process exits.  The paper has no counterpart; this is an
+ * operational variant of ifilt_spectrum with the same arguments, layout,
+ * results and synchronisation.
+ *   - n_fields * n_k must not exceed 512 (EINVAL otherwise).
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture on that device.
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and must be serialised by the caller.
+ *     Every scratch value a call reads is written earlier in the same call,
+ *     so nothing has to be cleared between calls. */
+ifilt_status ifilt_spectrum_noalloc(ifilt_mesh mesh, int32_t n_fields, int32_t n_k,
+                                    const double* k, const double* filtered,
+                                    double* energy, double* spec, double* kmid, void* stream);
+
 /* Device memory an ifilt_solve call with these options would take from the
  * stream-ordered allocator (upper bound), for admission control. */
 size_t ifilt_solve_scratch_bytes(ifilt_mesh mesh, const ifilt_solve_opts* opts,

@@ -68,7 +68,7 @@ COL_STATS_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("st
 
 # every symbol include/ifilt.h declares
 SYMBOLS = ["ifilt_prepare_mesh", "ifilt_prepare_mesh_host", "ifilt_mesh_upload", "ifilt_release_mesh", "ifilt_mesh_info", "ifilt_mesh_export", "ifilt_solve",
-           "ifilt_spectrum", "ifilt_solve_scratch_bytes", "ifilt_profile_enable", "ifilt_profile_read",
+           "ifilt_spectrum", "ifilt_spectrum_noalloc", "ifilt_solve_scratch_bytes", "ifilt_profile_enable", "ifilt_profile_read",
            "ifilt_profile_reset", "ifilt_last_error", "ifilt_version"]
 
 _lib = None
@@ -100,6 +100,8 @@ def load(path=None):
     lib.ifilt_solve.restype = i32
     lib.ifilt_spectrum.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.ifilt_spectrum.restype = i32
+    lib.ifilt_spectrum_noalloc.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.ifilt_spectrum_noalloc.restype = i32
     lib.ifilt_solve_scratch_bytes.argtypes = [vp, C.POINTER(SolveOpts), i32, i32]
     lib.ifilt_solve_scratch_bytes.restype = C.c_size_t
     lib.ifilt_profile_enable.argtypes = [i32]
@@ -248,6 +250,20 @@ def spectrum(mesh, filtered, k, stream=None):
     kmid = np.zeros(max(K - 1, 1))
     _check(lib.ifilt_spectrum(mesh.handle, F, K, _ptr(kk), _ptr(filtered), _ptr(energy), _ptr(spec),
                               _ptr(kmid), _stream_ptr(stream)))
+    return energy, spec[:, :K - 1], kmid[:K - 1]
+
+
+def spectrum_noalloc(mesh, filtered, k, stream=None):
+    """As `spectrum`, through the entry point that takes no device memory from
+    any allocator (its scratch is a fixed array inside the library)."""
+    lib = load()
+    kk = np.ascontiguousarray(k, dtype=np.float64).ravel()
+    F, K = filtered.shape[0], kk.size
+    energy = np.zeros((F, K))
+    spec = np.zeros((F, max(K - 1, 1)))
+    kmid = np.zeros(max(K - 1, 1))
+    _check(lib.ifilt_spectrum_noalloc(mesh.handle, F, K, _ptr(kk), _ptr(filtered), _ptr(energy), _ptr(spec),
+                                      _ptr(kmid), _stream_ptr(stream)))
     return energy, spec[:, :K - 1], kmid[:K - 1]
 
 

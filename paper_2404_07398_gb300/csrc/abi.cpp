@@ -335,6 +335,21 @@ ifilt_status ifilt_spectrum(ifilt_mesh m, int32_t n_fields, int32_t n_k, const d
   IFILT_GUARD_END
 }
 
+ifilt_status ifilt_spectrum_noalloc(ifilt_mesh m, int32_t n_fields, int32_t n_k, const double* k,
+                                    const double* filtered, double* energy, double* spec, double* kmid,
+                                    void* stream) {
+  IFILT_GUARD_BEGIN
+  check_uploaded(m);
+  if (n_fields <= 0 || n_k <= 0) fail(IFILT_EINVAL, "n_fields and n_k must be positive");
+  if (!k || !filtered || !energy) fail(IFILT_EINVAL, "null k, filtered or energy");
+  for (int32_t j = 0; j < n_k; j++)
+    if (!(k[j] > 0.0) || !std::isfinite(k[j]) || (j > 0 && !(k[j] > k[j - 1])))
+      fail(IFILT_EINVAL, "k must be positive, finite and strictly ascending");
+  DeviceScope ds(m->device);
+  return spectrum_noalloc(m, n_fields, n_k, k, filtered, energy, spec, kmid, (cudaStream_t)stream);
+  IFILT_GUARD_END
+}
+
 void ifilt_profile_enable(int32_t on) { g_prof.store(on != 0); }
 
 void ifilt_profile_reset(void) {

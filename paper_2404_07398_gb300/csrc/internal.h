@@ -175,6 +175,10 @@ Engine* make_engine(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st,
 void spectrum_device(ifilt_mesh_s* m, int32_t F, int32_t nk, const double* k_dev, const double* filtered,
                      double* energy, double* spec, double* kmid, double* partial, int nb, cudaStream_t st);
 
+// spectrum with its scratch in a fixed device array (noalloc.cu)
+ifilt_status spectrum_noalloc(ifilt_mesh_s* m, int32_t F, int32_t K, const double* k, const double* filtered,
+                              double* energy, double* spec, double* kmid, cudaStream_t st);
+
 // profiling (abi.cpp): per-kernel launch counts and CUDA-event samples
 bool profiling_on();
 void profile_add(const char* name, int64_t launches, int64_t samples, double sampled_ms,
