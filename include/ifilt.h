@@ -239,6 +239,65 @@ ifilt_status ifilt_spectrum_noalloc(ifilt_mesh mesh, int32_t n_fields, int32_t n
 size_t ifilt_solve_scratch_bytes(ifilt_mesh mesh, const ifilt_solve_opts* opts,
                                  int32_t n_fields, int32_t n_k);
 
+/* ------------------------------------------------------------------------
+ * Serving: a persistent request loop over resident prepared meshes.
+ *
+ * A worker thread keeps one batched solver per (mesh, order, precision,
+ * n = 2 form).  Requests are split into columns (field x system x scale) that
+ * join the solver's queue; at every step boundary (check_every iterations)
+ * finished columns retire and queued ones are admitted into the freed lanes
+ * while device memory stays within the budget (continuous batching).  The
+ * solvers run on separate streams, so the work of different meshes and
+ * orders overlaps on the device.  A column's result does not depend on which
+ * other columns share its batch beyond rounding (the batch width changes the
+ * grouping of partial sums), so a request gives the same result, within the
+ * solve tolerance, alone or in a mix.
+ * ------------------------------------------------------------------------ */
+typedef struct ifilt_server_s* ifilt_server;
+
+typedef struct {
+  int64_t memory_budget;     /* device bytes the solvers may hold; 0 = free memory at creation minus reserve */
+  int64_t reserve;           /* bytes kept free when memory_budget = 0; 0 = 2 GiB */
+  int32_t max_lanes;         /* lane capacity of each solver; 0 = 256 */
+  int32_t check_every;       /* iterations per step; 0 = 32 */
+} ifilt_server_opts;
+
+typedef struct {
+  int32_t state;             /* 0 queued, 1 running, 2 done, 3 failed */
+  int32_t status;            /* when done: IFILT_OK or IFILT_NOT_CONVERGED; when failed: the error */
+  int32_t columns, columns_done;
+  double t_submit, t_start, t_done;  /* seconds on the server's monotonic clock (t_start: handed to its solver) */
+} ifilt_request_info;
+
+/* Start a server on the current device.  Errors: EINVAL, ENOMEM, ECUDA. */
+ifilt_status ifilt_server_create(const ifilt_server_opts* opts, ifilt_server* out);
+
+/* Queue a request.  Arguments as ifilt_solve (method is ignored: requests are
+ * always batched).  `fields` (device) must hold its final values when the
+ * call is made; `fields`, `out` (device) and `stats` (host, may be NULL) must
+ * stay valid until the request is done.  `k` is copied.  *request receives an
+ * id for ifilt_server_wait.  The mesh must outlive the server's use of it.
+ * Errors: EINVAL (bad options, server failed or stopping). */
+ifilt_status ifilt_server_submit(ifilt_server server, ifilt_mesh mesh, const ifilt_solve_opts* opts,
+                                 int32_t n_fields, const double* fields, int32_t n_k, const double* k,
+                                 double* out, ifilt_col_stats* stats, int64_t* request);
+
+/* Wait up to timeout_ms (0 = just look) for a request to finish and fill
+ * *info.  Returns IFILT_OK with info->state telling where the request is;
+ * EINVAL for an unknown id.  Finished requests are forgotten by
+ * ifilt_server_forget. */
+ifilt_status ifilt_server_wait(ifilt_server server, int64_t request, int32_t timeout_ms, ifilt_request_info* info);
+
+/* Drop the record of a finished request. */
+ifilt_status ifilt_server_forget(ifilt_server server, int64_t request);
+
+/* Seconds on the server's clock (the clock of the request timestamps). */
+double ifilt_server_now(ifilt_server server);
+
+/* Stop the worker after the requests already queued have finished, free the
+ * solvers and the server.  NULL is ignored. */
+void ifilt_server_destroy(ifilt_server server);
+
 /* Per-kernel timing sampled with CUDA events on the launching stream while
  * profiling is on (off by default).  Each record: kernel name, launches,
  * sampled launches, summed sampled milliseconds, algorithmic bytes per launch

@@ -58,6 +58,16 @@ class MeshInfo(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("memory_budget", C.c_int64), ("reserve", C.c_int64), ("max_lanes", C.c_int32),
+                ("check_every", C.c_int32)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("columns", C.c_int32), ("columns_done", C.c_int32),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
 class KernelProfile(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("samples", C.c_int64),
                 ("sampled_ms", C.c_double), ("bytes_per_launch", C.c_double)]
@@ -69,7 +79,9 @@ COL_STATS_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("st
 # every symbol include/ifilt.h declares
 SYMBOLS = ["ifilt_prepare_mesh", "ifilt_prepare_mesh_host", "ifilt_mesh_upload", "ifilt_release_mesh", "ifilt_mesh_info", "ifilt_mesh_export", "ifilt_solve",
            "ifilt_spectrum", "ifilt_spectrum_noalloc", "ifilt_solve_scratch_bytes", "ifilt_profile_enable", "ifilt_profile_read",
-           "ifilt_profile_reset", "ifilt_last_error", "ifilt_version"]
+           "ifilt_profile_reset", "ifilt_last_error", "ifilt_version", "ifilt_server_create",
+           "ifilt_server_submit", "ifilt_server_wait", "ifilt_server_forget", "ifilt_server_now",
+           "ifilt_server_destroy"]
 
 _lib = None
 
@@ -114,6 +126,18 @@ def load(path=None):
     lib.ifilt_last_error.restype = C.c_char_p
     lib.ifilt_version.argtypes = []
     lib.ifilt_version.restype = C.c_char_p
+    lib.ifilt_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(vp)]
+    lib.ifilt_server_create.restype = i32
+    lib.ifilt_server_submit.argtypes = [vp, vp, C.POINTER(SolveOpts), i32, vp, i32, vp, vp, vp, C.POINTER(i64)]
+    lib.ifilt_server_submit.restype = i32
+    lib.ifilt_server_wait.argtypes = [vp, i64, i32, C.POINTER(RequestInfo)]
+    lib.ifilt_server_wait.restype = i32
+    lib.ifilt_server_forget.argtypes = [vp, i64]
+    lib.ifilt_server_forget.restype = i32
+    lib.ifilt_server_now.argtypes = [vp]
+    lib.ifilt_server_now.restype = dbl
+    lib.ifilt_server_destroy.argtypes = [vp]
+    lib.ifilt_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -291,3 +315,63 @@ def profile_read():
 
 def version():
     return load().ifilt_version().decode()
+
+
+class Server:
+    """A serving loop over resident prepared meshes (continuous batching).
+
+    submit() queues a request and returns its id; the caller keeps `fields`,
+    `out` and `stats` alive until wait() reports it done."""
+
+    def __init__(self, memory_budget=0, reserve=0, max_lanes=0, check_every=0):
+        o = ServerOpts(memory_budget=memory_budget, reserve=reserve, max_lanes=max_lanes, check_every=check_every)
+        h = C.c_void_p()
+        _check(load().ifilt_server_create(C.byref(o), C.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, mesh, fields, k, out=None, **opts):
+        import torch
+        info = mesh.info
+        assert fields.is_cuda and fields.dtype == torch.float64 and fields.is_contiguous()
+        F = fields.shape[0]
+        kk = np.ascontiguousarray(k, dtype=np.float64).ravel()
+        K = kk.size
+        if out is None:
+            out = torch.empty((F, K, info["n_comp"], info["n_out"]), dtype=torch.float64, device=fields.device)
+        nsys = 2 if info["placement"] == CELL else 1
+        stats = np.zeros(F * K * nsys, dtype=COL_STATS_DTYPE)
+        o = solve_opts(**opts)
+        rid = C.c_int64()
+        _check(load().ifilt_server_submit(self.handle, mesh.handle, C.byref(o), F, _ptr(fields), K, _ptr(kk),
+                                          _ptr(out), _ptr(stats), C.byref(rid)))
+        self._keep[rid.value] = (fields, out, stats, mesh)
+        return rid.value
+
+    def wait(self, rid, timeout_ms=0):
+        """Returns (state, info dict); state 2 = done, 3 = failed."""
+        i = RequestInfo()
+        _check(load().ifilt_server_wait(self.handle, rid, int(timeout_ms), C.byref(i)))
+        d = {f: getattr(i, f) for f, _ in RequestInfo._fields_}
+        return d["state"], d
+
+    def result(self, rid):
+        """(out, stats) of a finished request; forgets it."""
+        fields, out, stats, mesh = self._keep.pop(rid)
+        _check(load().ifilt_server_forget(self.handle, rid))
+        nsys = 2 if mesh.info["placement"] == CELL else 1
+        return out, stats.reshape(out.shape[0], out.shape[1], nsys)
+
+    def now(self):
+        return load().ifilt_server_now(self.handle)
+
+    def close(self):
+        if self.handle:
+            load().ifilt_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

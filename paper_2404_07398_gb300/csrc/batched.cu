@@ -1092,6 +1092,7 @@ class EngineT final : public Engine {
     return b;
   }
   int running() const override { return live_columns(); }
+  void set_budget(int64_t budget) override { budget_ = budget; }
   int pending() const override { return (int)pend_.size(); }
   cudaStream_t stream() const override { return st_; }
 

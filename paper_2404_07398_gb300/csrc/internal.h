@@ -159,6 +159,7 @@ class Engine {
   virtual void launch() = 0;
   virtual void settle(std::vector<ColumnDone>& done) = 0;
   virtual int64_t bytes_held() const = 0;   // device memory held now
+  virtual void set_budget(int64_t budget) = 0;
   virtual int running() const = 0;          // columns in the tiles
   virtual int pending() const = 0;          // columns waiting for lanes
   virtual cudaStream_t stream() const = 0;
