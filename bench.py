@@ -49,6 +49,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain-sample", type=int, default=2, help="columns timed on the plain FP64 path")
+    ap.add_argument("--serving", action="store_true", help="run the request-serving workload instead")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="arrival window of the serving run")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="mean Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-levels", default="6,8,9,10", help="icosahedral levels of the resident meshes")
+    ap.add_argument("--serve-out-gb", type=float, default=48.0, help="client cap on outstanding output memory")
     return ap.parse_args()
 
 
@@ -411,11 +416,109 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, world, rank):
+    """Poisson stream of filter requests over resident sphere meshes.
+
+    Each request: a uniformly chosen mesh, F in 1..16 fields from a seeded pool,
+    a contiguous run of K in 1..40 of the 40 wavenumbers, order n in {1, 2},
+    FP32 + FP64 refinement to 1e-6.  Arrivals for `serve_seconds`; the client
+    holds arrivals back while the outputs of in-flight requests exceed
+    `serve_out_gb` (latency counts from the arrival).  Requests still unfinished
+    after the window plus a drain limit are cancelled and reported."""
+    import torch
+    import synth
+    from paper_2404_07398_gb300 import api
+    api.load()
+    rng = np.random.default_rng(51)
+    levels = [int(x) for x in args.serve_levels.split(",")]
+    meshes, pools = [], []
+    t0 = time.time()
+    for i, lev in enumerate(levels):
+        m = synth.sphere_mesh(lev, 61 + 2 * i, 62 + 2 * i)
+        h = api.prepare_mesh(m, "vertex_scalar", max_order=2)
+        h8 = 7.5 * 2.0 ** (10 - lev)
+        fs = np.stack([synth.grf_sphere(m["coords"], seed=700 + 16 * i + j, n_features=128,
+                                        k_min=2 * np.pi / 20000.0, k_max=2 * np.pi / (2 * h8))
+                       for j in range(16)])[:, None, :]
+        meshes.append(h)
+        pools.append(torch.tensor(fs, device="cuda"))
+    setup_s = time.time() - t0
+    kgrid = synth.log_wavenumbers(4000.0, 10.0, N_K)
+    arrivals = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / args.serve_rate)
+        if t > args.serve_seconds:
+            break
+        mi = int(rng.integers(len(meshes)))
+        F = int(rng.integers(1, 17))
+        K = int(rng.integers(1, N_K + 1))
+        j0 = int(rng.integers(0, N_K - K + 1))
+        n = int(rng.integers(1, 3))
+        arrivals.append((t, mi, F, j0, K, n))
+    cap = args.serve_out_gb * 1e9
+    free, _ = torch.cuda.mem_get_info()
+    srv = api.Server(memory_budget=int(max(free - cap - 8e9, 4e9)))
+    pending = list(arrivals)
+    inflight = {}            # rid -> (arrival time, columns, out bytes)
+    lat, cols_done, done_n = [], 0, 0
+    start = time.perf_counter()
+    drain_limit = args.serve_seconds + 60.0
+
+    def out_bytes(mi, F, K):
+        return F * K * meshes[mi].info["n_out"] * 8
+
+    while (pending or inflight) and time.perf_counter() - start < drain_limit:
+        now = time.perf_counter() - start
+        held = sum(v[2] for v in inflight.values())
+        while pending and pending[0][0] <= now:
+            ta, mi, F, j0, K, n = pending[0]
+            ob = out_bytes(mi, F, K)
+            if inflight and held + ob > cap:
+                break
+            pending.pop(0)
+            rid = srv.submit(meshes[mi], pools[mi][:F], kgrid[j0:j0 + K], order=n, tol=1e-6,
+                             precision=api.PREC_FP32_IR)
+            inflight[rid] = (ta, F * K, ob)
+            held += ob
+        for rid in list(inflight):
+            state, info = srv.wait(rid, 0)
+            if state >= 2:
+                ta, nc, ob = inflight.pop(rid)
+                srv.result(rid)
+                if state == 2:
+                    lat.append(time.perf_counter() - start - ta)
+                    cols_done += nc
+                    done_n += 1
+        time.sleep(0.005)
+    elapsed = time.perf_counter() - start
+    unfinished = len(inflight) + len(pending)
+    srv.close()
+    line = {"metric": "serving: request latency and field-scales/s over resident meshes",
+            "mode": "serving", "n_gpus": world, "unit": "field-scales/s",
+            "value": round(cols_done / elapsed, 4), "higher_is_better": True,
+            "requests_offered": len(arrivals), "requests_done": done_n, "requests_unfinished": unfinished,
+            "offered_rate_per_s": round(len(arrivals) / args.serve_seconds, 3),
+            "achieved_rate_per_s": round(done_n / elapsed, 3),
+            "latency_s": {"p50": round(float(np.percentile(lat, 50)), 3) if lat else None,
+                          "p99": round(float(np.percentile(lat, 99)), 3) if lat else None,
+                          "max": round(float(np.max(lat)), 3) if lat else None},
+            "config": {"meshes": [m.info["n_rows"] for m in meshes], "levels": levels,
+                       "rate": args.serve_rate, "window_s": args.serve_seconds,
+                       "request": "F in 1..16, K in 1..40 contiguous of 40, n in {1,2}, FP32+FP64 IR to 1e-6",
+                       "client_output_cap_gb": args.serve_out_gb},
+            "elapsed_s": round(elapsed, 2), "setup_s": round(setup_s, 1)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.serving:
+        run_serving(args, world, rank)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -294,8 +294,10 @@ ifilt_status ifilt_server_forget(ifilt_server server, int64_t request);
 /* Seconds on the server's clock (the clock of the request timestamps). */
 double ifilt_server_now(ifilt_server server);
 
-/* Stop the worker after the requests already queued have finished, free the
- * solvers and the server.  NULL is ignored. */
+/* Stop the worker at its next step boundary, cancel every request that has
+ * not finished (state 3, status IFILT_EINVAL; its outputs are partial), free
+ * the solvers and the server.  Wait for requests first to drain.  NULL is
+ * ignored. */
 void ifilt_server_destroy(ifilt_server server);
 
 /* Per-kernel timing sampled with CUDA events on the launching stream while

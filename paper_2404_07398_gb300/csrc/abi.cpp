@@ -56,6 +56,13 @@ void* scratch_alloc(size_t bytes, cudaStream_t st) {
   cudaMemPool_t pool = pool_for_current_device();
   cudaError_t e = cudaMallocFromPoolAsync(&p, bytes < 256 ? 256 : bytes, pool, st);
   if (e != cudaSuccess) {
+    // give memory held by the pool but not in use back to the device, then retry once
+    cudaGetLastError();
+    cudaStreamSynchronize(st);
+    cudaMemPoolTrimTo(pool, 0);
+    e = cudaMallocFromPoolAsync(&p, bytes < 256 ? 256 : bytes, pool, st);
+  }
+  if (e != cudaSuccess) {
     cudaGetLastError();
     fail(IFILT_ENOMEM, "device scratch of %zu bytes not available: %s", bytes, cudaGetErrorString(e));
   }

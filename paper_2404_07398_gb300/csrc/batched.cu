@@ -1268,11 +1268,31 @@ class EngineT final : public Engine {
       pend_.pop_front();
       new_src += (int64_t)src_bytes();
     }
-    const int nreal = (int)(keep.size() + adm.size());
-    if (nreal == 0) {
-      release_tiles();
-      return;
+    // the tiles: when the device cannot hold them, admit fewer columns
+    Tiles<T> tn;
+    while (true) {
+      const int nr = (int)(keep.size() + adm.size());
+      if (nr == 0) {
+        release_tiles();
+        return;
+      }
+      try {
+        tn = alloc_tiles<T>(n_, NS, lanes_for(nr), st_);
+        break;
+      } catch (const Error& e) {
+        if (e.status != IFILT_ENOMEM) throw;
+        if (adm.empty()) {
+          if (tl_.base) return;  // cannot narrow now: keep the tiles, finished lanes stay idle
+          throw;
+        }
+        const size_t back = (adm.size() + 1) / 2;
+        for (size_t i = 0; i < back; i++) {
+          pend_.push_front(adm.back());
+          adm.pop_back();
+        }
+      }
     }
+    const int nreal = (int)(keep.size() + adm.size());
     const int Wn = lanes_for(nreal);
     const int ncn = Wn / LPC;
     HostCols Hn;
@@ -1294,7 +1314,6 @@ class EngineT final : public Engine {
       fresh[j] = 1;
     }
     for (int j = nreal; j < ncn; j++) Hn.done[j] = 1;
-    Tiles<T> tn = alloc_tiles<T>(n_, NS, Wn, st_);
     const int64_t rows = n_ * NS;
     if (tl_.base && !keep.empty()) {
       IFILT_CUDA(cudaMemcpyAsync(lane_map_, map.data(), Wn * 4, cudaMemcpyHostToDevice, st_));

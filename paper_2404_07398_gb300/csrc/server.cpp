@@ -156,9 +156,17 @@ struct ifilt_server_s {
               if (!kv.second.engine->idle()) return true;
             return false;
           };
-          while (incoming.empty() && !busy()) {
-            if (stopping) return;
-            cv_work.wait_for(lk, std::chrono::milliseconds(50));
+          while (incoming.empty() && !busy() && !stopping) cv_work.wait_for(lk, std::chrono::milliseconds(50));
+          if (stopping) {
+            // cancel whatever has not finished; the engines are freed by destroy
+            for (auto& kv : reqs)
+              if (kv.second.state < 2) {
+                kv.second.state = 3;
+                kv.second.status = IFILT_EINVAL;
+                kv.second.t_done = now();
+              }
+            cv_done.notify_all();
+            return;
           }
           ids.assign(incoming.begin(), incoming.end());
           incoming.clear();

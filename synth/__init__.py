@@ -23,4 +23,4 @@ from .fields import (  # noqa: F401
     grf_sphere,
     log_wavenumbers,
 )
-from .configs import workload  # noqa: F401
+from .configs import workload, sphere_mesh  # noqa: F401
