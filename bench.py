@@ -39,7 +39,7 @@ N_K = 40
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--level", type=int, default=10, help="icosahedral level (10 = the named workload)")
@@ -48,8 +48,11 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--plain-sample", type=int, default=2, help="columns timed on the plain FP64 path")
+    ap.add_argument("--plain-sample", type=int, default=3, help="scales (1-3) timed on the plain FP64 path")
     ap.add_argument("--serving", action="store_true", help="run the request-serving workload instead")
+    ap.add_argument("--concurrent", action="store_true",
+                    help="step the two placements' solvers together (one solve_many call); per-kernel "
+                         "event timings then overlap, so the roofline is not measured")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="arrival window of the serving run")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="mean Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-levels", default="6,8,9,10", help="icosahedral levels of the resident meshes")
@@ -148,6 +151,13 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def aggregate(units_per_rank, steps, ms_local, world):
+    """Whole-job throughput: every rank processes `units_per_rank` per step
+    (weak scaling, replicas); the job time is the slowest rank's."""
+    ms = max_over_ranks(ms_local, world)
+    return world * units_per_rank * steps / (ms / 1e3), ms
+
+
 def make_workload(level):
     import synth
     w = synth.workload("uv_batch", level=level)
@@ -185,32 +195,51 @@ class Ours:
         self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
         self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
         self.stats = None
+        self.sequential = not args.concurrent
 
     def step(self, fields=None):
+        """Both placements (in one call, their solvers stepping together, unless
+        sequential), then spectra."""
         f = self.fields if fields is None else fields
         api = self.api
-        _, sv, stv = api.solve(self.mv, f, self.k, out=self.out_v, **self.opts)
-        _, sc, stc = api.solve(self.mc, f, self.k, out=self.out_c, **self.opts)
+        if self.sequential:
+            res = [api.solve(self.mv, f, self.k, out=self.out_v, **self.opts)[:2],
+                   api.solve(self.mc, f, self.k, out=self.out_c, **self.opts)[:2]]
+            st = 0
+        else:
+            res, st = api.solve_many([(self.mv, f, self.k, self.out_v, self.opts),
+                                      (self.mc, f, self.k, self.out_c, self.opts)])
         ev = api.spectrum(self.mv, self.out_v, self.k)
         ec = api.spectrum(self.mc, self.out_c, self.k)
-        self.stats = (sv, sc, max(stv, stc))
+        self.stats = (res[0][1], res[1][1], st)
         return ev, ec
 
-    def plain_sample(self, ncols):
-        """Plain one-RHS FP64 CG (the paper's solver form, S assembled per scale)
-        on the cell placement at the `ncols` largest wavenumbers (the columns it
-        finishes fastest).  Returns (columns, seconds, per-column stats)."""
+    def plain_sample(self, idx):
+        """The paper's solver form -- one right-hand side at a time in FP64, S
+        assembled per scale as CSR, host convergence test every iteration -- and
+        the batched path on the same columns: cell placement, u and v, at the
+        wavenumbers `idx`.  Returns both throughputs and the plain iterations."""
         import torch
         api = self.api
-        ks = self.k[-ncols:]
+        ks = np.ascontiguousarray(self.k[idx])
         out = torch.empty((1, ks.size, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
-        t0 = time.time()
-        _, st, _ = api.solve(self.mc, self.fields, ks, out=out, order=2, tol=self.opts["tol"],
-                             precision=api.PREC_FP64, method=api.METHOD_PLAIN)
-        torch.cuda.synchronize()
-        dt = time.time() - t0
-        return 2 * ks.size, dt, st
+        res = {}
+        for name, kw in (("plain", dict(precision=api.PREC_FP64, method=api.METHOD_PLAIN)),
+                         ("batched", dict(precision=self.opts["precision"], n2_solver=api.N2_COMPLEX))):
+            torch.cuda.synchronize()
+            t0 = time.time()
+            _, st, _ = api.solve(self.mc, self.fields, ks, out=out, order=2, tol=self.opts["tol"], **kw)
+            torch.cuda.synchronize()
+            res[name] = (time.time() - t0, st.reshape(-1))
+        cols = 2 * ks.size
+        return {"columns": cols, "k_index": [int(i) for i in idx],
+                "plain_value": round(cols / res["plain"][0], 4), "batched_value": round(cols / res["batched"][0], 4),
+                "speedup": round(res["plain"][0] / res["batched"][0], 2),
+                "plain_iters": [int(x) for x in res["plain"][1]["iters"]],
+                "unit": UNIT,
+                "sample": "cell placement, u and v, at the listed wavenumber indices (of 40, ascending k): "
+                          "plain one-RHS FP64 CG (S = M + l^4/2 K M^-1 K assembled per scale, CSR SpMV, separate "
+                          "dot/axpy kernels, host test each iteration) vs the batched path, same columns"}
 
 
 def roofline(api, peak_gbs, peak_kind):
@@ -330,8 +359,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     ck = clocks.stop()
     api.profile_enable(False)
-    ms = max_over_ranks(e0.elapsed_time(e1), world)
-    value = world * units * args.steps / (ms / 1e3)
+    value, ms = aggregate(units, args.steps, e0.elapsed_time(e1), world)
     roof, recs = roofline(api, peak, pk)
     launches = total_launches(recs)
     stats = summarize_stats(o.stats)
@@ -358,13 +386,7 @@ def run_ours(args, world, rank, local):
 
     plain = None
     if args.plain_sample > 0 and rank == 0:
-        cols, dt, st = o.plain_sample(args.plain_sample)
-        st = st.reshape(-1)
-        plain = {"value": round(cols / dt, 4), "unit": UNIT, "columns": cols,
-                 "sample": f"plain one-RHS FP64 CG (S assembled per scale, CSR SpMV, host test each "
-                           f"iteration) on the cell placement, u and v at the {args.plain_sample} largest "
-                           f"wavenumbers (its fastest columns)",
-                 "iters": [int(x) for x in st["iters"]]}
+        plain = o.plain_sample([39, 30, 20][:args.plain_sample])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds)

@@ -200,6 +200,26 @@ ifilt_status ifilt_solve(ifilt_mesh mesh, const ifilt_solve_opts* opts,
                          const double* k, double* out, ifilt_col_stats* stats,
                          void* stream);
 
+/* One solve of a multi-item call: the arguments of ifilt_solve. */
+typedef struct {
+  ifilt_mesh mesh;
+  ifilt_solve_opts opts;
+  int32_t n_fields;
+  const double* fields;      /* device */
+  int32_t n_k;
+  const double* k;           /* host */
+  double* out;               /* device */
+  ifilt_col_stats* stats;    /* host or NULL */
+} ifilt_solve_item;
+
+/* Several solves at once (e.g. the vertex-vector and the cell placement of
+ * the same velocity field): every item gets its own batched solver on its
+ * own stream and the solvers step together, so one item's narrow final phase
+ * overlaps with the others' work.  Items use the batched method (their
+ * `method` is ignored).  Same results and errors as calling ifilt_solve for
+ * each item; returns the worst status.  Synchronises `stream`. */
+ifilt_status ifilt_solve_many(int32_t n_items, const ifilt_solve_item* items, void* stream);
+
 /* Coarse-grained energy spectrum of filtered fields (Sect. 1, 4, 5; the paper
  * gives no formula, the reading is):
  *   energy[f][j] = sum_i w_i 1/2 sum_c out[f][j][c][i]^2 / sum_i w_i over unknowns i

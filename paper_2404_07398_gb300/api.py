@@ -45,6 +45,11 @@ class SolveOpts(C.Structure):
                 ("check_every", C.c_int32), ("inner_tol", C.c_double), ("max_lanes", C.c_int32)]
 
 
+class SolveItem(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("opts", SolveOpts), ("n_fields", C.c_int32), ("fields", C.c_void_p),
+                ("n_k", C.c_int32), ("k", C.c_void_p), ("out", C.c_void_p), ("stats", C.c_void_p)]
+
+
 class ColStats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("status", C.c_int32), ("pad", C.c_int32),
                 ("rel_residual", C.c_double)]
@@ -78,7 +83,7 @@ COL_STATS_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("st
 
 # every symbol include/ifilt.h declares
 SYMBOLS = ["ifilt_prepare_mesh", "ifilt_prepare_mesh_host", "ifilt_mesh_upload", "ifilt_release_mesh", "ifilt_mesh_info", "ifilt_mesh_export", "ifilt_solve",
-           "ifilt_spectrum", "ifilt_spectrum_noalloc", "ifilt_solve_scratch_bytes", "ifilt_profile_enable", "ifilt_profile_read",
+           "ifilt_solve_many", "ifilt_spectrum", "ifilt_spectrum_noalloc", "ifilt_solve_scratch_bytes", "ifilt_profile_enable", "ifilt_profile_read",
            "ifilt_profile_reset", "ifilt_last_error", "ifilt_version", "ifilt_server_create",
            "ifilt_server_submit", "ifilt_server_wait", "ifilt_server_forget", "ifilt_server_now",
            "ifilt_server_destroy"]
@@ -110,6 +115,8 @@ def load(path=None):
     lib.ifilt_mesh_export.restype = i32
     lib.ifilt_solve.argtypes = [vp, C.POINTER(SolveOpts), i32, vp, i32, vp, vp, vp, vp]
     lib.ifilt_solve.restype = i32
+    lib.ifilt_solve_many.argtypes = [i32, C.POINTER(SolveItem), vp]
+    lib.ifilt_solve_many.restype = i32
     lib.ifilt_spectrum.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.ifilt_spectrum.restype = i32
     lib.ifilt_spectrum_noalloc.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
@@ -261,6 +268,38 @@ def solve(mesh, fields, k, out=None, stream=None, **opts):
                          _stream_ptr(stream))
     _check(st)
     return out, stats.reshape(F, K, nsys), st
+
+
+def solve_many(jobs, stream=None):
+    """Several solves at once; `jobs` is a list of (mesh, fields, k, out_or_None, opts-dict).
+    Returns [(out, stats)] in order and the worst status."""
+    import torch
+    items = (SolveItem * len(jobs))()
+    keep = []
+    results = []
+    for i, (mesh, fields, k, out, opts) in enumerate(jobs):
+        info = mesh.info
+        assert fields.is_cuda and fields.dtype == torch.float64 and fields.is_contiguous()
+        F = fields.shape[0]
+        assert tuple(fields.shape[1:]) == (info["n_comp"], info["n_in"])
+        kk = np.ascontiguousarray(k, dtype=np.float64).ravel()
+        if out is None:
+            out = torch.empty((F, kk.size, info["n_comp"], info["n_out"]), dtype=torch.float64, device=fields.device)
+        nsys = 2 if info["placement"] == CELL else 1
+        stats = np.zeros(F * kk.size * nsys, dtype=COL_STATS_DTYPE)
+        items[i].mesh = mesh.handle
+        items[i].opts = solve_opts(**opts)
+        items[i].n_fields = F
+        items[i].fields = fields.data_ptr()
+        items[i].n_k = kk.size
+        items[i].k = kk.ctypes.data
+        items[i].out = out.data_ptr()
+        items[i].stats = stats.ctypes.data
+        keep.append(kk)
+        results.append((out, stats.reshape(F, kk.size, nsys)))
+    st = load().ifilt_solve_many(len(jobs), items, _stream_ptr(stream))
+    _check(st)
+    return results, st
 
 
 def spectrum(mesh, filtered, k, stream=None):

@@ -303,6 +303,33 @@ ifilt_status ifilt_solve(ifilt_mesh m, const ifilt_solve_opts* o, int32_t n_fiel
   IFILT_GUARD_END
 }
 
+ifilt_status ifilt_solve_many(int32_t n_items, const ifilt_solve_item* items, void* stream) {
+  IFILT_GUARD_BEGIN
+  if (n_items <= 0 || !items) fail(IFILT_EINVAL, "need at least one item");
+  int dev = -1;
+  for (int32_t i = 0; i < n_items; i++) {
+    const ifilt_solve_item& it = items[i];
+    check_uploaded(it.mesh);
+    ifilt_solve_opts o = it.opts;
+    o.method = IFILT_METHOD_BATCHED;
+    check_opts(it.mesh, &o);
+    if (it.n_fields <= 0 || it.n_k <= 0) fail(IFILT_EINVAL, "item %d: n_fields and n_k must be positive", i);
+    if (!it.fields || !it.k || !it.out) fail(IFILT_EINVAL, "item %d: null fields, k or out", i);
+    for (int32_t j = 0; j < it.n_k; j++)
+      if (!(it.k[j] > 0.0) || !std::isfinite(it.k[j])) fail(IFILT_EINVAL, "item %d: k must be positive", i);
+    if (dev >= 0 && it.mesh->device != dev) fail(IFILT_EINVAL, "all items must live on one device");
+    dev = it.mesh->device;
+  }
+  DeviceScope ds(dev);
+  cudaStream_t st = (cudaStream_t)stream;
+  ifilt_status s = solve_many(n_items, items, st);
+  IFILT_CUDA(cudaStreamSynchronize(st));
+  IFILT_CUDA(cudaGetLastError());
+  if (s == IFILT_NOT_CONVERGED) set_last_error("some columns did not reach the tolerance");
+  return s;
+  IFILT_GUARD_END
+}
+
 size_t ifilt_solve_scratch_bytes(ifilt_mesh m, const ifilt_solve_opts* o, int32_t n_fields, int32_t n_k) {
   if (!m || !o || n_fields <= 0 || n_k <= 0) return 0;
   if (o->method == IFILT_METHOD_PLAIN && m->device < 0) return 0;

@@ -73,6 +73,11 @@ __device__ __forceinline__ void stp(T* p, const Pack<T>& v) {
   *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(&v);
 }
 
+// Fused multiply-add in the precision of T.  (A bare fma() on floats can bind
+// to the double overload and run on the FP64 pipe.)
+__device__ __forceinline__ float madd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double madd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Per-thread dot-product accumulator.  For FP32 vectors the FP64 unit of
 // GB300 is far too slow to take one operation per element, so partial sums
 // are carried as an unevaluated pair (s, c) on the FP32 pipes: each product
@@ -85,7 +90,7 @@ __device__ __forceinline__ void stp(T* p, const Pack<T>& v) {
 template <typename T>
 struct DotAcc {
   double d = 0.0;
-  __device__ __forceinline__ void add(T a, T b) { d = fma((double)a, (double)b, d); }
+  __device__ __forceinline__ void add(T a, T b) { d = __fma_rn((double)a, (double)b, d); }
   __device__ __forceinline__ void add_sum(T x) { d += (double)x; }
   __device__ __forceinline__ void flush() {}
   __device__ __forceinline__ double get() const { return d; }
@@ -117,7 +122,7 @@ struct DotAcc<float> {
   }
   __device__ __forceinline__ double get() const { return d + ((double)s + (double)c); }
 };
-constexpr int kFlushRows = 16;  // rows per compensated chain (lanes x 2 terms each)
+constexpr int kFlushRows = 64;  // rows per compensated chain
 
 // 4 consecutive ELL entries' values (NV per entry) converted to AT.
 template <typename MV, int NV, typename AT>
@@ -188,12 +193,12 @@ __device__ __forceinline__ T cvt(MV v) {
 // <p, q>: the row's few terms are summed in FP32, then added to the
 // compensated per-thread accumulator.
 template <typename T, bool CPLX, bool BLK>
-__device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, int l0, const double* __restrict__ mass,
+__device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, int l0, const T* __restrict__ mass,
                                               const T* sh, T (*acc)[Pack<T>::N], const T* __restrict__ p,
                                               T* __restrict__ q, DotAcc<T>* dacc) {
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
-  const T mr = (T)mass[r];
+  const T mr = mass[r];
   T rowdot[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; v++) rowdot[v] = (T)0;
@@ -210,8 +215,8 @@ __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, in
         const T qim = mr * pim + sh[v] * acc[b][v];
         qo.v[v] = qre;
         qo.v[v + 1] = qim;
-        rowdot[v] = fma(pre, qre, fma(-pim, qim, rowdot[v]));
-        rowdot[v + 1] = fma(pre, qim, fma(pim, qre, rowdot[v + 1]));
+        rowdot[v] = madd(pre, qre, madd(-pim, qim, rowdot[v]));
+        rowdot[v + 1] = madd(pre, qim, madd(pim, qre, rowdot[v + 1]));
       }
     } else {
 #pragma unroll
@@ -219,7 +224,7 @@ __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, in
         const T qv = mr * pr.v[v] + sh[v] * acc[b][v];
         qo.v[v] = qv;
         if constexpr (NS == 1) dacc[v].add(pr.v[v], qv);  // a single exact product
-        else rowdot[v] = fma(pr.v[v], qv, rowdot[v]);
+        else rowdot[v] = madd(pr.v[v], qv, rowdot[v]);
       }
     }
     stp(q + off, qo);
@@ -240,7 +245,7 @@ constexpr int kStageBytes = 48 * 1024;
 // neighbour rows of p) instead of three (slice descriptor, indices, values).
 template <typename T, typename MV, bool CPLX, bool BLK>
 __global__ void __launch_bounds__(kBlock, 4) spmm_kernel(EllView<MV> A, Params P, int n_slices, const T* __restrict__ p,
-                                                      T* __restrict__ q, const double* __restrict__ mass,
+                                                      T* __restrict__ q, const T* __restrict__ mass,
                                                       Cols C, double* __restrict__ partial) {
   if (*C.live == 0) return;
   constexpr int VEC = Pack<T>::N;
@@ -313,13 +318,13 @@ __global__ void __launch_bounds__(kBlock, 4) spmm_kernel(EllView<MV> A, Params P
               const T a = cvt<T>(vv[2 * t]), bb = cvt<T>(vv[2 * t + 1]);
 #pragma unroll
               for (int v = 0; v < VEC; v++) {
-                acc[0][v] = fma(a, pu.v[v], fma(bb, pv.v[v], acc[0][v]));
-                acc[1][v] = fma(a, pv.v[v], fma(-bb, pu.v[v], acc[1][v]));
+                acc[0][v] = madd(a, pu.v[v], madd(bb, pv.v[v], acc[0][v]));
+                acc[1][v] = madd(a, pv.v[v], madd(-bb, pu.v[v], acc[1][v]));
               }
             } else {
               const T a = cvt<T>(vv[t]);
 #pragma unroll
-              for (int v = 0; v < VEC; v++) acc[0][v] = fma(a, pu.v[v], acc[0][v]);
+              for (int v = 0; v < VEC; v++) acc[0][v] = madd(a, pu.v[v], acc[0][v]);
             }
           }
         }
@@ -393,15 +398,15 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(Params P, T* __restri
             rv.v[v] -= are * qv.v[v] - aim * qv.v[v + 1];
             rv.v[v + 1] -= are * qv.v[v + 1] + aim * qv.v[v];
             const T rre = rv.v[v], rim = rv.v[v + 1];
-            d1[v].add_sum(fma(rre, rre, -rim * rim));
+            d1[v].add_sum(madd(rre, rre, -rim * rim));
             d1[v + 1].add((T)2 * rre, rim);
-            d2[v / 2].add_sum(fma(rre, rre, rim * rim));
+            d2[v / 2].add_sum(madd(rre, rre, rim * rim));
           }
         } else {
 #pragma unroll
           for (int v = 0; v < VEC; v++) {
-            xv.v[v] = fma(a[v], pv.v[v], xv.v[v]);
-            rv.v[v] = fma(-a[v], qv.v[v], rv.v[v]);
+            xv.v[v] = madd(a[v], pv.v[v], xv.v[v]);
+            rv.v[v] = madd(-a[v], qv.v[v], rv.v[v]);
             d1[v].add(rv.v[v], rv.v[v]);
           }
         }
@@ -459,7 +464,7 @@ __global__ void __launch_bounds__(kBlock) direction_kernel(Params P, T* __restri
         }
       } else {
 #pragma unroll
-        for (int v = 0; v < VEC; v++) pv.v[v] = fma(bt[v], pv.v[v], rv.v[v]);
+        for (int v = 0; v < VEC; v++) pv.v[v] = madd(bt[v], pv.v[v], rv.v[v]);
       }
       stp(p + off, pv);
     }
@@ -1122,6 +1127,10 @@ class EngineT final : public Engine {
                                       ntiles * kBlock));
   }
   size_t src_bytes() const { return (size_t)2 * n_ * NS * sizeof(double); }
+  const T* mass_t() const {
+    if constexpr (sizeof(T) == 4) return m_->mass32;
+    else return m_->mass;
+  }
   int64_t tile_bytes(int W) const { return (int64_t)n_ * NS * W * (4 * sizeof(T) + sizeof(double)); }
   double shift_of(double k) const {
     const double ell = 1.0 / k;
@@ -1192,7 +1201,7 @@ class EngineT final : public Engine {
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
     for (int it = 0; it < m_it_; it++) {
       if (it == 0) rec(0);
-      spmm_kernel<T, MV, CPLX, BLK><<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, m_->mass, C_,
+      spmm_kernel<T, MV, CPLX, BLK><<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), C_,
                                                                 partial_);
       chk("spmm");
       if (it == 0) rec(1);
@@ -1441,7 +1450,7 @@ class EngineT final : public Engine {
       IFILT_CUDA(cudaEventElapsedTime(&c, ev_[4], ev_[5]));
       if (a > 0.01f) {  // the first iteration did work (kernels exit early when no column runs)
         const double vb = (double)n_ * NS * P_.W * sizeof(T);
-        const double mb = (double)E_->entries * (4.0 + E_->nval * sizeof(MV)) + (double)n_ * 8.0;
+        const double mb = (double)E_->entries * (4.0 + E_->nval * sizeof(MV)) + (double)n_ * sizeof(T);
         t_[0] += a;
         t_[1] += b;
         t_[2] += c;
@@ -1564,60 +1573,98 @@ size_t batched_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o, i
   return 2 * n * ns * W * (4 * tb + 8) + srcs + (size_t)152 * 8 * 2 * W * 8 + (1 << 20);
 }
 
-ifilt_status solve_batched(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, const double* fields, int32_t nk,
-                           const double* k, double* out, ifilt_col_stats* stats, cudaStream_t st) {
-  const HostPrepared& h = m->host;
+namespace {
+std::vector<ColumnJob> jobs_of(const ifilt_solve_item& it) {
+  const HostPrepared& h = it.mesh->host;
   const int nsys = h.placement == IFILT_CELL ? 2 : 1;
-  // every (field, system, scale) column; the largest scales (slowest columns) are admitted first
   std::vector<ColumnJob> jobs;
-  jobs.reserve((size_t)F * nsys * nk);
-  for (int f = 0; f < F; f++)
+  jobs.reserve((size_t)it.n_fields * nsys * it.n_k);
+  for (int f = 0; f < it.n_fields; f++)
     for (int s = 0; s < nsys; s++)
-      for (int j = 0; j < nk; j++) {
+      for (int j = 0; j < it.n_k; j++) {
         ColumnJob c;
-        c.field = fields + (int64_t)f * h.n_comp * h.n_in;
+        c.field = it.fields + (int64_t)f * h.n_comp * h.n_in;
         c.sys = s;
-        c.k = k[j];
-        c.out = out + ((int64_t)f * nk + j) * h.n_comp * h.n_out;
-        c.stat = stats ? &stats[((int64_t)f * nk + j) * nsys + s] : nullptr;
+        c.k = it.k[j];
+        c.out = it.out + ((int64_t)f * it.n_k + j) * h.n_comp * h.n_out;
+        c.stat = it.stats ? &it.stats[((int64_t)f * it.n_k + j) * nsys + s] : nullptr;
         jobs.push_back(c);
       }
+  // the largest scales (slowest columns) are admitted first
   std::stable_sort(jobs.begin(), jobs.end(), [](const ColumnJob& a, const ColumnJob& b) { return a.k < b.k; });
-  // CUDA graphs cannot be captured on the legacy default stream, so the
-  // engine runs on a private stream ordered after the caller's work.
-  cudaStream_t ws = nullptr;
+  return jobs;
+}
+}  // namespace
+
+ifilt_status solve_many(int32_t n, const ifilt_solve_item* items, cudaStream_t st) {
+  std::vector<cudaStream_t> ws(n, nullptr);
+  std::vector<Engine*> eng(n, nullptr);
   cudaEvent_t ev = nullptr;
-  IFILT_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
-  IFILT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  IFILT_CUDA(cudaEventRecord(ev, st));
-  IFILT_CUDA(cudaStreamWaitEvent(ws, ev, 0));
   ifilt_status result = IFILT_OK;
-  Engine* e = nullptr;
+  auto cleanup = [&]() {
+    for (int i = 0; i < n; i++) {
+      delete eng[i];
+      eng[i] = nullptr;
+      if (ws[i]) {
+        cudaStreamSynchronize(ws[i]);
+        cudaStreamDestroy(ws[i]);
+        ws[i] = nullptr;
+      }
+    }
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+  };
   try {
-    e = make_engine(m, o, ws, 0);
-    e->submit(jobs);
+    // CUDA graphs cannot be captured on the legacy default stream, so every
+    // engine runs on a private stream ordered after the caller's work.
+    IFILT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    IFILT_CUDA(cudaEventRecord(ev, st));
+    for (int i = 0; i < n; i++) {
+      IFILT_CUDA(cudaStreamCreateWithFlags(&ws[i], cudaStreamNonBlocking));
+      IFILT_CUDA(cudaStreamWaitEvent(ws[i], ev, 0));
+      ifilt_solve_opts o = items[i].opts;
+      o.method = IFILT_METHOD_BATCHED;
+      eng[i] = make_engine(items[i].mesh, o, ws[i], 0);
+      eng[i]->submit(jobs_of(items[i]));
+    }
     std::vector<ColumnDone> done;
-    while (!e->idle()) {
-      e->launch();
-      e->settle(done);
+    while (true) {
+      bool any = false;
+      for (int i = 0; i < n; i++)
+        if (!eng[i]->idle()) {
+          eng[i]->launch();
+          any = true;
+        }
+      if (!any) break;
+      for (int i = 0; i < n; i++) eng[i]->settle(done);
     }
     for (auto& d : done)
       if (d.status != IFILT_OK) result = IFILT_NOT_CONVERGED;
-    e->report_profile();
-    delete e;
-    e = nullptr;
+    for (int i = 0; i < n; i++) {
+      eng[i]->report_profile();
+      IFILT_CUDA(cudaEventRecord(ev, ws[i]));
+      IFILT_CUDA(cudaStreamWaitEvent(st, ev, 0));
+    }
   } catch (...) {
-    delete e;
-    cudaStreamSynchronize(ws);
-    cudaStreamDestroy(ws);
-    cudaEventDestroy(ev);
+    cleanup();
     throw;
   }
-  IFILT_CUDA(cudaEventRecord(ev, ws));
-  IFILT_CUDA(cudaStreamWaitEvent(st, ev, 0));
-  cudaStreamDestroy(ws);
-  cudaEventDestroy(ev);
+  cleanup();
   return result;
+}
+
+ifilt_status solve_batched(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, const double* fields, int32_t nk,
+                           const double* k, double* out, ifilt_col_stats* stats, cudaStream_t st) {
+  ifilt_solve_item it{};
+  it.mesh = m;
+  it.opts = o;
+  it.n_fields = F;
+  it.fields = fields;
+  it.n_k = nk;
+  it.k = k;
+  it.out = out;
+  it.stats = stats;
+  return solve_many(1, &it, st);
 }
 
 }  // namespace ifilt

@@ -134,6 +134,8 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
   if (slice_h < 4 || slice_h > 1024) fail(IFILT_EINVAL, "ell_slice must be between 4 and 1024 rows");
   m->perm = dev_copy(m, h.perm.data(), h.perm.size(), st);
   m->mass = dev_copy(m, h.mass.data(), h.mass.size(), st);
+  std::vector<float> m32(h.mass.begin(), h.mass.end());
+  m->mass32 = dev_copy(m, m32.data(), m32.size(), st);
   std::vector<double> dk = diagonal(h.K);
   m->diag_k = dev_copy(m, dk.data(), dk.size(), st);
   build_ell(m, h.K, slice_h, m->ell_k, st);

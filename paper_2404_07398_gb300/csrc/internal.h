@@ -90,6 +90,7 @@ struct ifilt_mesh_s {
   // device arrays
   int32_t* perm = nullptr;       // [n_rows]
   double* mass = nullptr;        // [n_rows]
+  float* mass32 = nullptr;       // [n_rows] the same in FP32 (FP32 kernels)
   double* diag_k = nullptr;      // [n_rows] diagonal of K (K~ for vectors)
   double* diag_g2 = nullptr;     // [n_rows]
   int64_t* proj_ptr = nullptr;
@@ -114,6 +115,7 @@ ifilt_status solve_plain(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, 
 ifilt_status solve_batched(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F,
                            const double* fields, int32_t nk, const double* k, double* out,
                            ifilt_col_stats* stats, cudaStream_t st);
+ifilt_status solve_many(int32_t n, const ifilt_solve_item* items, cudaStream_t st);
 size_t batched_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, int32_t nk);
 size_t plain_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o);
 

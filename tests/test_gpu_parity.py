@@ -231,3 +231,23 @@ def test_profiling_samples_in_graph_mode(lib):
     assert spmm and spmm[0]["samples"] > 0 and spmm[0]["sampled_ms"] > 0
     assert spmm[0]["bytes_per_launch"] > 0
     assert recs["(all kernels)"]["launches"] >= spmm[0]["launches"] * 5
+
+
+def test_solve_many_matches_separate_solves(lib):
+    """Two placements of one velocity field in one ifilt_solve_many call."""
+    import torch
+    m = _sphere(3, 67, polar=10.0)
+    hv = lib.prepare_mesh(m, "vertex_vector", max_order=2)
+    hc = lib.prepare_mesh(m, "cell", max_order=2)
+    rng = np.random.default_rng(10)
+    f = torch.tensor(rng.normal(size=(1, 2, hv.info["n_in"])), device="cuda")
+    ks = synth.log_wavenumbers(6000.0, 600.0, 5)
+    opts = dict(order=2, tol=1e-10, precision=lib.PREC_FP32_IR)
+    res, st = lib.solve_many([(hv, f, ks, None, opts), (hc, f, ks, None, opts)])
+    assert st == 0
+    for h, placement, (out, stats) in ((hv, "vertex_vector", res[0]), (hc, "cell", res[1])):
+        _, ref = _oracle(m, placement, f.cpu().numpy(), ks, 2)
+        _check(out.cpu().numpy(), ref, TOL_MIXED)
+        assert np.all(stats["status"] == 0)
+    hv.release()
+    hc.release()
