@@ -34,6 +34,12 @@ sys.path.insert(0, ROOT)
 METRIC = "solved field-scales/sec at 10.5M vertices, batched vs plain CG; p50/p99 latency"
 UNIT = "field-scales/s"
 N_K = 40
+# DRAM bytes per algorithmic byte of a kernel, from an ncu capture of the same
+# kernel on the level-8 sphere (dram__bytes_read.sum + dram__bytes_write.sum of
+# one launch over the bytes the profiler is told that launch moves); the
+# roofline's `traffic` is this ratio times the bytes of an average timed launch.
+# A kernel that changed since its capture has no entry.
+TRAFFIC_RATIO = {}
 
 
 def parse_args():
@@ -256,15 +262,20 @@ def roofline(api, peak_gbs, peak_kind):
         return None, recs
     _, r, avg_ms = best
     achieved = r["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
-    shares = {}
+    shares, kernels = {}, {}
     tot = sum(x["sampled_ms"] / x["samples"] * x["launches"] for x in recs if x["samples"])
     for x in recs:
         if x["samples"]:
-            shares[x["name"]] = round(x["sampled_ms"] / x["samples"] * x["launches"] / tot, 4)
+            a = x["sampled_ms"] / x["samples"]
+            shares[x["name"]] = round(a * x["launches"] / tot, 4)
+            kernels[x["name"]] = {"avg_launch_ms": round(a, 4), "launches": int(x["launches"]),
+                                  "gbs": round(x["bytes_per_launch"] / (a * 1e-3) / 1e9, 1)}
+    ratio = TRAFFIC_RATIO.get(r["name"])
     return {"bound": "hbm", "kernel": r["name"], "achieved": round(achieved, 1), "peak": peak_gbs,
             "peak_kind": f"{peak_kind} (copy)", "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
-            "traffic": None, "bytes_per_launch": r["bytes_per_launch"], "avg_launch_ms": round(avg_ms, 4),
-            "launches": r["launches"], "time_share_of_sampled": shares}, recs
+            "traffic": None if ratio is None else round(ratio * r["bytes_per_launch"]),
+            "bytes_per_launch": r["bytes_per_launch"], "avg_launch_ms": round(avg_ms, 4),
+            "launches": r["launches"], "time_share_of_sampled": shares, "kernels": kernels}, recs
 
 
 def total_launches(recs):

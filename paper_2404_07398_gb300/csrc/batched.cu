@@ -93,6 +93,10 @@ struct DotAcc {
   __device__ __forceinline__ void add(T a, T b) { d = __fma_rn((double)a, (double)b, d); }
   __device__ __forceinline__ void add_sum(T x) { d += (double)x; }
   __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ void spill(double& slot) {
+    slot += d;
+    d = 0.0;
+  }
   __device__ __forceinline__ double get() const { return d; }
 };
 template <>
@@ -117,6 +121,12 @@ struct DotAcc<float> {
   }
   __device__ __forceinline__ void flush() {
     d += (double)s + (double)c;
+    s = 0.f;
+    c = 0.f;
+  }
+  // flush into an FP64 slot kept elsewhere (shared memory), freeing d's registers
+  __device__ __forceinline__ void spill(double& slot) {
+    slot += (double)s + (double)c;
     s = 0.f;
     c = 0.f;
   }
@@ -166,7 +176,7 @@ struct Cols {
   int* refresh;     // column waits for its FP64 true residual / next refinement round
   int* round_it0;   // iteration count when the current inner round started
   int* round_cap;   // iterations allowed in the current inner round
-  int* live;        // [3] number of active columns, columns to refresh, columns not done
+  int* live;        // [4] number of active columns, columns to refresh, columns not done; device error flag
 };
 
 struct Params {
@@ -179,6 +189,7 @@ struct Params {
   double inner2;    // inner_tol^2 (0: run to the outer tolerance)
   int spt;          // ELL slices per SpMM tile
   int wmax;         // widest ELL slice
+  int stage_e;      // ELL entries one SpMM stage buffer holds
 };
 
 // ------------------------------------------------------------------ kernels
@@ -194,7 +205,7 @@ __device__ __forceinline__ T cvt(MV v) {
 // compensated per-thread accumulator.
 template <typename T, bool CPLX, bool BLK>
 __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, int l0, const T* __restrict__ mass,
-                                              const T* sh, T (*acc)[Pack<T>::N], const T* __restrict__ p,
+                                              const T* sh, T (*acc)[Pack<T>::N], const Pack<T>* own,
                                               T* __restrict__ q, DotAcc<T>* dacc) {
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
@@ -205,7 +216,7 @@ __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, in
 #pragma unroll
   for (int b = 0; b < NS; b++) {
     const int64_t off = r * rowW + (int64_t)b * W + l0;
-    const Pack<T> pr = ldp(p + off);
+    const Pack<T>& pr = own[b];
     Pack<T> qo;
     if constexpr (CPLX) {
 #pragma unroll
@@ -235,24 +246,73 @@ __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, in
   }
 }
 
-constexpr int kMaxSpt = 64;       // sliced-ELL slices staged per tile
-constexpr int kStageBytes = 48 * 1024;
+#ifndef IFILT_SPMM_MINB_BLK
+#define IFILT_SPMM_MINB_BLK 3  // resident blocks per SM asked of the compiler for 2x2-block FP32 SpMM
+#endif
+#ifndef IFILT_SPMM_MINB
+#define IFILT_SPMM_MINB 3      // resident blocks per SM asked of the compiler for the other SpMM instances
+#endif
+#ifndef IFILT_SPMM_EB_BLK
+#define IFILT_SPMM_EB_BLK 4    // gathered entries in flight per row for 2x2-block FP32 SpMM
+#endif
+constexpr int kMaxSpt = 64;            // sliced-ELL slices staged per tile
+constexpr int kStageBytes = 24 * 1024;  // one of the two stage buffers, when it holds several slices
+constexpr int kStageMax = 96 * 1024;    // one of the two stage buffers holding a single slice
+constexpr int kTilePasses = 8;          // rows per tile ~ this many passes of the block's row groups
+
+// Bulk (TMA engine) copies of a tile's ELL entries into shared memory,
+// completed on an mbarrier.  Both addresses and the size are multiples of 16
+// bytes: slices start on 8-entry boundaries and hold a multiple of 4 entries
+// per row, and the buffers are 16-byte aligned.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of `bar` for at most ~1 s of SM clock; false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > 2000000000LL) return false;
+  return true;
+}
 
 // q = M p + shift * (G p) for every lane, with the per-block partials of <p, q>.
-// Work is cut into tiles of `spt` ELL slices: the tile's column indices and
-// values are first copied cooperatively (coalesced 16-byte loads) into shared
-// memory, so a row then waits on one dependent global access (the gathered
-// neighbour rows of p) instead of three (slice descriptor, indices, values).
-template <typename T, typename MV, bool CPLX, bool BLK>
-__global__ void __launch_bounds__(kBlock, 4) spmm_kernel(EllView<MV> A, Params P, int n_slices, const T* __restrict__ p,
-                                                      T* __restrict__ q, const T* __restrict__ mass,
-                                                      Cols C, double* __restrict__ partial) {
+// Work is cut into tiles of `spt` ELL slices.  A tile's column indices and
+// values are bulk-copied into one of two shared-memory buffers while the block
+// works on the previous tile, so a row waits on one round of global loads: its
+// own row of p and all gathered neighbour rows (EB entries at a time) are
+// issued before any of them is used.
+template <typename T, typename MV, bool CPLX, bool BLK, int EB, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Params P, int n_slices, const T* __restrict__ p,
+                                                         T* __restrict__ q, const T* __restrict__ mass,
+                                                         Cols C, double* __restrict__ partial) {
   if (*C.live == 0) return;
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
   constexpr int NV = BLK ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ int s_w[kMaxSpt], s_o[kMaxSpt];
+  __shared__ int s_w[2][kMaxSpt], s_o[2][kMaxSpt];
+  __shared__ __align__(8) uint64_t bar[2];
   const int W = P.W;
   const int TPR = W / VEC;
   const int RPP = kBlock / TPR;
@@ -260,92 +320,164 @@ __global__ void __launch_bounds__(kBlock, 4) spmm_kernel(EllView<MV> A, Params P
   const int spt = P.spt;
   const int TR = spt * H;
   double* sred = reinterpret_cast<double*>(smraw);
-  int* scol = reinterpret_cast<int*>(smraw + (size_t)RPP * W * sizeof(double));
-  MV* sval = reinterpret_cast<MV*>(scol + (size_t)TR * P.wmax);
+  const size_t colb = ((size_t)P.stage_e * 4 + 15) / 16 * 16;
+  const size_t valb = ((size_t)P.stage_e * NV * sizeof(MV) + 15) / 16 * 16;
+  unsigned char* const sbase = smraw + (size_t)RPP * W * sizeof(double);
+  auto stage_col = [&](int b) { return reinterpret_cast<int*>(sbase + b * (colb + valb)); };
+  auto stage_val = [&](int b) { return reinterpret_cast<MV*>(sbase + b * (colb + valb) + colb); };
   const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
   const int l0 = g * VEC;
   const bool on = tr < RPP && tr < TR;
+  const int ntiles = (n_slices + spt - 1) / spt;
+  if (on) {
+#pragma unroll
+    for (int v = 0; v < VEC; v++) sred[tr * W + l0 + v] = 0.0;  // FP64 dot slots, one per thread and lane
+  }
+
+  auto issue = [&](int tile, int b) {  // one thread
+    const int s0 = tile * spt, s1 = min(s0 + spt, n_slices);
+    const int64_t ob = A.slice_off[s0], oe = A.slice_off[s1];
+    const uint32_t ne = (uint32_t)(oe - ob);
+    const uint32_t bc = ne * 4u, bv = ne * (uint32_t)(NV * sizeof(MV));
+    async_proxy_fence();  // earlier generic reads of the buffer come first
+    mbar_expect(&bar[b], bc + bv);  // with no bytes the phase completes here
+    if (ne > 0) {
+      bulk_to_smem(stage_col(b), A.col + ob, bc, &bar[b]);
+      bulk_to_smem(stage_val(b), A.val + ob * NV, bv, &bar[b]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    async_proxy_fence();
+  }
+  __syncthreads();
+  if ((int)blockIdx.x < ntiles) {
+    const int s0 = blockIdx.x * spt, cnt = min(s0 + spt, n_slices) - s0;
+    if (threadIdx.x == 0) issue(blockIdx.x, 0);
+    if ((int)threadIdx.x < cnt) {
+      s_w[0][threadIdx.x] = A.slice_w[s0 + threadIdx.x];
+      s_o[0][threadIdx.x] = (int)(A.slice_off[s0 + threadIdx.x] - A.slice_off[s0]);
+    }
+  }
+  __syncthreads();
+
   DotAcc<T> dacc[VEC];
   T sh[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; v++) sh[v] = on ? (T)C.shift[CPLX ? (l0 + v) >> 1 : l0 + v] : (T)0;
   const int64_t rowW = (int64_t)NS * W;
   int chain = 0;
-  const int ntiles = (n_slices + spt - 1) / spt;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int s0 = tile * spt, s1 = min(s0 + spt, n_slices);
-    const int64_t ob = A.slice_off[s0], oe = A.slice_off[s1];
-    if ((int)threadIdx.x < s1 - s0) {
-      s_w[threadIdx.x] = A.slice_w[s0 + threadIdx.x];
-      s_o[threadIdx.x] = (int)(A.slice_off[s0 + threadIdx.x] - ob);
+  unsigned inflight = (int)blockIdx.x < ntiles ? 1u : 0u;  // bit b: a copy into buffer b is outstanding
+  int it = 0;
+  bool failed = false;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+    const int b = it & 1;
+    const int next = tile + gridDim.x;
+    int nw = 0, no = 0, ncnt = 0;
+    if (next < ntiles) {
+      if (threadIdx.x == 0) issue(next, b ^ 1);
+      inflight |= 1u << (b ^ 1);
+      const int s0 = next * spt;
+      ncnt = min(s0 + spt, n_slices) - s0;
+      if ((int)threadIdx.x < ncnt) {  // consumed after this tile's rows
+        nw = A.slice_w[s0 + threadIdx.x];
+        no = (int)(A.slice_off[s0 + threadIdx.x] - A.slice_off[s0]);
+      }
     }
-    const int ne = (int)(oe - ob);  // a multiple of 4 entries
-    for (int i = threadIdx.x; i < ne / 4; i += kBlock)
-      reinterpret_cast<int4*>(scol)[i] = __ldg(reinterpret_cast<const int4*>(A.col + ob) + i);
-    if constexpr ((4 * NV * sizeof(MV)) % 16 == 0) {
-      const int n16 = ne * NV * (int)sizeof(MV) / 16;
-      for (int i = threadIdx.x; i < n16; i += kBlock)
-        reinterpret_cast<uint4*>(sval)[i] = __ldg(reinterpret_cast<const uint4*>(A.val + ob * NV) + i);
-    } else {
-      const int n8 = ne * NV * (int)sizeof(MV) / 8;
-      for (int i = threadIdx.x; i < n8; i += kBlock)
-        reinterpret_cast<uint2*>(sval)[i] = __ldg(reinterpret_cast<const uint2*>(A.val + ob * NV) + i);
+    bool late = false;
+    if (threadIdx.x == 0) late = !mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1));
+    if (__syncthreads_or(late)) {
+      failed = true;
+      break;
     }
-    __syncthreads();
-    const int64_t r0 = (int64_t)s0 * H;
+    inflight &= ~(1u << b);
+    const int* scol = stage_col(b);
+    const MV* sval = stage_val(b);
+    const int64_t r0 = (int64_t)tile * spt * H;
     const int rows = (int)min((int64_t)TR, (int64_t)P.n - r0);
     if (on) {
       for (int lr = tr; lr < rows; lr += RPP) {
         const int64_t r = r0 + lr;
         const int sl = lr / H;
-        const int w = s_w[sl];
-        const int eb = s_o[sl] + (lr - sl * H) * w;
+        const int w = s_w[b][sl];
+        const int eb = s_o[b][sl] + (lr - sl * H) * w;
+        Pack<T> pr[NS];
+#pragma unroll
+        for (int s = 0; s < NS; s++) pr[s] = ldp(p + r * rowW + (int64_t)s * W + l0);
         T acc[NS][VEC];
 #pragma unroll
-        for (int b = 0; b < NS; b++)
+        for (int s = 0; s < NS; s++)
 #pragma unroll
-          for (int v = 0; v < VEC; v++) acc[b][v] = (T)0;
-        for (int e = 0; e < w; e += 4) {
-          const int4 c4 = *reinterpret_cast<const int4*>(scol + eb + e);
-          const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
-          const MV* vv = sval + (size_t)(eb + e) * NV;
+          for (int v = 0; v < VEC; v++) acc[s][v] = (T)0;
+        for (int e = 0; e < w; e += EB) {
+          Pack<T> nb[EB][NS];
 #pragma unroll
-          for (int t = 0; t < 4; t++) {
-            const T* src = p + (int64_t)cc[t] * rowW + l0;
-            const Pack<T> pu = ldp(src);
-            if constexpr (BLK) {
-              const Pack<T> pv = ldp(src + W);
-              const T a = cvt<T>(vv[2 * t]), bb = cvt<T>(vv[2 * t + 1]);
+          for (int h = 0; h < EB; h += 4) {
+            if (h == 0 || e + h < w) {
+              const int4 c4 = *reinterpret_cast<const int4*>(scol + eb + e + h);
+              const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-              for (int v = 0; v < VEC; v++) {
-                acc[0][v] = madd(a, pu.v[v], madd(bb, pv.v[v], acc[0][v]));
-                acc[1][v] = madd(a, pv.v[v], madd(-bb, pu.v[v], acc[1][v]));
+              for (int t = 0; t < 4; t++)
+#pragma unroll
+                for (int s = 0; s < NS; s++) nb[h + t][s] = ldp(p + (int64_t)cc[t] * rowW + (int64_t)s * W + l0);
+            }
+          }
+#pragma unroll
+          for (int h = 0; h < EB; h += 4) {
+            if (h == 0 || e + h < w) {
+              const MV* vv = sval + (size_t)(eb + e + h) * NV;
+#pragma unroll
+              for (int t = 0; t < 4; t++) {
+                if constexpr (BLK) {
+                  const T a = cvt<T>(vv[2 * t]), bb = cvt<T>(vv[2 * t + 1]);
+#pragma unroll
+                  for (int v = 0; v < VEC; v++) {
+                    acc[0][v] = madd(a, nb[h + t][0].v[v], madd(bb, nb[h + t][1].v[v], acc[0][v]));
+                    acc[1][v] = madd(a, nb[h + t][1].v[v], madd(-bb, nb[h + t][0].v[v], acc[1][v]));
+                  }
+                } else {
+                  const T a = cvt<T>(vv[t]);
+#pragma unroll
+                  for (int v = 0; v < VEC; v++) acc[0][v] = madd(a, nb[h + t][0].v[v], acc[0][v]);
+                }
               }
-            } else {
-              const T a = cvt<T>(vv[t]);
-#pragma unroll
-              for (int v = 0; v < VEC; v++) acc[0][v] = madd(a, pu.v[v], acc[0][v]);
             }
           }
         }
         if (++chain == kFlushRows) {
           chain = 0;
 #pragma unroll
-          for (int v = 0; v < VEC; v++) dacc[v].flush();
+          for (int v = 0; v < VEC; v++) dacc[v].spill(sred[tr * W + l0 + v]);
         }
-        spmm_epilogue<T, CPLX, BLK>(r, rowW, W, l0, mass, sh, acc, p, q, dacc);
+        spmm_epilogue<T, CPLX, BLK>(r, rowW, W, l0, mass, sh, acc, pr, q, dacc);
       }
     }
-    __syncthreads();  // the next tile overwrites the stage
+    if ((int)threadIdx.x < ncnt) {
+      s_w[b ^ 1][threadIdx.x] = nw;
+      s_o[b ^ 1][threadIdx.x] = no;
+    }
+    __syncthreads();  // the buffer is free for the tile after next; the next tile's layout is visible
   }
-  if (tr < RPP) {
+  if (failed) {
+    // leave no bulk copy writing into this block's shared memory after it exits
+    if (threadIdx.x == 0) {
+      const int b0 = it & 1, b1 = b0 ^ 1;
+      if (inflight & (1u << b0)) (void)mbar_wait_bounded(&bar[b0], (uint32_t)((it >> 1) & 1));
+      if (inflight & (1u << b1)) (void)mbar_wait_bounded(&bar[b1], (uint32_t)(((it + 1) >> 1) & 1));
+      atomicExch(C.live + 3, 1);
+    }
+    return;
+  }
+  if (on) {
 #pragma unroll
-    for (int v = 0; v < VEC; v++) sred[tr * W + l0 + v] = dacc[v].get();
+    for (int v = 0; v < VEC; v++) dacc[v].spill(sred[tr * W + l0 + v]);
   }
   __syncthreads();
+  const int rg = min(RPP, TR);
   for (int l = threadIdx.x; l < W; l += kBlock) {
     double s = 0.0;
-    for (int t = 0; t < RPP; t++) s += sred[t * W + l];
+    for (int t = 0; t < rg; t++) s += sred[t * W + l];
     partial[(int64_t)blockIdx.x * P.pstride + l] = s;
   }
 }
@@ -1010,15 +1142,16 @@ class EngineT final : public Engine {
     wcap_ = lanes;
     ncap_ = wcap_ / LPC;
     entry_bytes_ = 4 + NVAL * sizeof(MV);
-    if ((size_t)E_->slice_h * E_->max_width * entry_bytes_ > (size_t)kStageBytes)
+    if (stage_bytes(1) > (size_t)kStageMax)
       fail(IFILT_EINVAL, "ELL slice of %d rows x %d entries exceeds the shared-memory stage", E_->slice_h,
            E_->max_width);
     int dev = 0;
     IFILT_CUDA(cudaGetDevice(&dev));
     IFILT_CUDA(cudaDeviceGetAttribute(&n_sms_, cudaDevAttrMultiProcessorCount, dev));
     nb_max_ = n_sms_ * (2048 / kBlock);
-    IFILT_CUDA(cudaFuncSetAttribute(spmm_kernel<T, MV, CPLX, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(kBlock * VEC * sizeof(double) + kStageBytes)));
+    IFILT_CUDA(cudaFuncSetAttribute((const void*)spmm_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kBlock * VEC * sizeof(double) +
+                                          2 * std::max(stage_bytes(1), (size_t)kStageBytes))));
     // fixed part: partial sums, column state, tables
     size_t total = (size_t)nb_max_ * 2 * wcap_ * 8 + (size_t)ncap_ * (8 * 16 + 4 * 10 + 4 * 8) +
                    (size_t)wcap_ * 8 + 64 * 256;
@@ -1112,19 +1245,36 @@ class EngineT final : public Engine {
   size_t smem_of(int W, int slots2) const {
     return (size_t)(kBlock / (W / VEC)) * (size_t)W * slots2 / 2 * sizeof(double);
   }
+  // SpMM instance: gathers issued EB entries at a time (4 when no row holds
+  // more, as for the cell operator); FP32 2x2 blocks trade occupancy for more
+  // loads in flight per thread.
+  using SpmmFn = void (*)(EllView<MV>, Params, int, const T*, T*, const T*, Cols, double*);
+  static constexpr int kMinB = (BLK && sizeof(T) == 4) ? IFILT_SPMM_MINB_BLK : IFILT_SPMM_MINB;
+  SpmmFn spmm_fn() const {
+    if constexpr (sizeof(T) == 8) return spmm_kernel<T, MV, CPLX, BLK, 4, kMinB>;
+    else if constexpr (BLK) return spmm_kernel<T, MV, CPLX, BLK, IFILT_SPMM_EB_BLK, kMinB>;
+    else return E_->max_width <= 4 ? spmm_kernel<T, MV, CPLX, BLK, 4, kMinB> : spmm_kernel<T, MV, CPLX, BLK, 8, kMinB>;
+  }
+  // ELL entries of a stage buffer holding `spt` slices (each slice starts on an
+  // 8-entry boundary, so a slice spans at most 7 entries more than it holds)
+  int64_t stage_entries(int spt) const { return (int64_t)spt * ((int64_t)E_->slice_h * E_->max_width + 8); }
+  size_t stage_bytes(int spt) const {
+    const int64_t e = stage_entries(spt);
+    return (size_t)((e * 4 + 15) / 16 * 16 + (e * NVAL * (int64_t)sizeof(MV) + 15) / 16 * 16);
+  }
   int spmm_spt(int W) const {
     const int RPP = kBlock / (W / VEC);
-    int spt = std::max(1, (RPP + E_->slice_h - 1) / E_->slice_h);
-    while (spt > 1 && (size_t)spt * E_->slice_h * E_->max_width * entry_bytes_ > (size_t)kStageBytes) spt--;
+    int spt = std::max(1, (RPP * kTilePasses + E_->slice_h - 1) / E_->slice_h);
+    while (spt > 1 && stage_bytes(spt) > (size_t)kStageBytes) spt--;
+    // keep several tiles per resident block so that the grid ends evenly
+    const long long want = (long long)n_sms_ * kMinB * 8;
+    while (spt > 1 && (E_->n_slices + spt - 1) / spt < want) spt--;
     return std::min(spt, kMaxSpt);
   }
-  size_t spmm_smem(int W) const {
-    return smem_of(W, 2) + (size_t)spmm_spt(W) * E_->slice_h * E_->max_width * entry_bytes_;
-  }
+  size_t spmm_smem(int W) const { return smem_of(W, 2) + 2 * stage_bytes(spmm_spt(W)); }
   int blocks_for(int W) const {
     const long long ntiles = (E_->n_slices + spmm_spt(W) - 1) / spmm_spt(W);
-    return std::min(nb_max_, grid_for((const void*)spmm_kernel<T, MV, CPLX, BLK>, kBlock, spmm_smem(W),
-                                      ntiles * kBlock));
+    return std::min(nb_max_, grid_for((const void*)spmm_fn(), kBlock, spmm_smem(W), ntiles * kBlock));
   }
   size_t src_bytes() const { return (size_t)2 * n_ * NS * sizeof(double); }
   const T* mass_t() const {
@@ -1201,7 +1351,7 @@ class EngineT final : public Engine {
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
     for (int it = 0; it < m_it_; it++) {
       if (it == 0) rec(0);
-      spmm_kernel<T, MV, CPLX, BLK><<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), C_,
+      spmm_fn()<<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), C_,
                                                                 partial_);
       chk("spmm");
       if (it == 0) rec(1);
@@ -1219,7 +1369,7 @@ class EngineT final : public Engine {
       if (it == 0) rec(5);
     }
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
-    IFILT_CUDA(cudaMemcpyAsync(h_cnt_, C_.live, 3 * sizeof(int), cudaMemcpyDeviceToHost, st_));
+    IFILT_CUDA(cudaMemcpyAsync(h_cnt_, C_.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st_));
   }
   int launches_per_step() const { return 7 + 5 * m_it_; }
 
@@ -1244,6 +1394,7 @@ class EngineT final : public Engine {
     P_.ncols = W / LPC;
     P_.pstride = 2 * W;
     P_.spt = W > 0 ? spmm_spt(W) : 1;
+    P_.stage_e = (int)stage_entries(P_.spt);
   }
 
   void release_tiles() {
@@ -1443,6 +1594,7 @@ class EngineT final : public Engine {
     launched_ = false;
     const int live = h_cnt_[0], notdone = h_cnt_[2];
     (void)live;
+    if (h_cnt_[3]) fail(IFILT_DEVICE_TIMEOUT, "SpMM stage copy did not complete within its wait limit");
     if (prof_) {
       float a = 0, b = 0, c = 0;
       IFILT_CUDA(cudaEventElapsedTime(&a, ev_[0], ev_[1]));

@@ -23,6 +23,8 @@ T* dev_copy(ifilt_mesh_s* m, const T* src, size_t count, cudaStream_t st) {
 }
 
 // Sliced ELL from CSR; padding entries point at their own row with value 0.
+// Every slice starts on an 8-entry boundary (so any run of slices can be
+// bulk-copied with 16-byte aligned addresses and sizes for every value type).
 void build_ell(ifilt_mesh_s* m, const HostCSR& a, int32_t slice_h, DevEll& out, cudaStream_t st) {
   const int32_t n = a.n, nv = a.nval;
   const int32_t ns = (n + slice_h - 1) / slice_h;
@@ -36,7 +38,7 @@ void build_ell(ifilt_mesh_s* m, const HostCSR& a, int32_t slice_h, DevEll& out, 
     w = (w + 3) / 4 * 4;
     width[s] = (int32_t)w;
     maxw = std::max(maxw, (int32_t)w);
-    off[s + 1] = off[s] + (int64_t)(r1 - s * slice_h) * w;
+    off[s + 1] = (off[s] + (int64_t)(r1 - s * slice_h) * w + 7) / 8 * 8;
   }
   const int64_t E = off[ns];
   std::vector<int32_t> col((size_t)E);

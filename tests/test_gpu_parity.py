@@ -116,6 +116,28 @@ def test_vector_and_cell_placements(lib, placement, order, n2, prec):
     _check(res, ref, TOL_FP64 if prec == 0 else TOL_MIXED)
 
 
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+def test_slice_heights_and_value_types(lib, placement):
+    """ELL slice heights that are not multiples of 8 leave gaps between slices
+    (each slice starts on an 8-entry boundary); SpMM tiles then span several
+    slices and gaps.  Every value type must still reproduce the oracle."""
+    import torch
+    m = _sphere(3, 58, polar=10.0)
+    P = oracle.build_problem(m, placement)
+    f = _fields(P, 2, 5)
+    ks = synth.log_wavenumbers(6000.0, 600.0, 3)
+    _, ref = _oracle(m, placement, f, ks, 2)
+    ft = torch.tensor(f, dtype=torch.float64, device="cuda")
+    for H in (4, 12, 100):
+        h = lib.prepare_mesh(m, placement, max_order=2, ell_slice=H)
+        for prec, tol in ((0, TOL_FP64), (1, TOL_MIXED), (2, TOL_MIXED)):
+            out, stats, st = lib.solve(h, ft, ks, order=2, tol=1e-12 if prec == 0 else 1e-10, precision=prec,
+                                       n2_solver=2)
+            assert st == 0, (H, prec)
+            _check(out.cpu().numpy(), ref, tol)
+        h.release()
+
+
 def test_ragged_batches_and_padding(lib):
     """3 fields x 5 scales = 15 columns (lanes padded to 16 / 32), split over
     several batches by a small lane budget; all-ocean mesh."""
