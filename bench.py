@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain-sample", type=int, default=3, help="scales (1-3) timed on the plain FP64 path")
     ap.add_argument("--serving", action="store_true", help="run the request-serving workload instead")
+    ap.add_argument("--precond", choices=["none", "jacobi"], default="none", help="Krylov preconditioner")
     ap.add_argument("--concurrent", action="store_true",
                     help="step the two placements' solvers together (one solve_many call); per-kernel "
                          "event timings then overlap, so the roofline is not measured")
@@ -177,7 +178,8 @@ def workload_config(args, w, world):
                         f"vertex-vector and cell placements; n=2; {N_K} wavenumbers 2pi/4000..2pi/10 km",
             "vertices": int(m["coords"].shape[0]), "triangles": int(m["tri"].shape[0]),
             "columns_per_step": 4 * N_K, "order": 2, "n2_solver": "complex", "tol": args.tol,
-            "precision": args.precision, "l2": "inputs larger than L2 (GBs per vector), no flush",
+            "precision": args.precision, "precond": getattr(args, "precond", "none"),
+            "l2": "inputs larger than L2 (GBs per vector), no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
@@ -196,7 +198,8 @@ class Ours:
         self.mc = api.prepare_mesh(w["mesh"], "cell", max_order=2)
         self.prepare_s = time.time() - t0
         prec = {"fp32": api.PREC_FP32_IR, "bf16": api.PREC_BF16_IR, "fp64": api.PREC_FP64}[args.precision]
-        self.opts = dict(order=2, tol=args.tol, precision=prec, n2_solver=api.N2_COMPLEX)
+        self.opts = dict(order=2, tol=args.tol, precision=prec, n2_solver=api.N2_COMPLEX,
+                         precond={"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI}[args.precond])
         K = self.k.size
         self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
         self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")

@@ -89,6 +89,15 @@ enum {
                                 symmetric systems).  Same solution, condition ~ l^2 instead of l^4. */
 };
 
+/* Preconditioning of the batched Krylov solve (the plain method takes none). */
+enum {
+  IFILT_PRECOND_NONE = 0,
+  IFILT_PRECOND_JACOBI = 1   /* z = D^-1 r, D the diagonal of the shifted operator of each column
+                                (m_i + s g_ii, or m_i + i s g_ii for the complex form); the
+                                preconditioned CG / COCG keeps the same solution and stopping test
+                                on the unpreconditioned residual */
+};
+
 typedef struct {
   int32_t n_vert;            /* V > 0 */
   int32_t n_tri;             /* T > 0 */
@@ -114,7 +123,7 @@ typedef struct {
   int32_t precision;         /* IFILT_PREC_* */
   int32_t method;            /* IFILT_METHOD_* */
   int32_t n2_solver;         /* IFILT_N2_* */
-  int32_t precond;           /* 0 none, 1 Jacobi (diagonal of the shifted operator) */
+  int32_t precond;           /* IFILT_PRECOND_*; batched method only */
   int32_t check_every;       /* batched: iterations per CUDA graph between host checks; 0 = 32 */
   double inner_tol;          /* FP32 inner solves: relative reduction per refinement round; 0 = 1e-4 */
   int32_t max_lanes;         /* batched: widest column tile in 32-bit lanes; 0 = library default */

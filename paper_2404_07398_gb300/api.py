@@ -19,6 +19,7 @@ GEOM_PLANAR_PERIODIC, GEOM_PLANAR, GEOM_SPHERE = 0, 1, 2
 PREC_FP64, PREC_FP32_IR, PREC_BF16_IR = 0, 1, 2
 METHOD_PLAIN, METHOD_BATCHED = 0, 1
 N2_AUTO, N2_REAL, N2_COMPLEX = 0, 1, 2
+PRECOND_NONE, PRECOND_JACOBI = 0, 1
 OK, NOT_CONVERGED = 0, 1
 EXPORT = dict(perm=0, k_rowptr=1, k_col=2, k_val=3, mass=4, g2_rowptr=5, g2_col=6, g2_val=7)
 PLACEMENTS = {"vertex_scalar": VERTEX_SCALAR, "vertex_vector": VERTEX_VECTOR, "cell": CELL}

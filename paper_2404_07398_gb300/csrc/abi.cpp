@@ -278,6 +278,10 @@ static void check_opts(ifilt_mesh m, const ifilt_solve_opts* o) {
   if (o->n2_solver < IFILT_N2_AUTO || o->n2_solver > IFILT_N2_COMPLEX) fail(IFILT_EINVAL, "unknown n2_solver");
   if (o->method == IFILT_METHOD_PLAIN && o->precision != IFILT_PREC_FP64)
     fail(IFILT_EINVAL, "the plain method runs in FP64 only");
+  if (o->precond != IFILT_PRECOND_NONE && o->precond != IFILT_PRECOND_JACOBI)
+    fail(IFILT_EINVAL, "unknown precond %d", o->precond);
+  if (o->method == IFILT_METHOD_PLAIN && o->precond != IFILT_PRECOND_NONE)
+    fail(IFILT_EINVAL, "the plain method takes no preconditioner");
   if (o->max_iter < 0 || o->check_every < 0 || o->max_lanes < 0 || o->inner_tol < 0)
     fail(IFILT_EINVAL, "negative option");
 }

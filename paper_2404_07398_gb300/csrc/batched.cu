@@ -134,6 +134,25 @@ struct DotAcc<float> {
 };
 constexpr int kFlushRows = 64;  // rows per compensated chain
 
+// Jacobi step z = D^-1 r on VEC lanes of one row, D the diagonal of the
+// shifted operator: m + s g for real columns, m + i s g for complex ones
+// (lanes in (re, im) pairs); m, g the row's mass and diagonal of G.
+template <typename T, bool CPLX, int VEC>
+__device__ __forceinline__ void jacobi(T m, T g, const T* sh, const T* rv, T* z) {
+  if constexpr (CPLX) {
+#pragma unroll
+    for (int v = 0; v < VEC; v += 2) {
+      const T bg = sh[v] * g;
+      const T inv = (T)1 / madd(m, m, bg * bg);
+      z[v] = madd(rv[v], m, rv[v + 1] * bg) * inv;
+      z[v + 1] = madd(rv[v + 1], m, -(rv[v] * bg)) * inv;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < VEC; v++) z[v] = rv[v] / madd(sh[v], g, m);
+  }
+}
+
 // 4 consecutive ELL entries' values (NV per entry) converted to AT.
 template <typename MV, int NV, typename AT>
 __device__ __forceinline__ void load_vals(const MV* __restrict__ p, AT* out) {
@@ -484,10 +503,11 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
 
 // x += alpha p ; r -= alpha q ; partial <r, r> (slots [0, W): lane-wise for real,
 // (re, im) pairs for complex) and ||r||^2 (complex only, slots W + column).
-template <typename T, bool CPLX, bool BLK>
+template <typename T, bool CPLX, bool BLK, bool PRE>
 __global__ void __launch_bounds__(kBlock, 4) update_kernel(Params P, T* __restrict__ x, const T* __restrict__ p,
                                                         T* __restrict__ r, const T* __restrict__ q, Cols C,
-                                                        double* __restrict__ partial) {
+                                                        double* __restrict__ partial, const T* __restrict__ mass,
+                                                        const T* __restrict__ gdiag) {
   if (*C.live == 0) return;
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
@@ -500,11 +520,12 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(Params P, T* __restri
   const int l0 = g * VEC;
   DotAcc<T> d1[VEC], d2[VEC / 2 > 0 ? VEC / 2 : 1];
   if (tr < RPP) {
-    T a[VEC];
+    T a[VEC], sh[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; v++) {
       if constexpr (CPLX) a[v] = (T)C.alpha[(l0 & ~1) + v];  // lanes (re, im) of one column
       else a[v] = (T)C.alpha[2 * (l0 + v)];
+      sh[v] = PRE ? (T)C.shift[CPLX ? (l0 + v) >> 1 : l0 + v] : (T)0;
     }
     const int64_t rowW = (int64_t)NS * W;
     int chain = 0;
@@ -516,6 +537,7 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(Params P, T* __restri
 #pragma unroll
         for (int v = 0; v < (VEC / 2 > 0 ? VEC / 2 : 1); v++) d2[v].flush();
       }
+      const T mr = PRE ? mass[row] : (T)0, gr = PRE ? gdiag[row] : (T)0;
 #pragma unroll
       for (int b = 0; b < NS; b++) {
         const int64_t off = row * rowW + (int64_t)b * W + l0;
@@ -529,18 +551,32 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(Params P, T* __restri
             xv.v[v + 1] += are * pv.v[v + 1] + aim * pv.v[v];
             rv.v[v] -= are * qv.v[v] - aim * qv.v[v + 1];
             rv.v[v + 1] -= are * qv.v[v + 1] + aim * qv.v[v];
-            const T rre = rv.v[v], rim = rv.v[v + 1];
-            d1[v].add_sum(madd(rre, rre, -rim * rim));
-            d1[v + 1].add((T)2 * rre, rim);
-            d2[v / 2].add_sum(madd(rre, rre, rim * rim));
           }
         } else {
 #pragma unroll
           for (int v = 0; v < VEC; v++) {
             xv.v[v] = madd(a[v], pv.v[v], xv.v[v]);
             rv.v[v] = madd(-a[v], qv.v[v], rv.v[v]);
-            d1[v].add(rv.v[v], rv.v[v]);
           }
+        }
+        // rho = <r, z> with z = r, or z = D^-1 r under Jacobi preconditioning
+        T zv[VEC];
+        if constexpr (PRE) jacobi<T, CPLX, VEC>(mr, gr, sh, rv.v, zv);
+        else {
+#pragma unroll
+          for (int v = 0; v < VEC; v++) zv[v] = rv.v[v];
+        }
+        if constexpr (CPLX) {
+#pragma unroll
+          for (int v = 0; v < VEC; v += 2) {
+            const T rre = rv.v[v], rim = rv.v[v + 1];
+            d1[v].add_sum(madd(rre, zv[v], -rim * zv[v + 1]));
+            d1[v + 1].add_sum(madd(rre, zv[v + 1], rim * zv[v]));
+            d2[v / 2].add_sum(madd(rre, rre, rim * rim));
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; v++) d1[v].add(rv.v[v], zv[v]);
         }
         stp(x + off, xv);
         stp(r + off, rv);
@@ -562,9 +598,10 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(Params P, T* __restri
 }
 
 // p = r + beta p
-template <typename T, bool CPLX, bool BLK>
+template <typename T, bool CPLX, bool BLK, bool PRE>
 __global__ void __launch_bounds__(kBlock) direction_kernel(Params P, T* __restrict__ p, const T* __restrict__ r,
-                                                           Cols C) {
+                                                           Cols C, const T* __restrict__ mass,
+                                                           const T* __restrict__ gdiag) {
   if (*C.live == 0) return;
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
@@ -574,19 +611,27 @@ __global__ void __launch_bounds__(kBlock) direction_kernel(Params P, T* __restri
   const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
   if (tr >= RPP) return;
   const int l0 = g * VEC;
-  T bt[VEC];
+  T bt[VEC], sh[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; v++) {
     if constexpr (CPLX) bt[v] = (T)C.beta[(l0 & ~1) + v];
     else bt[v] = (T)C.beta[2 * (l0 + v)];
+    sh[v] = PRE ? (T)C.shift[CPLX ? (l0 + v) >> 1 : l0 + v] : (T)0;
   }
   const int64_t rowW = (int64_t)NS * W;
   for (int64_t row = (int64_t)blockIdx.x * RPP + tr; row < P.n; row += (int64_t)gridDim.x * RPP) {
+    const T mr = PRE ? mass[row] : (T)0, gr = PRE ? gdiag[row] : (T)0;
 #pragma unroll
     for (int b = 0; b < NS; b++) {
       const int64_t off = row * rowW + (int64_t)b * W + l0;
       Pack<T> pv = ldv(p + off);
-      const Pack<T> rv = ldv(r + off);
+      Pack<T> rv = ldv(r + off);
+      if constexpr (PRE) {  // p = D^-1 r + beta p
+        T zv[VEC];
+        jacobi<T, CPLX, VEC>(mr, gr, sh, rv.v, zv);
+#pragma unroll
+        for (int v = 0; v < VEC; v++) rv.v[v] = zv[v];
+      }
       if constexpr (CPLX) {
 #pragma unroll
         for (int v = 0; v < VEC; v += 2) {
@@ -716,7 +761,8 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
                                                           const int* __restrict__ lane_src,
                                                           const double* __restrict__ mass, Cols C,
                                                           T* __restrict__ r, T* __restrict__ d, T* __restrict__ p,
-                                                          double* __restrict__ partial) {
+                                                          double* __restrict__ partial,
+                                                          const double* __restrict__ gdiag) {
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
   constexpr int NV = BLK ? 2 : 1;
@@ -792,6 +838,7 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
         (void)NV;
       }
       const double mr = mass[row];
+      const double gr = gdiag ? gdiag[row] : 0.0;
 #pragma unroll
       for (int b = 0; b < NS; b++) {
         const int64_t off = row * rowW + (int64_t)b * W + l0;
@@ -802,7 +849,9 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
           xo[2 * k] = t.v[0];
           xo[2 * k + 1] = t.v[1];
         }
-        Pack<T> ro, zo;
+        // r (rounded to T), the restarted direction p = z (z = r, or D^-1 r
+        // under Jacobi preconditioning) and rho = <r, z>
+        Pack<T> ro, po, zo;
 #pragma unroll
         for (int v = 0; v < VEC; v++) zo.v[v] = (T)0;
         if constexpr (CPLX) {
@@ -812,10 +861,19 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
             const double r_re = bre - (mr * xo[v] - sh[v] * acc[b][v + 1]);
             const double r_im = -(mr * xo[v + 1] + sh[v] * acc[b][v]);
             const T tre = (T)r_re, tim = (T)r_im;
+            T zre = tre, zim = tim;
+            if (gdiag) {
+              const double bg = sh[v] * gr;
+              const double inv = 1.0 / (mr * mr + bg * bg);
+              zre = (T)((r_re * mr + r_im * bg) * inv);
+              zim = (T)((r_im * mr - r_re * bg) * inv);
+            }
             ro.v[v] = tre;
             ro.v[v + 1] = tim;
-            d1[v] += (double)tre * tre - (double)tim * tim;
-            d1[v + 1] += 2.0 * (double)tre * tim;
+            po.v[v] = zre;
+            po.v[v + 1] = zim;
+            d1[v] += (double)tre * zre - (double)tim * zim;
+            d1[v + 1] += (double)tre * zim + (double)tim * zre;
             d2[v / 2] += r_re * r_re + r_im * r_im;
           }
         } else {
@@ -824,21 +882,23 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
             const double bv = bptr[src[v]][row * NS + b];
             const double rv = bv - (mr * xo[v] + sh[v] * acc[b][v]);
             const T t = (T)rv;
+            const T z = gdiag ? (T)(rv / (mr + sh[v] * gr)) : t;
             ro.v[v] = t;
-            d1[v] += (double)t * t;
+            po.v[v] = z;
+            d1[v] += (double)t * z;
             d2[v] += rv * rv;
           }
         }
         if (all) {
           stp(r + off, ro);
-          stp(p + off, ro);
+          stp(p + off, po);
           stp(d + off, zo);
         } else {
 #pragma unroll
           for (int v = 0; v < VEC; v++)
             if (mine[v]) {
               r[off + v] = ro.v[v];
-              p[off + v] = ro.v[v];
+              p[off + v] = po.v[v];
               d[off + v] = (T)0;
             }
         }
@@ -1281,6 +1341,16 @@ class EngineT final : public Engine {
     if constexpr (sizeof(T) == 4) return m_->mass32;
     else return m_->mass;
   }
+  // diagonal of G for Jacobi preconditioning (nullptr: none)
+  const double* gdiag64() const {
+    if (o_.precond != IFILT_PRECOND_JACOBI) return nullptr;
+    return E_ == &m_->ell_g2 ? m_->diag_g2 : m_->diag_k;
+  }
+  const T* gdiag_t() const {
+    if (o_.precond != IFILT_PRECOND_JACOBI) return nullptr;
+    if constexpr (sizeof(T) == 4) return E_ == &m_->ell_g2 ? m_->diag_g2_32 : m_->diag_k32;
+    else return gdiag64();
+  }
   int64_t tile_bytes(int W) const { return (int64_t)n_ * NS * W * (4 * sizeof(T) + sizeof(double)); }
   double shift_of(double k) const {
     const double ell = 1.0 / k;
@@ -1344,7 +1414,7 @@ class EngineT final : public Engine {
     accumulate_kernel<T, CPLX><<<ga, kBlock, 0, st_>>>(n_ * NS * W, W, C_.refresh, tl_.x64, tl_.d, C_.live);
     chk("accumulate");
     residual_kernel<T, CPLX, BLK><<<nb_, kBlock, sm4, st_>>>(A64_, P_, tl_.x64, bptr_, lane_src_, m_->mass, C_,
-                                                            tl_.r, tl_.d, tl_.p, partial_);
+                                                            tl_.r, tl_.d, tl_.p, partial_, gdiag64());
     chk("residual");
     finish_residual_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
     chk("finish_residual");
@@ -1358,13 +1428,21 @@ class EngineT final : public Engine {
       finish_alpha_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
       chk("finish_alpha");
       if (it == 0) rec(2);
-      update_kernel<T, CPLX, BLK><<<nb_, kBlock, sm3, st_>>>(P_, tl_.d, tl_.p, tl_.r, tl_.q, C_, partial_);
+      if (gdiag_t())
+        update_kernel<T, CPLX, BLK, true><<<nbu_, kBlock, sm3, st_>>>(P_, tl_.d, tl_.p, tl_.r, tl_.q, C_, partial_,
+                                                                    mass_t(), gdiag_t());
+      else
+        update_kernel<T, CPLX, BLK, false><<<nbu_, kBlock, sm3, st_>>>(P_, tl_.d, tl_.p, tl_.r, tl_.q, C_,
+                                                                     partial_, mass_t(), nullptr);
       chk("update");
       if (it == 0) rec(3);
-      finish_beta_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
+      finish_beta_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbu_, partial_, C_);
       chk("finish_beta");
       if (it == 0) rec(4);
-      direction_kernel<T, CPLX, BLK><<<nb_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_);
+      if (gdiag_t())
+        direction_kernel<T, CPLX, BLK, true><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_, mass_t(), gdiag_t());
+      else
+        direction_kernel<T, CPLX, BLK, false><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_, mass_t(), nullptr);
       chk("direction");
       if (it == 0) rec(5);
     }
@@ -1379,6 +1457,15 @@ class EngineT final : public Engine {
     exec_ = nullptr;
     graph_ = nullptr;
     nb_ = blocks_for(P_.W);
+    // the streaming kernels get their own grids: as many resident blocks as fit
+    const long long rows_threads = (long long)n_ * (P_.W / VEC);
+    const bool pre = gdiag_t() != nullptr;
+    nbu_ = std::min(nb_max_, grid_for(pre ? (const void*)update_kernel<T, CPLX, BLK, true>
+                                          : (const void*)update_kernel<T, CPLX, BLK, false>,
+                                      kBlock, smem_of(P_.W, 3), rows_threads));
+    nbd_ = std::min(nb_max_, grid_for(pre ? (const void*)direction_kernel<T, CPLX, BLK, true>
+                                          : (const void*)direction_kernel<T, CPLX, BLK, false>,
+                                      kBlock, 0, rows_threads));
     launch_check("before capture", nb_, 0, P_.W);
     if (!use_graph_) return;
     IFILT_CUDA(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
@@ -1660,7 +1747,7 @@ class EngineT final : public Engine {
   EllView<MV> A_{};
   EllView<double> A64_{};
   int64_t n_ = 0;
-  int wcap_ = 0, ncap_ = 0, nb_max_ = 0, n_sms_ = kNumSMs, nb_ = 1;
+  int wcap_ = 0, ncap_ = 0, nb_max_ = 0, n_sms_ = kNumSMs, nb_ = 1, nbu_ = 1, nbd_ = 1;
   size_t entry_bytes_ = 0;
   Params P_{};
   Cols C_{};

@@ -140,11 +140,15 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
   m->mass32 = dev_copy(m, m32.data(), m32.size(), st);
   std::vector<double> dk = diagonal(h.K);
   m->diag_k = dev_copy(m, dk.data(), dk.size(), st);
+  std::vector<float> dk32(dk.begin(), dk.end());
+  m->diag_k32 = dev_copy(m, dk32.data(), dk32.size(), st);
   build_ell(m, h.K, slice_h, m->ell_k, st);
   build_csr(m, h.K, m->csr_k, st);
   if (h.max_order >= 2) {
     std::vector<double> dg = diagonal(h.G2);
     m->diag_g2 = dev_copy(m, dg.data(), dg.size(), st);
+    std::vector<float> dg32(dg.begin(), dg.end());
+    m->diag_g2_32 = dev_copy(m, dg32.data(), dg32.size(), st);
     build_ell(m, h.G2, slice_h, m->ell_g2, st);
     build_csr(m, h.G2, m->csr_g2, st);
   }

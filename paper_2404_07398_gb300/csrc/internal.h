@@ -93,6 +93,8 @@ struct ifilt_mesh_s {
   float* mass32 = nullptr;       // [n_rows] the same in FP32 (FP32 kernels)
   double* diag_k = nullptr;      // [n_rows] diagonal of K (K~ for vectors)
   double* diag_g2 = nullptr;     // [n_rows]
+  float* diag_k32 = nullptr;     // [n_rows] FP32 copies (Jacobi preconditioning in FP32 kernels)
+  float* diag_g2_32 = nullptr;   // [n_rows]
   int64_t* proj_ptr = nullptr;
   int32_t* proj_cell = nullptr;
   double* proj_w = nullptr;

@@ -37,7 +37,7 @@ struct Request {
   double t_submit = 0, t_start = 0, t_done = 0;
 };
 
-using Key = std::tuple<ifilt_mesh, int, int, int>;  // mesh, order, precision, n = 2 form
+using Key = std::tuple<ifilt_mesh, int, int, int, int>;  // mesh, order, precision, n = 2 form, preconditioner
 
 struct EngineSlot {
   std::unique_ptr<ifilt::Engine> engine;
@@ -79,7 +79,7 @@ struct ifilt_server_s {
       o.max_lanes = opts.max_lanes;
       o.check_every = opts.check_every;
       const bool cplx = o.order >= 2 && o.n2_solver != IFILT_N2_REAL;
-      Key key{r->mesh, o.order, o.precision, o.order >= 2 ? (cplx ? 2 : 1) : 0};
+      Key key{r->mesh, o.order, o.precision, o.order >= 2 ? (cplx ? 2 : 1) : 0, o.precond};
       auto it = engines.find(key);
       if (it == engines.end()) {
         EngineSlot slot;
@@ -250,6 +250,7 @@ ifilt_status ifilt_server_submit(ifilt_server s, ifilt_mesh mesh, const ifilt_so
     if (o->order < 1 || o->order > mesh->host.max_order) fail(IFILT_EINVAL, "order outside the mesh's range");
     if (!(o->tol > 0.0)) fail(IFILT_EINVAL, "tol must be positive");
     if (o->precision < IFILT_PREC_FP64 || o->precision > IFILT_PREC_BF16_IR) fail(IFILT_EINVAL, "unknown precision");
+    if (o->precond != IFILT_PRECOND_NONE && o->precond != IFILT_PRECOND_JACOBI) fail(IFILT_EINVAL, "unknown precond");
     for (int32_t j = 0; j < n_k; j++)
       if (!(k[j] > 0.0)) fail(IFILT_EINVAL, "k must be positive");
     std::lock_guard<std::mutex> lk(s->mu);

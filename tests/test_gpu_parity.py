@@ -138,6 +138,37 @@ def test_slice_heights_and_value_types(lib, placement):
         h.release()
 
 
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+@pytest.mark.parametrize("order,n2,prec", [(1, 0, 1), (2, 1, 0), (2, 1, 1), (2, 2, 0), (2, 2, 1), (2, 2, 2)])
+def test_jacobi_preconditioning(lib, placement, order, n2, prec):
+    """Jacobi-preconditioned CG / COCG reaches the same filtered fields."""
+    m = _sphere(3, 59, polar=10.0)
+    P = oracle.build_problem(m, placement)
+    f = _fields(P, 2, 6)
+    ks = synth.log_wavenumbers(6000.0, 300.0, 4)
+    res, stats, st = _run(lib, m, placement, f, ks, order, tol=1e-12 if prec == 0 else 1e-10, precision=prec,
+                          n2_solver=n2, precond=lib.PRECOND_JACOBI)
+    assert st == 0, stats
+    _, ref = _oracle(m, placement, f, ks, order)
+    # The error of a solve stopped at relative residual tol is bounded by
+    # cond(S) * tol; the real n = 2 operator has condition ~ l^4 (up to ~1e3
+    # here), so its FP64 case gets 1e-9 where the others keep 1e-10.
+    tol = TOL_MIXED if prec else (1e-9 if (order, n2) == (2, 1) else TOL_FP64)
+    _check(res, ref, tol)
+
+
+def test_preconditioner_option_checked(lib):
+    import torch
+    m = _sphere(2, 60)
+    h = lib.prepare_mesh(m, "vertex_scalar", max_order=1)
+    f = torch.zeros((1, 1, h.info["n_in"]), dtype=torch.float64, device="cuda")
+    for kw in (dict(precond=7), dict(precond=lib.PRECOND_JACOBI, method=lib.METHOD_PLAIN)):
+        with pytest.raises(lib.IfiltError) as e:
+            lib.solve(h, f, [0.01], order=1, **kw)
+        assert e.value.status == -1
+    h.release()
+
+
 def test_ragged_batches_and_padding(lib):
     """3 fields x 5 scales = 15 columns (lanes padded to 16 / 32), split over
     several batches by a small lane budget; all-ocean mesh."""
