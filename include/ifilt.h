@@ -92,10 +92,16 @@ enum {
 /* Preconditioning of the batched Krylov solve (the plain method takes none). */
 enum {
   IFILT_PRECOND_NONE = 0,
-  IFILT_PRECOND_JACOBI = 1   /* z = D^-1 r, D the diagonal of the shifted operator of each column
+  IFILT_PRECOND_JACOBI = 1,  /* z = D^-1 r, D the diagonal of the shifted operator of each column
                                 (m_i + s g_ii, or m_i + i s g_ii for the complex form); the
                                 preconditioned CG / COCG keeps the same solution and stopping test
                                 on the unpreconditioned residual */
+  IFILT_PRECOND_MG = 2       /* z = one V-cycle of smoothed-aggregation multigrid on each column's
+                                S = M + s K (or M + i s K): two damped-Jacobi sweeps before and
+                                after each coarse correction, Jacobi sweeps on the coarsest level;
+                                a symmetric preconditioner, so CG / COCG apply.  Needs S built on
+                                K (order 1, or order 2 in the complex form) and the FP32 or BF16
+                                precision; EINVAL otherwise */
 };
 
 typedef struct {
@@ -192,6 +198,43 @@ ifilt_status ifilt_mesh_info(ifilt_mesh mesh, ifilt_mesh_info_t* out);
  * too small).  For tests of the integer layout against an independent
  * reference. */
 ifilt_status ifilt_mesh_export(ifilt_mesh mesh, int32_t what, void* dst, size_t bytes);
+
+/* Multigrid hierarchy of a mesh (IFILT_PRECOND_MG).  Built on the host from
+ * the prepared n = 1 operator K and the lumped mass the first time it is
+ * needed (this call or the first multigrid solve), then kept with the mesh;
+ * it does not depend on l.  The paper has no counterpart: it reports that ILU
+ * did not help (Sect. 2.2) and names better preconditioners as future work
+ * (Sect. 6).  Smoothed aggregation: greedy
+ * aggregates on the graph of K_l, prolongation P = (I - w D^-1 K_l) P_tent,
+ * restriction R = P^T, coarse pair (K, M)_{l+1} = R (K, M)_l P.  Vertex-vector
+ * meshes aggregate vertices and keep 2x2 blocks [[a, b], [-b, a]] on every level.
+ * Works on host-only meshes (no GPU needed). */
+#define IFILT_MG_MAX_LEVELS 16
+typedef struct {
+  int32_t n_levels;
+  int32_t rows[IFILT_MG_MAX_LEVELS];    /* rows (vertices for the vector placement) per level */
+  int64_t nnz_s[IFILT_MG_MAX_LEVELS];   /* stored entries of (K_l, M_l); level 0: of K */
+  int64_t nnz_p[IFILT_MG_MAX_LEVELS];   /* entries of P_l (0 on the last level) */
+} ifilt_multigrid_info;
+ifilt_status ifilt_mesh_multigrid(ifilt_mesh mesh, ifilt_multigrid_info* info);
+
+/* Export selectors for ifilt_mesh_multigrid_export (host copies, level >= 0).
+ * Values per entry: (K_l, M_l) pairs hold (k, m) for scalar rows and
+ * (k_a, k_b, m_a, m_b) for 2x2-block rows; P and R hold 1 or 2 values. */
+enum {
+  IFILT_MG_S_ROWPTR = 0,  /* int64 [rows_l+1] (level 0: empty) */
+  IFILT_MG_S_COL = 1,     /* int32 [nnz_s] */
+  IFILT_MG_S_VAL = 2,     /* double [nnz_s][2 or 4] */
+  IFILT_MG_P_ROWPTR = 3,  /* int64 [rows_l+1]: P_l, columns index level l+1 */
+  IFILT_MG_P_COL = 4,
+  IFILT_MG_P_VAL = 5,     /* double [nnz_p][1 or 2] */
+  IFILT_MG_DK = 6,        /* double [rows_l]: diagonal of K_l */
+  IFILT_MG_DM = 7         /* double [rows_l]: diagonal of M_l */
+};
+/* Copy one array of level `level` to `dst` of `bytes` bytes (EINVAL if too
+ * small or out of range); *written receives the byte count. */
+ifilt_status ifilt_mesh_multigrid_export(ifilt_mesh mesh, int32_t level, int32_t what, void* dst, size_t bytes,
+                                         size_t* written);
 
 /* Filter a batch of fields at a list of wavenumbers (Eq. 1-2 solved as in
  * Sect. 2.2.2).

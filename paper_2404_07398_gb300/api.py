@@ -19,7 +19,8 @@ GEOM_PLANAR_PERIODIC, GEOM_PLANAR, GEOM_SPHERE = 0, 1, 2
 PREC_FP64, PREC_FP32_IR, PREC_BF16_IR = 0, 1, 2
 METHOD_PLAIN, METHOD_BATCHED = 0, 1
 N2_AUTO, N2_REAL, N2_COMPLEX = 0, 1, 2
-PRECOND_NONE, PRECOND_JACOBI = 0, 1
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG = 0, 1, 2
+MG_MAX_LEVELS = 16
 OK, NOT_CONVERGED = 0, 1
 EXPORT = dict(perm=0, k_rowptr=1, k_col=2, k_val=3, mass=4, g2_rowptr=5, g2_col=6, g2_val=7)
 PLACEMENTS = {"vertex_scalar": VERTEX_SCALAR, "vertex_vector": VERTEX_VECTOR, "cell": CELL}
@@ -82,8 +83,16 @@ class KernelProfile(C.Structure):
 COL_STATS_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("status", np.int32),
                             ("pad", np.int32), ("rel_residual", np.float64)])
 
+class MultigridInfo(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("rows", C.c_int32 * MG_MAX_LEVELS), ("nnz_s", C.c_int64 * MG_MAX_LEVELS),
+                ("nnz_p", C.c_int64 * MG_MAX_LEVELS)]
+
+
+MG_EXPORT = {"s_rowptr": 0, "s_col": 1, "s_val": 2, "p_rowptr": 3, "p_col": 4, "p_val": 5, "dk": 6, "dm": 7}
+
 # every symbol include/ifilt.h declares
-SYMBOLS = ["ifilt_prepare_mesh", "ifilt_prepare_mesh_host", "ifilt_mesh_upload", "ifilt_release_mesh", "ifilt_mesh_info", "ifilt_mesh_export", "ifilt_solve",
+SYMBOLS = ["ifilt_prepare_mesh", "ifilt_prepare_mesh_host", "ifilt_mesh_upload", "ifilt_release_mesh", "ifilt_mesh_info", "ifilt_mesh_export",
+           "ifilt_mesh_multigrid", "ifilt_mesh_multigrid_export", "ifilt_solve",
            "ifilt_solve_many", "ifilt_spectrum", "ifilt_spectrum_noalloc", "ifilt_solve_scratch_bytes", "ifilt_profile_enable", "ifilt_profile_read",
            "ifilt_profile_reset", "ifilt_last_error", "ifilt_version", "ifilt_server_create",
            "ifilt_server_submit", "ifilt_server_wait", "ifilt_server_forget", "ifilt_server_now",
@@ -114,6 +123,10 @@ def load(path=None):
     lib.ifilt_mesh_info.restype = i32
     lib.ifilt_mesh_export.argtypes = [vp, i32, vp, C.c_size_t]
     lib.ifilt_mesh_export.restype = i32
+    lib.ifilt_mesh_multigrid.argtypes = [vp, C.POINTER(MultigridInfo)]
+    lib.ifilt_mesh_multigrid.restype = i32
+    lib.ifilt_mesh_multigrid_export.argtypes = [vp, i32, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+    lib.ifilt_mesh_multigrid_export.restype = i32
     lib.ifilt_solve.argtypes = [vp, C.POINTER(SolveOpts), i32, vp, i32, vp, vp, vp, vp]
     lib.ifilt_solve.restype = i32
     lib.ifilt_solve_many.argtypes = [i32, C.POINTER(SolveItem), vp]
@@ -208,6 +221,30 @@ class Mesh:
         out = np.zeros(max(int(cnt), 1), dtype=dt)
         _check(load().ifilt_mesh_export(self.handle, key, _ptr(out), out.nbytes))
         return out[:cnt]
+
+    def multigrid(self):
+        """Shape of the multigrid hierarchy (built on the host if needed)."""
+        info = MultigridInfo()
+        _check(load().ifilt_mesh_multigrid(self.handle, C.byref(info)))
+        L = info.n_levels
+        return {"levels": L, "rows": list(info.rows[:L]), "nnz_s": list(info.nnz_s[:L]),
+                "nnz_p": list(info.nnz_p[:L])}
+
+    def multigrid_export(self, level, what):
+        """One array of multigrid level `level` (see MG_EXPORT)."""
+        g = self.multigrid()
+        n = g["rows"][level]
+        blk = self.info["placement"] == VERTEX_VECTOR
+        cap = {"s_rowptr": (n + 1, np.int64), "s_col": (g["nnz_s"][level], np.int32),
+               "s_val": (g["nnz_s"][level] * (4 if blk else 2), np.float64), "p_rowptr": (n + 1, np.int64),
+               "p_col": (g["nnz_p"][level], np.int32), "p_val": (g["nnz_p"][level] * (2 if blk else 1), np.float64),
+               "dk": (n, np.float64), "dm": (n, np.float64)}
+        cnt, dt = cap[what]
+        out = np.zeros(max(int(cnt), 1), dtype=dt)
+        wrote = C.c_size_t(0)
+        _check(load().ifilt_mesh_multigrid_export(self.handle, level, MG_EXPORT[what], _ptr(out), out.nbytes,
+                                                  C.byref(wrote)))
+        return out[: wrote.value // out.itemsize]
 
 
 def _desc(mesh, placement, max_order, reorder, cell_A, ell_slice):

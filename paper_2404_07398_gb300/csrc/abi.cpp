@@ -12,6 +12,7 @@
 #include <string>
 
 #include "internal.h"
+#include "multigrid.h"
 
 namespace ifilt {
 
@@ -244,6 +245,50 @@ ifilt_status ifilt_mesh_info(ifilt_mesh m, ifilt_mesh_info_t* out) {
   IFILT_GUARD_END
 }
 
+ifilt_status ifilt_mesh_multigrid(ifilt_mesh m, ifilt_multigrid_info* info) {
+  IFILT_GUARD_BEGIN
+  check_mesh(m);
+  if (!info) fail(IFILT_EINVAL, "null info");
+  const MgHost& h = multigrid_host(m);
+  std::memset(info, 0, sizeof(*info));
+  info->n_levels = (int32_t)std::min<size_t>(h.levels.size(), IFILT_MG_MAX_LEVELS);
+  for (int32_t l = 0; l < info->n_levels; l++) {
+    info->rows[l] = h.levels[l].n;
+    info->nnz_s[l] = l == 0 ? m->host.K.nnz() : h.levels[l].S.nnz();
+    info->nnz_p[l] = h.levels[l].P.nnz();
+  }
+  return IFILT_OK;
+  IFILT_GUARD_END
+}
+
+ifilt_status ifilt_mesh_multigrid_export(ifilt_mesh m, int32_t level, int32_t what, void* dst, size_t bytes,
+                                         size_t* written) {
+  IFILT_GUARD_BEGIN
+  check_mesh(m);
+  if (!dst && bytes) fail(IFILT_EINVAL, "null destination");
+  const MgHost& h = multigrid_host(m);
+  if (level < 0 || level >= (int32_t)h.levels.size()) fail(IFILT_EINVAL, "level %d outside the hierarchy", level);
+  const MgHostLevel& L = h.levels[level];
+  const void* src = nullptr;
+  size_t need = 0;
+  switch (what) {
+    case IFILT_MG_S_ROWPTR: src = L.S.row_ptr.data(); need = L.S.row_ptr.size() * 8; break;
+    case IFILT_MG_S_COL: src = L.S.col.data(); need = L.S.col.size() * 4; break;
+    case IFILT_MG_S_VAL: src = L.S.val.data(); need = L.S.val.size() * 8; break;
+    case IFILT_MG_P_ROWPTR: src = L.P.row_ptr.data(); need = L.P.row_ptr.size() * 8; break;
+    case IFILT_MG_P_COL: src = L.P.col.data(); need = L.P.col.size() * 4; break;
+    case IFILT_MG_P_VAL: src = L.P.val.data(); need = L.P.val.size() * 8; break;
+    case IFILT_MG_DK: src = L.dk.data(); need = L.dk.size() * 8; break;
+    case IFILT_MG_DM: src = L.dm.data(); need = L.dm.size() * 8; break;
+    default: fail(IFILT_EINVAL, "unknown multigrid export selector %d", what);
+  }
+  if (bytes < need) fail(IFILT_EINVAL, "destination holds %zu bytes, %zu needed", bytes, need);
+  if (need) std::memcpy(dst, src, need);
+  if (written) *written = need;
+  return IFILT_OK;
+  IFILT_GUARD_END
+}
+
 ifilt_status ifilt_mesh_export(ifilt_mesh m, int32_t what, void* dst, size_t bytes) {
   IFILT_GUARD_BEGIN
   check_mesh(m);
@@ -278,8 +323,13 @@ static void check_opts(ifilt_mesh m, const ifilt_solve_opts* o) {
   if (o->n2_solver < IFILT_N2_AUTO || o->n2_solver > IFILT_N2_COMPLEX) fail(IFILT_EINVAL, "unknown n2_solver");
   if (o->method == IFILT_METHOD_PLAIN && o->precision != IFILT_PREC_FP64)
     fail(IFILT_EINVAL, "the plain method runs in FP64 only");
-  if (o->precond != IFILT_PRECOND_NONE && o->precond != IFILT_PRECOND_JACOBI)
+  if (o->precond < IFILT_PRECOND_NONE || o->precond > IFILT_PRECOND_MG)
     fail(IFILT_EINVAL, "unknown precond %d", o->precond);
+  if (o->precond == IFILT_PRECOND_MG) {
+    if (o->precision == IFILT_PREC_FP64) fail(IFILT_EINVAL, "multigrid preconditioning runs with FP32 or BF16 precision");
+    if (o->order >= 2 && o->n2_solver == IFILT_N2_REAL)
+      fail(IFILT_EINVAL, "multigrid preconditioning needs order 1 or the complex n = 2 form");
+  }
   if (o->method == IFILT_METHOD_PLAIN && o->precond != IFILT_PRECOND_NONE)
     fail(IFILT_EINVAL, "the plain method takes no preconditioner");
   if (o->max_iter < 0 || o->check_every < 0 || o->max_lanes < 0 || o->inner_tol < 0)

@@ -219,6 +219,23 @@ __device__ __forceinline__ T cvt(MV v) {
   else return (T)v;
 }
 
+// Epilogues of the gather kernel.  CG: q = M p + s (G p) with <p, q>.  The
+// multigrid operations on a level operator S = M + s K (M the lumped mass on
+// the finest level, a sparse matrix on the coarser ones):
+//   SMOOTH    out = x + w D^-1 (rhs - S x)   (damped Jacobi; optionally <rhs, out>)
+//   RESID     out = rhs - S x
+//   RESTRICT  out = R t                      (gather of the finer level)
+//   PROLONG   out = y + P x_c                (gather of the coarser level)
+constexpr int kEpiCG = 0, kEpiSmooth = 1, kEpiResid = 2, kEpiRestrict = 3, kEpiProlong = 4;
+
+template <typename T>
+struct MgArgs {
+  const T* dk;    // diagonal of K_l (SMOOTH)
+  const T* rhs;   // right-hand side of the level (SMOOTH, RESID)
+  const T* own;   // y of PROLONG
+  T omega;        // Jacobi weight (SMOOTH)
+};
+
 // q = M p + shift * acc for one row (all sub-rows), and the row's share of
 // <p, q>: the row's few terms are summed in FP32, then added to the
 // compensated per-thread accumulator.
@@ -262,6 +279,76 @@ __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, in
   if constexpr (CPLX || NS > 1) {
 #pragma unroll
     for (int v = 0; v < VEC; v++) dacc[v].add_sum(rowdot[v]);
+  }
+}
+
+// Multigrid epilogue for one row: acc holds the K part of the gather (or the
+// whole gather for RESTRICT / PROLONG), accm the M part on coarse levels
+// (NSET = 2); own is x_r (SMOOTH, RESID) or y_r (PROLONG); mdiag is the
+// diagonal of M_l (the lumped mass on the finest level).
+template <typename T, bool CPLX, bool BLK, int EPI, int NSET>
+__device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int l0, const T* __restrict__ mdiag,
+                                            const T* sh, T (*acc)[Pack<T>::N], T (*accm)[Pack<T>::N],
+                                            const Pack<T>* own, const MgArgs<T>& g, T* __restrict__ out,
+                                            DotAcc<T>* dacc, bool dot) {
+  constexpr int VEC = Pack<T>::N;
+  constexpr int NS = BLK ? 2 : 1;
+  T mr = (T)0, gr = (T)0;
+  if constexpr (EPI == kEpiSmooth || EPI == kEpiResid) mr = mdiag[r];
+  if constexpr (EPI == kEpiSmooth) gr = g.dk[r];
+  T rowdot[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; v++) rowdot[v] = (T)0;
+#pragma unroll
+  for (int b = 0; b < NS; b++) {
+    const int64_t off = r * rowW + (int64_t)b * W + l0;
+    Pack<T> o;
+    if constexpr (EPI == kEpiRestrict) {
+#pragma unroll
+      for (int v = 0; v < VEC; v++) o.v[v] = acc[b][v];
+    } else if constexpr (EPI == kEpiProlong) {
+#pragma unroll
+      for (int v = 0; v < VEC; v++) o.v[v] = own[b].v[v] + acc[b][v];
+    } else {
+      const Pack<T> rh = ldv(g.rhs + off);
+      T res[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; v++) {
+        const T mx = NSET == 2 ? accm[b][v] : mr * own[b].v[v];
+        T sx;
+        if constexpr (CPLX) sx = (v & 1) ? mx + sh[v] * acc[b][v - 1] : mx - sh[v] * acc[b][v + 1];
+        else sx = madd(sh[v], acc[b][v], mx);
+        res[v] = rh.v[v] - sx;
+      }
+      if constexpr (EPI == kEpiResid) {
+#pragma unroll
+        for (int v = 0; v < VEC; v++) o.v[v] = res[v];
+      } else {
+        T z[VEC];
+        jacobi<T, CPLX, VEC>(mr, gr, sh, res, z);
+#pragma unroll
+        for (int v = 0; v < VEC; v++) o.v[v] = madd(g.omega, z[v], own[b].v[v]);
+        if (dot) {
+          if constexpr (CPLX) {
+#pragma unroll
+            for (int v = 0; v < VEC; v += 2) {
+              rowdot[v] = madd(rh.v[v], o.v[v], madd(-rh.v[v + 1], o.v[v + 1], rowdot[v]));
+              rowdot[v + 1] = madd(rh.v[v], o.v[v + 1], madd(rh.v[v + 1], o.v[v], rowdot[v + 1]));
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < VEC; v++) rowdot[v] = madd(rh.v[v], o.v[v], rowdot[v]);
+          }
+        }
+      }
+    }
+    stp(out + off, o);
+  }
+  if constexpr (EPI == kEpiSmooth) {
+    if (dot) {
+#pragma unroll
+      for (int v = 0; v < VEC; v++) dacc[v].add_sum(rowdot[v]);
+    }
   }
 }
 
@@ -321,14 +408,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // works on the previous tile, so a row waits on one round of global loads: its
 // own row of p and all gathered neighbour rows (EB entries at a time) are
 // issued before any of them is used.
-template <typename T, typename MV, bool CPLX, bool BLK, int EB, int MINB>
+template <typename T, typename MV, bool CPLX, bool BLK, int EB, int MINB, int EPI = kEpiCG, int NSET = 1>
 __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Params P, int n_slices, const T* __restrict__ p,
                                                          T* __restrict__ q, const T* __restrict__ mass,
-                                                         Cols C, double* __restrict__ partial) {
+                                                         Cols C, double* __restrict__ partial, MgArgs<T> mg) {
   if (*C.live == 0) return;
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
-  constexpr int NV = BLK ? 2 : 1;
+  constexpr int NV = (BLK ? 2 : 1) * NSET;  // values per ELL entry
+  constexpr int NB = BLK ? 2 : 1;           // values of one operator per entry
+  const bool dot = EPI == kEpiCG || (EPI == kEpiSmooth && partial != nullptr);
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_w[2][kMaxSpt], s_o[2][kMaxSpt];
   __shared__ __align__(8) uint64_t bar[2];
@@ -422,13 +511,18 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
         const int w = s_w[b][sl];
         const int eb = s_o[b][sl] + (lr - sl * H) * w;
         Pack<T> pr[NS];
+        if constexpr (EPI == kEpiProlong) {
 #pragma unroll
-        for (int s = 0; s < NS; s++) pr[s] = ldp(p + r * rowW + (int64_t)s * W + l0);
-        T acc[NS][VEC];
+          for (int s = 0; s < NS; s++) pr[s] = ldv(mg.own + r * rowW + (int64_t)s * W + l0);
+        } else if constexpr (EPI != kEpiRestrict) {
+#pragma unroll
+          for (int s = 0; s < NS; s++) pr[s] = ldp(p + r * rowW + (int64_t)s * W + l0);
+        }
+        T acc[NS][VEC], accm[NS][VEC];
 #pragma unroll
         for (int s = 0; s < NS; s++)
 #pragma unroll
-          for (int v = 0; v < VEC; v++) acc[s][v] = (T)0;
+          for (int v = 0; v < VEC; v++) acc[s][v] = accm[s][v] = (T)0;
         for (int e = 0; e < w; e += EB) {
           Pack<T> nb[EB][NS];
 #pragma unroll
@@ -449,16 +543,29 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
 #pragma unroll
               for (int t = 0; t < 4; t++) {
                 if constexpr (BLK) {
-                  const T a = cvt<T>(vv[2 * t]), bb = cvt<T>(vv[2 * t + 1]);
+                  const T a = cvt<T>(vv[NV * t]), bb = cvt<T>(vv[NV * t + 1]);
 #pragma unroll
                   for (int v = 0; v < VEC; v++) {
                     acc[0][v] = madd(a, nb[h + t][0].v[v], madd(bb, nb[h + t][1].v[v], acc[0][v]));
                     acc[1][v] = madd(a, nb[h + t][1].v[v], madd(-bb, nb[h + t][0].v[v], acc[1][v]));
                   }
+                  if constexpr (NSET == 2) {
+                    const T am = cvt<T>(vv[NV * t + NB]), bm = cvt<T>(vv[NV * t + NB + 1]);
+#pragma unroll
+                    for (int v = 0; v < VEC; v++) {
+                      accm[0][v] = madd(am, nb[h + t][0].v[v], madd(bm, nb[h + t][1].v[v], accm[0][v]));
+                      accm[1][v] = madd(am, nb[h + t][1].v[v], madd(-bm, nb[h + t][0].v[v], accm[1][v]));
+                    }
+                  }
                 } else {
-                  const T a = cvt<T>(vv[t]);
+                  const T a = cvt<T>(vv[NV * t]);
 #pragma unroll
                   for (int v = 0; v < VEC; v++) acc[0][v] = madd(a, nb[h + t][0].v[v], acc[0][v]);
+                  if constexpr (NSET == 2) {
+                    const T am = cvt<T>(vv[NV * t + NB]);
+#pragma unroll
+                    for (int v = 0; v < VEC; v++) accm[0][v] = madd(am, nb[h + t][0].v[v], accm[0][v]);
+                  }
                 }
               }
             }
@@ -466,10 +573,13 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
         }
         if (++chain == kFlushRows) {
           chain = 0;
+          if (dot) {
 #pragma unroll
-          for (int v = 0; v < VEC; v++) dacc[v].spill(sred[tr * W + l0 + v]);
+            for (int v = 0; v < VEC; v++) dacc[v].spill(sred[tr * W + l0 + v]);
+          }
         }
-        spmm_epilogue<T, CPLX, BLK>(r, rowW, W, l0, mass, sh, acc, pr, q, dacc);
+        if constexpr (EPI == kEpiCG) spmm_epilogue<T, CPLX, BLK>(r, rowW, W, l0, mass, sh, acc, pr, q, dacc);
+        else mg_epilogue<T, CPLX, BLK, EPI, NSET>(r, rowW, W, l0, mass, sh, acc, accm, pr, mg, q, dacc, dot);
       }
     }
     if ((int)threadIdx.x < ncnt) {
@@ -488,6 +598,7 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
     }
     return;
   }
+  if (!dot) return;
   if (on) {
 #pragma unroll
     for (int v = 0; v < VEC; v++) dacc[v].spill(sred[tr * W + l0 + v]);
@@ -1308,7 +1419,7 @@ class EngineT final : public Engine {
   // SpMM instance: gathers issued EB entries at a time (4 when no row holds
   // more, as for the cell operator); FP32 2x2 blocks trade occupancy for more
   // loads in flight per thread.
-  using SpmmFn = void (*)(EllView<MV>, Params, int, const T*, T*, const T*, Cols, double*);
+  using SpmmFn = void (*)(EllView<MV>, Params, int, const T*, T*, const T*, Cols, double*, MgArgs<T>);
   static constexpr int kMinB = (BLK && sizeof(T) == 4) ? IFILT_SPMM_MINB_BLK : IFILT_SPMM_MINB;
   SpmmFn spmm_fn() const {
     if constexpr (sizeof(T) == 8) return spmm_kernel<T, MV, CPLX, BLK, 4, kMinB>;
@@ -1421,8 +1532,8 @@ class EngineT final : public Engine {
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
     for (int it = 0; it < m_it_; it++) {
       if (it == 0) rec(0);
-      spmm_fn()<<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), C_,
-                                                                partial_);
+      spmm_fn()<<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), C_, partial_,
+                                            MgArgs<T>{});
       chk("spmm");
       if (it == 0) rec(1);
       finish_alpha_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);

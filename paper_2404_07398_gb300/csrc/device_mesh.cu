@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "multigrid.h"
 
 namespace ifilt {
 namespace {
@@ -25,7 +26,10 @@ T* dev_copy(ifilt_mesh_s* m, const T* src, size_t count, cudaStream_t st) {
 // Sliced ELL from CSR; padding entries point at their own row with value 0.
 // Every slice starts on an 8-entry boundary (so any run of slices can be
 // bulk-copied with 16-byte aligned addresses and sizes for every value type).
-void build_ell(ifilt_mesh_s* m, const HostCSR& a, int32_t slice_h, DevEll& out, cudaStream_t st) {
+// `ncols` >= 0 marks a rectangular matrix: its padding entries repeat the
+// row's last column (0 for an empty row) so that they stay inside the source.
+void build_ell(ifilt_mesh_s* m, const HostCSR& a, int32_t slice_h, DevEll& out, cudaStream_t st,
+               int32_t ncols = -1) {
   const int32_t n = a.n, nv = a.nval;
   const int32_t ns = (n + slice_h - 1) / slice_h;
   std::vector<int64_t> off((size_t)ns + 1, 0);
@@ -52,8 +56,10 @@ void build_ell(ifilt_mesh_s* m, const HostCSR& a, int32_t slice_h, DevEll& out, 
         if (e < len) {
           col[base + e] = a.col[a.row_ptr[r] + e];
           for (int q = 0; q < nv; q++) v64[(size_t)(base + e) * nv + q] = a.val[(size_t)(a.row_ptr[r] + e) * nv + q];
-        } else {
+        } else if (ncols < 0) {
           col[base + e] = r;
+        } else {
+          col[base + e] = len > 0 ? a.col[a.row_ptr[r] + len - 1] : 0;
         }
       }
     }
@@ -164,6 +170,37 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
   std::vector<int32_t> ip((size_t)h.n_out, -1);
   for (int32_t r = 0; r < h.n_rows; r++) ip[h.perm[r]] = r;
   m->inv_perm = dev_copy(m, ip.data(), ip.size(), st);
+}
+
+const MgHost& multigrid_host(ifilt_mesh_s* m) {
+  std::lock_guard<std::mutex> lk(m->mg_mu);
+  if (!m->mg_host) m->mg_host = std::make_shared<MgHost>(build_multigrid(m->host, MgParams{}));
+  return *m->mg_host;
+}
+
+const std::vector<DevMgLevel>& multigrid_device(ifilt_mesh_s* m, cudaStream_t st) {
+  const MgHost& h = multigrid_host(m);
+  std::lock_guard<std::mutex> lk(m->mg_mu);
+  if (!m->mg_dev.empty()) return m->mg_dev;
+  if (m->device < 0) fail(IFILT_EINVAL, "mesh is not uploaded");
+  // coarse levels are small and their rows wide: short slices keep a stage small
+  constexpr int32_t kMgSlice = 16;
+  std::vector<DevMgLevel> dev(h.levels.size());
+  for (size_t l = 0; l < h.levels.size(); l++) {
+    const MgHostLevel& L = h.levels[l];
+    DevMgLevel& D = dev[l];
+    D.n = L.n;
+    if (l > 0) build_ell(m, L.S, kMgSlice, D.S, st);
+    if (l + 1 < h.levels.size()) {
+      build_ell(m, L.P, kMgSlice, D.P, st, h.levels[l + 1].n);
+      build_ell(m, L.R, kMgSlice, D.R, st, L.n);
+    }
+    std::vector<float> dk(L.dk.begin(), L.dk.end()), dm(L.dm.begin(), L.dm.end());
+    D.dk32 = dev_copy(m, dk.data(), dk.size(), st);
+    D.dm32 = dev_copy(m, dm.data(), dm.size(), st);
+  }
+  m->mg_dev = std::move(dev);
+  return m->mg_dev;
 }
 
 void free_mesh(ifilt_mesh_s* m) {

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -71,6 +73,18 @@ struct DevEll {
   __nv_bfloat16* val16 = nullptr;
 };
 
+// One level of the multigrid preconditioner on the device: the pair
+// (K_l, M_l) as one ELL with both values per entry (level 0 uses the mesh's
+// K and lumped mass instead), the prolongation P_l (rows of level l) and the
+// restriction R_l = P_l^T (rows of level l+1), FP32 diagonals of K_l and M_l.
+struct DevMgLevel {
+  int32_t n = 0;
+  DevEll S, P, R;
+  float* dk32 = nullptr;
+  float* dm32 = nullptr;
+};
+struct MgHost;  // multigrid.h
+
 struct DevCSR {
   int32_t n = 0;          // rows of the real (expanded) matrix
   int64_t nnz = 0;
@@ -102,6 +116,10 @@ struct ifilt_mesh_s {
   int32_t* inv_perm = nullptr;   // [n_out] device row of each output entry, -1 where not an unknown
   ifilt::DevEll ell_k, ell_g2;
   ifilt::DevCSR csr_k, csr_g2;   // real expanded CSR in FP64 (vector placement: interleaved u,v rows)
+  // multigrid preconditioner, built on first use (host) and uploaded on first device use
+  std::mutex mg_mu;
+  std::shared_ptr<ifilt::MgHost> mg_host;
+  std::vector<ifilt::DevMgLevel> mg_dev;
 };
 
 namespace ifilt {
@@ -109,6 +127,9 @@ namespace ifilt {
 // device upload (device_mesh.cu)
 void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st);
 void free_mesh(ifilt_mesh_s* m);
+// multigrid hierarchy of a mesh: built on the host once, uploaded once
+const MgHost& multigrid_host(ifilt_mesh_s* m);
+const std::vector<DevMgLevel>& multigrid_device(ifilt_mesh_s* m, cudaStream_t st);
 
 // solvers (solve_plain.cu, solve_batched.cu)
 ifilt_status solve_plain(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, const double* fields,

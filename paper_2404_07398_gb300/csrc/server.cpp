@@ -250,7 +250,10 @@ ifilt_status ifilt_server_submit(ifilt_server s, ifilt_mesh mesh, const ifilt_so
     if (o->order < 1 || o->order > mesh->host.max_order) fail(IFILT_EINVAL, "order outside the mesh's range");
     if (!(o->tol > 0.0)) fail(IFILT_EINVAL, "tol must be positive");
     if (o->precision < IFILT_PREC_FP64 || o->precision > IFILT_PREC_BF16_IR) fail(IFILT_EINVAL, "unknown precision");
-    if (o->precond != IFILT_PRECOND_NONE && o->precond != IFILT_PRECOND_JACOBI) fail(IFILT_EINVAL, "unknown precond");
+    if (o->precond < IFILT_PRECOND_NONE || o->precond > IFILT_PRECOND_MG) fail(IFILT_EINVAL, "unknown precond");
+    if (o->precond == IFILT_PRECOND_MG &&
+        (o->precision == IFILT_PREC_FP64 || (o->order >= 2 && o->n2_solver == IFILT_N2_REAL)))
+      fail(IFILT_EINVAL, "multigrid preconditioning needs FP32/BF16 and order 1 or the complex n = 2 form");
     for (int32_t j = 0; j < n_k; j++)
       if (!(k[j] > 0.0)) fail(IFILT_EINVAL, "k must be positive");
     std::lock_guard<std::mutex> lk(s->mu);

@@ -1,0 +1,127 @@
+"""Multigrid hierarchy built by the library on the host (no GPU).
+
+The hierarchy only preconditions the Krylov iteration, so the filtered fields
+do not depend on it; what is pinned here is that it is the smoothed-aggregation
+construction it claims to be:
+  * the level operators are Galerkin products R (K, M) P of the level above,
+    recomputed here with scipy from the exported P and the prepared K and
+    lumped mass (for the vertex-vector placement in the real 2x2-block form);
+  * for the scalar placements constants are kept: K 1 = 0 on every level and
+    P 1 = 1 (the prolongator smoothing does not disturb the near-null space),
+    so M keeps the total area;
+  * the hierarchy coarsens to a small last level and is deterministic.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2404_07398_gb300 import api as a
+    a.load()
+    return a
+
+
+def _mesh(level, seed):
+    m = synth.icosphere(level, radius=6371.0, jitter=0.2, seed=seed)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=seed + 1, polar_cap_deg=8.0)
+    return m
+
+
+def _csr(rowptr, col, val, shape):
+    return sp.csr_matrix((val, col, rowptr), shape=shape)
+
+
+def _blocks(rowptr, col, ab, shape):
+    """Real matrix of 2x2 blocks [[a, b], [-b, a]] (u block first, then v)."""
+    a, b = ab[0::2], ab[1::2]
+    A = _csr(rowptr, col, a, shape)
+    B = _csr(rowptr, col, b, shape)
+    return sp.bmat([[A, B], [-B, A]]).tocsr()
+
+
+def _level0(h):
+    n = h.info["n_rows"]
+    K = h.export("k_val")
+    rp, cl = h.export("k_rowptr"), h.export("k_col")
+    return rp, cl, K, h.export("mass"), n
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "cell", "vertex_vector"])
+def test_galerkin_products_and_constants(api, placement):
+    h = api.prepare_mesh_host(_mesh(4, 31), placement, max_order=1)
+    g = h.multigrid()
+    L = g["levels"]
+    assert L >= 3
+    rows = g["rows"]
+    assert all(rows[i + 1] * 1.25 <= rows[i] for i in range(L - 1))
+    assert rows[-1] <= 64 or L == api.MG_MAX_LEVELS
+    blk = placement == "vertex_vector"
+    rp, cl, kv, mass, n = _level0(h)
+    if blk:
+        K = _blocks(rp, cl, kv, (n, n))
+        M = sp.diags(np.concatenate([mass, mass])).tocsr()
+    else:
+        K = _csr(rp, cl, kv, (n, n))
+        M = sp.diags(mass).tocsr()
+    area = mass.sum() * (2 if blk else 1)
+    for level in range(L - 1):
+        nf, nc = rows[level], rows[level + 1]
+        prp, pcl, pv = (h.multigrid_export(level, w) for w in ("p_rowptr", "p_col", "p_val"))
+        P = _blocks(prp, pcl, pv, (nf, nc)) if blk else _csr(prp, pcl, pv, (nf, nc))
+        if not blk:
+            # constants: K 1 = 0 and P 1 = 1.  (The vector Laplacian's metric
+            # terms move its near-null space off the constants; no such check.)
+            one_f, one_c = np.ones(K.shape[0]), np.ones(P.shape[1])
+            assert np.abs(K @ one_f).max() <= 1e-12 * abs(K).max()
+            assert np.abs(P @ one_c - one_f).max() <= 1e-12
+        Kc = (P.T @ K @ P).tocsr()
+        Mc = (P.T @ M @ P).tocsr()
+        srp, scl, sv = (h.multigrid_export(level + 1, w) for w in ("s_rowptr", "s_col", "s_val"))
+        if blk:
+            Kl = _blocks(srp, scl, np.stack([sv[0::4], sv[1::4]], 1).ravel(), (nc, nc))
+            Ml = _blocks(srp, scl, np.stack([sv[2::4], sv[3::4]], 1).ravel(), (nc, nc))
+        else:
+            Kl = _csr(srp, scl, sv[0::2], (nc, nc))
+            Ml = _csr(srp, scl, sv[1::2], (nc, nc))
+        assert abs(Kl - Kc).max() <= 1e-11 * abs(Kc).max()
+        assert abs(Ml - Mc).max() <= 1e-11 * abs(Mc).max()
+        assert abs(Kl - Kl.T).max() <= 1e-11 * abs(Kl).max()
+        if not blk:
+            assert abs(Ml.sum() - area) <= 1e-10 * area
+        # diagonals reported for the Jacobi smoother
+        dk, dm = h.multigrid_export(level + 1, "dk"), h.multigrid_export(level + 1, "dm")
+        np.testing.assert_allclose(dk, Kl.diagonal()[:nc], rtol=0, atol=1e-12 * abs(Kl).max())
+        np.testing.assert_allclose(dm, Ml.diagonal()[:nc], rtol=0, atol=1e-12 * abs(Ml).max())
+        K, M = Kl, Ml
+
+
+def test_hierarchy_is_deterministic(api):
+    m = _mesh(3, 33)
+    a = api.prepare_mesh_host(m, "cell", max_order=1)
+    b = api.prepare_mesh_host(m, "cell", max_order=1)
+    ga, gb = a.multigrid(), b.multigrid()
+    assert ga == gb
+    for level in range(ga["levels"] - 1):
+        for w in ("p_col", "p_val"):
+            assert np.array_equal(a.multigrid_export(level, w), b.multigrid_export(level, w))
+
+
+def test_multigrid_export_checks(api):
+    h = api.prepare_mesh_host(_mesh(2, 35), "vertex_scalar", max_order=1)
+    g = h.multigrid()
+    import ctypes
+    lib = api.load()
+    buf = np.zeros(1 << 16)
+    wrote = ctypes.c_size_t(0)
+    ok = lib.ifilt_mesh_multigrid_export(h.handle, 0, 6, buf.ctypes.data, buf.nbytes, ctypes.byref(wrote))
+    assert ok == 0 and wrote.value == 8 * g["rows"][0]
+    assert lib.ifilt_mesh_multigrid_export(h.handle, g["levels"], 6, buf.ctypes.data, buf.nbytes, None) == -1
+    assert lib.ifilt_mesh_multigrid_export(h.handle, 0, 99, buf.ctypes.data, buf.nbytes, None) == -1
+    assert lib.ifilt_mesh_multigrid_export(h.handle, 0, 6, buf.ctypes.data, 8, None) == -1
