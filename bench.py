@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain-sample", type=int, default=3, help="scales (1-3) timed on the plain FP64 path")
     ap.add_argument("--serving", action="store_true", help="run the request-serving workload instead")
-    ap.add_argument("--precond", choices=["none", "jacobi"], default="none", help="Krylov preconditioner")
+    ap.add_argument("--precond", choices=["none", "jacobi", "mg"], default="none", help="Krylov preconditioner")
     ap.add_argument("--concurrent", action="store_true",
                     help="step the two placements' solvers together (one solve_many call); per-kernel "
                          "event timings then overlap, so the roofline is not measured")
@@ -199,7 +199,8 @@ class Ours:
         self.prepare_s = time.time() - t0
         prec = {"fp32": api.PREC_FP32_IR, "bf16": api.PREC_BF16_IR, "fp64": api.PREC_FP64}[args.precision]
         self.opts = dict(order=2, tol=args.tol, precision=prec, n2_solver=api.N2_COMPLEX,
-                         precond={"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI}[args.precond])
+                         precond={"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI,
+                                  "mg": api.PRECOND_MG}[args.precond])
         K = self.k.size
         self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
         self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
@@ -255,8 +256,8 @@ def roofline(api, peak_gbs, peak_kind):
     recs = api.profile_read()
     best = None
     for r in recs:
-        if r["samples"] == 0 or r["launches"] == 0:
-            continue
+        if r["samples"] == 0 or r["launches"] == 0 or r["name"].startswith("("):
+            continue  # "(...)": totals or multi-kernel spans, not one kernel
         avg_ms = r["sampled_ms"] / r["samples"]
         total = avg_ms * r["launches"]
         if best is None or total > best[0]:
@@ -266,11 +267,13 @@ def roofline(api, peak_gbs, peak_kind):
     _, r, avg_ms = best
     achieved = r["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
     shares, kernels = {}, {}
-    tot = sum(x["sampled_ms"] / x["samples"] * x["launches"] for x in recs if x["samples"])
+    single = [x for x in recs if x["samples"] and not x["name"].startswith("(")]
+    tot = sum(x["sampled_ms"] / x["samples"] * x["launches"] for x in single)
     for x in recs:
         if x["samples"]:
             a = x["sampled_ms"] / x["samples"]
-            shares[x["name"]] = round(a * x["launches"] / tot, 4)
+            if not x["name"].startswith("("):
+                shares[x["name"]] = round(a * x["launches"] / tot, 4)
             kernels[x["name"]] = {"avg_launch_ms": round(a, 4), "launches": int(x["launches"]),
                                   "gbs": round(x["bytes_per_launch"] / (a * 1e-3) / 1e9, 1)}
     ratio = TRAFFIC_RATIO.get(r["name"])

@@ -195,6 +195,7 @@ struct Cols {
   int* refresh;     // column waits for its FP64 true residual / next refinement round
   int* round_it0;   // iteration count when the current inner round started
   int* round_cap;   // iterations allowed in the current inner round
+  int* restart;     // multigrid: the next direction restarts (beta = 0)
   int* live;        // [4] number of active columns, columns to refresh, columns not done; device error flag
 };
 
@@ -206,6 +207,7 @@ struct Params {
   int maxit;
   double tol2_rel;  // tol^2
   double inner2;    // inner_tol^2 (0: run to the outer tolerance)
+  int mg;           // multigrid-preconditioned iteration order
   int spt;          // ELL slices per SpMM tile
   int wmax;         // widest ELL slice
   int stage_e;      // ELL entries one SpMM stage buffer holds
@@ -819,15 +821,17 @@ __global__ void finish_beta_kernel(Params P, int nb, const double* __restrict__ 
   if (threadIdx.y != 0 || !ok) return;
   double br = 0.0, bi = 0.0;
   if (C.active[col]) {
-    const double orr = C.rho[2 * col], ori = C.rho[2 * col + 1];
-    if (CPLX) cdiv(rre, rim, orr, ori, br, bi);
-    else br = rre / orr;
-    C.rho[2 * col] = rre;
-    C.rho[2 * col + 1] = rim;
+    if (!P.mg) {  // multigrid: rho and beta come from <r, z> (finish_rho_kernel)
+      const double orr = C.rho[2 * col], ori = C.rho[2 * col + 1];
+      if (CPLX) cdiv(rre, rim, orr, ori, br, bi);
+      else br = rre / orr;
+      C.rho[2 * col] = rre;
+      C.rho[2 * col + 1] = rim;
+    }
     C.rn2[col] = n2;
     const int it = ++C.iters[col];
     bool stop = false;
-    if (!(isfinite(n2) && isfinite(br) && isfinite(bi))) {
+    if (!(isfinite(n2) && isfinite(br) && isfinite(bi))) {  // (br, bi stay 0 under multigrid)
       C.status[col] = 2;
       C.done[col] = 1;
       stop = true;
@@ -1082,7 +1086,75 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
   C.round_it0[col] = C.iters[col];
   C.rounds[col]++;
   C.active[col] = 1;
+  C.restart[col] = P.mg;
   atomicAdd(C.live, 1);
+}
+
+// Multigrid order: beta = <r, z>_new / <r, z>_old from the partials of the
+// last smoothing sweep (z the V-cycle of r); beta = 0 on a restarted column.
+template <bool CPLX>
+__global__ void finish_rho_kernel(Params P, int nb, const double* __restrict__ partial, Cols C) {
+  __shared__ double buf[8][33];
+  const int col = blockIdx.x * 32 + threadIdx.x;
+  const bool ok = col < P.ncols;
+  const double zre = reduce_slot(partial, nb, P.pstride, ok ? (CPLX ? 2 * col : col) : -1, buf);
+  const double zim = CPLX ? reduce_slot(partial, nb, P.pstride, ok ? 2 * col + 1 : -1, buf) : 0.0;
+  if (threadIdx.y != 0 || !ok) return;
+  double br = 0.0, bi = 0.0;
+  if (C.active[col]) {
+    if (!(isfinite(zre) && isfinite(zim)) || (zre == 0.0 && zim == 0.0)) {
+      C.active[col] = 0;
+      C.done[col] = 1;
+      C.status[col] = 2;
+      atomicSub(C.live, 1);
+    } else {
+      if (C.restart[col]) {
+        C.restart[col] = 0;
+      } else {
+        const double orr = C.rho[2 * col], ori = C.rho[2 * col + 1];
+        if (CPLX) cdiv(zre, zim, orr, ori, br, bi);
+        else br = zre / orr;
+      }
+      C.rho[2 * col] = zre;
+      C.rho[2 * col + 1] = zim;
+    }
+  }
+  C.beta[2 * col] = br;
+  C.beta[2 * col + 1] = bi;
+}
+
+// x = w D^-1 rhs on a multigrid level (the first smoothing sweep from zero)
+template <typename T, bool CPLX, bool BLK>
+__global__ void __launch_bounds__(kBlock) mg_jacobi_kernel(Params P, const T* __restrict__ rhs, T* __restrict__ x,
+                                                           const T* __restrict__ mdiag, const T* __restrict__ kdiag,
+                                                           Cols C, T omega) {
+  if (*C.live == 0) return;
+  constexpr int VEC = Pack<T>::N;
+  constexpr int NS = BLK ? 2 : 1;
+  const int W = P.W;
+  const int TPR = W / VEC;
+  const int RPP = kBlock / TPR;
+  const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
+  if (tr >= RPP) return;
+  const int l0 = g * VEC;
+  T sh[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; v++) sh[v] = (T)C.shift[CPLX ? (l0 + v) >> 1 : l0 + v];
+  const int64_t rowW = (int64_t)NS * W;
+  for (int64_t row = (int64_t)blockIdx.x * RPP + tr; row < P.n; row += (int64_t)gridDim.x * RPP) {
+    const T mr = mdiag[row], kr = kdiag[row];
+#pragma unroll
+    for (int b = 0; b < NS; b++) {
+      const int64_t off = row * rowW + (int64_t)b * W + l0;
+      const Pack<T> rv = ldv(rhs + off);
+      T z[VEC];
+      jacobi<T, CPLX, VEC>(mr, kr, sh, rv.v, z);
+      Pack<T> o;
+#pragma unroll
+      for (int v = 0; v < VEC; v++) o.v[v] = omega * z[v];
+      stp(x + off, o);
+    }
+  }
 }
 
 // x64 += d on the lanes of refreshed columns
@@ -1201,11 +1273,12 @@ Tiles<T> alloc_tiles(int64_t n, int NS, int W, cudaStream_t st) {
 // Host copy of the per-column state, for retiring and re-packing columns.
 struct HostCols {
   std::vector<double> shift, rho, alpha, beta, rn2, target2, r0n2, tol2, rel;
-  std::vector<int> active, done, iters, rounds, status, refresh, round_it0, round_cap;
+  std::vector<int> active, done, iters, rounds, status, refresh, round_it0, round_cap, restart;
   void resize(int n) {
     for (auto* v : {&shift, &rn2, &target2, &r0n2, &tol2, &rel}) v->assign(n, 0.0);
     for (auto* v : {&rho, &alpha, &beta}) v->assign(2 * n, 0.0);
-    for (auto* v : {&active, &done, &iters, &rounds, &status, &refresh, &round_it0, &round_cap}) v->assign(n, 0);
+    for (auto* v : {&active, &done, &iters, &rounds, &status, &refresh, &round_it0, &round_cap, &restart})
+      v->assign(n, 0);
   }
   // entry j of this <- entry c of h
   void take(int j, const HostCols& h, int c) {
@@ -1228,6 +1301,7 @@ struct HostCols {
     refresh[j] = h.refresh[c];
     round_it0[j] = h.round_it0[c];
     round_cap[j] = h.round_cap[c];
+    restart[j] = h.restart[c];
   }
 };
 
@@ -1253,6 +1327,7 @@ void cols_download(const Cols& C, HostCols& H, int n, cudaStream_t st) {
   dn(H.refresh.data(), C.refresh, n * 4);
   dn(H.round_it0.data(), C.round_it0, n * 4);
   dn(H.round_cap.data(), C.round_cap, n * 4);
+  dn(H.restart.data(), C.restart, n * 4);
   IFILT_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -1277,6 +1352,7 @@ void cols_upload(const Cols& C, const HostCols& H, int n, cudaStream_t st) {
   up(C.refresh, H.refresh.data(), n * 4);
   up(C.round_it0, H.round_it0.data(), n * 4);
   up(C.round_cap, H.round_cap.data(), n * 4);
+  up(C.restart, H.restart.data(), n * 4);
   IFILT_CUDA(cudaStreamSynchronize(st));  // the host vectors must outlive the copies
 }
 
@@ -1324,7 +1400,7 @@ class EngineT final : public Engine {
                                     (int)(kBlock * VEC * sizeof(double) +
                                           2 * std::max(stage_bytes(1), (size_t)kStageBytes))));
     // fixed part: partial sums, column state, tables
-    size_t total = (size_t)nb_max_ * 2 * wcap_ * 8 + (size_t)ncap_ * (8 * 16 + 4 * 10 + 4 * 8) +
+    size_t total = (size_t)nb_max_ * 2 * wcap_ * 8 * 2 + (size_t)ncap_ * (8 * 16 + 4 * 12 + 4 * 8) +
                    (size_t)wcap_ * 8 + 64 * 256;
     char* cur = (char*)scratch_alloc(total, st_);
     fixed_ = cur;
@@ -1335,6 +1411,7 @@ class EngineT final : public Engine {
       return (void*)p;
     };
     partial_ = (double*)take((size_t)nb_max_ * 2 * wcap_ * 8);
+    partial2_ = (double*)take((size_t)nb_max_ * 2 * wcap_ * 8);
     C_.shift = (double*)take(ncap_ * 8);
     C_.rho = (double*)take(2 * ncap_ * 8);
     C_.alpha = (double*)take(2 * ncap_ * 8);
@@ -1352,6 +1429,7 @@ class EngineT final : public Engine {
     C_.refresh = (int*)take(ncap_ * 4);
     C_.round_it0 = (int*)take(ncap_ * 4);
     C_.round_cap = (int*)take(ncap_ * 4);
+    C_.restart = (int*)take(ncap_ * 4);
     C_.live = (int*)take(4 * 4);
     lane_src_ = (int*)take(wcap_ * 4);
     lane_map_ = (int*)take(wcap_ * 4);
@@ -1371,6 +1449,8 @@ class EngineT final : public Engine {
     m_it_ = o.check_every > 0 ? o.check_every : 32;
     const char* ng = getenv("IFILT_NO_GRAPH");
     use_graph_ = !(ng && ng[0] == '1');
+    if (o.precond == IFILT_PRECOND_MG) mg_setup();
+    P_.mg = mg_on_ ? 1 : 0;
     prof_ = profiling_on();
     if (prof_)
       for (auto& e : ev_) IFILT_CUDA(cudaEventCreate(&e));
@@ -1383,6 +1463,7 @@ class EngineT final : public Engine {
     for (auto& s : src_)
       if (s.buf) scratch_free(s.buf, st_);
     if (tl_.base) scratch_free(tl_.base, st_);
+    if (mg_base_) scratch_free(mg_base_, st_);
     if (fixed_) scratch_free(fixed_, st_);
     if (h_cnt_) cudaFreeHost(h_cnt_);
     for (auto& e : ev_)
@@ -1395,7 +1476,7 @@ class EngineT final : public Engine {
   }
   bool idle() const override { return live_columns() == 0 && pend_.empty(); }
   int64_t bytes_held() const override {
-    int64_t b = fixed_bytes_ + tl_.bytes;
+    int64_t b = fixed_bytes_ + tl_.bytes + mg_bytes_;
     for (auto& s : src_)
       if (s.buf) b += src_bytes();
     return b;
@@ -1462,7 +1543,9 @@ class EngineT final : public Engine {
     if constexpr (sizeof(T) == 4) return E_ == &m_->ell_g2 ? m_->diag_g2_32 : m_->diag_k32;
     else return gdiag64();
   }
-  int64_t tile_bytes(int W) const { return (int64_t)n_ * NS * W * (4 * sizeof(T) + sizeof(double)); }
+  int64_t tile_bytes(int W) const {
+    return (int64_t)n_ * NS * W * (4 * sizeof(T) + sizeof(double)) + mg_tile_bytes(W);
+  }
   double shift_of(double k) const {
     const double ell = 1.0 / k;
     if (o_.order == 1) return 0.5 * ell * ell;
@@ -1510,6 +1593,7 @@ class EngineT final : public Engine {
     const int fg = (P_.ncols + 31) / 32;
     const dim3 fb(32, 8);
     const unsigned evf = check ? cudaEventRecordDefault : cudaEventRecordExternal;
+    evf_ = evf;
     auto rec = [&](int i) {
       if (prof_) IFILT_CUDA(cudaEventRecordWithFlags(ev_[i], st_, evf));
     };
@@ -1531,6 +1615,21 @@ class EngineT final : public Engine {
     chk("finish_residual");
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
     for (int it = 0; it < m_it_; it++) {
+      if (mg_on_) {
+        // preconditioned order: z = V(r), beta from <r, z>, p = z + beta p, then q = S p ...
+        if (it == 0) rec(6);
+        mg_sample_ = it == 0;
+        const T* z = vcycle(0, tl_.r);
+        mg_sample_ = false;
+        chk("vcycle");
+        if (it == 0) rec(7);
+        finish_rho_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbz_, partial2_, C_);
+        chk("finish_rho");
+        if (it == 0) rec(4);
+        direction_kernel<T, CPLX, BLK, false><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, z, C_, mass_t(), nullptr);
+        chk("direction");
+        if (it == 0) rec(5);
+      }
       if (it == 0) rec(0);
       spmm_fn()<<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), C_, partial_,
                                             MgArgs<T>{});
@@ -1549,6 +1648,7 @@ class EngineT final : public Engine {
       if (it == 0) rec(3);
       finish_beta_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbu_, partial_, C_);
       chk("finish_beta");
+      if (mg_on_) continue;
       if (it == 0) rec(4);
       if (gdiag_t())
         direction_kernel<T, CPLX, BLK, true><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_, mass_t(), gdiag_t());
@@ -1560,7 +1660,7 @@ class EngineT final : public Engine {
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
     IFILT_CUDA(cudaMemcpyAsync(h_cnt_, C_.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st_));
   }
-  int launches_per_step() const { return 7 + 5 * m_it_; }
+  int launches_per_step() const { return 7 + 5 * m_it_ + (mg_on_ ? m_it_ * (mg_launches() + 1) : 0); }
 
   void capture() {
     if (exec_) cudaGraphExecDestroy(exec_);
@@ -1602,6 +1702,7 @@ class EngineT final : public Engine {
     graph_ = nullptr;
     if (tl_.base) scratch_free(tl_.base, st_);
     tl_ = Tiles<T>{};
+    mg_free();
     cur_.clear();
     set_width(0);
   }
@@ -1690,6 +1791,7 @@ class EngineT final : public Engine {
     tl_ = tn;
     cur_ = ncur;
     set_width(Wn);
+    if (mg_on_) mg_alloc(Wn);
     upload_tables();
     cols_upload(C_, Hn, ncn, st_);
     IFILT_CUDA(cudaMemcpyAsync(flags_, fresh.data(), ncn * 4, cudaMemcpyHostToDevice, st_));
@@ -1807,6 +1909,15 @@ class EngineT final : public Engine {
         by_[0] += 2.0 * vb + mb;
         by_[1] += 6.0 * vb;
         by_[2] += 3.0 * vb;
+        if (mg_on_ && mgl_->size() > 1) {
+          float d = 0, e = 0;
+          IFILT_CUDA(cudaEventElapsedTime(&d, ev_[6], ev_[7]));
+          IFILT_CUDA(cudaEventElapsedTime(&e, ev_[8], ev_[9]));
+          t_[3] += d;
+          t_[4] += e;
+          by_[3] += mg_bytes_per_cycle();
+          by_[4] += 3.0 * vb + (double)m_->ell_k.entries * (4.0 + NVAL * sizeof(T)) + 2.0 * n_ * sizeof(T);
+        }
         samples_++;
       }
     }
@@ -1843,10 +1954,16 @@ class EngineT final : public Engine {
       profile_add(nm, launches, samples_, t_[1], by_[1] / samples_);
       snprintf(nm, sizeof nm, "direction_%s%s_%s", k1, k2, k3);
       profile_add(nm, launches, samples_, t_[2], by_[2] / samples_);
+      if (t_[3] > 0.0) {  // the V-cycle as a whole (several kernels) and its first fine smoothing sweep
+        snprintf(nm, sizeof nm, "(vcycle)_%s%s_%s", k1, k2, k3);
+        profile_add(nm, launches, samples_, t_[3], by_[3] / samples_);
+        snprintf(nm, sizeof nm, "mgsmooth_%s%s_%s", k1, k2, k3);
+        profile_add(nm, launches, samples_, t_[4], by_[4] / samples_);
+      }
     }
     steps_ = 0;
     samples_ = 0;
-    t_[0] = t_[1] = t_[2] = by_[0] = by_[1] = by_[2] = 0;
+    for (int i = 0; i < 5; i++) t_[i] = by_[i] = 0;
   }
 
  private:
@@ -1881,8 +1998,218 @@ class EngineT final : public Engine {
   cudaGraphExec_t exec_ = nullptr;
   int m_it_ = 32;
   bool use_graph_ = true, launched_ = false, prof_ = false;
-  cudaEvent_t ev_[6] = {};
-  double t_[3] = {0, 0, 0}, by_[3] = {0, 0, 0};
+  // ------------------------------------------------------------ multigrid
+  static constexpr int kMgMinB = 3;
+  static constexpr int kMgCoarseSweeps = 4;  // Jacobi sweeps on the coarsest level
+  static constexpr double kMgOmega = 2.0 / 3.0;
+  struct MgBuf {
+    T* r = nullptr;  // right-hand side of the level (levels >= 1)
+    T* a = nullptr;
+    T* b = nullptr;
+  };
+  bool mg_on_ = false;
+  const std::vector<DevMgLevel>* mgl_ = nullptr;
+  std::vector<MgBuf> mgb_;
+  void* mg_base_ = nullptr;
+  int64_t mg_bytes_ = 0;
+  double* partial2_ = nullptr;
+  int nbz_ = 1;  // blocks of the last level-0 smoothing sweep (partials of <r, z>)
+
+  template <int EPI, int NSET>
+  static const void* mg_fn() {
+    return (const void*)spmm_kernel<T, T, CPLX, BLK, 4, kMgMinB, EPI, NSET>;
+  }
+  static int64_t stage_entries_of(const DevEll& E, int spt) {
+    return (int64_t)spt * ((int64_t)E.slice_h * E.max_width + 8);
+  }
+  static size_t stage_bytes_of(const DevEll& E, int spt, int vbytes) {
+    const int64_t e = stage_entries_of(E, spt);
+    return (size_t)((e * 4 + 15) / 16 * 16 + (e * vbytes + 15) / 16 * 16);
+  }
+  int spt_of(const DevEll& E, int W, int vbytes, int minb) const {
+    const int RPP = kBlock / (W / VEC);
+    int spt = std::max(1, (RPP * kTilePasses + E.slice_h - 1) / E.slice_h);
+    while (spt > 1 && stage_bytes_of(E, spt, vbytes) > (size_t)kStageBytes) spt--;
+    const long long want = (long long)n_sms_ * minb * 8;
+    while (spt > 1 && (E.n_slices + spt - 1) / spt < want) spt--;
+    return std::min(spt, kMaxSpt);
+  }
+
+  void mg_setup() {
+    if (sizeof(T) != 4) fail(IFILT_EINVAL, "multigrid preconditioning runs with FP32 or BF16 precision");
+    if (E_ != &m_->ell_k) fail(IFILT_EINVAL, "multigrid preconditioning needs order 1 or the complex n = 2 form");
+    mgl_ = &multigrid_device(m_, st_);
+    const int vb1 = NVAL * (int)sizeof(T), vb2 = 2 * vb1;
+    for (size_t l = 0; l < mgl_->size(); l++) {
+      const DevMgLevel& L = (*mgl_)[l];
+      const DevEll* ells[3] = {&L.S, &L.P, &L.R};
+      for (int i = 0; i < 3; i++)
+        if (ells[i]->n > 0 && stage_bytes_of(*ells[i], 1, i == 0 ? vb2 : vb1) > (size_t)kStageMax)
+          fail(IFILT_EINVAL, "multigrid level %zu: ELL slice exceeds the shared-memory stage", l);
+    }
+    if constexpr (sizeof(T) == 4) {
+      const int smax = (int)(kBlock * VEC * sizeof(double) + 2 * kStageMax);
+      const void* fns[] = {mg_fn<kEpiSmooth, 1>(), mg_fn<kEpiSmooth, 2>(), mg_fn<kEpiResid, 1>(),
+                           mg_fn<kEpiResid, 2>(), mg_fn<kEpiRestrict, 1>(), mg_fn<kEpiProlong, 1>()};
+      for (const void* f : fns)
+        IFILT_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+      mg_on_ = true;
+    }
+  }
+  int64_t mg_tile_bytes(int W) const {
+    if (!mg_on_) return 0;
+    int64_t b = 0;
+    for (size_t l = 0; l < mgl_->size(); l++) {
+      const int64_t rows = l == 0 ? n_ : (*mgl_)[l].n;
+      const int64_t vb = (rows * NS * W * (int64_t)sizeof(T) + 255) / 256 * 256;
+      b += (l == 0 ? 2 : 3) * vb;
+    }
+    return b;
+  }
+  void mg_free() {
+    if (mg_base_) scratch_free(mg_base_, st_);
+    mg_base_ = nullptr;
+    mg_bytes_ = 0;
+    mgb_.clear();
+  }
+  void mg_alloc(int W) {
+    mg_free();
+    mg_bytes_ = mg_tile_bytes(W);
+    char* p = (char*)scratch_alloc((size_t)mg_bytes_, st_);
+    mg_base_ = p;
+    mgb_.resize(mgl_->size());
+    for (size_t l = 0; l < mgl_->size(); l++) {
+      const int64_t rows = l == 0 ? n_ : (*mgl_)[l].n;
+      const int64_t vb = (rows * NS * W * (int64_t)sizeof(T) + 255) / 256 * 256;
+      if (l > 0) {
+        mgb_[l].r = (T*)p;
+        p += vb;
+      }
+      mgb_[l].a = (T*)p;
+      p += vb;
+      mgb_[l].b = (T*)p;
+      p += vb;
+    }
+  }
+
+  // one gather-kernel launch on a multigrid operator; returns its block count
+  template <int EPI, int NSET>
+  int mg_gather(const DevEll& E, const T* src, T* out, const T* mdiag, const T* kd, const T* rhs, const T* own,
+                double* partial) {
+    const int W = P_.W;
+    const int vbytes = NVAL * NSET * (int)sizeof(T);
+    Params Q = P_;
+    Q.n = E.n;
+    Q.spt = spt_of(E, W, vbytes, kMgMinB);
+    Q.stage_e = (int)stage_entries_of(E, Q.spt);
+    const size_t smem = smem_of(W, 2) + 2 * stage_bytes_of(E, Q.spt, vbytes);
+    const long long ntiles = (E.n_slices + Q.spt - 1) / Q.spt;
+    const int blocks = std::min(nb_max_, grid_for(mg_fn<EPI, NSET>(), kBlock, smem, ntiles * kBlock));
+    spmm_kernel<T, T, CPLX, BLK, 4, kMgMinB, EPI, NSET><<<blocks, kBlock, smem, st_>>>(
+        ell_view<T>(E), Q, E.n_slices, src, out, mdiag, C_, partial, MgArgs<T>{kd, rhs, own, (T)kMgOmega});
+    return blocks;
+  }
+  // S_l-operations: level 0 uses the mesh's K and lumped mass, coarser levels their (K, M) pair
+  // (FP32 engines only: the FP64 engine refuses multigrid in mg_setup)
+  int mg_smooth(size_t l, const T* x, T* out, const T* rhs, double* partial) {
+    if constexpr (sizeof(T) == 4) {
+      if (l == 0) return mg_gather<kEpiSmooth, 1>(m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial);
+      const DevMgLevel& L = (*mgl_)[l];
+      return mg_gather<kEpiSmooth, 2>(L.S, x, out, L.dm32, L.dk32, rhs, nullptr, partial);
+    } else {
+      return 0;
+    }
+  }
+  void mg_resid(size_t l, const T* x, T* out, const T* rhs) {
+    if constexpr (sizeof(T) == 4) {
+      if (l == 0) mg_gather<kEpiResid, 1>(m_->ell_k, x, out, mass_t(), nullptr, rhs, nullptr, nullptr);
+      else mg_gather<kEpiResid, 2>((*mgl_)[l].S, x, out, (*mgl_)[l].dm32, nullptr, rhs, nullptr, nullptr);
+    }
+  }
+  void mg_transfer(size_t l, bool restrict_, const T* src, T* out, const T* own) {
+    if constexpr (sizeof(T) == 4) {
+      const DevMgLevel& L = (*mgl_)[l];
+      if (restrict_) mg_gather<kEpiRestrict, 1>(L.R, src, out, nullptr, nullptr, nullptr, nullptr, nullptr);
+      else mg_gather<kEpiProlong, 1>(L.P, src, out, nullptr, nullptr, nullptr, own, nullptr);
+    }
+  }
+  void mg_jacobi(size_t l, const T* rhs, T* out) {
+    if constexpr (sizeof(T) == 4) {
+      const int32_t rows = l == 0 ? (int32_t)n_ : (*mgl_)[l].n;
+      const T* md = l == 0 ? mass_t() : (*mgl_)[l].dm32;
+      const T* kd = l == 0 ? m_->diag_k32 : (*mgl_)[l].dk32;
+      Params Q = P_;
+      Q.n = rows;
+      const int g = std::min(nb_max_, grid_for((const void*)mg_jacobi_kernel<T, CPLX, BLK>, kBlock, 0,
+                                               (long long)rows * (P_.W / VEC)));
+      mg_jacobi_kernel<T, CPLX, BLK><<<g, kBlock, 0, st_>>>(Q, rhs, out, md, kd, C_, (T)kMgOmega);
+    }
+  }
+  // One V-cycle on level l for the right-hand side rhs: two damped-Jacobi
+  // sweeps, coarse correction, two sweeps (Jacobi sweeps only on the last
+  // level).  Returns the buffer holding the result; on level 0 the last sweep
+  // also leaves the partials of <rhs, result> in partial2_.
+  T* vcycle(size_t l, const T* rhs) {
+    MgBuf& B = mgb_[l];
+    const bool last = l + 1 == mgl_->size();
+    mg_jacobi(l, rhs, B.a);
+    if (last) {
+      T* x = B.a;
+      T* y = B.b;
+      for (int s = 1; s < kMgCoarseSweeps; s++) {
+        const int nb = mg_smooth(l, x, y, rhs, (l == 0 && s + 1 == kMgCoarseSweeps) ? partial2_ : nullptr);
+        if (l == 0) nbz_ = nb;
+        std::swap(x, y);
+      }
+      return x;
+    }
+    const DevMgLevel& L = (*mgl_)[l];
+    if (l == 0) mark(8);
+    mg_smooth(l, B.a, B.b, rhs, nullptr);
+    if (l == 0) mark(9);
+    mg_resid(l, B.b, B.a, rhs);
+    (void)L;
+    mg_transfer(l, true, B.a, mgb_[l + 1].r, nullptr);
+    const T* xc = vcycle(l + 1, mgb_[l + 1].r);
+    mg_transfer(l, false, xc, B.a, B.b);
+    mg_smooth(l, B.a, B.b, rhs, nullptr);
+    const int nb = mg_smooth(l, B.b, B.a, rhs, l == 0 ? partial2_ : nullptr);
+    if (l == 0) nbz_ = nb;
+    return B.a;
+  }
+  void mark(int i) {
+    if (prof_ && mg_sample_) IFILT_CUDA(cudaEventRecordWithFlags(ev_[i], st_, evf_));
+  }
+  int mg_launches() const {
+    if (!mg_on_) return 0;
+    const int L = (int)mgl_->size();
+    return 7 * (L - 1) + kMgCoarseSweeps;
+  }
+  // algorithmic bytes of one V-cycle (vectors and operators, all levels)
+  double mg_bytes_per_cycle() const {
+    if (!mg_on_) return 0.0;
+    double b = 0.0;
+    const int W = P_.W;
+    for (size_t l = 0; l < mgl_->size(); l++) {
+      const DevMgLevel& L = (*mgl_)[l];
+      const double rows = l == 0 ? (double)n_ : (double)L.n;
+      const double vb = rows * NS * W * sizeof(T);
+      const DevEll& S = l == 0 ? m_->ell_k : L.S;
+      const double sb = (double)S.entries * (4.0 + (l == 0 ? 1 : 2) * NVAL * sizeof(T));
+      if (l + 1 == mgl_->size()) {
+        b += 2 * vb + (kMgCoarseSweeps - 1) * (3 * vb + sb);
+      } else {
+        const double vc = (double)(*mgl_)[l + 1].n * NS * W * sizeof(T);
+        b += 2 * vb + 4 * (3 * vb + sb) + (vb + vc) + (2 * vb + vc) +
+             (double)(L.P.entries + L.R.entries) * (4.0 + NVAL * sizeof(T));
+      }
+    }
+    return b;
+  }
+  cudaEvent_t ev_[10] = {};
+  unsigned evf_ = cudaEventRecordDefault;
+  bool mg_sample_ = false;
+  double t_[5] = {0, 0, 0, 0, 0}, by_[5] = {0, 0, 0, 0, 0};
   int64_t samples_ = 0, steps_ = 0, other_launches_ = 0;
 };
 

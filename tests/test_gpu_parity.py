@@ -157,15 +157,57 @@ def test_jacobi_preconditioning(lib, placement, order, n2, prec):
     _check(res, ref, tol)
 
 
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+@pytest.mark.parametrize("order,prec", [(1, 1), (2, 1), (2, 2)])
+def test_multigrid_preconditioning(lib, placement, order, prec):
+    """Multigrid-preconditioned CG (n = 1) / COCG (complex n = 2) reaches the
+    oracle's fields, with several levels in the hierarchy."""
+    m = _sphere(4, 61, polar=10.0)
+    P = oracle.build_problem(m, placement)
+    f = _fields(P, 2, 7)
+    ks = synth.log_wavenumbers(6000.0, 200.0, 5)
+    res, stats, st = _run(lib, m, placement, f, ks, order, tol=1e-10, precision=prec, n2_solver=2,
+                          precond=lib.PRECOND_MG)
+    assert st == 0, stats
+    _, ref = _oracle(m, placement, f, ks, order)
+    _check(res, ref, TOL_MIXED)
+
+
+@pytest.mark.parametrize("placement", ["vertex_vector", "cell"])
+def test_multigrid_cuts_iterations_at_large_scales(lib, placement):
+    """On a level-6 sphere the largest scales need far fewer iterations with
+    the V-cycle than without (its whole point), at the same tolerance."""
+    import torch
+    m = _sphere(6, 63, polar=5.0)
+    h = lib.prepare_mesh(m, placement, max_order=2)
+    assert h.multigrid()["levels"] >= 3
+    rng = np.random.default_rng(8)
+    f = torch.tensor(rng.normal(size=(1, 2, h.info["n_in"])), device="cuda")
+    ks = synth.log_wavenumbers(4000.0, 1000.0, 3)
+    its = {}
+    for pc in (lib.PRECOND_NONE, lib.PRECOND_MG):
+        out, stats, st = lib.solve(h, f, ks, order=2, tol=1e-9, precision=1, n2_solver=2, precond=pc)
+        assert st == 0
+        its[pc] = stats["iters"].reshape(-1)
+    h.release()
+    assert its[lib.PRECOND_MG].max() * 3 <= its[lib.PRECOND_NONE].max(), its
+
+
 def test_preconditioner_option_checked(lib):
     import torch
     m = _sphere(2, 60)
     h = lib.prepare_mesh(m, "vertex_scalar", max_order=1)
     f = torch.zeros((1, 1, h.info["n_in"]), dtype=torch.float64, device="cuda")
-    for kw in (dict(precond=7), dict(precond=lib.PRECOND_JACOBI, method=lib.METHOD_PLAIN)):
+    for kw in (dict(precond=7), dict(precond=lib.PRECOND_JACOBI, method=lib.METHOD_PLAIN),
+               dict(precond=lib.PRECOND_MG, precision=lib.PREC_FP64)):
         with pytest.raises(lib.IfiltError) as e:
             lib.solve(h, f, [0.01], order=1, **kw)
         assert e.value.status == -1
+    h2 = lib.prepare_mesh(m, "vertex_scalar", max_order=2)
+    with pytest.raises(lib.IfiltError) as e:
+        lib.solve(h2, f, [0.01], order=2, precision=lib.PREC_FP32_IR, n2_solver=lib.N2_REAL, precond=lib.PRECOND_MG)
+    assert e.value.status == -1
+    h2.release()
     h.release()
 
 
