@@ -56,7 +56,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain-sample", type=int, default=3, help="scales (1-3) timed on the plain FP64 path")
     ap.add_argument("--serving", action="store_true", help="run the request-serving workload instead")
-    ap.add_argument("--precond", choices=["none", "jacobi", "mg"], default="none", help="Krylov preconditioner")
+    ap.add_argument("--precond", choices=["none", "jacobi", "mg"], default="mg", help="Krylov preconditioner")
+    ap.add_argument("--check-every", type=int, default=0, help="iterations per solver step (0: library default)")
+    ap.add_argument("--inner-tol", type=float, default=0.0, help="FP32 inner reduction per round (0: default)")
     ap.add_argument("--concurrent", action="store_true",
                     help="step the two placements' solvers together (one solve_many call); per-kernel "
                          "event timings then overlap, so the roofline is not measured")
@@ -200,7 +202,8 @@ class Ours:
         prec = {"fp32": api.PREC_FP32_IR, "bf16": api.PREC_BF16_IR, "fp64": api.PREC_FP64}[args.precision]
         self.opts = dict(order=2, tol=args.tol, precision=prec, n2_solver=api.N2_COMPLEX,
                          precond={"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI,
-                                  "mg": api.PRECOND_MG}[args.precond])
+                                  "mg": api.PRECOND_MG}[args.precond],
+                         check_every=args.check_every, inner_tol=args.inner_tol)
         K = self.k.size
         self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
         self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
@@ -497,6 +500,10 @@ def run_serving(args, world, rank):
         arrivals.append((t, mi, F, j0, K, n))
     cap = args.serve_out_gb * 1e9
     free, _ = torch.cuda.mem_get_info()
+    pc = {"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI, "mg": api.PRECOND_MG}[args.precond]
+    if pc == api.PRECOND_MG:
+        for mh in meshes:
+            mh.multigrid()  # host hierarchy built before the arrival window
     srv = api.Server(memory_budget=int(max(free - cap - 8e9, 4e9)))
     pending = list(arrivals)
     inflight = {}            # rid -> (arrival time, columns, out bytes)
@@ -517,7 +524,7 @@ def run_serving(args, world, rank):
                 break
             pending.pop(0)
             rid = srv.submit(meshes[mi], pools[mi][:F], kgrid[j0:j0 + K], order=n, tol=1e-6,
-                             precision=api.PREC_FP32_IR)
+                             precision=api.PREC_FP32_IR, precond=pc)
             inflight[rid] = (ta, F * K, ob)
             held += ob
         for rid in list(inflight):

@@ -29,6 +29,6 @@ from .operators import (  # noqa: F401
 )
 from .reorder import rcm_order, check_rcm_order  # noqa: F401
 from .solve import (  # noqa: F401
-    cg, filter_field, filter_dense, residual_certificate, Problem, build_problem,
+    cg, filter_field, filter_dense, residual_certificate, relative_residual, Problem, build_problem,
 )
 from .spectrum import filtered_energy, spectrum  # noqa: F401

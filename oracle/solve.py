@@ -176,6 +176,27 @@ def filter_dense(problem, fld, ks, order):
     return np.stack(out)
 
 
+def _candidates(problem, fld, filtered_k):
+    """The unknowns of each system read back from an output block [n_comp][n_out]."""
+    ids = problem.out_ids
+    if problem.placement == "vertex_vector":
+        return [np.concatenate([filtered_k[0][ids], filtered_k[1][ids]])]
+    return [filtered_k[c][ids] for c in range(len(problem.systems(fld)))]
+
+
+def relative_residual(problem, fld, filtered_k, k, order):
+    """Per system, ||b - S x|| / ||b - S x0|| (2-norms) for the candidate x read
+    from `filtered_k`: the quantity the paper's solver drives below its tolerance
+    (Sect. 2.2.2, residual form with x0 as in `systems`)."""
+    ell = 1.0 / k
+    out = []
+    for (b, x0), x in zip(problem.systems(fld), _candidates(problem, fld, filtered_k)):
+        r0 = np.linalg.norm(b - problem.apply_S(x0, ell, order))
+        r = np.linalg.norm(b - problem.apply_S(x, ell, order))
+        out.append(r / r0 if r0 > 0 else r)
+    return out
+
+
 def residual_certificate(problem, fld, filtered_k, k, order):
     """For one wavenumber: per system (||b - S x||_{M^-1}, ||x||_M) where x is the
     candidate solution read back from `filtered_k` [n_comp][n_out].  The first

@@ -359,3 +359,30 @@ def test_certificate_bounds_error():
     (bound, _), = oracle.residual_certificate(P, f, cand, k, 2)
     err = np.sqrt(np.sum(P.A * (cand[0][P.out_ids] - exact[0][P.out_ids]) ** 2))
     assert err <= bound * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+def test_relative_residual_of_x0_exact_and_perturbed(placement):
+    """||b - S x|| / ||b - S x0||: exactly 1 at x0 (the paper's initial guess),
+    at rounding level for the dense solve, and equal to ||S e|| / ||r0|| for
+    a perturbation e of the dense solution."""
+    m = synth.icosphere(2, radius=6371.0, jitter=0.2, seed=23)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=24)
+    P = oracle.build_problem(m, placement)
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=(P.n_comp, P.n_in))
+    k = 2 * np.pi / 3000.0
+    exact = oracle.filter_dense(P, f, [k], 2)[0]
+    # x0 written back as an output block
+    x0_block = P.output(f, [x0 for _, x0 in P.systems(f)])
+    assert np.allclose(oracle.relative_residual(P, f, x0_block, k, 2), 1.0, rtol=1e-14)
+    assert max(oracle.relative_residual(P, f, exact, k, 2)) < 1e-9
+    cand = exact.copy()
+    e = 1e-5 * rng.normal(size=P.out_ids.size)
+    cand[0][P.out_ids] += e
+    rel = oracle.relative_residual(P, f, cand, k, 2)[0]
+    (b, x0), = P.systems(f)[:1]
+    ee = np.zeros_like(x0)
+    ee[: e.size] = e
+    r0 = np.linalg.norm(b - P.apply_S(x0, 1.0 / k, 2))
+    assert abs(rel - np.linalg.norm(P.apply_S(ee, 1.0 / k, 2)) / r0) <= 1e-6 * rel
