@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--precond", choices=["none", "jacobi", "mg"], default="mg", help="Krylov preconditioner")
     ap.add_argument("--check-every", type=int, default=0, help="iterations per solver step (0: library default)")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="FP32 inner reduction per round (0: default)")
+    ap.add_argument("--err-tol", type=float, default=1e-7,
+                    help="also stop each column only at a certified relative M-norm error bound (0: off)")
     ap.add_argument("--concurrent", action="store_true",
                     help="step the two placements' solvers together (one solve_many call); per-kernel "
                          "event timings then overlap, so the roofline is not measured")
@@ -181,6 +183,7 @@ def workload_config(args, w, world):
             "vertices": int(m["coords"].shape[0]), "triangles": int(m["tri"].shape[0]),
             "columns_per_step": 4 * N_K, "order": 2, "n2_solver": "complex", "tol": args.tol,
             "precision": args.precision, "precond": getattr(args, "precond", "none"),
+            "err_tol": getattr(args, "err_tol", 0.0),
             "l2": "inputs larger than L2 (GBs per vector), no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
@@ -203,7 +206,7 @@ class Ours:
         self.opts = dict(order=2, tol=args.tol, precision=prec, n2_solver=api.N2_COMPLEX,
                          precond={"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI,
                                   "mg": api.PRECOND_MG}[args.precond],
-                         check_every=args.check_every, inner_tol=args.inner_tol)
+                         check_every=args.check_every, inner_tol=args.inner_tol, err_tol=args.err_tol)
         K = self.k.size
         self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
         self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
@@ -237,11 +240,12 @@ class Ours:
         ks = np.ascontiguousarray(self.k[idx])
         out = torch.empty((1, ks.size, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
         res = {}
-        for name, kw in (("plain", dict(precision=api.PREC_FP64, method=api.METHOD_PLAIN)),
-                         ("batched", dict(precision=self.opts["precision"], n2_solver=api.N2_COMPLEX))):
+        for name, kw in (("plain", dict(order=2, tol=self.opts["tol"], precision=api.PREC_FP64,
+                                        method=api.METHOD_PLAIN)),
+                         ("batched", self.opts)):
             torch.cuda.synchronize()
             t0 = time.time()
-            _, st, _ = api.solve(self.mc, self.fields, ks, out=out, order=2, tol=self.opts["tol"], **kw)
+            _, st, _ = api.solve(self.mc, self.fields, ks, out=out, **kw)
             torch.cuda.synchronize()
             res[name] = (time.time() - t0, st.reshape(-1))
         cols = 2 * ks.size
@@ -252,7 +256,8 @@ class Ours:
                 "unit": UNIT,
                 "sample": "cell placement, u and v, at the listed wavenumber indices (of 40, ascending k): "
                           "plain one-RHS FP64 CG (S = M + l^4/2 K M^-1 K assembled per scale, CSR SpMV, separate "
-                          "dot/axpy kernels, host test each iteration) vs the batched path, same columns"}
+                          "dot/axpy kernels, host test each iteration, residual 1e-9) vs the batched path with "
+                          "the bench's options, same columns"}
 
 
 def roofline(api, peak_gbs, peak_kind):

@@ -130,9 +130,14 @@ typedef struct {
   int32_t method;            /* IFILT_METHOD_* */
   int32_t n2_solver;         /* IFILT_N2_* */
   int32_t precond;           /* IFILT_PRECOND_*; batched method only */
-  int32_t check_every;       /* batched: iterations per CUDA graph between host checks; 0 = 32 */
+  int32_t check_every;       /* batched: iterations per CUDA graph between host checks; 0 = 32
+                                (8 with IFILT_PRECOND_MG) */
   double inner_tol;          /* FP32 inner solves: relative reduction per refinement round; 0 = 1e-4 */
   int32_t max_lanes;         /* batched: widest column tile in 32-bit lanes; 0 = library default */
+  double err_tol;            /* batched: if > 0, a column also needs ||b - S x||_{M^-1} <= err_tol ||x||_M
+                                (x the filtered part: the real part in the complex n = 2 form), a
+                                bound on its relative error in the M-norm, because S >= M (and
+                                |e^H A e| >= e^H M e for A = M + i s K); 0 = the residual test only */
 } ifilt_solve_opts;
 
 typedef struct {
@@ -141,6 +146,7 @@ typedef struct {
   int32_t status;            /* IFILT_OK or IFILT_NOT_CONVERGED */
   int32_t pad;
   double rel_residual;       /* final true ||b - S x|| / ||b - S x0|| in FP64 (of the system solved) */
+  double err_bound;          /* batched: final ||b - S x||_{M^-1} / ||x||_M (see err_tol); plain: 0 */
 } ifilt_col_stats;
 
 typedef struct {

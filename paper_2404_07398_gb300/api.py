@@ -44,7 +44,8 @@ class MeshDesc(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("order", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("method", C.c_int32), ("n2_solver", C.c_int32), ("precond", C.c_int32),
-                ("check_every", C.c_int32), ("inner_tol", C.c_double), ("max_lanes", C.c_int32)]
+                ("check_every", C.c_int32), ("inner_tol", C.c_double), ("max_lanes", C.c_int32),
+                ("err_tol", C.c_double)]
 
 
 class SolveItem(C.Structure):
@@ -54,7 +55,7 @@ class SolveItem(C.Structure):
 
 class ColStats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("status", C.c_int32), ("pad", C.c_int32),
-                ("rel_residual", C.c_double)]
+                ("rel_residual", C.c_double), ("err_bound", C.c_double)]
 
 
 class MeshInfo(C.Structure):
@@ -81,7 +82,7 @@ class KernelProfile(C.Structure):
 
 
 COL_STATS_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("status", np.int32),
-                            ("pad", np.int32), ("rel_residual", np.float64)])
+                            ("pad", np.int32), ("rel_residual", np.float64), ("err_bound", np.float64)])
 
 class MultigridInfo(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("rows", C.c_int32 * MG_MAX_LEVELS), ("nnz_s", C.c_int64 * MG_MAX_LEVELS),
@@ -279,10 +280,10 @@ def prepare_mesh_host(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_s
 
 
 def solve_opts(order=1, tol=1e-9, precision=PREC_FP64, method=METHOD_BATCHED, n2_solver=N2_AUTO, max_iter=0,
-               precond=0, check_every=0, inner_tol=0.0, max_lanes=0):
+               precond=0, check_every=0, inner_tol=0.0, max_lanes=0, err_tol=0.0):
     return SolveOpts(order=order, tol=tol, max_iter=max_iter, precision=precision, method=method,
                      n2_solver=n2_solver, precond=precond, check_every=check_every, inner_tol=inner_tol,
-                     max_lanes=max_lanes)
+                     max_lanes=max_lanes, err_tol=err_tol)
 
 
 def solve(mesh, fields, k, out=None, stream=None, **opts):

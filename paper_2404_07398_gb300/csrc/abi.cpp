@@ -334,6 +334,9 @@ static void check_opts(ifilt_mesh m, const ifilt_solve_opts* o) {
     fail(IFILT_EINVAL, "the plain method takes no preconditioner");
   if (o->max_iter < 0 || o->check_every < 0 || o->max_lanes < 0 || o->inner_tol < 0)
     fail(IFILT_EINVAL, "negative option");
+  if (!(o->err_tol >= 0.0) || !std::isfinite(o->err_tol)) fail(IFILT_EINVAL, "err_tol must be >= 0 and finite");
+  if (o->method == IFILT_METHOD_PLAIN && o->err_tol > 0.0)
+    fail(IFILT_EINVAL, "the plain method stops on the residual only (err_tol = 0)");
 }
 
 ifilt_status ifilt_solve(ifilt_mesh m, const ifilt_solve_opts* o, int32_t n_fields, const double* fields, int32_t n_k,

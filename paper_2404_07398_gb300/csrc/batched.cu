@@ -187,6 +187,7 @@ struct Cols {
   double* r0n2;     // ||b - S x0||^2 (FP64), < 0 until the first residual round
   double* tol2;     // tol^2 * r0n2
   double* rel;      // last true relative residual
+  double* err;      // last certified relative error bound ||r||_{M^-1} / ||x||_M
   int* active;      // inner recursion running
   int* done;        // column finished (converged, capped or broken down)
   int* iters;
@@ -206,6 +207,7 @@ struct Params {
   int pstride;      // doubles per block in `partial`
   int maxit;
   double tol2_rel;  // tol^2
+  double err2;      // err_tol^2 (0: no error test)
   double inner2;    // inner_tol^2 (0: run to the outer tolerance)
   int mg;           // multigrid-preconditioned iteration order
   int spt;          // ELL slices per SpMM tile
@@ -886,14 +888,14 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
   extern __shared__ double sm[];
   const int W = P.W;
   const int ncolsW = CPLX ? W / 2 : W;
-  const int NSL = W + ncolsW;
+  const int NSL = W + 3 * ncolsW;  // <r, z> lanes, then per column ||r||^2, ||r||^2_{M^-1}, ||x||^2_M
   const int TPR = W / VEC;
   const int RPP = kBlock / TPR;
   const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
   const int l0 = g * VEC;
-  double d1[VEC], d2[VEC];
+  double d1[VEC], d2[VEC], e2[VEC], x2[VEC];
 #pragma unroll
-  for (int v = 0; v < VEC; v++) d1[v] = d2[v] = 0.0;
+  for (int v = 0; v < VEC; v++) d1[v] = d2[v] = e2[v] = x2[v] = 0.0;
   // Lanes of columns that are not being refreshed keep their inner state; a
   // thread none of whose columns is refreshed skips its loads altogether, so
   // the traffic follows the number of refreshed columns.
@@ -990,6 +992,8 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
             d1[v] += (double)tre * zre - (double)tim * zim;
             d1[v + 1] += (double)tre * zim + (double)tim * zre;
             d2[v / 2] += r_re * r_re + r_im * r_im;
+            e2[v / 2] += (r_re * r_re + r_im * r_im) / mr;
+            x2[v / 2] += mr * xo[v] * xo[v];  // the filtered field is the real part
           }
         } else {
 #pragma unroll
@@ -1002,6 +1006,8 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
             po.v[v] = z;
             d1[v] += (double)t * z;
             d2[v] += rv * rv;
+            e2[v] += rv * rv / mr;
+            x2[v] += mr * xo[v] * xo[v];
           }
         }
         if (all) {
@@ -1025,10 +1031,18 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
     for (int v = 0; v < VEC; v++) sm[tr * NSL + l0 + v] = d1[v];
     if constexpr (CPLX) {
 #pragma unroll
-      for (int v = 0; v < VEC / 2; v++) sm[tr * NSL + W + l0 / 2 + v] = d2[v];
+      for (int v = 0; v < VEC / 2; v++) {
+        sm[tr * NSL + W + l0 / 2 + v] = d2[v];
+        sm[tr * NSL + W + ncolsW + l0 / 2 + v] = e2[v];
+        sm[tr * NSL + W + 2 * ncolsW + l0 / 2 + v] = x2[v];
+      }
     } else {
 #pragma unroll
-      for (int v = 0; v < VEC; v++) sm[tr * NSL + W + l0 + v] = d2[v];
+      for (int v = 0; v < VEC; v++) {
+        sm[tr * NSL + W + l0 + v] = d2[v];
+        sm[tr * NSL + W + ncolsW + l0 + v] = e2[v];
+        sm[tr * NSL + W + 2 * ncolsW + l0 + v] = x2[v];
+      }
     }
   }
   __syncthreads();
@@ -1048,6 +1062,9 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
   const double rre = reduce_slot(partial, nb, P.pstride, ok ? (CPLX ? 2 * col : col) : -1, buf);
   const double rim = CPLX ? reduce_slot(partial, nb, P.pstride, ok ? 2 * col + 1 : -1, buf) : 0.0;
   const double n2 = reduce_slot(partial, nb, P.pstride, ok ? P.W + col : -1, buf);
+  const int ncolsW = CPLX ? P.W / 2 : P.W;
+  const double e2 = reduce_slot(partial, nb, P.pstride, ok ? P.W + ncolsW + col : -1, buf);
+  const double x2 = reduce_slot(partial, nb, P.pstride, ok ? P.W + 2 * ncolsW + col : -1, buf);
   if (threadIdx.y != 0 || !ok) return;
   if (!C.refresh[col]) return;
   C.refresh[col] = 0;
@@ -1057,12 +1074,17 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
   }
   const double r0 = C.r0n2[col];
   C.rel[col] = r0 > 0.0 ? sqrt(n2 / r0) : 0.0;
+  C.err[col] = x2 > 0.0 ? sqrt(e2 / x2) : (e2 > 0.0 ? INFINITY : 0.0);
+  // error test: ||r||^2_{M^-1} <= err_tol^2 ||x||^2_M; its equivalent in ||r||^2
+  // (at the current ratio of the two norms) bounds the inner target below
+  const bool err_ok = !(P.err2 > 0.0) || e2 <= P.err2 * x2;
+  const double tol2_eff = (P.err2 > 0.0 && e2 > 0.0) ? fmin(C.tol2[col], P.err2 * x2 * (n2 / e2)) : C.tol2[col];
   if (C.active[col]) {  // inner round stopped by its iteration cap
     C.active[col] = 0;
     atomicSub(C.live, 1);
   }
   if (C.done[col]) return;
-  if (!(n2 > C.tol2[col]) || r0 == 0.0) {
+  if ((!(n2 > C.tol2[col]) && err_ok) || r0 == 0.0) {
     C.done[col] = 1;
     return;
   }
@@ -1079,7 +1101,7 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
   C.rho[2 * col] = rre;
   C.rho[2 * col + 1] = rim;
   C.rn2[col] = n2;
-  C.target2[col] = fmax(P.inner2 * n2, 0.25 * C.tol2[col]);
+  C.target2[col] = fmax(P.inner2 * n2, 0.25 * tol2_eff);
   // later rounds get twice the length of the first (at least 256 iterations)
   if (C.rounds[col] == 1) C.round_cap[col] = max(256, 2 * (C.iters[col] - C.round_it0[col]));
   else if (C.rounds[col] == 0) C.round_cap[col] = P.maxit;
@@ -1272,10 +1294,10 @@ Tiles<T> alloc_tiles(int64_t n, int NS, int W, cudaStream_t st) {
 
 // Host copy of the per-column state, for retiring and re-packing columns.
 struct HostCols {
-  std::vector<double> shift, rho, alpha, beta, rn2, target2, r0n2, tol2, rel;
+  std::vector<double> shift, rho, alpha, beta, rn2, target2, r0n2, tol2, rel, err;
   std::vector<int> active, done, iters, rounds, status, refresh, round_it0, round_cap, restart;
   void resize(int n) {
-    for (auto* v : {&shift, &rn2, &target2, &r0n2, &tol2, &rel}) v->assign(n, 0.0);
+    for (auto* v : {&shift, &rn2, &target2, &r0n2, &tol2, &rel, &err}) v->assign(n, 0.0);
     for (auto* v : {&rho, &alpha, &beta}) v->assign(2 * n, 0.0);
     for (auto* v : {&active, &done, &iters, &rounds, &status, &refresh, &round_it0, &round_cap, &restart})
       v->assign(n, 0);
@@ -1293,6 +1315,7 @@ struct HostCols {
     r0n2[j] = h.r0n2[c];
     tol2[j] = h.tol2[c];
     rel[j] = h.rel[c];
+    err[j] = h.err[c];
     active[j] = h.active[c];
     done[j] = h.done[c];
     iters[j] = h.iters[c];
@@ -1319,6 +1342,7 @@ void cols_download(const Cols& C, HostCols& H, int n, cudaStream_t st) {
   dn(H.r0n2.data(), C.r0n2, n * 8);
   dn(H.tol2.data(), C.tol2, n * 8);
   dn(H.rel.data(), C.rel, n * 8);
+  dn(H.err.data(), C.err, n * 8);
   dn(H.active.data(), C.active, n * 4);
   dn(H.done.data(), C.done, n * 4);
   dn(H.iters.data(), C.iters, n * 4);
@@ -1344,6 +1368,7 @@ void cols_upload(const Cols& C, const HostCols& H, int n, cudaStream_t st) {
   up(C.r0n2, H.r0n2.data(), n * 8);
   up(C.tol2, H.tol2.data(), n * 8);
   up(C.rel, H.rel.data(), n * 8);
+  up(C.err, H.err.data(), n * 8);
   up(C.active, H.active.data(), n * 4);
   up(C.done, H.done.data(), n * 4);
   up(C.iters, H.iters.data(), n * 4);
@@ -1400,7 +1425,7 @@ class EngineT final : public Engine {
                                     (int)(kBlock * VEC * sizeof(double) +
                                           2 * std::max(stage_bytes(1), (size_t)kStageBytes))));
     // fixed part: partial sums, column state, tables
-    size_t total = (size_t)nb_max_ * 2 * wcap_ * 8 * 2 + (size_t)ncap_ * (8 * 16 + 4 * 12 + 4 * 8) +
+    size_t total = (size_t)nb_max_ * 8 * wcap_ * 8 + (size_t)ncap_ * (8 * 18 + 4 * 12 + 4 * 8) +
                    (size_t)wcap_ * 8 + 64 * 256;
     char* cur = (char*)scratch_alloc(total, st_);
     fixed_ = cur;
@@ -1410,8 +1435,8 @@ class EngineT final : public Engine {
       cur += (bytes + 255) / 256 * 256;
       return (void*)p;
     };
-    partial_ = (double*)take((size_t)nb_max_ * 2 * wcap_ * 8);
-    partial2_ = (double*)take((size_t)nb_max_ * 2 * wcap_ * 8);
+    partial_ = (double*)take((size_t)nb_max_ * 4 * wcap_ * 8);
+    partial2_ = (double*)take((size_t)nb_max_ * 4 * wcap_ * 8);
     C_.shift = (double*)take(ncap_ * 8);
     C_.rho = (double*)take(2 * ncap_ * 8);
     C_.alpha = (double*)take(2 * ncap_ * 8);
@@ -1421,6 +1446,7 @@ class EngineT final : public Engine {
     C_.r0n2 = (double*)take(ncap_ * 8);
     C_.tol2 = (double*)take(ncap_ * 8);
     C_.rel = (double*)take(ncap_ * 8);
+    C_.err = (double*)take(ncap_ * 8);
     C_.active = (int*)take(ncap_ * 4);
     C_.done = (int*)take(ncap_ * 4);
     C_.iters = (int*)take(ncap_ * 4);
@@ -1443,10 +1469,13 @@ class EngineT final : public Engine {
     P_.n = (int32_t)n_;
     P_.maxit = o.max_iter > 0 ? o.max_iter : 100000;
     P_.tol2_rel = o.tol * o.tol;
+    P_.err2 = o.err_tol * o.err_tol;
     const double itol = (sizeof(T) == 8) ? 0.0 : (o.inner_tol > 0 ? o.inner_tol : 1e-4);
     P_.inner2 = itol * itol;
     P_.wmax = E_->max_width;
-    m_it_ = o.check_every > 0 ? o.check_every : 32;
+    // iterations per step: a multigrid iteration costs several plain ones and
+    // its rounds are short, so its columns are checked more often
+    m_it_ = o.check_every > 0 ? o.check_every : (o.precond == IFILT_PRECOND_MG ? 8 : 32);
     const char* ng = getenv("IFILT_NO_GRAPH");
     use_graph_ = !(ng && ng[0] == '1');
     if (o.precond == IFILT_PRECOND_MG) mg_setup();
@@ -1589,7 +1618,7 @@ class EngineT final : public Engine {
   // one step: refinement prologue, m iterations, counters to the host
   void enqueue_step(bool check) {
     const int W = P_.W;
-    const size_t sm2 = spmm_smem(W), sm3 = smem_of(W, 3), sm4 = smem_of(W, 4);
+    const size_t sm2 = spmm_smem(W), sm3 = smem_of(W, 3), sm4 = smem_of(W, 8);
     const int fg = (P_.ncols + 31) / 32;
     const dim3 fb(32, 8);
     const unsigned evf = check ? cudaEventRecordDefault : cudaEventRecordExternal;
@@ -1690,7 +1719,7 @@ class EngineT final : public Engine {
   void set_width(int W) {
     P_.W = W;
     P_.ncols = W / LPC;
-    P_.pstride = 2 * W;
+    P_.pstride = 4 * W;
     P_.spt = W > 0 ? spmm_spt(W) : 1;
     P_.stage_e = (int)stage_entries(P_.spt);
   }
@@ -1860,13 +1889,15 @@ class EngineT final : public Engine {
     for (int c = 0; c < nc; c++) {
       if (!emit[c]) continue;
       Slot& sl = cur_[c];
-      const int status = (H.status[c] != 0 || H.rel[c] > o_.tol) ? IFILT_NOT_CONVERGED : IFILT_OK;
+      const bool err_bad = o_.err_tol > 0.0 && !(H.err[c] <= o_.err_tol);
+      const int status = (H.status[c] != 0 || H.rel[c] > o_.tol || err_bad) ? IFILT_NOT_CONVERGED : IFILT_OK;
       if (sl.job.stat) {
         sl.job.stat->iters = H.iters[c];
         sl.job.stat->refinements = H.rounds[c];
         sl.job.stat->status = status;
         sl.job.stat->pad = 0;
         sl.job.stat->rel_residual = H.rel[c];
+        sl.job.stat->err_bound = H.err[c];
       }
       done.push_back({sl.job.request, status});
       sl.retired = true;

@@ -248,6 +248,7 @@ ifilt_status solve_plain(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, 
           s.status = ok ? IFILT_OK : IFILT_NOT_CONVERGED;
           s.pad = 0;
           s.rel_residual = rel;
+          s.err_bound = 0.0;
         }
       }
     }

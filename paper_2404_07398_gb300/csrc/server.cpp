@@ -6,6 +6,7 @@
 // concurrently on the device.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -37,7 +38,8 @@ struct Request {
   double t_submit = 0, t_start = 0, t_done = 0;
 };
 
-using Key = std::tuple<ifilt_mesh, int, int, int, int>;  // mesh, order, precision, n = 2 form, preconditioner
+// mesh, order, precision, n = 2 form, preconditioner, error tolerance
+using Key = std::tuple<ifilt_mesh, int, int, int, int, double>;
 
 struct EngineSlot {
   std::unique_ptr<ifilt::Engine> engine;
@@ -79,7 +81,7 @@ struct ifilt_server_s {
       o.max_lanes = opts.max_lanes;
       o.check_every = opts.check_every;
       const bool cplx = o.order >= 2 && o.n2_solver != IFILT_N2_REAL;
-      Key key{r->mesh, o.order, o.precision, o.order >= 2 ? (cplx ? 2 : 1) : 0, o.precond};
+      Key key{r->mesh, o.order, o.precision, o.order >= 2 ? (cplx ? 2 : 1) : 0, o.precond, o.err_tol};
       auto it = engines.find(key);
       if (it == engines.end()) {
         EngineSlot slot;
@@ -249,6 +251,7 @@ ifilt_status ifilt_server_submit(ifilt_server s, ifilt_mesh mesh, const ifilt_so
     if (n_fields <= 0 || n_k <= 0) fail(IFILT_EINVAL, "n_fields and n_k must be positive");
     if (o->order < 1 || o->order > mesh->host.max_order) fail(IFILT_EINVAL, "order outside the mesh's range");
     if (!(o->tol > 0.0)) fail(IFILT_EINVAL, "tol must be positive");
+    if (!(o->err_tol >= 0.0) || !std::isfinite(o->err_tol)) fail(IFILT_EINVAL, "err_tol must be >= 0 and finite");
     if (o->precision < IFILT_PREC_FP64 || o->precision > IFILT_PREC_BF16_IR) fail(IFILT_EINVAL, "unknown precision");
     if (o->precond < IFILT_PRECOND_NONE || o->precond > IFILT_PRECOND_MG) fail(IFILT_EINVAL, "unknown precond");
     if (o->precond == IFILT_PRECOND_MG &&

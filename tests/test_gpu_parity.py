@@ -193,6 +193,39 @@ def test_multigrid_cuts_iterations_at_large_scales(lib, placement):
     assert its[lib.PRECOND_MG].max() * 3 <= its[lib.PRECOND_NONE].max(), its
 
 
+@pytest.mark.parametrize("placement,order,prec", [("vertex_scalar", 2, 1), ("vertex_vector", 2, 1), ("cell", 1, 1),
+                                                  ("cell", 2, 0)])
+def test_error_bound_stop_is_certified(lib, placement, order, prec):
+    """With err_tol each column stops only once ||r||_{M^-1} <= err_tol ||x||_M;
+    against the oracle's exact fields the M-norm error of every column is
+    within the reported bound, and the bound within err_tol."""
+    m = _sphere(4, 65, polar=10.0)
+    P = oracle.build_problem(m, placement)
+    f = _fields(P, 1, 9)
+    ks = synth.log_wavenumbers(6000.0, 200.0, 4)
+    err_tol = 1e-7
+    res, stats, st = _run(lib, m, placement, f, ks, order, tol=1e-4, precision=prec, n2_solver=2,
+                          precond=lib.PRECOND_MG if prec else 0, err_tol=err_tol)
+    assert st == 0, stats
+    _, ref = _oracle(m, placement, f, ks, order)
+    st3 = stats.reshape(len(ks), -1)
+    w = P.weights()
+    ids = P.out_ids
+    for j in range(len(ks)):
+        xs = [res[0, j, c][ids] for c in range(res.shape[2])]
+        rs = [ref[0, j, c][ids] for c in range(ref.shape[2])]
+        if placement == "vertex_vector":
+            xs, rs = [np.concatenate(xs)], [np.concatenate(rs)]
+            ww = np.concatenate([w, w])
+        else:
+            ww = w
+        for c, (x, r) in enumerate(zip(xs, rs)):
+            bound = st3[j, c]["err_bound"]
+            assert bound <= err_tol
+            err = np.sqrt(np.sum(ww * (x - r) ** 2) / np.sum(ww * x * x))
+            assert err <= bound * (1 + 1e-6) + 1e-13, (j, c, err, bound)
+
+
 def test_preconditioner_option_checked(lib):
     import torch
     m = _sphere(2, 60)
