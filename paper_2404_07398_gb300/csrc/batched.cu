@@ -1457,6 +1457,7 @@ class EngineT final : public Engine {
     C_.round_cap = (int*)take(ncap_ * 4);
     C_.restart = (int*)take(ncap_ * 4);
     C_.live = (int*)take(4 * 4);
+    tune_live_ = (int*)take(4 * 4);
     lane_src_ = (int*)take(wcap_ * 4);
     lane_map_ = (int*)take(wcap_ * 4);
     flags_ = (int*)take(ncap_ * 4);
@@ -1465,6 +1466,11 @@ class EngineT final : public Engine {
     col_out_ = (double**)take(ncap_ * 8);
     col_in_ = (const double**)take(ncap_ * 8);
     IFILT_CUDA(cudaMemsetAsync(C_.live, 0, 16, st_));
+    {
+      const int one[4] = {1, 0, 0, 0};
+      IFILT_CUDA(cudaMemcpyAsync(tune_live_, one, sizeof one, cudaMemcpyHostToDevice, st_));
+      IFILT_CUDA(cudaStreamSynchronize(st_));
+    }
     IFILT_CUDA(cudaMallocHost(&h_cnt_, 4 * sizeof(int)));
     P_.n = (int32_t)n_;
     P_.maxit = o.max_iter > 0 ? o.max_iter : 100000;
@@ -1545,7 +1551,7 @@ class EngineT final : public Engine {
   }
   int spmm_spt(int W) const {
     const int RPP = kBlock / (W / VEC);
-    int spt = std::max(1, (RPP * kTilePasses + E_->slice_h - 1) / E_->slice_h);
+    int spt = std::max(1, (RPP * tp_cg_ + E_->slice_h - 1) / E_->slice_h);
     while (spt > 1 && stage_bytes(spt) > (size_t)kStageBytes) spt--;
     // keep several tiles per resident block so that the grid ends evenly
     const long long want = (long long)n_sms_ * kMinB * 8;
@@ -1555,7 +1561,9 @@ class EngineT final : public Engine {
   size_t spmm_smem(int W) const { return smem_of(W, 2) + 2 * stage_bytes(spmm_spt(W)); }
   int blocks_for(int W) const {
     const long long ntiles = (E_->n_slices + spmm_spt(W) - 1) / spmm_spt(W);
-    return std::min(nb_max_, grid_for((const void*)spmm_fn(), kBlock, spmm_smem(W), ntiles * kBlock));
+    int nb = std::min(nb_max_, grid_for((const void*)spmm_fn(), kBlock, spmm_smem(W), ntiles * kBlock));
+    if (bpsm_cg_ > 0) nb = std::min(nb, n_sms_ * bpsm_cg_);
+    return nb;
   }
   size_t src_bytes() const { return (size_t)2 * n_ * NS * sizeof(double); }
   const T* mass_t() const {
@@ -1696,6 +1704,7 @@ class EngineT final : public Engine {
     if (graph_) cudaGraphDestroy(graph_);
     exec_ = nullptr;
     graph_ = nullptr;
+    autotune();
     nb_ = blocks_for(P_.W);
     // the streaming kernels get their own grids: as many resident blocks as fit
     const long long rows_threads = (long long)n_ * (P_.W / VEC);
@@ -2029,6 +2038,112 @@ class EngineT final : public Engine {
   cudaGraphExec_t exec_ = nullptr;
   int m_it_ = 32;
   bool use_graph_ = true, launched_ = false, prof_ = false;
+  // ------------------------------------------------------------ autotuning
+  // Launch shape of the gather kernels (rows per tile, blocks per SM), chosen
+  // per engine kind and tile-width bucket by timing the candidates on the live
+  // tiles at the first capture, and kept with the mesh for later engines.
+  // The timed launches write only outputs the next iteration recomputes (q,
+  // partial sums, multigrid scratch) and see a "live" flag forced to 1.
+  int tp_cg_ = kTilePasses, bpsm_cg_ = 0, tp_mg_ = kTilePasses, bpsm_mg_ = 0;  // bpsm 0: occupancy
+  Cols mg_cols_{};
+  int* tune_live_ = nullptr;
+  std::string tune_key(int W) const {
+    int wb = 4;
+    while (wb < W) wb <<= 1;
+    char b[96];
+    snprintf(b, sizeof b, "T%d/V%d/c%d/b%d/mg%d/E%d/W%d", (int)sizeof(T), (int)sizeof(MV), (int)CPLX, (int)BLK,
+             mg_on_ ? 1 : 0, E_ == &m_->ell_g2 ? 2 : 1, wb);
+    return b;
+  }
+  void autotune() {
+    mg_cols_ = C_;
+    const int W = P_.W;
+    if (W <= 0) return;
+    const char* env = getenv("IFILT_AUTOTUNE");
+    if (env && env[0] == '0') return;
+    const std::string key = tune_key(W);
+    {
+      std::lock_guard<std::mutex> lk(m_->tune_mu);
+      auto it = m_->tune.find(key);
+      if (it != m_->tune.end()) {
+        tp_cg_ = it->second[0];
+        bpsm_cg_ = it->second[1];
+        tp_mg_ = it->second[2];
+        bpsm_mg_ = it->second[3];
+        set_width(W);
+        return;
+      }
+    }
+    Cols Ct = C_;
+    Ct.live = tune_live_;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    IFILT_CUDA(cudaEventCreate(&e0));
+    IFILT_CUDA(cudaEventCreate(&e1));
+    auto timeit = [&](auto&& launch) {
+      launch();  // warm
+      IFILT_CUDA(cudaEventRecord(e0, st_));
+      for (int i = 0; i < 3; i++) launch();
+      IFILT_CUDA(cudaEventRecord(e1, st_));
+      IFILT_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      IFILT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      launch_check("autotune", 0, 0, W);
+      return ms;
+    };
+    const int tps[3] = {4, 8, 16};
+    int occ = 1;
+    float best = 1e30f;
+    int btp = kTilePasses, bb = 0;
+    for (int tp : tps) {
+      tp_cg_ = tp;
+      bpsm_cg_ = 0;
+      set_width(W);
+      IFILT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)spmm_fn(), kBlock, spmm_smem(W)));
+      for (int bps : {0, occ - 1}) {  // all resident blocks, or one fewer per SM
+        if (bps == occ - 1 && bps < 1) continue;
+        bpsm_cg_ = bps;
+        const int nb = blocks_for(W);
+        const size_t sm = spmm_smem(W);
+        const float ms = timeit([&] {
+          spmm_fn()<<<nb, kBlock, sm, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), Ct, partial_,
+                                             MgArgs<T>{});
+        });
+        if (ms < best) {
+          best = ms;
+          btp = tp;
+          bb = bps;
+        }
+      }
+    }
+    tp_cg_ = btp;
+    bpsm_cg_ = bb;
+    if (mg_on_) {
+      best = 1e30f;
+      btp = kTilePasses;
+      bb = 0;
+      mg_cols_ = Ct;
+      for (int tp : tps) {
+        for (int bps : {0, 2}) {
+          tp_mg_ = tp;
+          bpsm_mg_ = bps;
+          const float ms = timeit([&] { mg_smooth(0, mgb_[0].a, mgb_[0].b, tl_.r, nullptr); });
+          if (ms < best) {
+            best = ms;
+            btp = tp;
+            bb = bps;
+          }
+        }
+      }
+      mg_cols_ = C_;
+      tp_mg_ = btp;
+      bpsm_mg_ = bb;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_width(W);
+    std::lock_guard<std::mutex> lk(m_->tune_mu);
+    m_->tune[key] = {tp_cg_, bpsm_cg_, tp_mg_, bpsm_mg_};
+  }
   // ------------------------------------------------------------ multigrid
   static constexpr int kMgMinB = 3;
   static constexpr int kMgCoarseSweeps = 4;  // Jacobi sweeps on the coarsest level
@@ -2059,7 +2174,7 @@ class EngineT final : public Engine {
   }
   int spt_of(const DevEll& E, int W, int vbytes, int minb) const {
     const int RPP = kBlock / (W / VEC);
-    int spt = std::max(1, (RPP * kTilePasses + E.slice_h - 1) / E.slice_h);
+    int spt = std::max(1, (RPP * tp_mg_ + E.slice_h - 1) / E.slice_h);
     while (spt > 1 && stage_bytes_of(E, spt, vbytes) > (size_t)kStageBytes) spt--;
     const long long want = (long long)n_sms_ * minb * 8;
     while (spt > 1 && (E.n_slices + spt - 1) / spt < want) spt--;
@@ -2135,9 +2250,10 @@ class EngineT final : public Engine {
     Q.stage_e = (int)stage_entries_of(E, Q.spt);
     const size_t smem = smem_of(W, 2) + 2 * stage_bytes_of(E, Q.spt, vbytes);
     const long long ntiles = (E.n_slices + Q.spt - 1) / Q.spt;
-    const int blocks = std::min(nb_max_, grid_for(mg_fn<EPI, NSET>(), kBlock, smem, ntiles * kBlock));
+    int blocks = std::min(nb_max_, grid_for(mg_fn<EPI, NSET>(), kBlock, smem, ntiles * kBlock));
+    if (bpsm_mg_ > 0) blocks = std::min(blocks, n_sms_ * bpsm_mg_);
     spmm_kernel<T, T, CPLX, BLK, 4, kMgMinB, EPI, NSET><<<blocks, kBlock, smem, st_>>>(
-        ell_view<T>(E), Q, E.n_slices, src, out, mdiag, C_, partial, MgArgs<T>{kd, rhs, own, (T)kMgOmega});
+        ell_view<T>(E), Q, E.n_slices, src, out, mdiag, mg_cols_, partial, MgArgs<T>{kd, rhs, own, (T)kMgOmega});
     return blocks;
   }
   // S_l-operations: level 0 uses the mesh's K and lumped mass, coarser levels their (K, M) pair

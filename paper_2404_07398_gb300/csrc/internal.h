@@ -1,7 +1,9 @@
 // Internal declarations of libifilt (not part of the C ABI).
 #pragma once
 
+#include <array>
 #include <cstdint>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -120,6 +122,9 @@ struct ifilt_mesh_s {
   std::mutex mg_mu;
   std::shared_ptr<ifilt::MgHost> mg_host;
   std::vector<ifilt::DevMgLevel> mg_dev;
+  // autotuned launch shapes of the batched solver, per engine kind and tile width
+  std::mutex tune_mu;
+  std::map<std::string, std::array<int, 4>> tune;
 };
 
 namespace ifilt {
