@@ -244,12 +244,11 @@ struct MgArgs {
 // <p, q>: the row's few terms are summed in FP32, then added to the
 // compensated per-thread accumulator.
 template <typename T, bool CPLX, bool BLK>
-__device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, int l0, const T* __restrict__ mass,
+__device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, int l0, const T mr,
                                               const T* sh, T (*acc)[Pack<T>::N], const Pack<T>* own,
                                               T* __restrict__ q, DotAcc<T>* dacc) {
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
-  const T mr = mass[r];
   T rowdot[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; v++) rowdot[v] = (T)0;
@@ -291,15 +290,12 @@ __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, in
 // (NSET = 2); own is x_r (SMOOTH, RESID) or y_r (PROLONG); mdiag is the
 // diagonal of M_l (the lumped mass on the finest level).
 template <typename T, bool CPLX, bool BLK, int EPI, int NSET>
-__device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int l0, const T* __restrict__ mdiag,
-                                            const T* sh, T (*acc)[Pack<T>::N], T (*accm)[Pack<T>::N],
-                                            const Pack<T>* own, const MgArgs<T>& g, T* __restrict__ out,
-                                            DotAcc<T>* dacc, bool dot) {
+__device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int l0, const T mr, const T gr,
+                                            const Pack<T>* rhs, const T* sh, T (*acc)[Pack<T>::N],
+                                            T (*accm)[Pack<T>::N], const Pack<T>* own, const MgArgs<T>& g,
+                                            T* __restrict__ out, DotAcc<T>* dacc, bool dot) {
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
-  T mr = (T)0, gr = (T)0;
-  if constexpr (EPI == kEpiSmooth || EPI == kEpiResid) mr = mdiag[r];
-  if constexpr (EPI == kEpiSmooth) gr = g.dk[r];
   T rowdot[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; v++) rowdot[v] = (T)0;
@@ -314,7 +310,7 @@ __device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int 
 #pragma unroll
       for (int v = 0; v < VEC; v++) o.v[v] = own[b].v[v] + acc[b][v];
     } else {
-      const Pack<T> rh = ldv(g.rhs + off);
+      const Pack<T>& rh = rhs[b];
       T res[VEC];
 #pragma unroll
       for (int v = 0; v < VEC; v++) {
@@ -361,6 +357,9 @@ __device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int 
 #endif
 #ifndef IFILT_SPMM_MINB
 #define IFILT_SPMM_MINB 3      // resident blocks per SM asked of the compiler for the other SpMM instances
+#endif
+#ifndef IFILT_MG_MINB_BLK
+#define IFILT_MG_MINB_BLK 2    // resident blocks per SM asked for the 2x2-block multigrid sweeps and residuals
 #endif
 #ifndef IFILT_SPMM_EB_BLK
 #define IFILT_SPMM_EB_BLK 4    // gathered entries in flight per row for 2x2-block FP32 SpMM
@@ -522,6 +521,15 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
 #pragma unroll
           for (int s = 0; s < NS; s++) pr[s] = ldp(p + r * rowW + (int64_t)s * W + l0);
         }
+        // the row's own operands are loaded with its gathers: one round of global loads per row
+        T mrow = (T)0, grow = (T)0;
+        Pack<T> rrow[NS];
+        if constexpr (EPI == kEpiCG || EPI == kEpiSmooth || EPI == kEpiResid) mrow = mass[r];
+        if constexpr (EPI == kEpiSmooth) grow = mg.dk[r];
+        if constexpr (EPI == kEpiSmooth || EPI == kEpiResid) {
+#pragma unroll
+          for (int s = 0; s < NS; s++) rrow[s] = ldv(mg.rhs + r * rowW + (int64_t)s * W + l0);
+        }
         T acc[NS][VEC], accm[NS][VEC];
 #pragma unroll
         for (int s = 0; s < NS; s++)
@@ -582,8 +590,9 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
             for (int v = 0; v < VEC; v++) dacc[v].spill(sred[tr * W + l0 + v]);
           }
         }
-        if constexpr (EPI == kEpiCG) spmm_epilogue<T, CPLX, BLK>(r, rowW, W, l0, mass, sh, acc, pr, q, dacc);
-        else mg_epilogue<T, CPLX, BLK, EPI, NSET>(r, rowW, W, l0, mass, sh, acc, accm, pr, mg, q, dacc, dot);
+        if constexpr (EPI == kEpiCG) spmm_epilogue<T, CPLX, BLK>(r, rowW, W, l0, mrow, sh, acc, pr, q, dacc);
+        else
+          mg_epilogue<T, CPLX, BLK, EPI, NSET>(r, rowW, W, l0, mrow, grow, rrow, sh, acc, accm, pr, mg, q, dacc, dot);
       }
     }
     if ((int)threadIdx.x < ncnt) {
@@ -2161,9 +2170,14 @@ class EngineT final : public Engine {
   double* partial2_ = nullptr;
   int nbz_ = 1;  // blocks of the last level-0 smoothing sweep (partials of <r, z>)
 
+  // 2x2-block sweeps and residuals hold the row's right-hand side too: fewer blocks, no spills
+  template <int EPI>
+  static constexpr int mg_minb() {
+    return (BLK && (EPI == kEpiSmooth || EPI == kEpiResid)) ? IFILT_MG_MINB_BLK : kMgMinB;
+  }
   template <int EPI, int NSET>
   static const void* mg_fn() {
-    return (const void*)spmm_kernel<T, T, CPLX, BLK, 4, kMgMinB, EPI, NSET>;
+    return (const void*)spmm_kernel<T, T, CPLX, BLK, 4, mg_minb<EPI>(), EPI, NSET>;
   }
   static int64_t stage_entries_of(const DevEll& E, int spt) {
     return (int64_t)spt * ((int64_t)E.slice_h * E.max_width + 8);
@@ -2246,13 +2260,13 @@ class EngineT final : public Engine {
     const int vbytes = NVAL * NSET * (int)sizeof(T);
     Params Q = P_;
     Q.n = E.n;
-    Q.spt = spt_of(E, W, vbytes, kMgMinB);
+    Q.spt = spt_of(E, W, vbytes, mg_minb<EPI>());
     Q.stage_e = (int)stage_entries_of(E, Q.spt);
     const size_t smem = smem_of(W, 2) + 2 * stage_bytes_of(E, Q.spt, vbytes);
     const long long ntiles = (E.n_slices + Q.spt - 1) / Q.spt;
     int blocks = std::min(nb_max_, grid_for(mg_fn<EPI, NSET>(), kBlock, smem, ntiles * kBlock));
     if (bpsm_mg_ > 0) blocks = std::min(blocks, n_sms_ * bpsm_mg_);
-    spmm_kernel<T, T, CPLX, BLK, 4, kMgMinB, EPI, NSET><<<blocks, kBlock, smem, st_>>>(
+    spmm_kernel<T, T, CPLX, BLK, 4, mg_minb<EPI>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
         ell_view<T>(E), Q, E.n_slices, src, out, mdiag, mg_cols_, partial, MgArgs<T>{kd, rhs, own, (T)kMgOmega});
     return blocks;
   }
