@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
 // x += alpha p ; r -= alpha q ; partial <r, r> (slots [0, W): lane-wise for real,
 // (re, im) pairs for complex) and ||r||^2 (complex only, slots W + column).
 template <typename T, bool CPLX, bool BLK, bool PRE>
-__global__ void __launch_bounds__(kBlock, 4) update_kernel(Params P, T* __restrict__ x, const T* __restrict__ p,
+__global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T* __restrict__ x, const T* __restrict__ p,
                                                         T* __restrict__ r, const T* __restrict__ q, Cols C,
                                                         double* __restrict__ partial, const T* __restrict__ mass,
                                                         const T* __restrict__ gdiag) {
