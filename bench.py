@@ -63,6 +63,7 @@ def parse_args():
     ap.add_argument("--inner-tol", type=float, default=0.0, help="FP32 inner reduction per round (0: default)")
     ap.add_argument("--err-tol", type=float, default=1e-7,
                     help="also stop each column only at a certified relative M-norm error bound (0: off)")
+    ap.add_argument("--reorder", choices=["rcm", "hilbert"], default="rcm", help="device row order of the meshes")
     ap.add_argument("--concurrent", action="store_true",
                     help="step the two placements' solvers together (one solve_many call); per-kernel "
                          "event timings then overlap, so the roofline is not measured")
@@ -185,7 +186,7 @@ def workload_config(args, w, world):
             "vertices": int(m["coords"].shape[0]), "triangles": int(m["tri"].shape[0]),
             "columns_per_step": 4 * N_K, "order": 2, "n2_solver": "complex", "tol": args.tol,
             "precision": args.precision, "precond": getattr(args, "precond", "none"),
-            "err_tol": getattr(args, "err_tol", 0.0),
+            "err_tol": getattr(args, "err_tol", 0.0), "reorder": getattr(args, "reorder", "rcm"),
             "l2": "inputs larger than L2 (GBs per vector), no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
@@ -201,8 +202,9 @@ class Ours:
         self.k = np.ascontiguousarray(w["k"])
         self.fields = torch.tensor(w["fields"], dtype=torch.float64, device="cuda")
         t0 = time.time()
-        self.mv = api.prepare_mesh(w["mesh"], "vertex_vector", max_order=2)
-        self.mc = api.prepare_mesh(w["mesh"], "cell", max_order=2)
+        ro = {"rcm": api.REORDER_RCM, "hilbert": api.REORDER_HILBERT}[args.reorder]
+        self.mv = api.prepare_mesh(w["mesh"], "vertex_vector", max_order=2, reorder=ro)
+        self.mc = api.prepare_mesh(w["mesh"], "cell", max_order=2, reorder=ro)
         self.prepare_s = time.time() - t0
         prec = {"fp32": api.PREC_FP32_IR, "bf16": api.PREC_BF16_IR, "fp64": api.PREC_FP64}[args.precision]
         self.opts = dict(order=2, tol=args.tol, precision=prec, n2_solver=api.N2_COMPLEX,

@@ -61,7 +61,16 @@ enum {
   IFILT_GEOM_SPHERE = 2            /* coords [V][3] on a sphere of `radius`; flat chordal triangles */
 };
 
-enum { IFILT_REORDER_NONE = 0, IFILT_REORDER_RCM = 1 };
+/* Device row order.  RCM: reverse Cuthill-McKee on the graph of K (component
+ * start = least (degree, id), neighbours by (degree, id), reversed).  HILBERT:
+ * by a space-filling-curve key of each unknown's position (the vertex, or the
+ * triangle's corner average ((a + b) + c) / 3 in FP64), ties by id -- sphere:
+ * cube face of the direction (largest |component|, ties to x then y, +axis
+ * before -axis) then the Hilbert index of the two other components divided by
+ * the largest, each mapped to [0, 1] and quantised to 16 bits as
+ * floor(t * 2^16) clamped; plane: the coordinates scaled to the mesh's bounding
+ * box.  The curve starts at (0, 0) and ends at (2^16 - 1, 0). */
+enum { IFILT_REORDER_NONE = 0, IFILT_REORDER_RCM = 1, IFILT_REORDER_HILBERT = 2 };
 
 /* Arithmetic of the solve. */
 enum {

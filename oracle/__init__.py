@@ -27,7 +27,7 @@ from .mesh import ocean_subset, cell_subset, edge_vectors  # noqa: F401
 from .operators import (  # noqa: F401
     scalar_vertex_operators, vector_vertex_operators, cell_operators, order_operator,
 )
-from .reorder import rcm_order, check_rcm_order  # noqa: F401
+from .reorder import rcm_order, check_rcm_order, hilbert_index, curve_keys, curve_order  # noqa: F401
 from .solve import (  # noqa: F401
     cg, filter_field, filter_dense, residual_certificate, relative_residual, Problem, build_problem,
 )

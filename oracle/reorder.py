@@ -99,3 +99,90 @@ def check_rcm_order(indptr, indices, order):
         (k3_prev[1] < k3_next[1]) | ((k3_prev[1] == k3_next[1]) & (k3_prev[2] < k3_next[2]))))
     assert np.all(lt[both]), "breadth-first children not in (degree, id) order"
     return True
+
+
+# ---------------------------------------------------------------- space-filling curve
+# A second device order the library offers: unknowns sorted by a Hilbert-curve
+# key of their position, ties by id.  The oracle restates the rule on its own:
+#   * position: the vertex, or the corner average ((a + b) + c) / 3 of a triangle;
+#   * sphere: cube face of the direction (largest |component|, ties to x then y,
+#     face 2k for +axis k and 2k+1 for -axis k), the two other components divided
+#     by the largest, mapped to [0, 1] by (t + 1) / 2; plane: coordinates scaled
+#     to the bounding box of all vertices;
+#   * each coordinate quantised to 16 bits as floor(t * 2^16) clamped to the grid;
+#   * key = face * 2^32 + Hilbert index on the 2^16 x 2^16 grid, the curve
+#     starting at (0, 0) and ending at (2^16 - 1, 0).
+
+CURVE_BITS = 16
+
+
+def hilbert_index(x, y, bits):
+    """Position of grid cell (x, y) along the Hilbert curve of order `bits`.
+
+    Recursive definition: the square splits into four quadrants visited in the
+    order lower-left, upper-left, upper-right, lower-right; each quadrant holds
+    a copy of the curve, transposed in the two lower quadrants and additionally
+    reflected through the centre in the lower-right one, so that consecutive
+    quadrants join."""
+    if bits == 0:
+        return 0
+    half = 1 << (bits - 1)
+    right, upper = x >= half, y >= half
+    lx, ly = x - half * right, y - half * upper
+    if not upper:
+        if right:
+            lx, ly = half - 1 - lx, half - 1 - ly
+        lx, ly = ly, lx
+    quadrant = {(False, False): 0, (False, True): 1, (True, True): 2, (True, False): 3}[(right, upper)]
+    return quadrant * half * half + hilbert_index(lx, ly, bits - 1)
+
+
+def _quantise(t):
+    q = np.floor(np.asarray(t, dtype=np.float64) * float(1 << CURVE_BITS))
+    return np.clip(np.nan_to_num(q, nan=0.0), 0, (1 << CURVE_BITS) - 1).astype(np.int64)
+
+
+def curve_keys(pos, sphere, all_coords=None):
+    """Keys of points `pos` [n][2 or 3]; `all_coords` gives the bounding box (plane)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    n = pos.shape[0]
+    if sphere:
+        a = np.abs(pos)
+        axis = np.where((a[:, 0] >= a[:, 1]) & (a[:, 0] >= a[:, 2]), 0, np.where(a[:, 1] >= a[:, 2], 1, 2))
+        face = 2 * axis + (pos[np.arange(n), axis] < 0)
+        others = {0: (1, 2), 1: (0, 2), 2: (0, 1)}
+        u = np.empty(n)
+        v = np.empty(n)
+        for k in range(3):
+            sel = axis == k
+            m = a[sel, k]
+            u[sel] = pos[sel, others[k][0]] / m
+            v[sel] = pos[sel, others[k][1]] / m
+        iu, iv = _quantise((u + 1.0) * 0.5), _quantise((v + 1.0) * 0.5)
+    else:
+        c = np.asarray(all_coords, dtype=np.float64)
+        lo, hi = c[:, :2].min(axis=0), c[:, :2].max(axis=0)
+        span = np.where(hi > lo, hi - lo, 1.0)
+        iu, iv = _quantise((pos[:, 0] - lo[0]) / span[0]), _quantise((pos[:, 1] - lo[1]) / span[1])
+        face = np.zeros(n, dtype=np.int64)
+    d = np.array([hilbert_index(int(x), int(y), CURVE_BITS) for x, y in zip(iu, iv)], dtype=np.int64)
+    return face.astype(np.int64) * (1 << (2 * CURVE_BITS)) + d
+
+
+def curve_order(mesh, placement):
+    """Device order of the unknowns under the curve rule: original ids, order[new]."""
+    from .mesh import ocean_subset
+    coords = np.asarray(mesh["coords"], dtype=np.float64)
+    tri = np.asarray(mesh["tri"])
+    sphere = coords.shape[1] == 3
+    kept, verts, _ = ocean_subset(coords.shape[0], tri, mesh.get("ocean"))
+    if placement == "cell":
+        t = tri[kept]
+        pos = ((coords[t[:, 0]] + coords[t[:, 1]]) + coords[t[:, 2]]) / 3.0
+        ids = np.asarray(kept)
+    else:
+        pos = coords[verts]
+        ids = np.asarray(verts)
+    keys = curve_keys(pos, sphere, coords)
+    idx = np.lexsort((np.arange(ids.size), keys))
+    return ids[idx]

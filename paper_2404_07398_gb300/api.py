@@ -20,6 +20,7 @@ PREC_FP64, PREC_FP32_IR, PREC_BF16_IR = 0, 1, 2
 METHOD_PLAIN, METHOD_BATCHED = 0, 1
 N2_AUTO, N2_REAL, N2_COMPLEX = 0, 1, 2
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG = 0, 1, 2
+REORDER_NONE, REORDER_RCM, REORDER_HILBERT = 0, 1, 2
 MG_MAX_LEVELS = 16
 OK, NOT_CONVERGED = 0, 1
 EXPORT = dict(perm=0, k_rowptr=1, k_col=2, k_val=3, mass=4, g2_rowptr=5, g2_col=6, g2_val=7)

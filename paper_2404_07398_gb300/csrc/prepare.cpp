@@ -76,6 +76,72 @@ void bucket(int32_t n, const std::vector<int32_t>& key, std::vector<int64_t>& pt
   for (size_t i = 0; i < key.size(); i++) idx[fill[key[i]]++] = (int32_t)i;
 }
 
+// Index of grid cell (x, y), 0 <= x, y < 2^bits, along the Hilbert curve that
+// starts at (0, 0) and ends at (2^bits - 1, 0).  Top bit first: the quadrant
+// gives two bits of the index (lower-left 0, upper-left 1, upper-right 2,
+// lower-right 3), then the coordinates inside the quadrant are mapped into the
+// sub-curve's own frame (the lower quadrants are transposed, the lower-right
+// one also reflected) and the next bit is read.
+uint64_t hilbert_index(uint32_t x, uint32_t y, int bits) {
+  uint64_t d = 0;
+  for (int b = bits - 1; b >= 0; b--) {
+    const uint32_t s = 1u << b;
+    const uint32_t rx = (x >> b) & 1u, ry = (y >> b) & 1u;
+    d += (uint64_t)s * s * ((3u * rx) ^ ry);
+    x &= s - 1;
+    y &= s - 1;
+    if (ry == 0) {
+      if (rx == 1) {
+        x = s - 1 - x;
+        y = s - 1 - y;
+      }
+      std::swap(x, y);
+    }
+  }
+  return d;
+}
+
+constexpr int kCurveBits = 16;
+
+inline uint32_t quantise(double t) {  // t in [0, 1] -> 0 .. 2^bits - 1
+  const double q = std::floor(t * (double)(1u << kCurveBits));
+  if (!(q > 0.0)) return 0;
+  if (q >= (double)((1u << kCurveBits) - 1)) return (1u << kCurveBits) - 1;
+  return (uint32_t)q;
+}
+
+// Space-filling-curve key of a point.  Sphere: the cube face of the direction
+// (largest |component|, ties to x then y; +axis before -axis) and the two other
+// components divided by the largest, each in [-1, 1]; plane: the coordinates
+// scaled to the mesh's bounding box.
+uint64_t curve_key(const double* p, bool sphere, const double* lo, const double* span) {
+  if (sphere) {
+    const double ax = std::fabs(p[0]), ay = std::fabs(p[1]), az = std::fabs(p[2]);
+    int face;
+    double u, v, m;
+    if (ax >= ay && ax >= az) {
+      face = p[0] >= 0.0 ? 0 : 1;
+      m = ax;
+      u = p[1];
+      v = p[2];
+    } else if (ay >= az) {
+      face = p[1] >= 0.0 ? 2 : 3;
+      m = ay;
+      u = p[0];
+      v = p[2];
+    } else {
+      face = p[2] >= 0.0 ? 4 : 5;
+      m = az;
+      u = p[0];
+      v = p[1];
+    }
+    const uint32_t iu = quantise((u / m + 1.0) * 0.5), iv = quantise((v / m + 1.0) * 0.5);
+    return ((uint64_t)face << (2 * kCurveBits)) | hilbert_index(iu, iv, kCurveBits);
+  }
+  const uint32_t ix = quantise((p[0] - lo[0]) / span[0]), iy = quantise((p[1] - lo[1]) / span[1]);
+  return hilbert_index(ix, iy, kCurveBits);
+}
+
 std::vector<int32_t> reverse_cuthill_mckee(const Graph& g) {
   const int32_t n = g.n;
   std::vector<int32_t> deg(n);
@@ -226,7 +292,7 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   if (d.geometry == IFILT_GEOM_PLANAR_PERIODIC && !(d.period_x > 0 && d.period_y > 0))
     fail(IFILT_EINVAL, "periodic geometry needs positive periods");
   if (d.geometry == IFILT_GEOM_SPHERE && !(d.radius > 0)) fail(IFILT_EINVAL, "sphere needs radius > 0");
-  if (d.reorder != IFILT_REORDER_NONE && d.reorder != IFILT_REORDER_RCM) fail(IFILT_EINVAL, "unknown reorder %d", d.reorder);
+  if (d.reorder < IFILT_REORDER_NONE || d.reorder > IFILT_REORDER_HILBERT) fail(IFILT_EINVAL, "unknown reorder %d", d.reorder);
 
   const int32_t V = d.n_vert, T = d.n_tri;
   const int32_t* tri = d.tri;
@@ -338,8 +404,41 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
 
   // ---- 2. device order
   std::vector<int32_t> order(N), rank(N);
-  if (d.reorder == IFILT_REORDER_RCM) order = reverse_cuthill_mckee(g);
-  else std::iota(order.begin(), order.end(), 0);
+  if (d.reorder == IFILT_REORDER_RCM) {
+    order = reverse_cuthill_mckee(g);
+  } else if (d.reorder == IFILT_REORDER_HILBERT) {
+    // positions: the vertex, or the triangle's corner average ((a + b) + c) / 3
+    const bool sphere = d.geometry == IFILT_GEOM_SPHERE;
+    double lo[2] = {0, 0}, span[2] = {1, 1};
+    if (!sphere) {
+      double hi[2] = {d.coords[0], d.coords[1]};
+      lo[0] = d.coords[0];
+      lo[1] = d.coords[1];
+      for (int32_t v = 0; v < V; v++)
+        for (int k = 0; k < 2; k++) {
+          lo[k] = std::min(lo[k], d.coords[2 * (int64_t)v + k]);
+          hi[k] = std::max(hi[k], d.coords[2 * (int64_t)v + k]);
+        }
+      for (int k = 0; k < 2; k++) span[k] = hi[k] > lo[k] ? hi[k] - lo[k] : 1.0;
+    }
+    std::vector<std::pair<uint64_t, int32_t>> key(N);
+    for (int32_t i = 0; i < N; i++) {
+      double pos[3];
+      if (cells) {
+        const int32_t* tv = tri + 3 * (int64_t)kept[i];
+        for (int k = 0; k < dim; k++)
+          pos[k] = ((d.coords[dim * (int64_t)tv[0] + k] + d.coords[dim * (int64_t)tv[1] + k]) +
+                    d.coords[dim * (int64_t)tv[2] + k]) / 3.0;
+      } else {
+        for (int k = 0; k < dim; k++) pos[k] = d.coords[dim * (int64_t)verts[i] + k];
+      }
+      key[i] = {curve_key(pos, sphere, lo, span), i};
+    }
+    std::sort(key.begin(), key.end());
+    for (int32_t r = 0; r < N; r++) order[r] = key[r].second;
+  } else {
+    std::iota(order.begin(), order.end(), 0);
+  }
   for (int32_t r = 0; r < N; r++) rank[order[r]] = r;
 
   hp.n_rows = N;

@@ -226,6 +226,26 @@ def test_error_bound_stop_is_certified(lib, placement, order, prec):
             assert err <= bound * (1 + 1e-6) + 1e-13, (j, c, err, bound)
 
 
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+def test_space_filling_curve_order(lib, placement):
+    """The Hilbert device order changes only the layout (and the multigrid
+    aggregates): the filtered fields still match the oracle."""
+    import torch
+    m = _sphere(4, 67, polar=10.0)
+    P = oracle.build_problem(m, placement)
+    f = _fields(P, 1, 10)
+    ks = synth.log_wavenumbers(6000.0, 300.0, 4)
+    h = lib.prepare_mesh(m, placement, max_order=2, reorder=lib.REORDER_HILBERT)
+    ft = torch.tensor(f, dtype=torch.float64, device="cuda")
+    for opts in (dict(precision=1, precond=lib.PRECOND_MG), dict(precision=0)):
+        out, stats, st = lib.solve(h, ft, ks, order=2, tol=1e-12 if opts["precision"] == 0 else 1e-10,
+                                   n2_solver=2, **opts)
+        assert st == 0
+        _, ref = _oracle(m, placement, f, ks, 2)
+        _check(out.cpu().numpy(), ref, TOL_FP64 if opts["precision"] == 0 else TOL_MIXED)
+    h.release()
+
+
 def test_preconditioner_option_checked(lib):
     import torch
     m = _sphere(2, 60)
