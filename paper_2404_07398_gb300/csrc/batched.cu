@@ -2407,8 +2407,10 @@ size_t batched_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o, i
   const size_t n = (size_t)h.n_rows;
   const size_t cols = (size_t)W / (cplx ? 2 : 1);
   const size_t srcs = std::min<size_t>((size_t)F * nsys, cols) * n * ns * 16;
+  // multigrid: two fine scratch vectors and three per coarser level (coarsening >= 1.25x per level)
+  const size_t mg = o.precond == IFILT_PRECOND_MG ? n * ns * W * tb * (2 + 3 * 4) : 0;
   // tiles twice (old and new during a re-pack), sources, partial sums and tables
-  return 2 * n * ns * W * (4 * tb + 8) + srcs + (size_t)152 * 8 * 2 * W * 8 + (1 << 20);
+  return 2 * n * ns * W * (4 * tb + 8) + mg + srcs + (size_t)152 * 8 * 8 * W * 8 + (1 << 20);
 }
 
 namespace {

@@ -86,6 +86,34 @@ def test_request_same_alone_and_in_mix(lib):
     h2.release()
 
 
+def test_multigrid_requests_in_the_mix(lib):
+    """Multigrid and unpreconditioned requests on one mesh run in separate
+    engines of the server and both match the oracle."""
+    import torch
+    m = _sphere(4, 87)
+    h = lib.prepare_mesh(m, "vertex_scalar", max_order=2)
+    rng = np.random.default_rng(13)
+    f = torch.tensor(rng.normal(size=(2, 1, h.info["n_in"])), device="cuda")
+    ks = synth.log_wavenumbers(5000.0, 300.0, 4)
+    srv = lib.Server(max_lanes=32, check_every=8)
+    try:
+        ids = [srv.submit(h, f, ks, order=2, tol=1e-10, precision=lib.PREC_FP32_IR, precond=pc)
+               for pc in (lib.PRECOND_MG, lib.PRECOND_NONE, lib.PRECOND_MG)]
+        infos = _wait_all(srv, ids)
+        outs = [srv.result(rid)[0].cpu().numpy() for rid in ids]
+    finally:
+        srv.close()
+    for rid in ids:
+        assert infos[rid]["state"] == 2 and infos[rid]["status"] == 0
+    P = oracle.build_problem(m, "vertex_scalar")
+    for fi in range(2):
+        ref, _ = oracle.filter_field(P, f[fi].cpu().numpy(), ks, 2)
+        for o in outs:
+            for j in range(ks.size):
+                assert _rel(o[fi, j, 0], ref[j, 0]) <= 1e-6
+    h.release()
+
+
 def test_small_memory_budget_still_completes(lib):
     """A budget that holds only a few lanes at a time: columns wait for memory
     and are admitted as others retire."""
