@@ -1234,7 +1234,7 @@ __global__ void gather_lanes_kernel(int64_t rows, int Wold, int Wnew, const int*
 // The FP64 solution (real part) of every column flagged in `emit`, written to
 // its caller block out[comp][o] in original mesh order; land entries copy the
 // input (scalar, cell) or are zero (vector).
-template <bool CPLX, bool BLK>
+template <bool CPLX, bool BLK, bool DFX>
 __global__ void output_kernel(Params P, int32_t n_out, const int32_t* __restrict__ inv,
                               const double* __restrict__ x64, double* const* __restrict__ col_out,
                               const double* const* __restrict__ col_in, const int* __restrict__ emit) {
@@ -1249,10 +1249,274 @@ __global__ void output_kernel(Params P, int32_t n_out, const int32_t* __restrict
 #pragma unroll
     for (int b = 0; b < NS; b++) {
       double v;
-      if (r >= 0) v = x64[((int64_t)r * NS + b) * P.W + lane];
+      if (r >= 0) {
+        const int64_t i = ((int64_t)r * NS + b) * P.W + lane;
+        if constexpr (DFX) {  // double-float pair (FP32 engines)
+          const float2 h = reinterpret_cast<const float2*>(x64)[i];
+          v = (double)h.x + (double)h.y;
+        } else {
+          v = x64[i];
+        }
+      }
       else v = BLK ? 0.0 : in[o];
       out[(int64_t)b * n_out + o] = v;
     }
+  }
+}
+
+
+// ------------------------------------------------------------ double-float
+// The FP32 engines keep the refined solution x and the right-hand sides as
+// unevaluated pairs hi + lo of floats (about 48 significant bits) and compute
+// the true residual with them on the FP32 pipes: products split exactly with an
+// FMA, sums by two-sum (Dekker; Knuth).  GB300's FP64 rate is a small fraction
+// of its FP32 rate, and this residual is recomputed for every refinement round.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_from(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ DF df_norm(float s, float e) {  // |e| small relative to s
+  const float t = __fadd_rn(s, e);
+  return {t, __fsub_rn(e, __fsub_rn(t, s))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float z = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
+  return df_norm(s, __fadd_rn(err, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_norm(p, e);
+}
+__device__ __forceinline__ DF df_add_f(DF a, float b) { return df_add(a, DF{b, 0.f}); }
+
+// x64 = x0 (refined-solution lanes of newly admitted columns) as double-float pairs
+template <bool CPLX, bool BLK>
+__global__ void init_lanes_df_kernel(Params P, const double* const* __restrict__ xptr, const int* __restrict__ lane_src,
+                                     const int* __restrict__ fresh, DF* __restrict__ x) {
+  constexpr int NS = BLK ? 2 : 1;
+  const int64_t total = (int64_t)P.n * NS * P.W;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i % P.W);
+    if (!fresh[CPLX ? l >> 1 : l]) continue;
+    const int64_t rs = i / P.W;
+    x[i] = (CPLX && (l & 1)) ? DF{0.f, 0.f} : df_from(xptr[lane_src[l]][rs]);
+  }
+}
+template <bool CPLX>
+__global__ void accumulate_df_kernel(int64_t total, int W, const int* __restrict__ refresh, DF* __restrict__ x,
+                                     const float* __restrict__ d, const int* __restrict__ live) {
+  if (live[1] == 0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i % W);
+    if (refresh[CPLX ? l >> 1 : l]) x[i] = df_add_f(x[i], d[i]);
+  }
+}
+// a right-hand side b (double) rewritten in place as double-float pairs
+__global__ void to_df_kernel(int64_t n, double* __restrict__ v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const DF a = df_from(v[i]);
+    reinterpret_cast<DF*>(v)[i] = a;
+  }
+}
+
+// The refinement residual of the FP32 engines, as residual_kernel computes it
+// in FP64 but in double-float arithmetic: r = b - (M x + shift * (G x)) with the
+// operator values split hi + lo (val32 and val32lo), the lumped mass likewise,
+// x and b as pairs.  Writes r (rounded to float), the restarted p (= r, or
+// D^-1 r with Jacobi) and d = 0 on the refreshed lanes, and per-block partials
+// of <r, z>, ||r||^2, ||r||^2_{M^-1} and ||x||^2_M (compensated FP32 sums of
+// the rounded values, flushed to FP64).
+template <bool CPLX, bool BLK>
+__global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A, const float* __restrict__ vlo, Params P,
+                                                               const DF* __restrict__ x, const DF* const* __restrict__ bptr,
+                                                               const int* __restrict__ lane_src,
+                                                               const float* __restrict__ mhi, const float* __restrict__ mlo,
+                                                               Cols C, float* __restrict__ r, float* __restrict__ d,
+                                                               float* __restrict__ p, double* __restrict__ partial,
+                                                               const float* __restrict__ gdiag) {
+  constexpr int VEC = Pack<float>::N;
+  constexpr int NS = BLK ? 2 : 1;
+  constexpr int NV = BLK ? 2 : 1;
+  if (C.live[1] == 0) return;
+  extern __shared__ double sm[];
+  const int W = P.W;
+  const int ncolsW = CPLX ? W / 2 : W;
+  const int NSL = W + 3 * ncolsW;
+  const int TPR = W / VEC;
+  const int RPP = kBlock / TPR;
+  const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
+  const int l0 = g * VEC;
+  DotAcc<float> d1[VEC], d2[VEC], e2[VEC], x2[VEC];
+  bool mine[VEC];
+  bool any = false, all = true;
+#pragma unroll
+  for (int v = 0; v < VEC; v++) {
+    mine[v] = C.refresh[CPLX ? (l0 + v) >> 1 : l0 + v] != 0;
+    any |= mine[v];
+    all &= mine[v];
+  }
+  if (tr < RPP && any) {
+    DF sh[VEC];
+    int src[VEC];
+    float shf[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; v++) {
+      const double s = C.shift[CPLX ? (l0 + v) >> 1 : l0 + v];
+      sh[v] = df_from(s);
+      shf[v] = (float)s;
+      src[v] = lane_src[l0 + v];
+    }
+    const int64_t rowW = (int64_t)NS * W;
+    int chain = 0;
+    for (int64_t row = (int64_t)blockIdx.x * RPP + tr; row < P.n; row += (int64_t)gridDim.x * RPP) {
+      const int s = (int)(row / A.slice_h);
+      const int w = A.slice_w[s];
+      const int64_t base = A.slice_off[s] + (row - (int64_t)s * A.slice_h) * w;
+      DF acc[NS][VEC];
+#pragma unroll
+      for (int b = 0; b < NS; b++)
+#pragma unroll
+        for (int v = 0; v < VEC; v++) acc[b][v] = DF{0.f, 0.f};
+      for (int e = 0; e < w; e++) {
+        const int c = A.col[base + e];
+        const DF* xs = x + (int64_t)c * rowW + l0;
+        DF xu[VEC], xw[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; v++) {
+          xu[v] = xs[v];
+          if constexpr (BLK) xw[v] = xs[W + v];
+        }
+        if constexpr (BLK) {
+          const DF a{A.val[(base + e) * NV], vlo[(base + e) * NV]};
+          const DF bb{A.val[(base + e) * NV + 1], vlo[(base + e) * NV + 1]};
+#pragma unroll
+          for (int v = 0; v < VEC; v++) {
+            acc[0][v] = df_add(acc[0][v], df_add(df_mul(a, xu[v]), df_mul(bb, xw[v])));
+            acc[1][v] = df_add(acc[1][v], df_add(df_mul(a, xw[v]), df_neg(df_mul(bb, xu[v]))));
+          }
+        } else {
+          const DF a{A.val[base + e], vlo[base + e]};
+#pragma unroll
+          for (int v = 0; v < VEC; v++) acc[0][v] = df_add(acc[0][v], df_mul(a, xu[v]));
+        }
+      }
+      const DF mr{mhi[row], mlo[row]};
+      const float mrf = mhi[row];
+      const float gr = gdiag ? gdiag[row] : 0.f;
+      if (++chain == kFlushRows) {
+        chain = 0;
+#pragma unroll
+        for (int v = 0; v < VEC; v++) {
+          d1[v].flush();
+          d2[v].flush();
+          e2[v].flush();
+          x2[v].flush();
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < NS; b++) {
+        const int64_t off = row * rowW + (int64_t)b * W + l0;
+        DF xo[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; v++) xo[v] = x[off + v];
+        Pack<float> ro, po, zo;
+#pragma unroll
+        for (int v = 0; v < VEC; v++) zo.v[v] = 0.f;
+        if constexpr (CPLX) {
+#pragma unroll
+          for (int v = 0; v < VEC; v += 2) {
+            const DF bre = bptr[src[v]][row * NS + b];
+            // r_re = b - (m x_re - s acc_im),  r_im = -(m x_im + s acc_re)
+            const DF q_re = df_add(df_mul(mr, xo[v]), df_neg(df_mul(sh[v], acc[b][v + 1])));
+            const DF q_im = df_add(df_mul(mr, xo[v + 1]), df_mul(sh[v], acc[b][v]));
+            const DF rre = df_add(bre, df_neg(q_re));
+            const DF rim = df_neg(q_im);
+            const float tre = rre.hi + rre.lo, tim = rim.hi + rim.lo;
+            float zre = tre, zim = tim;
+            if (gdiag) {
+              const float bg = shf[v] * gr;
+              const float inv = 1.f / __fmaf_rn(mrf, mrf, bg * bg);
+              zre = __fmaf_rn(tre, mrf, tim * bg) * inv;
+              zim = __fmaf_rn(tim, mrf, -(tre * bg)) * inv;
+            }
+            ro.v[v] = tre;
+            ro.v[v + 1] = tim;
+            po.v[v] = zre;
+            po.v[v + 1] = zim;
+            d1[v].add_sum(__fmaf_rn(tre, zre, -(tim * zim)));
+            d1[v + 1].add_sum(__fmaf_rn(tre, zim, tim * zre));
+            const float nn = __fmaf_rn(tre, tre, tim * tim);
+            d2[v / 2].add_sum(nn);
+            e2[v / 2].add_sum(nn / mrf);
+            const float xr = xo[v].hi;
+            x2[v / 2].add_sum(mrf * xr * xr);  // the filtered field is the real part
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; v++) {
+            const DF bv = bptr[src[v]][row * NS + b];
+            const DF q = df_add(df_mul(mr, xo[v]), df_mul(sh[v], acc[b][v]));
+            const DF rv = df_add(bv, df_neg(q));
+            const float t = rv.hi + rv.lo;
+            const float z = gdiag ? t / __fmaf_rn(shf[v], gr, mrf) : t;
+            ro.v[v] = t;
+            po.v[v] = z;
+            d1[v].add(t, z);
+            d2[v].add(t, t);
+            e2[v].add_sum(t * t / mrf);
+            x2[v].add_sum(mrf * xo[v].hi * xo[v].hi);
+          }
+        }
+        if (all) {
+          stp(r + off, ro);
+          stp(p + off, po);
+          stp(d + off, zo);
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; v++)
+            if (mine[v]) {
+              r[off + v] = ro.v[v];
+              p[off + v] = po.v[v];
+              d[off + v] = 0.f;
+            }
+        }
+      }
+    }
+  }
+  if (tr < RPP) {
+#pragma unroll
+    for (int v = 0; v < VEC; v++) sm[tr * NSL + l0 + v] = d1[v].get();
+    if constexpr (CPLX) {
+#pragma unroll
+      for (int v = 0; v < VEC / 2; v++) {
+        sm[tr * NSL + W + l0 / 2 + v] = d2[v].get();
+        sm[tr * NSL + W + ncolsW + l0 / 2 + v] = e2[v].get();
+        sm[tr * NSL + W + 2 * ncolsW + l0 / 2 + v] = x2[v].get();
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < VEC; v++) {
+        sm[tr * NSL + W + l0 + v] = d2[v].get();
+        sm[tr * NSL + W + ncolsW + l0 + v] = e2[v].get();
+        sm[tr * NSL + W + 2 * ncolsW + l0 + v] = x2[v].get();
+      }
+    }
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < NSL; l += kBlock) {
+    double s = 0.0;
+    for (int t = 0; t < RPP; t++) s += sm[t * NSL + l];
+    partial[(int64_t)blockIdx.x * P.pstride + l] = s;
   }
 }
 
@@ -1620,6 +1884,11 @@ class EngineT final : public Engine {
     q.buf = (double*)scratch_alloc(src_bytes(), st_);
     q.refs = 1;
     launch_rhs(m_, j.field, j.sys, q.buf, q.buf + (size_t)n_ * NS, st_);
+    if constexpr (sizeof(T) == 4) {  // b as double-float pairs for the FP32 engines' residual
+      const int g = grid_for((const void*)to_df_kernel, kBlock, 0, n_ * NS);
+      to_df_kernel<<<g, kBlock, 0, st_>>>(n_ * NS, q.buf);
+      other_launches_++;
+    }
     other_launches_++;
     return s;
   }
@@ -1650,14 +1919,31 @@ class EngineT final : public Engine {
       if (e != cudaSuccess) fail(IFILT_ECUDA, "%s (W=%d, blocks=%d): %s", what, W, nb_, cudaGetErrorString(e));
     };
     const int ga = grid_for((const void*)accumulate_kernel<T, CPLX>, kBlock, 0, n_ * NS * W);
+    const int nr = std::min(nb_max_, grid_for((const void*)residual_df_kernel<CPLX, BLK>, kBlock, sm4,
+                                              (long long)n_ * (W / VEC)));
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
     chk("scan");
-    accumulate_kernel<T, CPLX><<<ga, kBlock, 0, st_>>>(n_ * NS * W, W, C_.refresh, tl_.x64, tl_.d, C_.live);
+    if constexpr (sizeof(T) == 4)
+      accumulate_df_kernel<CPLX><<<ga, kBlock, 0, st_>>>(n_ * NS * W, W, C_.refresh, reinterpret_cast<DF*>(tl_.x64),
+                                                        tl_.d, C_.live);
+    else
+      accumulate_kernel<T, CPLX><<<ga, kBlock, 0, st_>>>(n_ * NS * W, W, C_.refresh, tl_.x64, tl_.d, C_.live);
     chk("accumulate");
-    residual_kernel<T, CPLX, BLK><<<nb_, kBlock, sm4, st_>>>(A64_, P_, tl_.x64, bptr_, lane_src_, m_->mass, C_,
-                                                            tl_.r, tl_.d, tl_.p, partial_, gdiag64());
+    rec(10);
+    int nbr = nb_;
+    if constexpr (sizeof(T) == 4) {
+      nbr = nr;
+      residual_df_kernel<CPLX, BLK><<<nr, kBlock, sm4, st_>>>(
+          ell_view<float>(*E_), E_->val32lo, P_, reinterpret_cast<const DF*>(tl_.x64),
+          reinterpret_cast<const DF* const*>(bptr_), lane_src_, m_->mass32, m_->mass32lo, C_, tl_.r, tl_.d, tl_.p,
+          partial_, gdiag_t());
+    } else {
+      residual_kernel<T, CPLX, BLK><<<nb_, kBlock, sm4, st_>>>(A64_, P_, tl_.x64, bptr_, lane_src_, m_->mass, C_,
+                                                              tl_.r, tl_.d, tl_.p, partial_, gdiag64());
+    }
     chk("residual");
-    finish_residual_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
+    rec(11);
+    finish_residual_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbr, partial_, C_);
     chk("finish_residual");
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
     for (int it = 0; it < m_it_; it++) {
@@ -1843,7 +2129,11 @@ class EngineT final : public Engine {
     cols_upload(C_, Hn, ncn, st_);
     IFILT_CUDA(cudaMemcpyAsync(flags_, fresh.data(), ncn * 4, cudaMemcpyHostToDevice, st_));
     const int g = grid_for((const void*)init_lanes_kernel<CPLX, BLK>, kBlock, 0, rows * Wn);
-    init_lanes_kernel<CPLX, BLK><<<g, kBlock, 0, st_>>>(P_, xptr_, lane_src_, flags_, tl_.x64);
+    if constexpr (sizeof(T) == 4)
+      init_lanes_df_kernel<CPLX, BLK><<<g, kBlock, 0, st_>>>(P_, xptr_, lane_src_, flags_,
+                                                             reinterpret_cast<DF*>(tl_.x64));
+    else
+      init_lanes_kernel<CPLX, BLK><<<g, kBlock, 0, st_>>>(P_, xptr_, lane_src_, flags_, tl_.x64);
     other_launches_++;
     launch_check("init lanes", g, 0, Wn);
     IFILT_CUDA(cudaStreamSynchronize(st_));
@@ -1900,7 +2190,8 @@ class EngineT final : public Engine {
     if (!any) return;
     IFILT_CUDA(cudaMemcpyAsync(flags_, emit.data(), nc * 4, cudaMemcpyHostToDevice, st_));
     dim3 og((unsigned)std::min<long long>((h.n_out + kBlock - 1) / kBlock, 1024), (unsigned)nc);
-    output_kernel<CPLX, BLK><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, col_out_, col_in_, flags_);
+    output_kernel<CPLX, BLK, sizeof(T) == 4><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, col_out_,
+                                                                     col_in_, flags_);
     other_launches_++;
     launch_check("output", (int)og.x, 0, P_.W);
     IFILT_CUDA(cudaStreamSynchronize(st_));
@@ -1945,6 +2236,9 @@ class EngineT final : public Engine {
     (void)live;
     if (h_cnt_[3]) fail(IFILT_DEVICE_TIMEOUT, "SpMM stage copy did not complete within its wait limit");
     if (prof_) {
+      float tr = 0;
+      IFILT_CUDA(cudaEventElapsedTime(&tr, ev_[10], ev_[11]));
+      t_res_ += tr;
       float a = 0, b = 0, c = 0;
       IFILT_CUDA(cudaEventElapsedTime(&a, ev_[0], ev_[1]));
       IFILT_CUDA(cudaEventElapsedTime(&b, ev_[2], ev_[3]));
@@ -2010,6 +2304,15 @@ class EngineT final : public Engine {
         profile_add(nm, launches, samples_, t_[4], by_[4] / samples_);
       }
     }
+    if (prof_ && steps_ > 0) {  // every step's FP64 residual (work follows the refreshed columns)
+      const char* k1 = CPLX ? "c" : "r";
+      const char* k2 = BLK ? "b" : "s";
+      const char* k3 = sizeof(T) == 8 ? "f64" : "f32";
+      char nm[40];
+      snprintf(nm, sizeof nm, "(residual64)_%s%s_%s", k1, k2, k3);
+      profile_add(nm, steps_, steps_, t_res_, 0.0);
+    }
+    t_res_ = 0.0;
     steps_ = 0;
     samples_ = 0;
     for (int i = 0; i < 5; i++) t_[i] = by_[i] = 0;
@@ -2367,10 +2670,11 @@ class EngineT final : public Engine {
     }
     return b;
   }
-  cudaEvent_t ev_[10] = {};
+  cudaEvent_t ev_[12] = {};
   unsigned evf_ = cudaEventRecordDefault;
   bool mg_sample_ = false;
   double t_[5] = {0, 0, 0, 0, 0}, by_[5] = {0, 0, 0, 0, 0};
+  double t_res_ = 0.0;  // FP64 true-residual kernel, every step
   int64_t samples_ = 0, steps_ = 0, other_launches_ = 0;
 };
 

@@ -64,10 +64,11 @@ void build_ell(ifilt_mesh_s* m, const HostCSR& a, int32_t slice_h, DevEll& out, 
       }
     }
   }
-  std::vector<float> v32(v64.size());
+  std::vector<float> v32(v64.size()), v32lo(v64.size());
   std::vector<__nv_bfloat16> v16(v64.size());
   for (size_t i = 0; i < v64.size(); i++) {
     v32[i] = (float)v64[i];
+    v32lo[i] = (float)(v64[i] - (double)v32[i]);
     v16[i] = __float2bfloat16_rn((float)v64[i]);
   }
   out.n = n;
@@ -81,6 +82,7 @@ void build_ell(ifilt_mesh_s* m, const HostCSR& a, int32_t slice_h, DevEll& out, 
   out.col = dev_copy(m, col.data(), col.size(), st);
   out.val64 = dev_copy(m, v64.data(), v64.size(), st);
   out.val32 = dev_copy(m, v32.data(), v32.size(), st);
+  out.val32lo = dev_copy(m, v32lo.data(), v32lo.size(), st);
   out.val16 = dev_copy(m, v16.data(), v16.size(), st);
 }
 
@@ -142,8 +144,10 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
   if (slice_h < 4 || slice_h > 1024) fail(IFILT_EINVAL, "ell_slice must be between 4 and 1024 rows");
   m->perm = dev_copy(m, h.perm.data(), h.perm.size(), st);
   m->mass = dev_copy(m, h.mass.data(), h.mass.size(), st);
-  std::vector<float> m32(h.mass.begin(), h.mass.end());
+  std::vector<float> m32(h.mass.begin(), h.mass.end()), m32lo(h.mass.size());
+  for (size_t i = 0; i < m32.size(); i++) m32lo[i] = (float)(h.mass[i] - (double)m32[i]);
   m->mass32 = dev_copy(m, m32.data(), m32.size(), st);
+  m->mass32lo = dev_copy(m, m32lo.data(), m32lo.size(), st);
   std::vector<double> dk = diagonal(h.K);
   m->diag_k = dev_copy(m, dk.data(), dk.size(), st);
   std::vector<float> dk32(dk.begin(), dk.end());

@@ -72,6 +72,7 @@ struct DevEll {
   int32_t* col = nullptr;
   double* val64 = nullptr;
   float* val32 = nullptr;
+  float* val32lo = nullptr;  // val64 - val32 rounded to float (double-float residual)
   __nv_bfloat16* val16 = nullptr;
 };
 
@@ -107,6 +108,7 @@ struct ifilt_mesh_s {
   int32_t* perm = nullptr;       // [n_rows]
   double* mass = nullptr;        // [n_rows]
   float* mass32 = nullptr;       // [n_rows] the same in FP32 (FP32 kernels)
+  float* mass32lo = nullptr;     // [n_rows] mass - mass32 rounded to float (double-float residual)
   double* diag_k = nullptr;      // [n_rows] diagonal of K (K~ for vectors)
   double* diag_g2 = nullptr;     // [n_rows]
   float* diag_k32 = nullptr;     // [n_rows] FP32 copies (Jacobi preconditioning in FP32 kernels)
