@@ -75,8 +75,9 @@ enum { IFILT_REORDER_NONE = 0, IFILT_REORDER_RCM = 1, IFILT_REORDER_HILBERT = 2 
 /* Arithmetic of the solve. */
 enum {
   IFILT_PREC_FP64 = 0,       /* FP64 matrix, vectors and dots */
-  IFILT_PREC_FP32_IR = 1,    /* FP32 matrix and Krylov vectors, FP64 dots, FP64 true residual
-                                and iterative-refinement correction */
+  IFILT_PREC_FP32_IR = 1,    /* FP32 matrix and Krylov vectors, FP64-accurate dots, true residual
+                                and iterative-refinement correction in double-float (hi + lo FP32
+                                pairs) when tol >= 1e-10 and err_tol is 0 or >= 1e-8, else FP64 */
   IFILT_PREC_BF16_IR = 2     /* as FP32_IR with BF16-stored matrix values */
 };
 

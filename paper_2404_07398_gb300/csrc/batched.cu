@@ -1757,6 +1757,9 @@ class EngineT final : public Engine {
     m_it_ = o.check_every > 0 ? o.check_every : (o.precond == IFILT_PRECOND_MG ? 8 : 32);
     const char* ng = getenv("IFILT_NO_GRAPH");
     use_graph_ = !(ng && ng[0] == '1');
+    // double-float refinement residual on the FP32 engines, unless a tolerance asks for more than its
+    // about 48 bits carry on hard columns; then FP64, as on the FP64 engine
+    df_ = sizeof(T) == 4 && o.tol >= kDfMinTol && (!(o.err_tol > 0.0) || o.err_tol >= kDfMinErrTol);
     if (o.precond == IFILT_PRECOND_MG) mg_setup();
     P_.mg = mg_on_ ? 1 : 0;
     prof_ = profiling_on();
@@ -1884,7 +1887,7 @@ class EngineT final : public Engine {
     q.buf = (double*)scratch_alloc(src_bytes(), st_);
     q.refs = 1;
     launch_rhs(m_, j.field, j.sys, q.buf, q.buf + (size_t)n_ * NS, st_);
-    if constexpr (sizeof(T) == 4) {  // b as double-float pairs for the FP32 engines' residual
+    if (df_) {  // b as double-float pairs for the double-float residual
       const int g = grid_for((const void*)to_df_kernel, kBlock, 0, n_ * NS);
       to_df_kernel<<<g, kBlock, 0, st_>>>(n_ * NS, q.buf);
       other_launches_++;
@@ -1923,24 +1926,33 @@ class EngineT final : public Engine {
                                               (long long)n_ * (W / VEC)));
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
     chk("scan");
-    if constexpr (sizeof(T) == 4)
-      accumulate_df_kernel<CPLX><<<ga, kBlock, 0, st_>>>(n_ * NS * W, W, C_.refresh, reinterpret_cast<DF*>(tl_.x64),
-                                                        tl_.d, C_.live);
-    else
+    bool done_acc = false;
+    if constexpr (sizeof(T) == 4) {
+      if (df_) {
+        accumulate_df_kernel<CPLX><<<ga, kBlock, 0, st_>>>(n_ * NS * W, W, C_.refresh,
+                                                          reinterpret_cast<DF*>(tl_.x64), tl_.d, C_.live);
+        done_acc = true;
+      }
+    }
+    if (!done_acc)
       accumulate_kernel<T, CPLX><<<ga, kBlock, 0, st_>>>(n_ * NS * W, W, C_.refresh, tl_.x64, tl_.d, C_.live);
     chk("accumulate");
     rec(10);
     int nbr = nb_;
+    bool done_res = false;
     if constexpr (sizeof(T) == 4) {
-      nbr = nr;
-      residual_df_kernel<CPLX, BLK><<<nr, kBlock, sm4, st_>>>(
-          ell_view<float>(*E_), E_->val32lo, P_, reinterpret_cast<const DF*>(tl_.x64),
-          reinterpret_cast<const DF* const*>(bptr_), lane_src_, m_->mass32, m_->mass32lo, C_, tl_.r, tl_.d, tl_.p,
-          partial_, gdiag_t());
-    } else {
+      if (df_) {
+        nbr = nr;
+        done_res = true;
+        residual_df_kernel<CPLX, BLK><<<nr, kBlock, sm4, st_>>>(
+            ell_view<float>(*E_), E_->val32lo, P_, reinterpret_cast<const DF*>(tl_.x64),
+            reinterpret_cast<const DF* const*>(bptr_), lane_src_, m_->mass32, m_->mass32lo, C_, tl_.r, tl_.d, tl_.p,
+            partial_, gdiag_t());
+      }
+    }
+    if (!done_res)
       residual_kernel<T, CPLX, BLK><<<nb_, kBlock, sm4, st_>>>(A64_, P_, tl_.x64, bptr_, lane_src_, m_->mass, C_,
                                                               tl_.r, tl_.d, tl_.p, partial_, gdiag64());
-    }
     chk("residual");
     rec(11);
     finish_residual_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbr, partial_, C_);
@@ -2129,7 +2141,7 @@ class EngineT final : public Engine {
     cols_upload(C_, Hn, ncn, st_);
     IFILT_CUDA(cudaMemcpyAsync(flags_, fresh.data(), ncn * 4, cudaMemcpyHostToDevice, st_));
     const int g = grid_for((const void*)init_lanes_kernel<CPLX, BLK>, kBlock, 0, rows * Wn);
-    if constexpr (sizeof(T) == 4)
+    if (df_)
       init_lanes_df_kernel<CPLX, BLK><<<g, kBlock, 0, st_>>>(P_, xptr_, lane_src_, flags_,
                                                              reinterpret_cast<DF*>(tl_.x64));
     else
@@ -2190,8 +2202,12 @@ class EngineT final : public Engine {
     if (!any) return;
     IFILT_CUDA(cudaMemcpyAsync(flags_, emit.data(), nc * 4, cudaMemcpyHostToDevice, st_));
     dim3 og((unsigned)std::min<long long>((h.n_out + kBlock - 1) / kBlock, 1024), (unsigned)nc);
-    output_kernel<CPLX, BLK, sizeof(T) == 4><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, col_out_,
-                                                                     col_in_, flags_);
+    if (df_)
+      output_kernel<CPLX, BLK, true><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, col_out_, col_in_,
+                                                             flags_);
+    else
+      output_kernel<CPLX, BLK, false><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, col_out_,
+                                                              col_in_, flags_);
     other_launches_++;
     launch_check("output", (int)og.x, 0, P_.W);
     IFILT_CUDA(cudaStreamSynchronize(st_));
@@ -2670,6 +2686,8 @@ class EngineT final : public Engine {
     }
     return b;
   }
+  static constexpr double kDfMinTol = 1e-10, kDfMinErrTol = 1e-8;
+  bool df_ = false;  // refined solution, right-hand sides and true residual as double-float pairs
   cudaEvent_t ev_[12] = {};
   unsigned evf_ = cudaEventRecordDefault;
   bool mg_sample_ = false;
