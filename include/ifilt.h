@@ -51,7 +51,16 @@ typedef enum {
 enum {
   IFILT_VERTEX_SCALAR = 0,   /* scalar at vertices, median-dual volumes, P1 FE (Sect. 2.1.1)     */
   IFILT_VERTEX_VECTOR = 1,   /* (u, v) from cells filtered at vertices with metric terms (Sect. 2.1.2) */
-  IFILT_CELL = 2             /* (u, v) at triangles, simplified Laplacian of Eq. 6, per component */
+  IFILT_CELL = 2,            /* (u, v) at triangles, simplified Laplacian of Eq. 6, per component */
+  IFILT_VERTEX_VORONOI = 3,  /* scalar at vertices, quasi-hexagonal control volumes, finite volumes
+                                (Eq. 3-5): A_v (D phi)_v = l^2 sum (phi_v - phi_v') l_vv' / d_vv',
+                                d the edge length, l the distance between the circumcentres on its
+                                two sides (signed; the edge midpoint on a coast), A_v the area of the
+                                circumcentric (Voronoi) dual cell */
+  IFILT_CELL_CIRCUMCENTER = 4 /* scalar at triangle circumcentres, finite volumes: A_c (D phi)_c =
+                                l^2 sum (phi_c - phi_c') l_e / d_cc', l_e the shared edge's length,
+                                d_cc' the distance between the two circumcentres; EMESH where they
+                                coincide */
 };
 
 /* Mesh geometry. */

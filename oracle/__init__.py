@@ -26,6 +26,7 @@ that check the oracle against closed forms live in tests/.
 from .mesh import ocean_subset, cell_subset, edge_vectors  # noqa: F401
 from .operators import (  # noqa: F401
     scalar_vertex_operators, vector_vertex_operators, cell_operators, order_operator,
+    voronoi_vertex_operators, circumcenter_cell_operators,
 )
 from .reorder import rcm_order, check_rcm_order, hilbert_index, curve_keys, curve_order  # noqa: F401
 from .solve import (  # noqa: F401

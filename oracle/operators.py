@@ -11,6 +11,8 @@ a split-square grid whose cotangent weight is exactly 0 is still an entry).
                             cell-to-vertex projection R_vc = int N_v M_c (Sect. 2.1.2).
   cell_operators          : A * (graph Laplacian of edge-adjacent ocean triangles) and
                             the triangle areas A_c (Eq. 6).
+  voronoi_vertex_operators: quasi-hexagonal finite volumes around the vertices (Eq. 3-5).
+  circumcenter_cell_operators: finite volumes for scalars at triangle circumcentres.
   order_operator          : G_n = K (M^-1 K)^(n-1), so that S = M + (1/2) l^(2n) G_n
                             (Sect. 2.1.1 for n = 2; the paper notes the generalisation).
 
@@ -162,6 +164,92 @@ def cell_operators(mesh, cell_A=None):
     e2 = edge_vectors(mesh, t[:, 0], t[:, 2])
     area = 0.5 * np.linalg.norm(np.cross(e1, e2), axis=1)
     return dict(K=(Aconst * L).tocsr(), A=area, cell_ids=kept, pairs=pairs)
+
+
+def _circumcentres(e1, e2):
+    """Circumcentre of each flat triangle as a vector from its corner 0 (e1, e2 the
+    edges from corner 0): the point O = a e1 + b e2 equidistant from the three
+    corners, from the 2 x 2 Gram system O . e1 = |e1|^2 / 2, O . e2 = |e2|^2 / 2."""
+    g11 = np.einsum("ij,ij->i", e1, e1)
+    g22 = np.einsum("ij,ij->i", e2, e2)
+    g12 = np.einsum("ij,ij->i", e1, e2)
+    det = g11 * g22 - g12 * g12
+    a = (0.5 * g11 * g22 - 0.5 * g22 * g12) / det
+    b = (0.5 * g22 * g11 - 0.5 * g11 * g12) / det
+    return a[:, None] * e1 + b[:, None] * e2
+
+
+def voronoi_vertex_operators(mesh):
+    """Quasi-hexagonal control volumes around the vertices (Eq. 3-5):
+    A_v (D phi)_v = l^2 sum_v' (phi_v - phi_v') l_vv' / d_vv' with d_vv' the edge
+    length and l_vv' the distance between the circumcentres of the triangles on
+    both sides (signed: a circumcentre beyond the edge counts negative; on a
+    coast the edge midpoint stands in for the missing side), and A_v the area
+    of the circumcentric dual cell (sum of the kites d h / 4 of the half-dual
+    segments h around v).  Returns dict(K, A, vert_ids, kept_tri) with K the
+    l-free operator."""
+    V = mesh["coords"].shape[0]
+    tri = np.asarray(mesh["tri"], dtype=np.int64)
+    kept_tri, vert_ids, tl = ocean_subset(V, tri, mesh.get("ocean"))
+    t = tri[kept_tri]
+    n = vert_ids.size
+    e1 = edge_vectors(mesh, t[:, 0], t[:, 1])
+    e2 = edge_vectors(mesh, t[:, 0], t[:, 2])
+    nrm = np.cross(e1, e2)
+    nhat = nrm / np.linalg.norm(nrm, axis=1)[:, None]
+    O = _circumcentres(e1, e2)
+    corner = [np.zeros_like(e1), e1, e2]  # corners relative to corner 0
+    rows, cols, vals = [], [], []
+    area = np.zeros(n)
+    for k, a, b in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        pab = corner[b] - corner[a]
+        d = np.linalg.norm(pab, axis=1)
+        # signed distance of O from the line (a, b), positive on the side of corner k
+        h = np.einsum("ij,ij->i", np.cross(pab, O - corner[a]), nhat) / d
+        w = -h / d
+        rows += [tl[:, a], tl[:, b]]
+        cols += [tl[:, b], tl[:, a]]
+        vals += [w, w]
+        area += np.bincount(tl[:, a], weights=0.25 * d * h, minlength=n)
+        area += np.bincount(tl[:, b], weights=0.25 * d * h, minlength=n)
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    diag = -np.bincount(rows, weights=vals, minlength=n)
+    idx = np.arange(n)
+    K = _coo(np.concatenate([rows, idx]), np.concatenate([cols, idx]), np.concatenate([vals, diag]), n)
+    return dict(K=K, A=area, vert_ids=vert_ids, kept_tri=kept_tri)
+
+
+def circumcenter_cell_operators(mesh):
+    """Scalars at triangle circumcentres (the paper's equation for them):
+    A_c (D phi)_c = l^2 sum_c' (phi_c - phi_c') l_e / d_cc' with l_e the length
+    of the shared edge and d_cc' the distance between the two circumcentres;
+    A_c the triangle area.  Returns dict(K, A, cell_ids)."""
+    V = mesh["coords"].shape[0]
+    tri = np.asarray(mesh["tri"], dtype=np.int64)
+    kept, pairs = cell_subset(V, tri, mesh.get("ocean"))
+    n = kept.size
+    t = tri[kept]
+    e1 = edge_vectors(mesh, t[:, 0], t[:, 1])
+    e2 = edge_vectors(mesh, t[:, 0], t[:, 2])
+    area = 0.5 * np.linalg.norm(np.cross(e1, e2), axis=1)
+    O = _circumcentres(e1, e2)  # from each triangle's corner 0
+    i, j = pairs[:, 0], pairs[:, 1]
+    w = np.empty(i.size)
+    for q in range(i.size):
+        ti, tj = t[i[q]], t[j[q]]
+        shared = [v for v in ti if v in set(tj.tolist())]
+        a, b = shared[0], shared[1]
+        le = np.linalg.norm(edge_vectors(mesh, np.array([a]), np.array([b]))[0])
+        # both circumcentres as vectors from the shared vertex a
+        oi = O[i[q]] - edge_vectors(mesh, np.array([ti[0]]), np.array([a]))[0]
+        oj = O[j[q]] - edge_vectors(mesh, np.array([tj[0]]), np.array([a]))[0]
+        w[q] = le / np.linalg.norm(oi - oj)
+    deg = np.bincount(np.concatenate([i, j]), weights=np.concatenate([w, w]), minlength=n)
+    idx = np.arange(n)
+    K = _coo(np.concatenate([i, j, idx]), np.concatenate([j, i, idx]), np.concatenate([-w, -w, deg]), n)
+    return dict(K=K.tocsr(), A=area, cell_ids=kept, pairs=pairs)
 
 
 def order_operator(K, A, n):

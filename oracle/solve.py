@@ -29,7 +29,8 @@ from dataclasses import dataclass, field as dc_field
 import numpy as np
 import scipy.sparse as sp
 
-from .operators import scalar_vertex_operators, vector_vertex_operators, cell_operators
+from .operators import (scalar_vertex_operators, vector_vertex_operators, cell_operators,
+                        voronoi_vertex_operators, circumcenter_cell_operators)
 
 
 @dataclass
@@ -52,7 +53,7 @@ class Problem:
 
     def systems(self, fld):
         """[(b, x0)] of the independent systems of one field [n_comp][n_in]."""
-        if self.placement == "vertex_scalar":
+        if self.placement in ("vertex_scalar", "vertex_voronoi"):
             phi = fld[0][self.parts["vert_ids"]]
             return [(self.A * phi, phi.copy())]
         if self.placement == "vertex_vector":
@@ -60,14 +61,14 @@ class Problem:
             R = self.parts["R"]
             b = np.concatenate([R @ fld[0][kc], R @ fld[1][kc]])
             return [(b, b / self.A)]
-        if self.placement == "cell":
+        if self.placement in ("cell", "cell_circumcenter"):
             ids = self.parts["cell_ids"]
             return [(self.A * fld[c][ids], fld[c][ids].copy()) for c in range(self.n_comp)]
         raise ValueError(self.placement)
 
     def output(self, fld, sols):
         """Assemble [n_comp][n_out] from the system solutions."""
-        if self.placement == "vertex_scalar":
+        if self.placement in ("vertex_scalar", "vertex_voronoi"):
             out = np.array(fld, dtype=np.float64, copy=True)
             out[0][self.out_ids] = sols[0]
             return out
@@ -103,6 +104,12 @@ def build_problem(mesh, placement, cell_A=None):
     if placement == "cell":
         o = cell_operators(mesh, cell_A)
         return Problem(placement, o["K"], o["A"], T, T, 2, o["cell_ids"], parts=o)
+    if placement == "vertex_voronoi":
+        o = voronoi_vertex_operators(mesh)
+        return Problem(placement, o["K"], o["A"], V, V, 1, o["vert_ids"], parts=o)
+    if placement == "cell_circumcenter":
+        o = circumcenter_cell_operators(mesh)
+        return Problem(placement, o["K"], o["A"], T, T, 1, o["cell_ids"], parts=o)
     raise ValueError(placement)
 
 

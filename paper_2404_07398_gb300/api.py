@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libifilt.so")
 
-VERTEX_SCALAR, VERTEX_VECTOR, CELL = 0, 1, 2
+VERTEX_SCALAR, VERTEX_VECTOR, CELL, VERTEX_VORONOI, CELL_CIRCUMCENTER = 0, 1, 2, 3, 4
 GEOM_PLANAR_PERIODIC, GEOM_PLANAR, GEOM_SPHERE = 0, 1, 2
 PREC_FP64, PREC_FP32_IR, PREC_BF16_IR = 0, 1, 2
 METHOD_PLAIN, METHOD_BATCHED = 0, 1
@@ -24,7 +24,8 @@ REORDER_NONE, REORDER_RCM, REORDER_HILBERT = 0, 1, 2
 MG_MAX_LEVELS = 16
 OK, NOT_CONVERGED = 0, 1
 EXPORT = dict(perm=0, k_rowptr=1, k_col=2, k_val=3, mass=4, g2_rowptr=5, g2_col=6, g2_val=7)
-PLACEMENTS = {"vertex_scalar": VERTEX_SCALAR, "vertex_vector": VERTEX_VECTOR, "cell": CELL}
+PLACEMENTS = {"vertex_scalar": VERTEX_SCALAR, "vertex_vector": VERTEX_VECTOR, "cell": CELL,
+              "vertex_voronoi": VERTEX_VORONOI, "cell_circumcenter": CELL_CIRCUMCENTER}
 GEOMS = {"planar_periodic": GEOM_PLANAR_PERIODIC, "planar": GEOM_PLANAR, "sphere": GEOM_SPHERE}
 
 

@@ -188,6 +188,19 @@ std::vector<int32_t> reverse_cuthill_mckee(const Graph& g) {
 }
 
 // Position of column c in row r of a CSR with sorted columns.
+// Circumcentre of a (flat) triangle tv, as a vector from its vertex `from`
+// (edge vectors are minimum images on periodic planes):  with e1, e2 the edges
+// from `from`, n = e1 x e2, it is (|e1|^2 e2 x n + |e2|^2 n x e1) / (2 |n|^2).
+inline V3 circumcentre_from(const Geometry& geo, const int32_t* tv, int from) {
+  int o[2], k = 0;
+  for (int i = 0; i < 3; i++)
+    if (tv[i] != from) o[k++] = tv[i];
+  const V3 e1 = geo.edge(from, o[0]), e2 = geo.edge(from, o[1]);
+  const V3 n = cross(e1, e2);
+  const double n2 = dot(n, n);
+  return scale(add(scale(cross(e2, n), dot(e1, e1)), scale(cross(n, e1), dot(e2, e2))), 0.5 / n2);
+}
+
 inline int64_t find_entry(const HostCSR& a, int32_t r, int32_t c) {
   const int32_t* b = a.col.data() + a.row_ptr[r];
   const int32_t* e = a.col.data() + a.row_ptr[r + 1];
@@ -286,7 +299,8 @@ HostCSR product_kmk(const HostCSR& K, const std::vector<double>& mass) {
 HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   if (d.n_vert <= 0 || d.n_tri <= 0 || !d.coords || !d.tri)
     fail(IFILT_EINVAL, "mesh needs n_vert > 0, n_tri > 0, coords and tri");
-  if (d.placement < IFILT_VERTEX_SCALAR || d.placement > IFILT_CELL) fail(IFILT_EINVAL, "unknown placement %d", d.placement);
+  if (d.placement < IFILT_VERTEX_SCALAR || d.placement > IFILT_CELL_CIRCUMCENTER)
+    fail(IFILT_EINVAL, "unknown placement %d", d.placement);
   if (d.geometry < IFILT_GEOM_PLANAR_PERIODIC || d.geometry > IFILT_GEOM_SPHERE) fail(IFILT_EINVAL, "unknown geometry %d", d.geometry);
   if (d.max_order < 1 || d.max_order > 2) fail(IFILT_EINVAL, "max_order must be 1 or 2");
   if (d.geometry == IFILT_GEOM_PLANAR_PERIODIC && !(d.period_x > 0 && d.period_y > 0))
@@ -352,7 +366,7 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
 
   // ---- graph of the n = 1 operator (compact ids)
   Graph g;
-  const bool cells = d.placement == IFILT_CELL;
+  const bool cells = d.placement == IFILT_CELL || d.placement == IFILT_CELL_CIRCUMCENTER;
   if (!cells) {
     g.n = Nv;
     g.ptr.assign((size_t)Nv + 1, 0);
@@ -444,8 +458,10 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   hp.n_rows = N;
   hp.perm.resize(N);
   for (int32_t r = 0; r < N; r++) hp.perm[r] = cells ? kept[order[r]] : verts[order[r]];
-  hp.n_comp = d.placement == IFILT_VERTEX_SCALAR ? 1 : 2;
-  hp.n_in = d.placement == IFILT_VERTEX_SCALAR ? V : T;
+  const bool scalar_in = d.placement == IFILT_VERTEX_SCALAR || d.placement == IFILT_VERTEX_VORONOI ||
+                         d.placement == IFILT_CELL_CIRCUMCENTER;
+  hp.n_comp = scalar_in ? 1 : 2;
+  hp.n_in = (d.placement == IFILT_VERTEX_SCALAR || d.placement == IFILT_VERTEX_VORONOI) ? V : T;
   hp.n_out = cells ? T : V;
 
   // ---- 3. operator and mass in device order
@@ -453,13 +469,87 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   hp.K = pattern_from_graph(g, order, rank, nval);
   HostCSR& K = hp.K;
   hp.mass.assign(N, 0.0);
-  if (cells) {
+  if (d.placement == IFILT_CELL_CIRCUMCENTER) {
+    // flux weight of a shared edge: its length over the distance between the two circumcentres,
+    // both circumcentres taken relative to the edge's first vertex (minimum-image edges)
+    for (int32_t r = 0; r < N; r++) hp.mass[r] = area[order[r]];
+    std::vector<double> offd(K.col.size(), 0.0);
+    for (int32_t r = 0; r < N; r++) {
+      const int32_t c = order[r];
+      const int32_t* tv = tri + 3 * (int64_t)kept[c];
+      for (int64_t q = K.row_ptr[r]; q < K.row_ptr[r + 1]; q++) {
+        const int32_t r2 = K.col[q];
+        if (r2 == r) continue;
+        const int32_t* tw = tri + 3 * (int64_t)kept[order[r2]];
+        // shared edge (a, b)
+        int a = -1, b = -1;
+        for (int i = 0; i < 3; i++)
+          for (int j = 0; j < 3; j++)
+            if (tv[i] == tw[j]) {
+              if (a < 0) a = tv[i];
+              else b = tv[i];
+            }
+        if (a < 0 || b < 0) fail(IFILT_EMESH, "neighbouring triangles %d and %d share no edge", kept[c], kept[order[r2]]);
+        const V3 oc = circumcentre_from(geo, tv, a), oc2 = circumcentre_from(geo, tw, a);
+        const double le = norm(geo.edge(a, b)), dcc = norm(sub(oc, oc2));
+        if (!(dcc > 1e-12 * le)) fail(IFILT_EMESH, "triangles %d and %d have coincident circumcentres", kept[c],
+                                      kept[order[r2]]);
+        offd[q] = -le / dcc;
+      }
+    }
+    for (int32_t r = 0; r < N; r++) {
+      double sdiag = 0.0;
+      int64_t pd = -1;
+      for (int64_t q = K.row_ptr[r]; q < K.row_ptr[r + 1]; q++) {
+        if (K.col[q] == r) pd = q;
+        else sdiag -= offd[q];
+      }
+      for (int64_t q = K.row_ptr[r]; q < K.row_ptr[r + 1]; q++) K.val[q] = q == pd ? sdiag : offd[q];
+    }
+  } else if (cells) {
     const double Ac = d.cell_A > 0 ? d.cell_A : std::sqrt(3.0);
     for (int32_t r = 0; r < N; r++) {
       int64_t b = K.row_ptr[r], e = K.row_ptr[r + 1];
       for (int64_t q = b; q < e; q++) K.val[q] = (K.col[q] == r) ? Ac * (double)(e - b - 1) : -Ac;
       hp.mass[r] = area[order[r]];
     }
+  } else if (d.placement == IFILT_VERTEX_VORONOI) {
+    // per triangle and edge: h = signed distance from the circumcentre to the edge midpoint,
+    // positive toward the opposite corner; the edge's flux weight gains h / d (l_vv' is the sum of
+    // the h of its triangles) and each end's dual cell the kite area d h / 4
+    std::vector<double> offd(K.col.size(), 0.0);
+    for (int32_t c = 0; c < Tk; c++) {
+      const int32_t* tv = tri + 3 * (int64_t)kept[c];
+      int32_t rr[3] = {rank[vid[tv[0]]], rank[vid[tv[1]]], rank[vid[tv[2]]]};
+      const V3 o = circumcentre_from(geo, tv, tv[0]);  // relative to corner 0
+      for (int k = 0; k < 3; k++) {
+        const int a = (k + 1) % 3, b = (k + 2) % 3;
+        const V3 pa = geo.edge(tv[0], tv[a]), pb = geo.edge(tv[0], tv[b]), pk = geo.edge(tv[0], tv[k]);
+        const V3 e = sub(pb, pa);
+        const double de = norm(e);
+        const V3 mid = scale(add(pa, pb), 0.5);
+        const V3 t = scale(e, 1.0 / de);
+        V3 toward = sub(pk, mid);
+        toward = sub(toward, scale(t, dot(toward, t)));
+        const V3 u = scale(toward, 1.0 / norm(toward));
+        const double h = dot(sub(o, mid), u);
+        offd[find_entry(K, rr[a], rr[b])] -= h / de;
+        offd[find_entry(K, rr[b], rr[a])] -= h / de;
+        hp.mass[rr[a]] += 0.25 * de * h;
+        hp.mass[rr[b]] += 0.25 * de * h;
+      }
+    }
+    for (int32_t r = 0; r < N; r++) {
+      double sdiag = 0.0;
+      int64_t pd = -1;
+      for (int64_t q = K.row_ptr[r]; q < K.row_ptr[r + 1]; q++) {
+        if (K.col[q] == r) pd = q;
+        else sdiag -= offd[q];
+      }
+      for (int64_t q = K.row_ptr[r]; q < K.row_ptr[r + 1]; q++) K.val[q] = q == pd ? sdiag : offd[q];
+    }
+    for (int32_t r = 0; r < N; r++)
+      if (!(hp.mass[r] > 0.0)) fail(IFILT_EMESH, "vertex %d has a non-positive circumcentric dual area", hp.perm[r]);
   } else {
     const bool vec = d.placement == IFILT_VERTEX_VECTOR;
     const bool sphere = d.geometry == IFILT_GEOM_SPHERE;

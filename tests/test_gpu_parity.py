@@ -18,8 +18,12 @@ TOL_FP64 = 1e-10
 TOL_MIXED = 1e-6
 
 
-def _sphere(level, seed, polar=0.0, ocean=True):
-    m = synth.icosphere(level, radius=6371.0, jitter=0.2, seed=seed)
+def _sphere(level, seed, polar=0.0, ocean=True, placement=None):
+    # Circumcentre placements assume a well-centred (orthogonal) mesh, as the
+    # quasi-hexagonal meshes they come from are: a heavily jittered sphere has
+    # near-right triangles whose circumcentres almost coincide (huge l/d).
+    jitter = 0.05 if placement == "cell_circumcenter" else 0.2
+    m = synth.icosphere(level, radius=6371.0, jitter=jitter, seed=seed)
     m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=seed + 1, polar_cap_deg=polar) if ocean else None
     return m
 
@@ -102,10 +106,10 @@ def test_scalar_vertex_mixed_precision(lib, prec, order, n2):
     _check(res, ref, TOL_MIXED)
 
 
-@pytest.mark.parametrize("placement", ["vertex_vector", "cell"])
+@pytest.mark.parametrize("placement", ["vertex_vector", "cell", "vertex_voronoi", "cell_circumcenter"])
 @pytest.mark.parametrize("order,n2,prec", [(1, 0, 0), (2, 1, 0), (2, 2, 0), (2, 2, 1), (1, 0, 1)])
 def test_vector_and_cell_placements(lib, placement, order, n2, prec):
-    m = _sphere(3, 55, polar=10.0)
+    m = _sphere(3, 55, polar=10.0, placement=placement)
     P = oracle.build_problem(m, placement)
     f = _fields(P, 1, 3)
     ks = synth.log_wavenumbers(6000.0, 600.0, 4)
@@ -114,6 +118,20 @@ def test_vector_and_cell_placements(lib, placement, order, n2, prec):
     assert st == 0, stats
     _, ref = _oracle(m, placement, f, ks, order)
     _check(res, ref, TOL_FP64 if prec == 0 else TOL_MIXED)
+
+
+@pytest.mark.parametrize("placement", ["vertex_voronoi", "cell_circumcenter"])
+@pytest.mark.parametrize("order,n2", [(1, 0), (2, 1)])
+def test_finite_volume_placements_plain_method(lib, placement, order, n2):
+    """The paper's one-RHS FP64 CG on the two finite-volume placements."""
+    m = _sphere(3, 57, polar=10.0, placement=placement)
+    P = oracle.build_problem(m, placement)
+    f = _fields(P, 1, 4)
+    ks = synth.log_wavenumbers(6000.0, 600.0, 3)
+    res, stats, st = _run(lib, m, placement, f, ks, order, tol=1e-12, method=lib.METHOD_PLAIN, n2_solver=n2)
+    assert st == 0, stats
+    _, ref = _oracle(m, placement, f, ks, order)
+    _check(res, ref, TOL_FP64 if order == 1 else 1e-9)
 
 
 @pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
@@ -157,12 +175,13 @@ def test_jacobi_preconditioning(lib, placement, order, n2, prec):
     _check(res, ref, tol)
 
 
-@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell", "vertex_voronoi",
+                                       "cell_circumcenter"])
 @pytest.mark.parametrize("order,prec", [(1, 1), (2, 1), (2, 2)])
 def test_multigrid_preconditioning(lib, placement, order, prec):
     """Multigrid-preconditioned CG (n = 1) / COCG (complex n = 2) reaches the
     oracle's fields, with several levels in the hierarchy."""
-    m = _sphere(4, 61, polar=10.0)
+    m = _sphere(4, 61, polar=10.0, placement=placement)
     P = oracle.build_problem(m, placement)
     f = _fields(P, 2, 7)
     ks = synth.log_wavenumbers(6000.0, 200.0, 5)
@@ -300,13 +319,14 @@ def test_land_entries_pass_through(lib):
     assert np.array_equal(res[0, 0, 0][land], f[0, 0][land])
 
 
-def test_spectrum_matches_oracle(lib):
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_voronoi", "cell_circumcenter"])
+def test_spectrum_matches_oracle(lib, placement):
     import torch
-    m = _sphere(4, 61)
-    P = oracle.build_problem(m, "vertex_scalar")
+    m = _sphere(4, 61, placement=placement)
+    P = oracle.build_problem(m, placement)
     f = _fields(P, 2, 7)
     ks = synth.log_wavenumbers(4000.0, 300.0, 6)
-    h = lib.prepare_mesh(m, "vertex_scalar", max_order=2)
+    h = lib.prepare_mesh(m, placement, max_order=2)
     out, stats, st = lib.solve(h, torch.tensor(f, device="cuda"), ks, order=2, tol=1e-13)
     E, spec, kmid = lib.spectrum(h, out, ks)
     h.release()
