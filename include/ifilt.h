@@ -44,7 +44,9 @@ typedef enum {
   IFILT_ENOMEM = -2,         /* device or host allocation failed */
   IFILT_ECUDA = -3,          /* a CUDA call failed */
   IFILT_EMESH = -4,          /* malformed mesh (index out of range, degenerate triangle, ...) */
-  IFILT_DEVICE_TIMEOUT = -5  /* a bounded device-side wait expired */
+  IFILT_DEVICE_TIMEOUT = -5, /* a bounded device-side wait expired */
+  IFILT_ECACHE = -6          /* mesh cache file missing, unreadable, corrupt, of another format or
+                                preparation revision, or written for another mesh */
 } ifilt_status;
 
 /* Data placements (Sect. 2.1, Fig. 1). */
@@ -134,7 +136,7 @@ typedef struct {
   int32_t geometry;          /* IFILT_GEOM_* */
   double period_x, period_y; /* periodic plane only */
   double radius;             /* sphere only (metric factor m = tan(lat)/radius, Sect. 2.1.2) */
-  int32_t placement;         /* IFILT_VERTEX_SCALAR / _VECTOR / IFILT_CELL */
+  int32_t placement;         /* IFILT_VERTEX_SCALAR ... IFILT_CELL_CIRCUMCENTER */
   int32_t max_order;         /* highest filter order n the mesh must serve: 1 or 2 */
   int32_t reorder;           /* IFILT_REORDER_* : device row order */
   double cell_A;             /* constant A of Eq. 6 (cell placement); 0 selects sqrt(3) */
@@ -260,6 +262,40 @@ enum {
  * small or out of range); *written receives the byte count. */
 ifilt_status ifilt_mesh_multigrid_export(ifilt_mesh mesh, int32_t level, int32_t what, void* dst, size_t bytes,
                                          size_t* written);
+
+/* ---- Mesh cache files.  Preparation depends on the mesh only (Sect. 2.2
+ * separates it from the solves, whose every scale and field reuse it); at
+ * 10 M vertices its host half and the multigrid hierarchy take tens of
+ * seconds, so a prepared mesh can be written to a file and read back in
+ * another process, bit for bit.  Files are little-endian and carry the
+ * descriptor key, a format number, the preparation code's revision and a
+ * checksum of their contents. */
+
+/* 64-bit key of a descriptor (never 0): a hash of every field, of the arrays it
+ * points to (coords [V][dim], tri [T][3], ocean taken as 0/1 flags) and of the
+ * preparation revision.  Equal keys mean the same prepared mesh, up to hash
+ * collisions.  Errors: EINVAL (null pointers, non-positive sizes). */
+ifilt_status ifilt_mesh_key(const ifilt_mesh_desc* desc, uint64_t* key);
+
+#define IFILT_SAVE_MULTIGRID 1  /* also write the multigrid hierarchy (built first if needed) */
+/* Write the host half of `mesh` (what ifilt_prepare_mesh_host computes, and
+ * the hierarchy with IFILT_SAVE_MULTIGRID) to the host path `path`, replacing
+ * any file there.  The file is written under a temporary name in the same
+ * directory and renamed into place.  Errors: EINVAL (null mesh or path,
+ * unknown flags), ECACHE (cannot write). */
+ifilt_status ifilt_mesh_save(ifilt_mesh mesh, const char* path, int32_t flags);
+
+/* Read a file written by ifilt_mesh_save into a new host-only handle, as
+ * ifilt_prepare_mesh_host returns (ifilt_mesh_upload makes it solvable; the
+ * hierarchy, if the file holds it, is not rebuilt).  expect_key != 0 demands
+ * the key of the descriptor the mesh was prepared from (ifilt_mesh_key).
+ * Every array is checked before the handle is returned: sizes, row pointers,
+ * index ranges, sorted columns, finite values.  Errors: EINVAL (null
+ * arguments), ECACHE (see the status), ENOMEM. */
+ifilt_status ifilt_mesh_load_host(const char* path, uint64_t expect_key, ifilt_mesh* out);
+
+/* Descriptor key of a prepared or loaded mesh (0 if unknown). */
+ifilt_status ifilt_mesh_get_key(ifilt_mesh mesh, uint64_t* key);
 
 /* Filter a batch of fields at a list of wavenumbers (Eq. 1-2 solved as in
  * Sect. 2.2.2).

@@ -23,6 +23,8 @@ PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG = 0, 1, 2
 REORDER_NONE, REORDER_RCM, REORDER_HILBERT = 0, 1, 2
 MG_MAX_LEVELS = 16
 OK, NOT_CONVERGED = 0, 1
+ECACHE = -6
+SAVE_MULTIGRID = 1
 EXPORT = dict(perm=0, k_rowptr=1, k_col=2, k_val=3, mass=4, g2_rowptr=5, g2_col=6, g2_val=7)
 PLACEMENTS = {"vertex_scalar": VERTEX_SCALAR, "vertex_vector": VERTEX_VECTOR, "cell": CELL,
               "vertex_voronoi": VERTEX_VORONOI, "cell_circumcenter": CELL_CIRCUMCENTER}
@@ -95,7 +97,8 @@ MG_EXPORT = {"s_rowptr": 0, "s_col": 1, "s_val": 2, "p_rowptr": 3, "p_col": 4, "
 
 # every symbol include/ifilt.h declares
 SYMBOLS = ["ifilt_prepare_mesh", "ifilt_prepare_mesh_host", "ifilt_mesh_upload", "ifilt_release_mesh", "ifilt_mesh_info", "ifilt_mesh_export",
-           "ifilt_mesh_multigrid", "ifilt_mesh_multigrid_export", "ifilt_solve",
+           "ifilt_mesh_multigrid", "ifilt_mesh_multigrid_export", "ifilt_mesh_key", "ifilt_mesh_get_key",
+           "ifilt_mesh_save", "ifilt_mesh_load_host", "ifilt_solve",
            "ifilt_solve_many", "ifilt_spectrum", "ifilt_spectrum_noalloc", "ifilt_solve_scratch_bytes", "ifilt_profile_enable", "ifilt_profile_read",
            "ifilt_profile_reset", "ifilt_last_error", "ifilt_version", "ifilt_server_create",
            "ifilt_server_submit", "ifilt_server_wait", "ifilt_server_forget", "ifilt_server_now",
@@ -130,6 +133,14 @@ def load(path=None):
     lib.ifilt_mesh_multigrid.restype = i32
     lib.ifilt_mesh_multigrid_export.argtypes = [vp, i32, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
     lib.ifilt_mesh_multigrid_export.restype = i32
+    lib.ifilt_mesh_key.argtypes = [C.POINTER(MeshDesc), C.POINTER(C.c_uint64)]
+    lib.ifilt_mesh_key.restype = i32
+    lib.ifilt_mesh_get_key.argtypes = [vp, C.POINTER(C.c_uint64)]
+    lib.ifilt_mesh_get_key.restype = i32
+    lib.ifilt_mesh_save.argtypes = [vp, C.c_char_p, i32]
+    lib.ifilt_mesh_save.restype = i32
+    lib.ifilt_mesh_load_host.argtypes = [C.c_char_p, C.c_uint64, C.POINTER(vp)]
+    lib.ifilt_mesh_load_host.restype = i32
     lib.ifilt_solve.argtypes = [vp, C.POINTER(SolveOpts), i32, vp, i32, vp, vp, vp, vp]
     lib.ifilt_solve.restype = i32
     lib.ifilt_solve_many.argtypes = [i32, C.POINTER(SolveItem), vp]
@@ -189,17 +200,22 @@ def _ptr(a):
     return C.c_void_p(a.data_ptr())
 
 
+def _info(handle):
+    info = MeshInfo()
+    _check(load().ifilt_mesh_info(handle, C.byref(info)))
+    return {f: getattr(info, f) for f, _ in MeshInfo._fields_ if f != "pad"}
+
+
 class Mesh:
     """A prepared mesh (device-resident handle)."""
 
     def __init__(self, handle):
         self.handle = handle
-        info = MeshInfo()
-        _check(load().ifilt_mesh_info(handle, C.byref(info)))
-        self.info = {f: getattr(info, f) for f, _ in MeshInfo._fields_ if f != "pad"}
+        self.info = _info(handle)
 
     def upload(self, stream=None):
         _check(load().ifilt_mesh_upload(self.handle, _stream_ptr(stream)))
+        self.info = _info(self.handle)   # device layout fields are known now
 
     def release(self):
         if self.handle:
@@ -224,6 +240,17 @@ class Mesh:
         out = np.zeros(max(int(cnt), 1), dtype=dt)
         _check(load().ifilt_mesh_export(self.handle, key, _ptr(out), out.nbytes))
         return out[:cnt]
+
+    @property
+    def key(self):
+        """Key of the descriptor the mesh was prepared from (see mesh_key)."""
+        k = C.c_uint64(0)
+        _check(load().ifilt_mesh_get_key(self.handle, C.byref(k)))
+        return k.value
+
+    def save(self, path, multigrid=False):
+        """Write the host half (and the multigrid hierarchy) to a cache file."""
+        _check(load().ifilt_mesh_save(self.handle, os.fsencode(path), SAVE_MULTIGRID if multigrid else 0))
 
     def multigrid(self):
         """Shape of the multigrid hierarchy (built on the host if needed)."""
@@ -279,6 +306,45 @@ def prepare_mesh_host(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_s
     h = C.c_void_p()
     _check(load().ifilt_prepare_mesh_host(C.byref(d), C.byref(h)))
     return Mesh(h)
+
+
+def mesh_key(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_slice=0):
+    """64-bit key of a mesh descriptor (names its cache file)."""
+    d, keep = _desc(mesh, placement, max_order, reorder, cell_A, ell_slice)
+    k = C.c_uint64(0)
+    _check(load().ifilt_mesh_key(C.byref(d), C.byref(k)))
+    return k.value
+
+
+def load_mesh_host(path, key=0):
+    """Read a cache file written by Mesh.save into a host-only Mesh; `key` != 0
+    must match the key of the descriptor it was prepared from."""
+    h = C.c_void_p()
+    _check(load().ifilt_mesh_load_host(os.fsencode(path), key, C.byref(h)))
+    return Mesh(h)
+
+
+def prepare_mesh_cached(mesh, placement, cache_dir, max_order=2, reorder=1, cell_A=0.0, ell_slice=0,
+                        multigrid=True, upload=True, stream=None):
+    """prepare_mesh through a directory of cache files named by the descriptor
+    key: load the file if it is there and valid, else prepare on the host and
+    write it (with the multigrid hierarchy if `multigrid`).  Returns
+    (Mesh, hit) with the mesh uploaded if `upload`."""
+    key = mesh_key(mesh, placement, max_order, reorder, cell_A, ell_slice)
+    path = os.path.join(cache_dir, f"{key:016x}.ifmesh")
+    hit = False
+    try:
+        m = load_mesh_host(path, key)
+        hit = True
+    except IfiltError as e:
+        if e.status != ECACHE:
+            raise
+        m = prepare_mesh_host(mesh, placement, max_order, reorder, cell_A, ell_slice)
+        os.makedirs(cache_dir, exist_ok=True)
+        m.save(path, multigrid=multigrid)
+    if upload:
+        m.upload(stream)
+    return m, hit
 
 
 def solve_opts(order=1, tol=1e-9, precision=PREC_FP64, method=METHOD_BATCHED, n2_solver=N2_AUTO, max_iter=0,

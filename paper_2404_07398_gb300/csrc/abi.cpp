@@ -161,6 +161,8 @@ ifilt_status ifilt_prepare_mesh(const ifilt_mesh_desc* desc, void* stream, ifilt
   try {
     IFILT_CUDA(cudaGetDevice(&m->device));
     m->host = prepare_host(*desc);
+    m->host.key = mesh_key(*desc);
+    m->slice_h = desc->ell_slice;
     upload_mesh(m, desc->ell_slice, st);
   } catch (...) {
     free_mesh(m);
@@ -180,6 +182,7 @@ ifilt_status ifilt_prepare_mesh_host(const ifilt_mesh_desc* desc, ifilt_mesh* ou
   ifilt_mesh_s* m = new ifilt_mesh_s();
   try {
     m->host = prepare_host(*desc);
+    m->host.key = mesh_key(*desc);
     m->slice_h = desc->ell_slice;
   } catch (...) {
     delete m;
@@ -205,6 +208,41 @@ ifilt_status ifilt_mesh_upload(ifilt_mesh m, void* stream) {
     m->device = -1;
     throw;
   }
+  return IFILT_OK;
+  IFILT_GUARD_END
+}
+
+ifilt_status ifilt_mesh_key(const ifilt_mesh_desc* desc, uint64_t* key) {
+  IFILT_GUARD_BEGIN
+  if (!desc || !key) fail(IFILT_EINVAL, "null argument");
+  *key = mesh_key(*desc);
+  return IFILT_OK;
+  IFILT_GUARD_END
+}
+
+ifilt_status ifilt_mesh_get_key(ifilt_mesh m, uint64_t* key) {
+  IFILT_GUARD_BEGIN
+  check_mesh(m);
+  if (!key) fail(IFILT_EINVAL, "null argument");
+  *key = m->host.key;
+  return IFILT_OK;
+  IFILT_GUARD_END
+}
+
+ifilt_status ifilt_mesh_save(ifilt_mesh m, const char* path, int32_t flags) {
+  IFILT_GUARD_BEGIN
+  check_mesh(m);
+  save_mesh(m, path, flags);
+  return IFILT_OK;
+  IFILT_GUARD_END
+}
+
+ifilt_status ifilt_mesh_load_host(const char* path, uint64_t expect_key, ifilt_mesh* out) {
+  IFILT_GUARD_BEGIN
+  if (!out) fail(IFILT_EINVAL, "null argument");
+  *out = nullptr;
+  *out = load_mesh_host(path, expect_key);
+  set_last_error("");
   return IFILT_OK;
   IFILT_GUARD_END
 }

@@ -46,6 +46,7 @@ struct HostCSR {
 };
 
 struct HostPrepared {
+  uint64_t key = 0;               // ifilt_mesh_key of the descriptor it was prepared from
   int32_t placement = 0, geometry = 0, max_order = 1, reorder = 1;
   int32_t n_rows = 0, n_in = 0, n_out = 0, n_comp = 1;
   std::vector<int32_t> perm;      // device row -> original index (vertex or triangle)
@@ -136,6 +137,10 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st);
 void free_mesh(ifilt_mesh_s* m);
 // multigrid hierarchy of a mesh: built on the host once, uploaded once
 const MgHost& multigrid_host(ifilt_mesh_s* m);
+// mesh cache files (cache.cpp)
+uint64_t mesh_key(const ifilt_mesh_desc& d);
+void save_mesh(ifilt_mesh_s* m, const char* path, int32_t flags);
+ifilt_mesh_s* load_mesh_host(const char* path, uint64_t expect_key);
 const std::vector<DevMgLevel>& multigrid_device(ifilt_mesh_s* m, cudaStream_t st);
 
 // solvers (solve_plain.cu, solve_batched.cu)

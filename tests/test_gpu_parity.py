@@ -419,3 +419,30 @@ def test_solve_many_matches_separate_solves(lib):
         assert np.all(stats["status"] == 0)
     hv.release()
     hc.release()
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "cell"])
+def test_cached_mesh_solves_identically(lib, tmp_path, monkeypatch, placement):
+    """A mesh read back from its cache file (with the multigrid hierarchy)
+    gives bit-identical filtered fields to the freshly prepared mesh (at
+    fixed launch shapes: the autotuner may pick other grids per mesh, which
+    changes the order of the dot-product partial sums)."""
+    import torch
+    monkeypatch.setenv("IFILT_AUTOTUNE", "0")
+    m = _sphere(4, 67, polar=10.0)
+    P = oracle.build_problem(m, placement)
+    f = torch.tensor(_fields(P, 2, 9), device="cuda")
+    ks = synth.log_wavenumbers(5000.0, 300.0, 4)
+    a, hit = lib.prepare_mesh_cached(m, placement, tmp_path)
+    assert not hit
+    b, hit = lib.prepare_mesh_cached(m, placement, tmp_path)
+    assert hit
+    for opts in (dict(precision=0, tol=1e-12), dict(precision=1, tol=1e-10, precond=lib.PRECOND_MG, n2_solver=2)):
+        ra, sa, st = lib.solve(a, f, ks, order=2, **opts)
+        assert st == 0
+        rb, sb, st = lib.solve(b, f, ks, order=2, **opts)
+        assert st == 0
+        assert torch.equal(ra, rb)
+        assert np.array_equal(sa["iters"], sb["iters"])
+    a.release()
+    b.release()
