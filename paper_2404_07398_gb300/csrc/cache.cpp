@@ -39,7 +39,7 @@ constexpr char kMagic[8] = {'I', 'F', 'I', 'L', 'T', 'M', 'C', 0};
 constexpr uint32_t kFormat = 1;
 // Bumped whenever preparation or the multigrid construction changes what it
 // produces, so that files written by an older library are prepared again.
-constexpr uint32_t kPrepareRevision = 1;
+constexpr uint32_t kPrepareRevision = 2;
 
 // splitmix64 output function (Steele, Lea and Flood, OOPSLA 2014) as a mixer.
 inline uint64_t mix64(uint64_t z) {

@@ -21,6 +21,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "host_parallel.h"
 #include "internal.h"
 #include "multigrid.h"
 
@@ -67,38 +68,99 @@ V scale(const V& a, const V& s) {
   return a * s;
 }
 
-// C = A B (Gustavson, columns of each row in increasing order)
-template <typename VA, typename VB, typename VC>
-Csr<VC> multiply(const Csr<VA>& A, const Csr<VB>& B) {
-  Csr<VC> C;
-  C.n = A.n;
-  C.m = B.m;
-  C.ptr.assign((size_t)A.n + 1, 0);
-  std::vector<int32_t> mark((size_t)B.m, -1);
-  std::vector<VC> acc((size_t)B.m);
-  std::vector<int32_t> cols;
-  for (int32_t i = 0; i < A.n; i++) {
-    cols.clear();
-    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; e++) {
-      const int32_t k = A.col[e];
-      for (int64_t f = B.ptr[k]; f < B.ptr[k + 1]; f++) {
-        const int32_t j = B.col[f];
-        if (mark[j] != i) {
-          mark[j] = i;
-          acc[j] = VC{};
-          cols.push_back(j);
+constexpr int64_t kRowChunk = 4096;  // rows per parallel chunk (fixed: results do not depend on threads)
+
+// Builds a CSR row by row, in parallel.  gather(i, cand) appends row i's
+// contributions (column, value) in their summation order; each column's
+// contributions are summed from zero in that order (a stable sort by column
+// keeps it), columns come out ascending, and keep(sum) decides whether the
+// entry is stored.  Two passes over the rows: sizes, then contents written in
+// place.  When every entry is kept, `columns(i, cols)` (if given) lists row i's
+// columns, with repeats, for the first pass without forming the values.
+template <typename V, typename Gather, typename Keep, typename Columns>
+Csr<V> build_rows(int32_t n, int32_t m, Gather gather, Keep keep, Columns columns) {
+  constexpr bool kCountCols = !std::is_same<Columns, std::nullptr_t>::value;
+  Csr<V> C;
+  C.n = n;
+  C.m = m;
+  C.ptr.assign((size_t)n + 1, 0);
+  using Cand = std::pair<int32_t, V>;
+  const int nt = host_threads();
+  std::vector<std::vector<Cand>> scratch((size_t)nt);
+  std::vector<std::vector<int32_t>> cscratch((size_t)nt);
+  auto sorted_row = [&](int32_t i, std::vector<Cand>& c) {
+    c.clear();
+    gather(i, c);
+    stable_sort_small(c.data(), (int64_t)c.size(), [](const Cand& a, const Cand& b) { return a.first < b.first; });
+  };
+  parallel_range(n, kRowChunk, [&](int64_t b, int64_t e, int w) {
+    for (int64_t i = b; i < e; i++) {
+      int64_t cnt = 0;
+      if constexpr (kCountCols) {
+        std::vector<int32_t>& c = cscratch[(size_t)w];
+        c.clear();
+        columns((int32_t)i, c);
+        stable_sort_small(c.data(), (int64_t)c.size(), [](int32_t x, int32_t y) { return x < y; });
+        for (size_t t = 0; t < c.size(); t++) cnt += (t == 0 || c[t] != c[t - 1]) ? 1 : 0;
+      } else {
+        std::vector<Cand>& c = scratch[(size_t)w];
+        sorted_row((int32_t)i, c);
+        for (size_t t = 0; t < c.size();) {
+          const int32_t col = c[t].first;
+          V acc{};
+          for (; t < c.size() && c[t].first == col; t++) acc += c[t].second;
+          cnt += keep(acc) ? 1 : 0;
         }
-        acc[j] += scale(A.val[e], B.val[f]);
+      }
+      C.ptr[i + 1] = cnt;
+    }
+  });
+  for (int32_t i = 0; i < n; i++) C.ptr[i + 1] += C.ptr[i];
+  C.col.resize((size_t)C.ptr[n]);
+  C.val.resize((size_t)C.ptr[n]);
+  parallel_range(n, kRowChunk, [&](int64_t b, int64_t e, int w) {
+    std::vector<Cand>& c = scratch[(size_t)w];
+    for (int64_t i = b; i < e; i++) {
+      sorted_row((int32_t)i, c);
+      int64_t o = C.ptr[i];
+      for (size_t t = 0; t < c.size();) {
+        const int32_t col = c[t].first;
+        V acc{};
+        for (; t < c.size() && c[t].first == col; t++) acc += c[t].second;
+        if (keep(acc)) {
+          C.col[o] = col;
+          C.val[o] = acc;
+          o++;
+        }
       }
     }
-    std::sort(cols.begin(), cols.end());
-    for (int32_t j : cols) {
-      C.col.push_back(j);
-      C.val.push_back(acc[j]);
-    }
-    C.ptr[i + 1] = (int64_t)C.col.size();
-  }
+  });
   return C;
+}
+template <typename V, typename Gather, typename Keep>
+Csr<V> build_rows(int32_t n, int32_t m, Gather gather, Keep keep) {
+  return build_rows<V>(n, m, gather, keep, nullptr);
+}
+
+// C = A B (Gustavson order: row i of C sums A(i, k) B(k, :) over k ascending;
+// every structural entry is kept)
+template <typename VA, typename VB, typename VC>
+Csr<VC> multiply(const Csr<VA>& A, const Csr<VB>& B) {
+  return build_rows<VC>(
+      A.n, B.m,
+      [&](int32_t i, std::vector<std::pair<int32_t, VC>>& c) {
+        for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; e++) {
+          const int32_t k = A.col[e];
+          for (int64_t f = B.ptr[k]; f < B.ptr[k + 1]; f++) c.emplace_back(B.col[f], scale(A.val[e], B.val[f]));
+        }
+      },
+      [](const VC&) { return true; },
+      [&](int32_t i, std::vector<int32_t>& c) {
+        for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; e++) {
+          const int32_t k = A.col[e];
+          c.insert(c.end(), B.col.begin() + B.ptr[k], B.col.begin() + B.ptr[k + 1]);
+        }
+      });
 }
 
 // R = P^T with conjugated values
@@ -163,20 +225,34 @@ double lambda_max(const Csr<V>& K, const std::vector<double>& dinv) {
     s = s * 6364136223846793005ull + 1442695040888963407ull;
     x[i] = V(0.5 + (double)(s >> 11) * (1.0 / 9007199254740992.0));
   }
+  constexpr int64_t kChunk = 16384;
+  const int64_t nc = ((int64_t)n + kChunk - 1) / kChunk;
+  std::vector<double> px((size_t)nc), py((size_t)nc);
   double lam = 0.0;
   for (int it = 0; it < 40; it++) {
-    double nx = 0.0, ny = 0.0;
-    for (int32_t i = 0; i < n; i++) {
-      V t{};
-      for (int64_t e = K.ptr[i]; e < K.ptr[i + 1]; e++) t += K.val[e] * x[K.col[e]];
-      y[i] = t * dinv[i];
-      nx += std::norm(cplx(x[i]));
-      ny += std::norm(cplx(y[i]));
+    parallel_range(n, kChunk, [&](int64_t b, int64_t e, int) {
+      double sx = 0.0, sy = 0.0;
+      for (int64_t i = b; i < e; i++) {
+        V t{};
+        for (int64_t q = K.ptr[i]; q < K.ptr[i + 1]; q++) t += K.val[q] * x[K.col[q]];
+        y[i] = t * dinv[i];
+        sx += std::norm(cplx(x[i]));
+        sy += std::norm(cplx(y[i]));
+      }
+      px[(size_t)(b / kChunk)] = sx;
+      py[(size_t)(b / kChunk)] = sy;
+    });
+    double nx = 0.0, ny = 0.0;  // chunk partials added in chunk order
+    for (int64_t c = 0; c < nc; c++) {
+      nx += px[(size_t)c];
+      ny += py[(size_t)c];
     }
     if (nx == 0.0 || ny == 0.0) return 1.0;
     lam = std::sqrt(ny / nx);
     const double inv = 1.0 / std::sqrt(ny);
-    for (int32_t i = 0; i < n; i++) x[i] = y[i] * inv;
+    parallel_range(n, kChunk, [&](int64_t b, int64_t e, int) {
+      for (int64_t i = b; i < e; i++) x[i] = y[i] * inv;
+    });
   }
   return lam > 0.0 ? lam : 1.0;
 }
@@ -188,10 +264,12 @@ Csr<V> from_host(const HostCSR& a) {
   c.ptr = a.row_ptr;
   c.col = a.col;
   c.val.resize(a.col.size());
-  for (size_t e = 0; e < a.col.size(); e++) {
-    if constexpr (std::is_same<V, cplx>::value) c.val[e] = cplx(a.val[2 * e], a.val[2 * e + 1]);
-    else c.val[e] = a.val[e];
-  }
+  parallel_range((int64_t)a.col.size(), 1 << 20, [&](int64_t b, int64_t e, int) {
+    for (int64_t q = b; q < e; q++) {
+      if constexpr (std::is_same<V, cplx>::value) c.val[q] = cplx(a.val[2 * q], a.val[2 * q + 1]);
+      else c.val[q] = a.val[q];
+    }
+  });
   return c;
 }
 
@@ -200,12 +278,12 @@ constexpr int nval_of() {
   return std::is_same<V, cplx>::value ? 2 : 1;
 }
 template <typename V>
-void put(std::vector<double>& out, const V& v) {
+void put(double* out, const V& v) {
   if constexpr (std::is_same<V, cplx>::value) {
-    out.push_back(v.real());
-    out.push_back(v.imag());
+    out[0] = v.real();
+    out[1] = v.imag();
   } else {
-    out.push_back(v);
+    out[0] = v;
   }
 }
 
@@ -216,8 +294,11 @@ HostCSR to_host(const Csr<V>& c) {
   h.nval = nval_of<V>();
   h.row_ptr = c.ptr;
   h.col = c.col;
-  h.val.reserve(c.val.size() * h.nval);
-  for (const V& v : c.val) put(h.val, v);
+  h.val.resize(c.val.size() * h.nval);
+  const int nv = h.nval;
+  parallel_range((int64_t)c.val.size(), 1 << 20, [&](int64_t b, int64_t e, int) {
+    for (int64_t q = b; q < e; q++) put(h.val.data() + q * nv, c.val[q]);
+  });
   return h;
 }
 template <typename V>
@@ -227,11 +308,14 @@ HostCSR to_host(const Csr<Pair<V>>& c) {
   h.nval = 2 * nval_of<V>();
   h.row_ptr = c.ptr;
   h.col = c.col;
-  h.val.reserve(c.val.size() * h.nval);
-  for (const auto& v : c.val) {
-    put(h.val, v.k);
-    put(h.val, v.m);
-  }
+  h.val.resize(c.val.size() * h.nval);
+  const int nv = h.nval, half = nval_of<V>();
+  parallel_range((int64_t)c.val.size(), 1 << 20, [&](int64_t b, int64_t e, int) {
+    for (int64_t q = b; q < e; q++) {
+      put(h.val.data() + q * nv, c.val[q].k);
+      put(h.val.data() + q * nv + half, c.val[q].m);
+    }
+  });
   return h;
 }
 
@@ -240,39 +324,31 @@ MgHost build(const HostPrepared& hp, const MgParams& prm) {
   MgHost out;
   // level 0: (K, M) with M the lumped mass on the diagonal
   const Csr<V> K0 = from_host<V>(hp.K);
-  Csr<Pair<V>> S;
-  S.n = S.m = K0.n;
-  S.ptr.assign((size_t)K0.n + 1, 0);
-  for (int32_t i = 0; i < K0.n; i++) {
-    bool has_diag = false;
-    for (int64_t e = K0.ptr[i]; e < K0.ptr[i + 1]; e++) has_diag |= K0.col[e] == i;
-    bool placed = has_diag;
-    for (int64_t e = K0.ptr[i]; e < K0.ptr[i + 1]; e++) {
-      if (!placed && K0.col[e] > i) {  // a row without a stored diagonal gets one
-        S.col.push_back(i);
-        S.val.push_back(Pair<V>{V{}, V(hp.mass[i])});
-        placed = true;
-      }
-      S.col.push_back(K0.col[e]);
-      S.val.push_back(Pair<V>{K0.val[e], K0.col[e] == i ? V(hp.mass[i]) : V{}});
-    }
-    if (!placed) {
-      S.col.push_back(i);
-      S.val.push_back(Pair<V>{V{}, V(hp.mass[i])});
-    }
-    S.ptr[i + 1] = (int64_t)S.col.size();
-  }
+  // (K, M) on K's pattern; a row without a stored diagonal gets one
+  Csr<Pair<V>> S = build_rows<Pair<V>>(
+      K0.n, K0.n,
+      [&](int32_t i, std::vector<std::pair<int32_t, Pair<V>>>& c) {
+        bool has_diag = false;
+        for (int64_t e = K0.ptr[i]; e < K0.ptr[i + 1]; e++) {
+          has_diag |= K0.col[e] == i;
+          c.emplace_back(K0.col[e], Pair<V>{K0.val[e], K0.col[e] == i ? V(hp.mass[i]) : V{}});
+        }
+        if (!has_diag) c.emplace_back(i, Pair<V>{V{}, V(hp.mass[i])});
+      },
+      [](const Pair<V>&) { return true; });
   for (int level = 0;; level++) {
     MgHostLevel L;
     L.n = S.n;
     L.dk.assign((size_t)S.n, 0.0);
     L.dm.assign((size_t)S.n, 0.0);
-    for (int32_t i = 0; i < S.n; i++)
-      for (int64_t e = S.ptr[i]; e < S.ptr[i + 1]; e++)
-        if (S.col[e] == i) {
-          L.dk[i] = re(S.val[e].k);
-          L.dm[i] = re(S.val[e].m);
-        }
+    parallel_range(S.n, kRowChunk, [&](int64_t b, int64_t e, int) {
+      for (int64_t i = b; i < e; i++)
+        for (int64_t q = S.ptr[i]; q < S.ptr[i + 1]; q++)
+          if (S.col[q] == i) {
+            L.dk[i] = re(S.val[q].k);
+            L.dm[i] = re(S.val[q].m);
+          }
+    });
     if (level > 0) L.S = to_host(S);
     const bool last = S.n <= prm.coarsest_rows || level + 1 >= prm.max_levels;
     if (!last) {
@@ -282,41 +358,24 @@ MgHost build(const HostPrepared& hp, const MgParams& prm) {
       K.ptr = S.ptr;
       K.col = S.col;
       K.val.resize(S.val.size());
-      for (size_t e = 0; e < S.val.size(); e++) K.val[e] = S.val[e].k;
+      parallel_range((int64_t)S.val.size(), 1 << 20, [&](int64_t b, int64_t e, int) {
+        for (int64_t q = b; q < e; q++) K.val[q] = S.val[q].k;
+      });
       int32_t na = 0;
       const std::vector<int32_t> agg = aggregate(K, na);
       if (na > 0 && (double)na <= prm.min_ratio * (double)S.n) {
         std::vector<double> dinv((size_t)S.n, 0.0);
         for (int32_t i = 0; i < S.n; i++) dinv[i] = L.dk[i] > 0.0 ? 1.0 / L.dk[i] : 0.0;
         const double w = (4.0 / 3.0) / lambda_max(K, dinv);
-        // P = P_tent - w D^-1 K P_tent, row by row
-        Csr<V> P;
-        P.n = S.n;
-        P.m = na;
-        P.ptr.assign((size_t)S.n + 1, 0);
-        std::vector<int32_t> mark((size_t)na, -1);
-        std::vector<V> acc((size_t)na);
-        std::vector<int32_t> cols;
-        for (int32_t i = 0; i < S.n; i++) {
-          cols.clear();
-          auto add = [&](int32_t a, const V& v) {
-            if (mark[a] != i) {
-              mark[a] = i;
-              acc[a] = V{};
-              cols.push_back(a);
-            }
-            acc[a] += v;
-          };
-          add(agg[i], V(1.0));
-          for (int64_t e = K.ptr[i]; e < K.ptr[i + 1]; e++) add(agg[K.col[e]], K.val[e] * (-w * dinv[i]));
-          std::sort(cols.begin(), cols.end());
-          for (int32_t a : cols)
-            if (mag(acc[a]) != 0.0) {
-              P.col.push_back(a);
-              P.val.push_back(acc[a]);
-            }
-          P.ptr[i + 1] = (int64_t)P.col.size();
-        }
+        // P = P_tent - w D^-1 K P_tent, row by row; exact zeros are dropped
+        const Csr<V> P = build_rows<V>(
+            S.n, na,
+            [&](int32_t i, std::vector<std::pair<int32_t, V>>& c) {
+              c.emplace_back(agg[i], V(1.0));
+              for (int64_t e = K.ptr[i]; e < K.ptr[i + 1]; e++)
+                c.emplace_back(agg[K.col[e]], K.val[e] * (-w * dinv[i]));
+            },
+            [](const V& v) { return mag(v) != 0.0; });
         const Csr<V> R = transpose(P);
         const Csr<Pair<V>> SP = multiply<Pair<V>, V, Pair<V>>(S, P);
         Csr<Pair<V>> Sc = multiply<V, Pair<V>, Pair<V>>(R, SP);

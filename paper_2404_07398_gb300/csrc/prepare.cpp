@@ -24,6 +24,7 @@
 #include <cstring>
 #include <numeric>
 
+#include "host_parallel.h"
 #include "internal.h"
 
 namespace ifilt {
@@ -233,6 +234,11 @@ HostCSR pattern_from_graph(const Graph& g, const std::vector<int32_t>& order,
 }
 
 // G = K M^-1 K with the structural product pattern (explicit zeros kept).
+// Rows are independent: each gathers its candidate products in the order
+// (entry e of row i, entry f of row K.col[e]), sorts them stably by column and
+// sums each column's run in that order, so every value is the same sum, in the
+// same order, whatever the number of threads.  Two passes: row sizes from the
+// columns alone, then columns and sums written in place.
 HostCSR product_kmk(const HostCSR& K, const std::vector<double>& mass) {
   const int32_t n = K.n;
   const int nv = K.nval;
@@ -240,57 +246,63 @@ HostCSR product_kmk(const HostCSR& K, const std::vector<double>& mass) {
   G.n = n;
   G.nval = nv;
   G.row_ptr.assign((size_t)n + 1, 0);
-  std::vector<int32_t> mark(n, -1);
-  std::vector<double> acc((size_t)n * nv, 0.0);
-  std::vector<int32_t> cols;
-  // pass 1: pattern sizes
-  for (int32_t i = 0; i < n; i++) {
-    int64_t cnt = 0;
-    for (int64_t e = K.row_ptr[i]; e < K.row_ptr[i + 1]; e++) {
-      int32_t j = K.col[e];
-      for (int64_t f = K.row_ptr[j]; f < K.row_ptr[j + 1]; f++) {
-        int32_t k = K.col[f];
-        if (mark[k] != i) {
-          mark[k] = i;
-          cnt++;
-        }
+  struct Cand {
+    int32_t k;
+    int64_t e, f;
+  };
+  const int nt = host_threads();
+  std::vector<std::vector<Cand>> scratch((size_t)nt);
+  std::vector<std::vector<int32_t>> cscratch((size_t)nt);
+  constexpr int64_t kRows = 4096;
+  parallel_range(n, kRows, [&](int64_t b, int64_t e, int w) {
+    std::vector<int32_t>& c = cscratch[(size_t)w];
+    for (int64_t i = b; i < e; i++) {
+      c.clear();
+      for (int64_t q = K.row_ptr[i]; q < K.row_ptr[i + 1]; q++) {
+        const int32_t j = K.col[q];
+        c.insert(c.end(), K.col.begin() + K.row_ptr[j], K.col.begin() + K.row_ptr[j + 1]);
       }
+      stable_sort_small(c.data(), (int64_t)c.size(), [](int32_t x, int32_t y) { return x < y; });
+      int64_t cnt = 0;
+      for (size_t t = 0; t < c.size(); t++) cnt += (t == 0 || c[t] != c[t - 1]) ? 1 : 0;
+      G.row_ptr[i + 1] = cnt;
     }
-    G.row_ptr[i + 1] = G.row_ptr[i] + cnt;
-  }
+  });
+  for (int32_t i = 0; i < n; i++) G.row_ptr[i + 1] += G.row_ptr[i];
   G.col.resize(G.row_ptr.back());
   G.val.resize((size_t)G.row_ptr.back() * nv);
-  std::fill(mark.begin(), mark.end(), -1);
-  for (int32_t i = 0; i < n; i++) {
-    cols.clear();
-    for (int64_t e = K.row_ptr[i]; e < K.row_ptr[i + 1]; e++) {
-      int32_t j = K.col[e];
-      const double inv = 1.0 / mass[j];
-      for (int64_t f = K.row_ptr[j]; f < K.row_ptr[j + 1]; f++) {
-        int32_t k = K.col[f];
-        if (mark[k] != i) {
-          mark[k] = i;
-          cols.push_back(k);
-          for (int q = 0; q < nv; q++) acc[(size_t)k * nv + q] = 0.0;
+  parallel_range(n, kRows, [&](int64_t b, int64_t e, int w) {
+    std::vector<Cand>& c = scratch[(size_t)w];
+    for (int64_t i = b; i < e; i++) {
+      c.clear();
+      for (int64_t q = K.row_ptr[i]; q < K.row_ptr[i + 1]; q++) {
+        const int32_t j = K.col[q];
+        for (int64_t f = K.row_ptr[j]; f < K.row_ptr[j + 1]; f++) c.push_back(Cand{K.col[f], q, f});
+      }
+      stable_sort_small(c.data(), (int64_t)c.size(), [](const Cand& x, const Cand& y) { return x.k < y.k; });
+      int64_t o = G.row_ptr[i];
+      for (size_t t = 0; t < c.size(); o++) {
+        const int32_t col = c[t].k;
+        double s0 = 0.0, s1 = 0.0;
+        for (; t < c.size() && c[t].k == col; t++) {
+          const int64_t ee = c[t].e, ff = c[t].f;
+          const double inv = 1.0 / mass[K.col[ee]];
+          if (nv == 1) {
+            s0 += K.val[ee] * inv * K.val[ff];
+          } else {
+            // blocks [[a, b], [-b, a]] multiply like a + i b
+            const double a1 = K.val[2 * ee] * inv, b1 = K.val[2 * ee + 1] * inv;
+            const double a2 = K.val[2 * ff], b2 = K.val[2 * ff + 1];
+            s0 += a1 * a2 - b1 * b2;
+            s1 += a1 * b2 + b1 * a2;
+          }
         }
-        if (nv == 1) {
-          acc[k] += K.val[e] * inv * K.val[f];
-        } else {
-          // blocks [[a, b], [-b, a]] multiply like a + i b
-          double a1 = K.val[2 * e] * inv, b1 = K.val[2 * e + 1] * inv;
-          double a2 = K.val[2 * f], b2 = K.val[2 * f + 1];
-          acc[2 * (size_t)k] += a1 * a2 - b1 * b2;
-          acc[2 * (size_t)k + 1] += a1 * b2 + b1 * a2;
-        }
+        G.col[o] = col;
+        G.val[(size_t)o * nv] = s0;
+        if (nv == 2) G.val[(size_t)o * nv + 1] = s1;
       }
     }
-    std::sort(cols.begin(), cols.end());
-    int64_t o = G.row_ptr[i];
-    for (size_t t = 0; t < cols.size(); t++) {
-      G.col[o + t] = cols[t];
-      for (int q = 0; q < nv; q++) G.val[(size_t)(o + t) * nv + q] = acc[(size_t)cols[t] * nv + q];
-    }
-  }
+  });
   return G;
 }
 

@@ -125,3 +125,21 @@ def test_multigrid_export_checks(api):
     assert lib.ifilt_mesh_multigrid_export(h.handle, g["levels"], 6, buf.ctypes.data, buf.nbytes, None) == -1
     assert lib.ifilt_mesh_multigrid_export(h.handle, 0, 99, buf.ctypes.data, buf.nbytes, None) == -1
     assert lib.ifilt_mesh_multigrid_export(h.handle, 0, 6, buf.ctypes.data, 8, None) == -1
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+def test_host_threads_do_not_change_results(api, monkeypatch, placement):
+    """Preparation and the hierarchy run on host threads in chunks fixed by
+    the problem size: 1, 3 and 8 threads give the same bytes."""
+    m = _mesh(6, 37)
+    seen = []
+    for threads in ("1", "3", "8"):
+        monkeypatch.setenv("IFILT_HOST_THREADS", threads)
+        h = api.prepare_mesh_host(m, placement, max_order=2)
+        g = h.multigrid()
+        arrays = [h.export(w) for w in ("perm", "k_col", "k_val", "mass", "g2_rowptr", "g2_col", "g2_val")]
+        for level in range(g["levels"]):
+            arrays += [h.multigrid_export(level, w) for w in ("s_col", "s_val", "p_col", "p_val", "dk", "dm")]
+        seen.append(b"".join(a.tobytes() for a in arrays))
+        h.release()
+    assert seen[0] == seen[1] == seen[2]
