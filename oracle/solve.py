@@ -183,6 +183,42 @@ def filter_dense(problem, fld, ks, order):
     return np.stack(out)
 
 
+def shifted_factors(order):
+    """Partial fractions of the filter's response (Eq. 1 with gamma = 1/2):
+    with x standing for l^2 times the discrete -Laplacian's eigenvalue,
+        1 / (1 + x^n / 2) = sum_j (1/n) / (1 - x / r_j),   r_j^n = -2,
+    r_j = 2^(1/n) exp(i pi (2j + 1) / n), j = 0 .. n-1 (the residue of the
+    simple pole r_j is -r_j / n).  Each term is one solve with M + sigma_j K,
+    sigma_j = -l^2 / r_j, on the pattern of K alone.  Returns the list of
+    (sigma_j / l^2, 1/n) pairs."""
+    n = int(order)
+    out = []
+    for j in range(n):
+        r = 2.0 ** (1.0 / n) * np.exp(1j * np.pi * (2 * j + 1) / n)
+        out.append((-1.0 / r, 1.0 / n))
+    return out
+
+
+def filter_shifted(problem, fld, ks, order):
+    """The filtered fields as the sum over the partial fractions of
+    `shifted_factors`: phi_l = sum_j (1/n) (M + sigma_j K)^-1 b, one sparse
+    complex LU per term (small meshes; a second route to `filter_dense`)."""
+    import scipy.sparse.linalg as spla
+    K = problem.K.tocsc().astype(np.complex128)
+    M = sp.diags(problem.A.astype(np.complex128)).tocsc()
+    out = []
+    for k in ks:
+        ell2 = 1.0 / (k * k)
+        sols = []
+        for b, _ in problem.systems(fld):
+            acc = np.zeros(b.shape, dtype=np.complex128)
+            for sig, w in shifted_factors(order):
+                acc += w * spla.spsolve((M + (sig * ell2) * K).tocsc(), b.astype(np.complex128))
+            sols.append(acc.real.copy())
+        out.append(problem.output(fld, sols))
+    return np.stack(out)
+
+
 def _candidates(problem, fld, filtered_k):
     """The unknowns of each system read back from an output block [n_comp][n_out]."""
     ids = problem.out_ids

@@ -25,7 +25,7 @@ def _fft_filter_split_square(f, n, ell, order):
     return np.real(np.fft.ifft2(np.fft.fft2(f.reshape(n, n)) * H)).ravel()
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
 def test_split_square_matches_fourier_closed_form(order):
     w = synth.workload("periodic32")
     P = oracle.build_problem(w["mesh"], "vertex_scalar")
@@ -57,7 +57,7 @@ def test_split_square_weights_exact():
     assert K.nnz == 64 * 7      # six mesh edges per vertex plus the diagonal
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_equilateral_plane_waves_are_eigenvectors(order):
     """Equilateral lattice (side a): cot 60 deg = 1/sqrt(3), A_v = sqrt(3)/2 a^2, so
     M^-1 K has the symbol (4 / (3 a^2)) sum_{3 edge directions} (1 - cos kappa.e).
@@ -386,3 +386,37 @@ def test_relative_residual_of_x0_exact_and_perturbed(placement):
     ee[: e.size] = e
     r0 = np.linalg.norm(b - P.apply_S(x0, 1.0 / k, 2))
     assert abs(rel - np.linalg.norm(P.apply_S(ee, 1.0 / k, 2)) / r0) <= 1e-6 * rel
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
+def test_shifted_factors_reproduce_the_response(order):
+    """sum_j w_j / (1 - x / r_j) equals 1 / (1 + x^n / 2) on a range of x >= 0
+    (the partial fractions behind the shifted solves), the weights sum to one
+    and the poles come in conjugate pairs (one real pole -2^(1/n) for odd n)."""
+    fac = oracle.shifted_factors(order)
+    x = np.concatenate([[0.0], np.logspace(-3, 4, 60)])
+    resp = sum(w / (1.0 + s * x) for s, w in fac)        # -x / r_j = sigma_j x
+    np.testing.assert_allclose(resp.imag, 0.0, atol=1e-12)
+    np.testing.assert_allclose(resp.real, 1.0 / (1.0 + 0.5 * x ** order), rtol=1e-11, atol=1e-15)
+    assert abs(sum(w for _, w in fac) - 1.0) < 1e-15
+    sig = np.array([s for s, _ in fac])
+    assert all(np.min(np.abs(sig - s.conjugate())) < 1e-14 for s in sig)
+    assert sum(abs(s.imag) < 1e-15 for s in sig) == order % 2
+    # every sigma has a real part >= -|sigma| cos(pi / n): M + sigma K is never singular for K >= 0
+    assert all(abs(s) > 0 and abs(np.angle(s)) < np.pi for s in sig)
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell", "vertex_voronoi"])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
+def test_shifted_solves_match_dense_solve(placement, order):
+    """phi_l as a sum of shifted solves on K's pattern equals the dense solve of
+    S = M + (1/2) l^(2n) K (M^-1 K)^(n-1), for every placement and order."""
+    m = synth.icosphere(2, radius=6371.0, jitter=0.2, seed=25)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=26, polar_cap_deg=10.0)
+    P = oracle.build_problem(m, placement)
+    rng = np.random.default_rng(order)
+    f = rng.normal(size=(P.n_comp, P.n_in))
+    ks = 2 * np.pi / np.array([4000.0, 1500.0, 600.0])
+    a = oracle.filter_shifted(P, f, ks, order)
+    b = oracle.filter_dense(P, f, ks, order)
+    assert np.max(np.abs(a - b)) < 1e-10 * np.max(np.abs(b))
