@@ -140,3 +140,53 @@ def test_bad_arguments_are_rejected(api):
     h = api.prepare_mesh_host(m, "vertex_scalar", max_order=1)
     assert h.info["n_rows"] == m["coords"].shape[0]
     h.release()
+
+
+def test_plain_c_client(api, tmp_path):
+    """The header compiles as strict C99 and a C program drives the host-side
+    entry points through the shared library (split square: K has 4 on the
+    diagonal, -1 on the axis edges, 0 on the diagonals; A_v = 1)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = tmp_path / "abi_client"
+    lib_dir = os.path.dirname(api.LIB_PATH)
+    cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "abi_client.c"), "-o", str(exe), "-L", lib_dir, "-lifilt",
+           "-Wl,-rpath," + lib_dir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe), str(tmp_path / "c.ifmesh")], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    out = dict(line.split(" ", 1) for line in r.stdout.strip().splitlines())
+    rows, nnz_k = out["rows"].split()[0], out["rows"].split()[2]
+    assert int(rows) == 36 and int(nnz_k) == 36 * 7
+    f = out["k_sum"].split()
+    assert float(f[0]) == 0.0 and int(f[2]) == 36 * 4 and int(f[4]) == 36 and abs(float(f[6]) - 36.0) < 1e-12
+    assert out["error"] == "message: yes"
+    kv = out["key_match"].split()
+    assert kv[0] == "1" and int(kv[2]) == api.ECACHE and int(kv[4]) >= 1
+
+
+def test_concurrent_preparation_is_deterministic(api):
+    """Host preparation called from several threads at once (ctypes drops the
+    GIL) gives every caller the same mesh as a lone call."""
+    from concurrent.futures import ThreadPoolExecutor
+    m = synth.icosphere(5, radius=6371.0, jitter=0.2, seed=45)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=46)
+
+    def run(placement):
+        h = api.prepare_mesh_host(m, placement, max_order=2)
+        g = h.multigrid()
+        blob = b"".join(h.export(w).tobytes() for w in ("perm", "k_col", "k_val", "mass", "g2_col", "g2_val"))
+        blob += b"".join(h.multigrid_export(level, "p_val").tobytes() for level in range(g["levels"] - 1))
+        h.release()
+        return blob
+
+    alone = {p: run(p) for p in ("vertex_scalar", "cell")}
+    with ThreadPoolExecutor(max_workers=6) as ex:
+        jobs = [(p, ex.submit(run, p)) for p in ("vertex_scalar", "cell") * 3]
+        for p, fut in jobs:
+            assert fut.result() == alone[p]
