@@ -567,75 +567,95 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
     const bool sphere = d.geometry == IFILT_GEOM_SPHERE;
     const double inv_r2 = sphere ? 1.0 / (d.radius * d.radius) : 0.0;
     const size_t nnz = K.col.size();
+    // Two phases so that rows can be assembled in parallel with the serial
+    // sums: (a) per triangle, its cotangent weights (and for vectors the metric
+    // factor and zonal derivatives of the basis functions); (b) per row, the
+    // contributions of the row's triangles in increasing triangle order (the
+    // incidence lists are ascending), which is the order a triangle-by-triangle
+    // scatter would add them in.
+    std::vector<double> tw((size_t)Tk * 3), tcoef, tmet, tdx;
+    if (vec) {
+      tcoef.resize(Tk);
+      tmet.resize(Tk);
+      tdx.resize((size_t)Tk * 3);
+    }
+    parallel_range(Tk, 4096, [&](int64_t cb, int64_t ce, int) {
+      for (int64_t c = cb; c < ce; c++) {
+        const int32_t* tv = tri + 3 * (int64_t)kept[c];
+        // stiffness: corner k receives nothing, its opposite edge (a, b) gets -1/2 cot
+        for (int k = 0; k < 3; k++) {
+          const int a = (k + 1) % 3, b = (k + 2) % 3;
+          const V3 u = geo.edge(tv[k], tv[a]), v = geo.edge(tv[k], tv[b]);
+          tw[3 * (size_t)c + k] = -0.5 * dot(u, v) / norm(cross(u, v));
+        }
+        if (vec) {
+          // metric factor m = tan(lat)/R and zonal unit vector at the centroid direction
+          double m = 0.0;
+          V3 east{1.0, 0.0, 0.0};
+          if (sphere) {
+            V3 cdir = add(add(geo.pos(tv[0]), geo.pos(tv[1])), geo.pos(tv[2]));
+            cdir = scale(cdir, 1.0 / norm(cdir));
+            const double lat = std::asin(std::max(-1.0, std::min(1.0, cdir.z)));
+            m = std::tan(lat) / d.radius;
+            const double h = std::sqrt(cdir.x * cdir.x + cdir.y * cdir.y);
+            east = {-cdir.y / h, cdir.x / h, 0.0};
+          }
+          // P1 gradients on the flat triangle: grad N_k = n x (x_{k+2} - x_{k+1}) / (2A)
+          const V3 e1 = geo.edge(tv[0], tv[1]), e2 = geo.edge(tv[0], tv[2]);
+          V3 nrm = cross(e1, e2);
+          const double twoA = norm(nrm);
+          nrm = scale(nrm, 1.0 / twoA);
+          for (int k = 0; k < 3; k++) {
+            const V3 eab = geo.edge(tv[(k + 1) % 3], tv[(k + 2) % 3]);
+            tdx[3 * (size_t)c + k] = dot(scale(cross(nrm, eab), 1.0 / twoA), east);
+          }
+          tcoef[c] = inv_r2 + m * m;
+          tmet[c] = m;
+        }
+      }
+    });
     std::vector<double> stiff(nnz, 0.0), mmass, tm;
     if (vec) {
       mmass.assign(nnz, 0.0);
       tm.assign(nnz, 0.0);
     }
-    for (int32_t c = 0; c < Tk; c++) {
-      const int32_t* tv = tri + 3 * (int64_t)kept[c];
-      int32_t rr[3] = {rank[vid[tv[0]]], rank[vid[tv[1]]], rank[vid[tv[2]]]};
-      const double A = area[c];
-      for (int q = 0; q < 3; q++) hp.mass[rr[q]] += A / 3.0;
-      // stiffness: corner k receives nothing, its opposite edge (a, b) gets -1/2 cot
-      for (int k = 0; k < 3; k++) {
-        int a = (k + 1) % 3, b = (k + 2) % 3;
-        V3 u = geo.edge(tv[k], tv[a]), v = geo.edge(tv[k], tv[b]);
-        double w = -0.5 * dot(u, v) / norm(cross(u, v));
-        stiff[find_entry(K, rr[a], rr[b])] += w;
-        stiff[find_entry(K, rr[b], rr[a])] += w;
-      }
-      if (vec) {
-        // metric factor m = tan(lat)/R and zonal unit vector at the centroid direction
-        double m = 0.0;
-        V3 east{1.0, 0.0, 0.0};
-        if (sphere) {
-          V3 cdir = add(add(geo.pos(tv[0]), geo.pos(tv[1])), geo.pos(tv[2]));
-          cdir = scale(cdir, 1.0 / norm(cdir));
-          double lat = std::asin(std::max(-1.0, std::min(1.0, cdir.z)));
-          m = std::tan(lat) / d.radius;
-          double h = std::sqrt(cdir.x * cdir.x + cdir.y * cdir.y);
-          east = {-cdir.y / h, cdir.x / h, 0.0};
-        }
-        // P1 gradients on the flat triangle: grad N_k = n x (x_{k+2} - x_{k+1}) / (2A)
-        V3 e1 = geo.edge(tv[0], tv[1]), e2 = geo.edge(tv[0], tv[2]);
-        V3 nrm = cross(e1, e2);
-        double twoA = norm(nrm);
-        nrm = scale(nrm, 1.0 / twoA);
-        double dx[3];
-        for (int k = 0; k < 3; k++) {
-          V3 eab = geo.edge(tv[(k + 1) % 3], tv[(k + 2) % 3]);
-          dx[k] = dot(scale(cross(nrm, eab), 1.0 / twoA), east);
-        }
-        const double coef = inv_r2 + m * m;
-        for (int a = 0; a < 3; a++)
+    parallel_range(N, 4096, [&](int64_t rb, int64_t re, int) {
+      for (int64_t r = rb; r < re; r++) {
+        const int32_t v = order[r];
+        for (int64_t e = inc_ptr[v]; e < inc_ptr[v + 1]; e++) {
+          const int32_t c = inc_idx[e] / 3, a = inc_idx[e] % 3;
+          const int32_t* tv = tri + 3 * (int64_t)kept[c];
+          const double A = area[c];
+          hp.mass[r] += A / 3.0;
           for (int b = 0; b < 3; b++) {
-            int64_t p = find_entry(K, rr[a], rr[b]);
-            // consistent P1 mass: A/6 on the diagonal, A/12 off it
-            mmass[p] += coef * (a == b ? A / 6.0 : A / 12.0);
-            // int N = A/3; m and d_x N are constant on the triangle
-            if (a != b) tm[p] += m * (A / 3.0) * (dx[b] - dx[a]);
+            const int64_t p = find_entry(K, (int32_t)r, rank[vid[tv[b]]]);
+            if (b != a) stiff[p] += tw[3 * (size_t)c + (3 - a - b)];
+            if (vec) {
+              // consistent P1 mass: A/6 on the diagonal, A/12 off it
+              mmass[p] += tcoef[c] * (a == b ? A / 6.0 : A / 12.0);
+              // int N = A/3; m and d_x N are constant on the triangle
+              if (a != b) tm[p] += tmet[c] * (A / 3.0) * (tdx[3 * (size_t)c + b] - tdx[3 * (size_t)c + a]);
+            }
           }
+        }
+        // diagonal stiffness: minus the off-diagonal row sum (basis functions sum to one)
+        double sum = 0.0;
+        int64_t pd = -1;
+        for (int64_t q = K.row_ptr[r]; q < K.row_ptr[r + 1]; q++) {
+          if (K.col[q] == r) pd = q;
+          else sum += stiff[q];
+        }
+        stiff[pd] = -sum;
+        for (int64_t q = K.row_ptr[r]; q < K.row_ptr[r + 1]; q++) {
+          if (vec) {
+            K.val[2 * q] = stiff[q] + mmass[q];
+            K.val[2 * q + 1] = tm[q];
+          } else {
+            K.val[q] = stiff[q];
+          }
+        }
       }
-    }
-    // diagonal stiffness: minus the off-diagonal row sum (basis functions sum to one)
-    for (int32_t r = 0; r < N; r++) {
-      double s = 0.0;
-      int64_t pd = -1;
-      for (int64_t q = K.row_ptr[r]; q < K.row_ptr[r + 1]; q++) {
-        if (K.col[q] == r) pd = q;
-        else s += stiff[q];
-      }
-      stiff[pd] = -s;
-    }
-    for (size_t q = 0; q < nnz; q++) {
-      if (vec) {
-        K.val[2 * q] = stiff[q] + mmass[q];
-        K.val[2 * q + 1] = tm[q];
-      } else {
-        K.val[q] = stiff[q];
-      }
-    }
+    });
   }
   if (d.placement == IFILT_VERTEX_VECTOR) {
     // Projection of cell velocities to vertices: R_vc = A_c / 3 (Sect. 2.1.2)
