@@ -24,6 +24,16 @@
  *     ifilt_last_error() returns a message (thread-local).  IFILT_NOT_CONVERGED
  *     is a warning: outputs are written, per-column stats say which columns
  *     missed the tolerance.  No call aborts the process or waits without bound.
+ *
+ * Environment variables (read at each call that uses them):
+ *   IFILT_HOST_THREADS  host worker threads for preparation and the multigrid
+ *                       setup (default: hardware threads, at most 64); results
+ *                       are the same bytes for any value
+ *   IFILT_AUTOTUNE=0    keep the default launch shapes of the batched solver
+ *                       instead of timing candidates on the first solve of a
+ *                       mesh (results then depend on nothing but the inputs)
+ *   IFILT_NO_GRAPH=1    launch every kernel directly instead of through CUDA graphs
+ *   IFILT_TRACE=1       print each batched-solver launch to stderr (read once)
  */
 #ifndef IFILT_H
 #define IFILT_H

@@ -373,6 +373,14 @@ ifilt_mesh_s* load_mesh_host(const char* path, uint64_t expect_key) {
     fail(IFILT_ECACHE, "cache file %s has format %u revision %u; this library writes %u / %u", path, fr[0], fr[1],
          kFormat, kPrepareRevision);
   if (expect_key && hdr[0] != expect_key) fail(IFILT_ECACHE, "cache file %s was written for another mesh", path);
+  {
+    // the payload length must be what the file holds (no allocation beyond the file's size)
+    const long here = std::ftell(fl.f);
+    if (here < 0 || std::fseek(fl.f, 0, SEEK_END) != 0) fail(IFILT_ECACHE, "cannot size cache file %s", path);
+    const long end = std::ftell(fl.f);
+    if (end < 0 || std::fseek(fl.f, here, SEEK_SET) != 0) fail(IFILT_ECACHE, "cannot size cache file %s", path);
+    if ((uint64_t)(end - here) != hdr[1]) fail(IFILT_ECACHE, "cache file %s is truncated or has trailing bytes", path);
+  }
   std::unique_ptr<ifilt_mesh_s> m(new ifilt_mesh_s());
   HostPrepared& h = m->host;
   h.key = hdr[0];

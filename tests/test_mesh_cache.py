@@ -147,6 +147,11 @@ def test_bad_files_are_refused(api, tmp_path):
         _refused(api, bad)
     bad.write_bytes(bytes(raw) + b"\0")
     _refused(api, bad)
+    # a header that claims a huge payload is refused before anything is allocated
+    b = bytearray(raw)
+    struct.pack_into("<Q", b, 24, 1 << 40)
+    bad.write_bytes(bytes(b))
+    assert "truncated" in _refused(api, bad)
     h.release()
 
 
