@@ -147,19 +147,26 @@ typedef struct {
   double period_x, period_y; /* periodic plane only */
   double radius;             /* sphere only (metric factor m = tan(lat)/radius, Sect. 2.1.2) */
   int32_t placement;         /* IFILT_VERTEX_SCALAR ... IFILT_CELL_CIRCUMCENTER */
-  int32_t max_order;         /* highest filter order n the mesh must serve: 1 or 2 */
+  int32_t max_order;         /* highest filter order n the mesh must serve, 1 .. IFILT_MAX_ORDER;
+                                orders >= 3 store G_n = K (M^-1 K)^(n-1) for n = 3 .. max_order */
   int32_t reorder;           /* IFILT_REORDER_* : device row order */
   double cell_A;             /* constant A of Eq. 6 (cell placement); 0 selects sqrt(3) */
   int32_t ell_slice;         /* rows per sliced-ELL slice, 4..1024; 0 = library default (64) */
 } ifilt_mesh_desc;
 
+#define IFILT_MAX_ORDER 4
+
 typedef struct {
-  int32_t order;             /* filter order n, 1 <= n <= mesh max_order */
+  int32_t order;             /* filter order n, 1 <= n <= mesh max_order.  n >= 3 (the paper's
+                                generalisation of Sect. 2.1.1) is solved on the explicit operator
+                                S = M + 1/2 l^(2n) G_n by CG in real arithmetic: the plain method,
+                                or the batched method without multigrid (the condition number
+                                grows like l^(2n), so FP32 inner solves suit small scales only) */
   double tol;                /* stop when ||r|| <= tol * ||r0|| (r0 = b - S phi, Sect. 2.2.2); the paper uses 1e-9 */
   int32_t max_iter;          /* cap on Krylov iterations per column (all refinement rounds); 0 = 100000 */
   int32_t precision;         /* IFILT_PREC_* */
   int32_t method;            /* IFILT_METHOD_* */
-  int32_t n2_solver;         /* IFILT_N2_* */
+  int32_t n2_solver;         /* IFILT_N2_* (order 2 only; orders >= 3 take AUTO or REAL) */
   int32_t precond;           /* IFILT_PRECOND_*; batched method only */
   int32_t check_every;       /* batched: iterations per CUDA graph between host checks; 0 = 32
                                 (8 with IFILT_PRECOND_MG) */
@@ -204,11 +211,21 @@ enum {
   IFILT_EXPORT_G2_VAL = 7      /* double [nnz_g2] (vector: [nnz_g2][2]) */
 };
 
+/* Higher-order operators G_n = K (M^-1 K)^(n-1), 2 <= n <= max_order, as host
+ * copies: part 0 row pointers (int64 [n_rows+1]), 1 columns (int32 [nnz]),
+ * 2 values (double [nnz], vector placement [nnz][2] for the 2x2 blocks).
+ * dst = NULL with bytes = 0 only reports the size.  *written (if not NULL)
+ * receives the byte count.  Errors: EINVAL (order outside 2..max_order,
+ * unknown part, destination too small). */
+ifilt_status ifilt_mesh_export_gn(ifilt_mesh mesh, int32_t order, int32_t part, void* dst, size_t bytes,
+                                  size_t* written);
+
 /* Build and cache the mesh-only arrays on the current device (Sect. 2.2.1):
  * ocean subset, device row order, the l-free operator K of the placement
  * (P1 stiffness for vertices, Sect. 2.1.1; stiffness plus metric terms and the
  * metric operator T for vectors, Sect. 2.1.2; A * graph Laplacian for cells,
- * Eq. 6), the lumped mass, K M^-1 K when max_order >= 2, FP64 CSR and
+ * Eq. 6), the lumped mass, K M^-1 K when max_order >= 2 (and G_n up to
+ * max_order), FP64 CSR and
  * FP64/FP32/BF16 sliced-ELL copies.  Host inputs are read during the call only.
  * On success *out owns device memory until ifilt_release_mesh.  Errors:
  * EINVAL (null or inconsistent arguments), EMESH (index out of range, repeated

@@ -22,6 +22,7 @@ N2_AUTO, N2_REAL, N2_COMPLEX = 0, 1, 2
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG = 0, 1, 2
 REORDER_NONE, REORDER_RCM, REORDER_HILBERT = 0, 1, 2
 MG_MAX_LEVELS = 16
+MAX_ORDER = 4
 OK, NOT_CONVERGED = 0, 1
 ECACHE = -6
 SAVE_MULTIGRID = 1
@@ -97,7 +98,8 @@ MG_EXPORT = {"s_rowptr": 0, "s_col": 1, "s_val": 2, "p_rowptr": 3, "p_col": 4, "
 
 # every symbol include/ifilt.h declares
 SYMBOLS = ["ifilt_prepare_mesh", "ifilt_prepare_mesh_host", "ifilt_mesh_upload", "ifilt_release_mesh", "ifilt_mesh_info", "ifilt_mesh_export",
-           "ifilt_mesh_multigrid", "ifilt_mesh_multigrid_export", "ifilt_mesh_key", "ifilt_mesh_get_key",
+           "ifilt_mesh_multigrid", "ifilt_mesh_multigrid_export", "ifilt_mesh_export_gn", "ifilt_mesh_key",
+           "ifilt_mesh_get_key",
            "ifilt_mesh_save", "ifilt_mesh_load_host", "ifilt_solve",
            "ifilt_solve_many", "ifilt_spectrum", "ifilt_spectrum_noalloc", "ifilt_solve_scratch_bytes", "ifilt_profile_enable", "ifilt_profile_read",
            "ifilt_profile_reset", "ifilt_last_error", "ifilt_version", "ifilt_server_create",
@@ -133,6 +135,8 @@ def load(path=None):
     lib.ifilt_mesh_multigrid.restype = i32
     lib.ifilt_mesh_multigrid_export.argtypes = [vp, i32, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
     lib.ifilt_mesh_multigrid_export.restype = i32
+    lib.ifilt_mesh_export_gn.argtypes = [vp, i32, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+    lib.ifilt_mesh_export_gn.restype = i32
     lib.ifilt_mesh_key.argtypes = [C.POINTER(MeshDesc), C.POINTER(C.c_uint64)]
     lib.ifilt_mesh_key.restype = i32
     lib.ifilt_mesh_get_key.argtypes = [vp, C.POINTER(C.c_uint64)]
@@ -240,6 +244,17 @@ class Mesh:
         out = np.zeros(max(int(cnt), 1), dtype=dt)
         _check(load().ifilt_mesh_export(self.handle, key, _ptr(out), out.nbytes))
         return out[:cnt]
+
+    def export_gn(self, order, part):
+        """G_n = K (M^-1 K)^(n-1) for 2 <= n <= max_order: part "rowptr", "col" or "val"."""
+        p = {"rowptr": 0, "col": 1, "val": 2}[part]
+        need = C.c_size_t(0)
+        lib = load()
+        _check(lib.ifilt_mesh_export_gn(self.handle, order, p, None, 0, C.byref(need)))
+        dt = {0: np.int64, 1: np.int32, 2: np.float64}[p]
+        out = np.zeros(max(need.value // np.dtype(dt).itemsize, 1), dtype=dt)
+        _check(lib.ifilt_mesh_export_gn(self.handle, order, p, _ptr(out), out.nbytes, C.byref(need)))
+        return out[: need.value // out.itemsize]
 
     @property
     def key(self):

@@ -327,6 +327,30 @@ ifilt_status ifilt_mesh_multigrid_export(ifilt_mesh m, int32_t level, int32_t wh
   IFILT_GUARD_END
 }
 
+ifilt_status ifilt_mesh_export_gn(ifilt_mesh m, int32_t order, int32_t part, void* dst, size_t bytes,
+                                  size_t* written) {
+  IFILT_GUARD_BEGIN
+  check_mesh(m);
+  const HostPrepared& h = m->host;
+  if (order < 2 || order > h.max_order) fail(IFILT_EINVAL, "order %d outside 2..%d (mesh max_order)", order, h.max_order);
+  const HostCSR& G = order == 2 ? h.G2 : h.Gn[(size_t)order - 3];
+  const void* src = nullptr;
+  size_t need = 0;
+  switch (part) {
+    case 0: src = G.row_ptr.data(); need = G.row_ptr.size() * 8; break;
+    case 1: src = G.col.data(); need = G.col.size() * 4; break;
+    case 2: src = G.val.data(); need = G.val.size() * 8; break;
+    default: fail(IFILT_EINVAL, "unknown part %d (0 row pointers, 1 columns, 2 values)", part);
+  }
+  if (written) *written = need;
+  if (!dst && bytes == 0) return IFILT_OK;
+  if (!dst) fail(IFILT_EINVAL, "null destination");
+  if (bytes < need) fail(IFILT_EINVAL, "destination holds %zu bytes, %zu needed", bytes, need);
+  if (need) std::memcpy(dst, src, need);
+  return IFILT_OK;
+  IFILT_GUARD_END
+}
+
 ifilt_status ifilt_mesh_export(ifilt_mesh m, int32_t what, void* dst, size_t bytes) {
   IFILT_GUARD_BEGIN
   check_mesh(m);
@@ -359,13 +383,15 @@ static void check_opts(ifilt_mesh m, const ifilt_solve_opts* o) {
   if (o->precision < IFILT_PREC_FP64 || o->precision > IFILT_PREC_BF16_IR) fail(IFILT_EINVAL, "unknown precision");
   if (o->method != IFILT_METHOD_PLAIN && o->method != IFILT_METHOD_BATCHED) fail(IFILT_EINVAL, "unknown method");
   if (o->n2_solver < IFILT_N2_AUTO || o->n2_solver > IFILT_N2_COMPLEX) fail(IFILT_EINVAL, "unknown n2_solver");
+  if (o->order >= 3 && o->n2_solver == IFILT_N2_COMPLEX)
+    fail(IFILT_EINVAL, "the complex factorisation serves order 2 only; orders >= 3 run in real arithmetic");
   if (o->method == IFILT_METHOD_PLAIN && o->precision != IFILT_PREC_FP64)
     fail(IFILT_EINVAL, "the plain method runs in FP64 only");
   if (o->precond < IFILT_PRECOND_NONE || o->precond > IFILT_PRECOND_MG)
     fail(IFILT_EINVAL, "unknown precond %d", o->precond);
   if (o->precond == IFILT_PRECOND_MG) {
     if (o->precision == IFILT_PREC_FP64) fail(IFILT_EINVAL, "multigrid preconditioning runs with FP32 or BF16 precision");
-    if (o->order >= 2 && o->n2_solver == IFILT_N2_REAL)
+    if (!(o->order == 1 || complex_form(*o)))
       fail(IFILT_EINVAL, "multigrid preconditioning needs order 1 or the complex n = 2 form");
   }
   if (o->method == IFILT_METHOD_PLAIN && o->precond != IFILT_PRECOND_NONE)
@@ -427,9 +453,14 @@ ifilt_status ifilt_solve_many(int32_t n_items, const ifilt_solve_item* items, vo
 
 size_t ifilt_solve_scratch_bytes(ifilt_mesh m, const ifilt_solve_opts* o, int32_t n_fields, int32_t n_k) {
   if (!m || !o || n_fields <= 0 || n_k <= 0) return 0;
+  if (o->order < 1 || o->order > m->host.max_order) return 0;
   if (o->method == IFILT_METHOD_PLAIN && m->device < 0) return 0;
-  if (o->method == IFILT_METHOD_PLAIN) return plain_scratch_bytes(m, *o);
-  return batched_scratch_bytes(m, *o, n_fields, n_k);
+  try {
+    if (o->method == IFILT_METHOD_PLAIN) return plain_scratch_bytes(m, *o);
+    return batched_scratch_bytes(m, *o, n_fields, n_k);
+  } catch (...) {
+    return 0;
+  }
 }
 
 ifilt_status ifilt_spectrum(ifilt_mesh m, int32_t n_fields, int32_t n_k, const double* k, const double* filtered,

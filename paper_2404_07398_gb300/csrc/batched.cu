@@ -1678,7 +1678,11 @@ class EngineT final : public Engine {
       : m_(m), o_(o), st_(st), budget_(budget) {
     const HostPrepared& h = m->host;
     n_ = h.n_rows;
-    E_ = (o.order >= 2 && !CPLX) ? &m->ell_g2 : &m->ell_k;
+    // the operator G of S = M + shift G: K for order 1 and the complex n = 2 form, K M^-1 K for the
+    // real n = 2 form, G_n for the orders above
+    op_ = CPLX ? 1 : o.order;
+    if (op_ >= 3 && (size_t)(op_ - 3) >= m->ell_gn.size()) fail(IFILT_EINVAL, "mesh holds no order-%d operator", op_);
+    E_ = op_ == 1 ? &m->ell_k : (op_ == 2 ? &m->ell_g2 : &m->ell_gn[(size_t)op_ - 3]);
     A_ = ell_view<MV>(*E_);
     A64_ = ell_view<double>(*E_);
     int lanes = o.max_lanes > 0 ? o.max_lanes : 256;
@@ -1849,11 +1853,12 @@ class EngineT final : public Engine {
   // diagonal of G for Jacobi preconditioning (nullptr: none)
   const double* gdiag64() const {
     if (o_.precond != IFILT_PRECOND_JACOBI) return nullptr;
-    return E_ == &m_->ell_g2 ? m_->diag_g2 : m_->diag_k;
+    return op_ == 1 ? m_->diag_k : (op_ == 2 ? m_->diag_g2 : m_->diag_gn[(size_t)op_ - 3]);
   }
   const T* gdiag_t() const {
     if (o_.precond != IFILT_PRECOND_JACOBI) return nullptr;
-    if constexpr (sizeof(T) == 4) return E_ == &m_->ell_g2 ? m_->diag_g2_32 : m_->diag_k32;
+    if constexpr (sizeof(T) == 4)
+      return op_ == 1 ? m_->diag_k32 : (op_ == 2 ? m_->diag_g2_32 : m_->diag_gn32[(size_t)op_ - 3]);
     else return gdiag64();
   }
   int64_t tile_bytes(int W) const {
@@ -1863,7 +1868,9 @@ class EngineT final : public Engine {
     const double ell = 1.0 / k;
     if (o_.order == 1) return 0.5 * ell * ell;
     if (CPLX) return ell * ell / std::sqrt(2.0);
-    return 0.5 * ell * ell * ell * ell;
+    double l2n = 1.0;  // l^(2n)
+    for (int i = 0; i < o_.order; i++) l2n *= ell * ell;
+    return 0.5 * l2n;
   }
 
   // source slot (b, x0) of a (field, system), built on first use
@@ -2340,6 +2347,7 @@ class EngineT final : public Engine {
   cudaStream_t st_;
   int64_t budget_;
   const DevEll* E_ = nullptr;
+  int op_ = 1;  // which operator E_ holds: 1 = K, 2 = K M^-1 K, n = G_n
   EllView<MV> A_{};
   EllView<double> A64_{};
   int64_t n_ = 0;
@@ -2380,7 +2388,7 @@ class EngineT final : public Engine {
     while (wb < W) wb <<= 1;
     char b[96];
     snprintf(b, sizeof b, "T%d/V%d/c%d/b%d/mg%d/E%d/W%d", (int)sizeof(T), (int)sizeof(MV), (int)CPLX, (int)BLK,
-             mg_on_ ? 1 : 0, E_ == &m_->ell_g2 ? 2 : 1, wb);
+             mg_on_ ? 1 : 0, op_, wb);
     return b;
   }
   void autotune() {
@@ -2709,7 +2717,7 @@ Engine* make_kind(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st, i
 }  // namespace
 
 Engine* make_engine(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st, int64_t budget) {
-  const bool cplx = o.order >= 2 && o.n2_solver != IFILT_N2_REAL;
+  const bool cplx = complex_form(o);
   const bool blk = m->host.placement == IFILT_VERTEX_VECTOR;
   if (o.precision == IFILT_PREC_FP64) return make_kind<double, double>(m, o, st, budget, cplx, blk);
   if (o.precision == IFILT_PREC_BF16_IR) return make_kind<float, __nv_bfloat16>(m, o, st, budget, cplx, blk);
@@ -2718,7 +2726,7 @@ Engine* make_engine(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st,
 
 size_t batched_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, int32_t nk) {
   const HostPrepared& h = m->host;
-  const bool cplx = o.order >= 2 && o.n2_solver != IFILT_N2_REAL;
+  const bool cplx = complex_form(o);
   const int nsys = h.placement == IFILT_CELL ? 2 : 1;
   const int ns = h.placement == IFILT_VERTEX_VECTOR ? 2 : 1;
   const int vec = o.precision == IFILT_PREC_FP64 ? 2 : 4;

@@ -36,7 +36,7 @@ namespace ifilt {
 namespace {
 
 constexpr char kMagic[8] = {'I', 'F', 'I', 'L', 'T', 'M', 'C', 0};
-constexpr uint32_t kFormat = 1;
+constexpr uint32_t kFormat = 2;
 // Bumped whenever preparation or the multigrid construction changes what it
 // produces, so that files written by an older library are prepared again.
 constexpr uint32_t kPrepareRevision = 2;
@@ -205,7 +205,7 @@ void check_finite(const std::vector<double>& v, size_t n, const char* what) {
 void check_prepared(const HostPrepared& h) {
   if (h.placement < IFILT_VERTEX_SCALAR || h.placement > IFILT_CELL_CIRCUMCENTER ||
       h.geometry < IFILT_GEOM_PLANAR_PERIODIC || h.geometry > IFILT_GEOM_SPHERE || h.max_order < 1 ||
-      h.max_order > 2 || h.reorder < IFILT_REORDER_NONE || h.reorder > IFILT_REORDER_HILBERT)
+      h.max_order > IFILT_MAX_ORDER || h.reorder < IFILT_REORDER_NONE || h.reorder > IFILT_REORDER_HILBERT)
     bad("header");
   const bool vec = h.placement == IFILT_VERTEX_VECTOR;
   const int32_t n_comp = (h.placement == IFILT_VERTEX_VECTOR || h.placement == IFILT_CELL) ? 2 : 1;
@@ -222,6 +222,8 @@ void check_prepared(const HostPrepared& h) {
   check_csr(h.K, h.n_rows, h.n_rows, nv, "operator K");
   if (h.max_order >= 2) check_csr(h.G2, h.n_rows, h.n_rows, nv, "operator K M^-1 K");
   else if (h.G2.nnz() != 0 || !h.G2.col.empty()) bad("operator K M^-1 K");
+  if (h.Gn.size() != (size_t)std::max(0, h.max_order - 2)) bad("higher-order operators");
+  for (const HostCSR& G : h.Gn) check_csr(G, h.n_rows, h.n_rows, nv, "higher-order operator");
   if (vec) {
     if (h.proj_ptr.size() != (size_t)h.n_rows + 1 || h.proj_ptr[0] != 0) bad("projection");
     for (int32_t r = 0; r < h.n_rows; r++)
@@ -320,6 +322,8 @@ void save_mesh(ifilt_mesh_s* m, const char* path, int32_t flags) {
       w.vec(h.mass);
       w.csr(h.K);
       w.csr(h.G2);
+      w.scalar<int32_t>((int32_t)h.Gn.size());
+      for (const HostCSR& G : h.Gn) w.csr(G);
       w.vec(h.proj_ptr);
       w.vec(h.proj_cell);
       w.vec(h.proj_w);
@@ -400,6 +404,10 @@ ifilt_mesh_s* load_mesh_host(const char* path, uint64_t expect_key) {
   r.vec(h.mass);
   r.csr(h.K);
   r.csr(h.G2);
+  const int32_t n_gn = r.scalar<int32_t>();
+  if (n_gn < 0 || n_gn > IFILT_MAX_ORDER - 2) bad("higher-order operator count");
+  h.Gn.resize((size_t)n_gn);
+  for (HostCSR& G : h.Gn) r.csr(G);
   r.vec(h.proj_ptr);
   r.vec(h.proj_cell);
   r.vec(h.proj_w);

@@ -162,6 +162,18 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
     build_ell(m, h.G2, slice_h, m->ell_g2, st);
     build_csr(m, h.G2, m->csr_g2, st);
   }
+  m->ell_gn.assign(h.Gn.size(), DevEll{});
+  m->csr_gn.assign(h.Gn.size(), DevCSR{});
+  m->diag_gn.assign(h.Gn.size(), nullptr);
+  m->diag_gn32.assign(h.Gn.size(), nullptr);
+  for (size_t i = 0; i < h.Gn.size(); i++) {
+    std::vector<double> dg = diagonal(h.Gn[i]);
+    m->diag_gn[i] = dev_copy(m, dg.data(), dg.size(), st);
+    std::vector<float> dg32(dg.begin(), dg.end());
+    m->diag_gn32[i] = dev_copy(m, dg32.data(), dg32.size(), st);
+    build_ell(m, h.Gn[i], slice_h, m->ell_gn[i], st);
+    build_csr(m, h.Gn[i], m->csr_gn[i], st);
+  }
   if (h.placement == IFILT_VERTEX_VECTOR) {
     m->proj_ptr = dev_copy(m, h.proj_ptr.data(), h.proj_ptr.size(), st);
     m->proj_cell = dev_copy(m, h.proj_cell.data(), h.proj_cell.size(), st);

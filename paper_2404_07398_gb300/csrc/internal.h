@@ -53,6 +53,7 @@ struct HostPrepared {
   std::vector<double> mass;       // lumped mass per row
   HostCSR K;                      // n = 1 operator, l-free, device order, sorted columns
   HostCSR G2;                     // K M^-1 K (max_order >= 2)
+  std::vector<HostCSR> Gn;        // G_n = G_(n-1) M^-1 K for n = 3 .. max_order (index n - 3)
   // vertex-vector right-hand side: b_i = sum over incident ocean triangles c of (A_c / 3) u_c
   std::vector<int64_t> proj_ptr;
   std::vector<int32_t> proj_cell;
@@ -60,6 +61,9 @@ struct HostPrepared {
 };
 
 HostPrepared prepare_host(const ifilt_mesh_desc& d);
+
+// The complex-shift factorisation serves order 2 only (orders >= 3 run on G_n in real arithmetic).
+inline bool complex_form(const ifilt_solve_opts& o) { return o.order == 2 && o.n2_solver != IFILT_N2_REAL; }
 
 // ---------------------------------------------------------------- device side
 // Sliced ELL: rows are cut into slices of `slice_h`; slice s holds its rows
@@ -121,6 +125,11 @@ struct ifilt_mesh_s {
   int32_t* inv_perm = nullptr;   // [n_out] device row of each output entry, -1 where not an unknown
   ifilt::DevEll ell_k, ell_g2;
   ifilt::DevCSR csr_k, csr_g2;   // real expanded CSR in FP64 (vector placement: interleaved u,v rows)
+  // orders n >= 3 (index n - 3): G_n as ELL and CSR, its diagonal in FP64 and FP32
+  std::vector<ifilt::DevEll> ell_gn;
+  std::vector<ifilt::DevCSR> csr_gn;
+  std::vector<double*> diag_gn;
+  std::vector<float*> diag_gn32;
   // multigrid preconditioner, built on first use (host) and uploaded on first device use
   std::mutex mg_mu;
   std::shared_ptr<ifilt::MgHost> mg_host;

@@ -121,8 +121,16 @@ struct PlainWork {
 
 }  // namespace
 
+// the explicit operator of order n: K, K M^-1 K or G_n
+static const DevCSR& order_csr(const ifilt_mesh_s* m, int order) {
+  if (order == 1) return m->csr_k;
+  if (order == 2) return m->csr_g2;
+  if ((size_t)(order - 3) >= m->csr_gn.size()) fail(IFILT_EINVAL, "mesh holds no order-%d operator", order);
+  return m->csr_gn[(size_t)order - 3];
+}
+
 size_t plain_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o) {
-  const DevCSR& G = o.order >= 2 ? m->csr_g2 : m->csr_k;
+  const DevCSR& G = order_csr(m, o.order);
   size_t n = (size_t)G.n;
   return (size_t)G.nnz * 8 + 6 * n * 8 + 4096 * 8 + 1024;
 }
@@ -130,7 +138,7 @@ size_t plain_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o) {
 ifilt_status solve_plain(ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, const double* fields, int32_t nk,
                          const double* k, double* out, ifilt_col_stats* stats, cudaStream_t st) {
   const HostPrepared& h = m->host;
-  const DevCSR& G = o.order >= 2 ? m->csr_g2 : m->csr_k;
+  const DevCSR& G = order_csr(m, o.order);
   const int32_t n = G.n;  // real unknowns
   const int nsub = h.placement == IFILT_VERTEX_VECTOR ? 2 : 1;
   const int nsys = h.placement == IFILT_CELL ? 2 : 1;

@@ -233,13 +233,14 @@ HostCSR pattern_from_graph(const Graph& g, const std::vector<int32_t>& order,
   return a;
 }
 
-// G = K M^-1 K with the structural product pattern (explicit zeros kept).
+// G = A M^-1 K with the structural product pattern (explicit zeros kept):
+// K M^-1 K for order 2 (A = K), and G_n = G_(n-1) M^-1 K for higher orders.
 // Rows are independent: each gathers its candidate products in the order
-// (entry e of row i, entry f of row K.col[e]), sorts them stably by column and
+// (entry e of row i of A, entry f of row A.col[e] of K), sorts them stably by column and
 // sums each column's run in that order, so every value is the same sum, in the
 // same order, whatever the number of threads.  Two passes: row sizes from the
 // columns alone, then columns and sums written in place.
-HostCSR product_kmk(const HostCSR& K, const std::vector<double>& mass) {
+HostCSR product_amk(const HostCSR& A, const HostCSR& K, const std::vector<double>& mass) {
   const int32_t n = K.n;
   const int nv = K.nval;
   HostCSR G;
@@ -258,8 +259,8 @@ HostCSR product_kmk(const HostCSR& K, const std::vector<double>& mass) {
     std::vector<int32_t>& c = cscratch[(size_t)w];
     for (int64_t i = b; i < e; i++) {
       c.clear();
-      for (int64_t q = K.row_ptr[i]; q < K.row_ptr[i + 1]; q++) {
-        const int32_t j = K.col[q];
+      for (int64_t q = A.row_ptr[i]; q < A.row_ptr[i + 1]; q++) {
+        const int32_t j = A.col[q];
         c.insert(c.end(), K.col.begin() + K.row_ptr[j], K.col.begin() + K.row_ptr[j + 1]);
       }
       stable_sort_small(c.data(), (int64_t)c.size(), [](int32_t x, int32_t y) { return x < y; });
@@ -275,8 +276,8 @@ HostCSR product_kmk(const HostCSR& K, const std::vector<double>& mass) {
     std::vector<Cand>& c = scratch[(size_t)w];
     for (int64_t i = b; i < e; i++) {
       c.clear();
-      for (int64_t q = K.row_ptr[i]; q < K.row_ptr[i + 1]; q++) {
-        const int32_t j = K.col[q];
+      for (int64_t q = A.row_ptr[i]; q < A.row_ptr[i + 1]; q++) {
+        const int32_t j = A.col[q];
         for (int64_t f = K.row_ptr[j]; f < K.row_ptr[j + 1]; f++) c.push_back(Cand{K.col[f], q, f});
       }
       stable_sort_small(c.data(), (int64_t)c.size(), [](const Cand& x, const Cand& y) { return x.k < y.k; });
@@ -286,12 +287,12 @@ HostCSR product_kmk(const HostCSR& K, const std::vector<double>& mass) {
         double s0 = 0.0, s1 = 0.0;
         for (; t < c.size() && c[t].k == col; t++) {
           const int64_t ee = c[t].e, ff = c[t].f;
-          const double inv = 1.0 / mass[K.col[ee]];
+          const double inv = 1.0 / mass[A.col[ee]];
           if (nv == 1) {
-            s0 += K.val[ee] * inv * K.val[ff];
+            s0 += A.val[ee] * inv * K.val[ff];
           } else {
             // blocks [[a, b], [-b, a]] multiply like a + i b
-            const double a1 = K.val[2 * ee] * inv, b1 = K.val[2 * ee + 1] * inv;
+            const double a1 = A.val[2 * ee] * inv, b1 = A.val[2 * ee + 1] * inv;
             const double a2 = K.val[2 * ff], b2 = K.val[2 * ff + 1];
             s0 += a1 * a2 - b1 * b2;
             s1 += a1 * b2 + b1 * a2;
@@ -314,7 +315,7 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   if (d.placement < IFILT_VERTEX_SCALAR || d.placement > IFILT_CELL_CIRCUMCENTER)
     fail(IFILT_EINVAL, "unknown placement %d", d.placement);
   if (d.geometry < IFILT_GEOM_PLANAR_PERIODIC || d.geometry > IFILT_GEOM_SPHERE) fail(IFILT_EINVAL, "unknown geometry %d", d.geometry);
-  if (d.max_order < 1 || d.max_order > 2) fail(IFILT_EINVAL, "max_order must be 1 or 2");
+  if (d.max_order < 1 || d.max_order > IFILT_MAX_ORDER) fail(IFILT_EINVAL, "max_order must be 1 .. %d", IFILT_MAX_ORDER);
   if (d.geometry == IFILT_GEOM_PLANAR_PERIODIC && !(d.period_x > 0 && d.period_y > 0))
     fail(IFILT_EINVAL, "periodic geometry needs positive periods");
   if (d.geometry == IFILT_GEOM_SPHERE && !(d.radius > 0)) fail(IFILT_EINVAL, "sphere needs radius > 0");
@@ -677,7 +678,9 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
     }
   }
   // ---- 4. order-2 product
-  if (d.max_order >= 2) hp.G2 = product_kmk(K, hp.mass);
+  if (d.max_order >= 2) hp.G2 = product_amk(K, K, hp.mass);
+  for (int n = 3; n <= d.max_order; n++)
+    hp.Gn.push_back(product_amk(n == 3 ? hp.G2 : hp.Gn.back(), K, hp.mass));
   return hp;
 }
 

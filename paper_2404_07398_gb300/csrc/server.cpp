@@ -80,7 +80,7 @@ struct ifilt_server_s {
       o.method = IFILT_METHOD_BATCHED;
       o.max_lanes = opts.max_lanes;
       o.check_every = opts.check_every;
-      const bool cplx = o.order >= 2 && o.n2_solver != IFILT_N2_REAL;
+      const bool cplx = ifilt::complex_form(o);
       Key key{r->mesh, o.order, o.precision, o.order >= 2 ? (cplx ? 2 : 1) : 0, o.precond, o.err_tol};
       auto it = engines.find(key);
       if (it == engines.end()) {
@@ -254,8 +254,11 @@ ifilt_status ifilt_server_submit(ifilt_server s, ifilt_mesh mesh, const ifilt_so
     if (!(o->err_tol >= 0.0) || !std::isfinite(o->err_tol)) fail(IFILT_EINVAL, "err_tol must be >= 0 and finite");
     if (o->precision < IFILT_PREC_FP64 || o->precision > IFILT_PREC_BF16_IR) fail(IFILT_EINVAL, "unknown precision");
     if (o->precond < IFILT_PRECOND_NONE || o->precond > IFILT_PRECOND_MG) fail(IFILT_EINVAL, "unknown precond");
+    if (o->n2_solver < IFILT_N2_AUTO || o->n2_solver > IFILT_N2_COMPLEX) fail(IFILT_EINVAL, "unknown n2_solver");
+    if (o->order >= 3 && o->n2_solver == IFILT_N2_COMPLEX)
+      fail(IFILT_EINVAL, "the complex factorisation serves order 2 only");
     if (o->precond == IFILT_PRECOND_MG &&
-        (o->precision == IFILT_PREC_FP64 || (o->order >= 2 && o->n2_solver == IFILT_N2_REAL)))
+        (o->precision == IFILT_PREC_FP64 || !(o->order == 1 || ifilt::complex_form(*o))))
       fail(IFILT_EINVAL, "multigrid preconditioning needs FP32/BF16 and order 1 or the complex n = 2 form");
     for (int32_t j = 0; j < n_k; j++)
       if (!(k[j] > 0.0)) fail(IFILT_EINVAL, "k must be positive");

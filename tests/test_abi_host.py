@@ -135,7 +135,7 @@ def test_malformed_meshes_are_rejected(api, bad):
 def test_bad_arguments_are_rejected(api):
     m = synth.icosphere(1, radius=1.0, jitter=0.0)
     with pytest.raises(api.IfiltError) as e:
-        api.prepare_mesh_host(m, "vertex_scalar", max_order=3)
+        api.prepare_mesh_host(m, "vertex_scalar", max_order=5)
     assert e.value.status == -1
     h = api.prepare_mesh_host(m, "vertex_scalar", max_order=1)
     assert h.info["n_rows"] == m["coords"].shape[0]

@@ -446,3 +446,34 @@ def test_cached_mesh_solves_identically(lib, tmp_path, monkeypatch, placement):
         assert np.array_equal(sa["iters"], sb["iters"])
     a.release()
     b.release()
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+@pytest.mark.parametrize("order", [3, 4])
+def test_higher_orders(lib, placement, order):
+    """Orders n >= 3 on the explicit operator S = M + 1/2 l^(2n) G_n (the
+    paper's generalisation of Sect. 2.1.1): plain FP64 CG, batched FP64, and
+    batched FP32 with FP64 refinement (plain and Jacobi-preconditioned)
+    against the oracle.  The FP64 bound is 1e-9: stopped at 1e-12 of the
+    initial residual, the error is at most cond(S) * 1e-12 with cond(S) up to
+    about 2e3 here (order 4, cell placement)."""
+    import torch
+    m = _sphere(3, 55, polar=10.0)
+    P = oracle.build_problem(m, placement)
+    f = _fields(P, 1, 3)
+    ks = 2 * np.pi / np.array([3000.0, 1500.0, 800.0])
+    _, ref = _oracle(m, placement, f, ks, order)
+    h = lib.prepare_mesh(m, placement, max_order=4)
+    ft = torch.tensor(f, dtype=torch.float64, device="cuda")
+    cases = ((dict(method=lib.METHOD_PLAIN, tol=1e-12), 1e-9),
+             (dict(tol=1e-12), 1e-9),
+             (dict(tol=1e-10, precision=lib.PREC_FP32_IR), TOL_MIXED),
+             (dict(tol=1e-10, precision=lib.PREC_FP32_IR, precond=lib.PRECOND_JACOBI), TOL_MIXED))
+    for opts, tol in cases:
+        out, stats, st = lib.solve(h, ft, ks, order=order, **opts)
+        assert st == 0, (opts, stats)
+        _check(out.cpu().numpy(), ref, tol)
+    for bad in (dict(n2_solver=lib.N2_COMPLEX), dict(precision=lib.PREC_FP32_IR, precond=lib.PRECOND_MG)):
+        with pytest.raises(lib.IfiltError):
+            lib.solve(h, ft, ks, order=order, **bad)
+    h.release()

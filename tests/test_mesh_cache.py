@@ -132,7 +132,7 @@ def test_bad_files_are_refused(api, tmp_path):
     bad = tmp_path / "bad.ifmesh"
     cases = {
         "magic": lambda b: b.__setitem__(0, ord("J")),
-        "format": lambda b: b.__setitem__(8, 2),
+        "format": lambda b: b.__setitem__(8, 99),
         "revision": lambda b: b.__setitem__(12, 99),
         "payload byte": lambda b: b.__setitem__(HEADER + 100, b[HEADER + 100] ^ 0x10),
         "last byte": lambda b: b.__setitem__(len(b) - 1, b[-1] ^ 1),
