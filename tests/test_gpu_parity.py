@@ -477,3 +477,26 @@ def test_higher_orders(lib, placement, order):
         with pytest.raises(lib.IfiltError):
             lib.solve(h, ft, ks, order=order, **bad)
     h.release()
+
+
+def test_iteration_cap_reports_not_converged(lib):
+    """max_iter caps every column: the call returns IFILT_NOT_CONVERGED (a
+    warning), each capped column says status 1 with its true residual above
+    the tolerance, the outputs are written (finite), and the same call without
+    the cap converges."""
+    import torch
+    m = _sphere(4, 69, polar=10.0)
+    P = oracle.build_problem(m, "cell")
+    f = torch.tensor(_fields(P, 1, 11), device="cuda")
+    ks = synth.log_wavenumbers(4000.0, 400.0, 4)
+    h = lib.prepare_mesh(m, "cell", max_order=2)
+    for opts in (dict(method=lib.METHOD_PLAIN, tol=1e-10), dict(tol=1e-10),
+                 dict(tol=1e-9, precision=lib.PREC_FP32_IR, precond=lib.PRECOND_MG, n2_solver=2)):
+        out, stats, st = lib.solve(h, f, ks, order=2, max_iter=3, **opts)
+        assert st == lib.NOT_CONVERGED, opts
+        assert (stats["status"] == 1).all(), stats
+        assert (stats["iters"] <= 3).all() and (stats["rel_residual"] > opts["tol"]).all()
+        assert torch.isfinite(out).all()
+        out, stats, st = lib.solve(h, f, ks, order=2, **opts)
+        assert st == 0 and (stats["status"] == 0).all()
+    h.release()
