@@ -11,6 +11,8 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 #include "multigrid.h"
 
@@ -146,6 +148,15 @@ void check_uploaded(ifilt_mesh m) {
 
 }  // namespace
 
+// An NVTX range around each heavy entry point, so that a timeline tool shows
+// where the library's time goes (no cost without a tool attached).
+struct ApiRange {
+  explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+  ~ApiRange() { nvtxRangePop(); }
+  ApiRange(const ApiRange&) = delete;
+  ApiRange& operator=(const ApiRange&) = delete;
+};
+
 extern "C" {
 
 const char* ifilt_last_error(void) { return g_last_error.c_str(); }
@@ -153,6 +164,7 @@ const char* ifilt_last_error(void) { return g_last_error.c_str(); }
 const char* ifilt_version(void) { return "ifilt 0.1 (sm_103a)"; }
 
 ifilt_status ifilt_prepare_mesh(const ifilt_mesh_desc* desc, void* stream, ifilt_mesh* out) {
+  ApiRange range_("ifilt_prepare_mesh");
   IFILT_GUARD_BEGIN
   if (!desc || !out) fail(IFILT_EINVAL, "null argument");
   *out = nullptr;
@@ -176,6 +188,7 @@ ifilt_status ifilt_prepare_mesh(const ifilt_mesh_desc* desc, void* stream, ifilt
 }
 
 ifilt_status ifilt_prepare_mesh_host(const ifilt_mesh_desc* desc, ifilt_mesh* out) {
+  ApiRange range_("ifilt_prepare_mesh_host");
   IFILT_GUARD_BEGIN
   if (!desc || !out) fail(IFILT_EINVAL, "null argument");
   *out = nullptr;
@@ -195,6 +208,7 @@ ifilt_status ifilt_prepare_mesh_host(const ifilt_mesh_desc* desc, ifilt_mesh* ou
 }
 
 ifilt_status ifilt_mesh_upload(ifilt_mesh m, void* stream) {
+  ApiRange range_("ifilt_mesh_upload");
   IFILT_GUARD_BEGIN
   check_mesh(m);
   if (m->device >= 0) return IFILT_OK;
@@ -230,6 +244,7 @@ ifilt_status ifilt_mesh_get_key(ifilt_mesh m, uint64_t* key) {
 }
 
 ifilt_status ifilt_mesh_save(ifilt_mesh m, const char* path, int32_t flags) {
+  ApiRange range_("ifilt_mesh_save");
   IFILT_GUARD_BEGIN
   check_mesh(m);
   save_mesh(m, path, flags);
@@ -238,6 +253,7 @@ ifilt_status ifilt_mesh_save(ifilt_mesh m, const char* path, int32_t flags) {
 }
 
 ifilt_status ifilt_mesh_load_host(const char* path, uint64_t expect_key, ifilt_mesh* out) {
+  ApiRange range_("ifilt_mesh_load_host");
   IFILT_GUARD_BEGIN
   if (!out) fail(IFILT_EINVAL, "null argument");
   *out = nullptr;
@@ -284,6 +300,7 @@ ifilt_status ifilt_mesh_info(ifilt_mesh m, ifilt_mesh_info_t* out) {
 }
 
 ifilt_status ifilt_mesh_multigrid(ifilt_mesh m, ifilt_multigrid_info* info) {
+  ApiRange range_("ifilt_mesh_multigrid");
   IFILT_GUARD_BEGIN
   check_mesh(m);
   if (!info) fail(IFILT_EINVAL, "null info");
@@ -405,6 +422,7 @@ static void check_opts(ifilt_mesh m, const ifilt_solve_opts* o) {
 
 ifilt_status ifilt_solve(ifilt_mesh m, const ifilt_solve_opts* o, int32_t n_fields, const double* fields, int32_t n_k,
                          const double* k, double* out, ifilt_col_stats* stats, void* stream) {
+  ApiRange range_("ifilt_solve");
   IFILT_GUARD_BEGIN
   check_uploaded(m);
   check_opts(m, o);
@@ -425,6 +443,7 @@ ifilt_status ifilt_solve(ifilt_mesh m, const ifilt_solve_opts* o, int32_t n_fiel
 }
 
 ifilt_status ifilt_solve_many(int32_t n_items, const ifilt_solve_item* items, void* stream) {
+  ApiRange range_("ifilt_solve_many");
   IFILT_GUARD_BEGIN
   if (n_items <= 0 || !items) fail(IFILT_EINVAL, "need at least one item");
   int dev = -1;
@@ -465,6 +484,7 @@ size_t ifilt_solve_scratch_bytes(ifilt_mesh m, const ifilt_solve_opts* o, int32_
 
 ifilt_status ifilt_spectrum(ifilt_mesh m, int32_t n_fields, int32_t n_k, const double* k, const double* filtered,
                             double* energy, double* spec, double* kmid, void* stream) {
+  ApiRange range_("ifilt_spectrum");
   IFILT_GUARD_BEGIN
   check_uploaded(m);
   if (n_fields <= 0 || n_k <= 0) fail(IFILT_EINVAL, "n_fields and n_k must be positive");
