@@ -64,6 +64,10 @@ void build_ell(ifilt_mesh_s* m, const HostCSR& a, int32_t slice_h, DevEll& out, 
       }
     }
   }
+  // every index the gather kernels will follow stays inside the source vector
+  const int32_t limit = ncols < 0 ? n : ncols;
+  for (int64_t e = 0; e < E; e++)
+    if (col[e] < 0 || col[e] >= limit) fail(IFILT_EINVAL, "internal: ELL column %d outside 0..%d", col[e], limit - 1);
   std::vector<float> v32(v64.size()), v32lo(v64.size());
   std::vector<__nv_bfloat16> v16(v64.size());
   for (size_t i = 0; i < v64.size(); i++) {
@@ -89,6 +93,10 @@ void build_ell(ifilt_mesh_s* m, const HostCSR& a, int32_t slice_h, DevEll& out, 
 // Real FP64 CSR; block matrices are expanded to interleaved rows (u_i at 2i, v_i at 2i+1):
 // block (a, b) at (i, j) gives u_i: a u_j + b v_j and v_i: -b u_j + a v_j.
 void build_csr(ifilt_mesh_s* m, const HostCSR& a, DevCSR& out, cudaStream_t st) {
+  if (a.row_ptr.size() != (size_t)a.n + 1 || a.row_ptr[0] != 0 || a.row_ptr[a.n] != (int64_t)a.col.size())
+    fail(IFILT_EINVAL, "internal: inconsistent CSR row pointers");
+  for (int32_t c : a.col)
+    if (c < 0 || c >= a.n) fail(IFILT_EINVAL, "internal: CSR column %d outside 0..%d", c, a.n - 1);
   if (a.nval == 1) {
     out.n = a.n;
     out.nnz = a.nnz();
