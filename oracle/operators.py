@@ -19,9 +19,13 @@ a split-square grid whose cotangent weight is exactly 0 is still an entry).
 Parity: the scalar and cell operators are pinned by closed forms on regular
 periodic grids and by a brute-force gradient re-derivation (tests).  The vector
 operator is pinned by its reduction to two scalar problems on the plane, by
-symmetry of [[K~, T], [-T, K~]] and by a quadrature re-derivation of T and of
-the metric mass term; the metric coefficients themselves follow the paper's
-formula as read and are otherwise parity unpinned.
+symmetry of [[K~, T], [-T, K~]], by a quadrature re-derivation of T and of the
+metric mass term, and on the sphere by the exact filter response of vector
+spherical harmonics (rigid rotation, poloidal and toroidal Y_2^1 are
+eigenfunctions of the vector Laplacian whose components carry the metric
+terms): second-order convergence, and a flipped sign of T or of the metric
+term fails it.  The finite-volume operators are pinned by the cotangent
+identity, area tiling, lattice closed forms and brute-force circumcentres.
 """
 
 import numpy as np
