@@ -1868,6 +1868,7 @@ class EngineT final : public Engine {
     const double ell = 1.0 / k;
     if (o_.order == 1) return 0.5 * ell * ell;
     if (CPLX) return ell * ell / std::sqrt(2.0);
+    if (o_.order == 2) return 0.5 * ell * ell * ell * ell;
     double l2n = 1.0;  // l^(2n)
     for (int i = 0; i < o_.order; i++) l2n *= ell * ell;
     return 0.5 * l2n;
