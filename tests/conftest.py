@@ -11,6 +11,9 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device and the compiled library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    # temporary files of the tests (cache files, a compiled C client) stay in the checkout
+    if not config.option.basetemp:
+        config.option.basetemp = os.path.join(ROOT, ".pytest_tmp")
 
 
 @pytest.fixture(scope="session")
