@@ -190,3 +190,25 @@ def test_concurrent_preparation_is_deterministic(api):
         jobs = [(p, ex.submit(run, p)) for p in ("vertex_scalar", "cell") * 3]
         for p, fut in jobs:
             assert fut.result() == alone[p]
+
+
+def test_product_path_has_no_fallback(tmp_path):
+    """Without the compiled library the binding raises (no CPU fallback), and
+    nothing in the package imports the oracle."""
+    import ast
+    import subprocess
+    import sys
+    code = ("import paper_2404_07398_gb300.api as a\n"
+            "a.LIB_PATH = '" + str(tmp_path / "absent.so") + "'\n"
+            "try:\n    a.load()\nexcept RuntimeError as e:\n    print('raised', 'missing' in str(e))\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=120)
+    assert r.stdout.strip() == "raised True", r.stdout + r.stderr
+    pkg = os.path.join(ROOT, "paper_2404_07398_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            tree = ast.parse(open(os.path.join(pkg, f)).read())
+            for node in ast.walk(tree):
+                if isinstance(node, ast.Import):
+                    assert not any(a.name.split(".")[0] == "oracle" for a in node.names), f
+                elif isinstance(node, ast.ImportFrom):
+                    assert (node.module or "").split(".")[0] != "oracle", f
