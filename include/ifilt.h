@@ -152,6 +152,10 @@ typedef struct {
   int32_t reorder;           /* IFILT_REORDER_* : device row order */
   double cell_A;             /* constant A of Eq. 6 (cell placement); 0 selects sqrt(3) */
   int32_t ell_slice;         /* rows per sliced-ELL slice, 4..1024; 0 = library default (64) */
+  double mg_strength;        /* multigrid aggregation threshold theta in [0, 1): aggregates follow
+                                only connections |k_ij| >= theta sqrt(|k_ii k_jj|), and coarse levels
+                                get smoother weights scaled to their operators; 0 = every neighbour
+                                and weight 2/3 on all levels (the default hierarchy) */
 } ifilt_mesh_desc;
 
 #define IFILT_MAX_ORDER 4
@@ -283,7 +287,8 @@ enum {
   IFILT_MG_P_COL = 4,
   IFILT_MG_P_VAL = 5,     /* double [nnz_p][1 or 2] */
   IFILT_MG_DK = 6,        /* double [rows_l]: diagonal of K_l */
-  IFILT_MG_DM = 7         /* double [rows_l]: diagonal of M_l */
+  IFILT_MG_DM = 7,        /* double [rows_l]: diagonal of M_l */
+  IFILT_MG_OMEGA = 8      /* double [2]: prolongator-smoothing weight, smoother weight of level l */
 };
 /* Copy one array of level `level` to `dst` of `bytes` bytes (EINVAL if too
  * small or out of range); *written receives the byte count. */

@@ -43,7 +43,7 @@ class MeshDesc(C.Structure):
                 ("ocean", C.c_void_p), ("geometry", C.c_int32), ("period_x", C.c_double),
                 ("period_y", C.c_double), ("radius", C.c_double), ("placement", C.c_int32),
                 ("max_order", C.c_int32), ("reorder", C.c_int32), ("cell_A", C.c_double),
-                ("ell_slice", C.c_int32)]
+                ("ell_slice", C.c_int32), ("mg_strength", C.c_double)]
 
 
 class SolveOpts(C.Structure):
@@ -94,7 +94,8 @@ class MultigridInfo(C.Structure):
                 ("nnz_p", C.c_int64 * MG_MAX_LEVELS)]
 
 
-MG_EXPORT = {"s_rowptr": 0, "s_col": 1, "s_val": 2, "p_rowptr": 3, "p_col": 4, "p_val": 5, "dk": 6, "dm": 7}
+MG_EXPORT = {"s_rowptr": 0, "s_col": 1, "s_val": 2, "p_rowptr": 3, "p_col": 4, "p_val": 5, "dk": 6, "dm": 7,
+             "omega": 8}
 
 # every symbol include/ifilt.h declares
 SYMBOLS = ["ifilt_prepare_mesh", "ifilt_prepare_mesh_host", "ifilt_mesh_upload", "ifilt_release_mesh", "ifilt_mesh_info", "ifilt_mesh_export",
@@ -283,7 +284,7 @@ class Mesh:
         cap = {"s_rowptr": (n + 1, np.int64), "s_col": (g["nnz_s"][level], np.int32),
                "s_val": (g["nnz_s"][level] * (4 if blk else 2), np.float64), "p_rowptr": (n + 1, np.int64),
                "p_col": (g["nnz_p"][level], np.int32), "p_val": (g["nnz_p"][level] * (2 if blk else 1), np.float64),
-               "dk": (n, np.float64), "dm": (n, np.float64)}
+               "dk": (n, np.float64), "dm": (n, np.float64), "omega": (2, np.float64)}
         cnt, dt = cap[what]
         out = np.zeros(max(int(cnt), 1), dtype=dt)
         wrote = C.c_size_t(0)
@@ -292,7 +293,7 @@ class Mesh:
         return out[: wrote.value // out.itemsize]
 
 
-def _desc(mesh, placement, max_order, reorder, cell_A, ell_slice):
+def _desc(mesh, placement, max_order, reorder, cell_A, ell_slice, mg_strength=0.0):
     coords = np.ascontiguousarray(mesh["coords"], dtype=np.float64)
     tri = np.ascontiguousarray(mesh["tri"], dtype=np.int32)
     ocean = mesh.get("ocean")
@@ -301,31 +302,32 @@ def _desc(mesh, placement, max_order, reorder, cell_A, ell_slice):
                  ocean=None if ocean is None else ocean.ctypes.data, geometry=GEOMS[mesh["geom"]],
                  period_x=float(mesh.get("period_x", 0.0)), period_y=float(mesh.get("period_y", 0.0)),
                  radius=float(mesh.get("radius", 0.0)), placement=PLACEMENTS.get(placement, placement),
-                 max_order=max_order, reorder=reorder, cell_A=float(cell_A), ell_slice=ell_slice)
+                 max_order=max_order, reorder=reorder, cell_A=float(cell_A), ell_slice=ell_slice,
+                 mg_strength=float(mg_strength))
     return d, (coords, tri, ocean)   # keep the arrays alive with the descriptor
 
 
-def prepare_mesh(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_slice=0, stream=None):
+def prepare_mesh(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_slice=0, stream=None, mg_strength=0.0):
     """`mesh` is a dict with coords [V][2|3], tri [T][3], geom, period_x, period_y,
     radius and optional ocean [V] (uint8).  Returns a device-resident Mesh."""
-    d, keep = _desc(mesh, placement, max_order, reorder, cell_A, ell_slice)
+    d, keep = _desc(mesh, placement, max_order, reorder, cell_A, ell_slice, mg_strength)
     h = C.c_void_p()
     _check(load().ifilt_prepare_mesh(C.byref(d), _stream_ptr(stream), C.byref(h)))
     return Mesh(h)
 
 
-def prepare_mesh_host(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_slice=0):
+def prepare_mesh_host(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_slice=0, mg_strength=0.0):
     """Host half of the preparation (no GPU needed): the Mesh answers info and
     export; `upload()` makes it solvable."""
-    d, keep = _desc(mesh, placement, max_order, reorder, cell_A, ell_slice)
+    d, keep = _desc(mesh, placement, max_order, reorder, cell_A, ell_slice, mg_strength)
     h = C.c_void_p()
     _check(load().ifilt_prepare_mesh_host(C.byref(d), C.byref(h)))
     return Mesh(h)
 
 
-def mesh_key(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_slice=0):
+def mesh_key(mesh, placement, max_order=2, reorder=1, cell_A=0.0, ell_slice=0, mg_strength=0.0):
     """64-bit key of a mesh descriptor (names its cache file)."""
-    d, keep = _desc(mesh, placement, max_order, reorder, cell_A, ell_slice)
+    d, keep = _desc(mesh, placement, max_order, reorder, cell_A, ell_slice, mg_strength)
     k = C.c_uint64(0)
     _check(load().ifilt_mesh_key(C.byref(d), C.byref(k)))
     return k.value
@@ -340,12 +342,12 @@ def load_mesh_host(path, key=0):
 
 
 def prepare_mesh_cached(mesh, placement, cache_dir, max_order=2, reorder=1, cell_A=0.0, ell_slice=0,
-                        multigrid=True, upload=True, stream=None):
+                        multigrid=True, upload=True, stream=None, mg_strength=0.0):
     """prepare_mesh through a directory of cache files named by the descriptor
     key: load the file if it is there and valid, else prepare on the host and
     write it (with the multigrid hierarchy if `multigrid`).  Returns
     (Mesh, hit) with the mesh uploaded if `upload`."""
-    key = mesh_key(mesh, placement, max_order, reorder, cell_A, ell_slice)
+    key = mesh_key(mesh, placement, max_order, reorder, cell_A, ell_slice, mg_strength)
     path = os.path.join(cache_dir, f"{key:016x}.ifmesh")
     hit = False
     try:
@@ -354,7 +356,7 @@ def prepare_mesh_cached(mesh, placement, cache_dir, max_order=2, reorder=1, cell
     except IfiltError as e:
         if e.status != ECACHE:
             raise
-        m = prepare_mesh_host(mesh, placement, max_order, reorder, cell_A, ell_slice)
+        m = prepare_mesh_host(mesh, placement, max_order, reorder, cell_A, ell_slice, mg_strength)
         os.makedirs(cache_dir, exist_ok=True)
         m.save(path, multigrid=multigrid)
     if upload:

@@ -326,6 +326,7 @@ ifilt_status ifilt_mesh_multigrid_export(ifilt_mesh m, int32_t level, int32_t wh
   const MgHostLevel& L = h.levels[level];
   const void* src = nullptr;
   size_t need = 0;
+  double omega[2];
   switch (what) {
     case IFILT_MG_S_ROWPTR: src = L.S.row_ptr.data(); need = L.S.row_ptr.size() * 8; break;
     case IFILT_MG_S_COL: src = L.S.col.data(); need = L.S.col.size() * 4; break;
@@ -335,6 +336,13 @@ ifilt_status ifilt_mesh_multigrid_export(ifilt_mesh m, int32_t level, int32_t wh
     case IFILT_MG_P_VAL: src = L.P.val.data(); need = L.P.val.size() * 8; break;
     case IFILT_MG_DK: src = L.dk.data(); need = L.dk.size() * 8; break;
     case IFILT_MG_DM: src = L.dm.data(); need = L.dm.size() * 8; break;
+    case IFILT_MG_OMEGA: {
+      omega[0] = L.omega_p;
+      omega[1] = L.omega_s;
+      src = omega;
+      need = sizeof omega;
+      break;
+    }
     default: fail(IFILT_EINVAL, "unknown multigrid export selector %d", what);
   }
   if (bytes < need) fail(IFILT_EINVAL, "destination holds %zu bytes, %zu needed", bytes, need);

@@ -2583,7 +2583,7 @@ class EngineT final : public Engine {
   // one gather-kernel launch on a multigrid operator; returns its block count
   template <int EPI, int NSET>
   int mg_gather(const DevEll& E, const T* src, T* out, const T* mdiag, const T* kd, const T* rhs, const T* own,
-                double* partial) {
+                double* partial, double omega = kMgOmega) {
     const int W = P_.W;
     const int vbytes = NVAL * NSET * (int)sizeof(T);
     Params Q = P_;
@@ -2595,16 +2595,17 @@ class EngineT final : public Engine {
     int blocks = std::min(nb_max_, grid_for(mg_fn<EPI, NSET>(), kBlock, smem, ntiles * kBlock));
     if (bpsm_mg_ > 0) blocks = std::min(blocks, n_sms_ * bpsm_mg_);
     spmm_kernel<T, T, CPLX, BLK, 4, mg_minb<EPI>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
-        ell_view<T>(E), Q, E.n_slices, src, out, mdiag, mg_cols_, partial, MgArgs<T>{kd, rhs, own, (T)kMgOmega});
+        ell_view<T>(E), Q, E.n_slices, src, out, mdiag, mg_cols_, partial, MgArgs<T>{kd, rhs, own, (T)omega});
     return blocks;
   }
   // S_l-operations: level 0 uses the mesh's K and lumped mass, coarser levels their (K, M) pair
   // (FP32 engines only: the FP64 engine refuses multigrid in mg_setup)
   int mg_smooth(size_t l, const T* x, T* out, const T* rhs, double* partial) {
     if constexpr (sizeof(T) == 4) {
-      if (l == 0) return mg_gather<kEpiSmooth, 1>(m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial);
       const DevMgLevel& L = (*mgl_)[l];
-      return mg_gather<kEpiSmooth, 2>(L.S, x, out, L.dm32, L.dk32, rhs, nullptr, partial);
+      if (l == 0)
+        return mg_gather<kEpiSmooth, 1>(m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial, L.omega);
+      return mg_gather<kEpiSmooth, 2>(L.S, x, out, L.dm32, L.dk32, rhs, nullptr, partial, L.omega);
     } else {
       return 0;
     }
@@ -2631,7 +2632,7 @@ class EngineT final : public Engine {
       Q.n = rows;
       const int g = std::min(nb_max_, grid_for((const void*)mg_jacobi_kernel<T, CPLX, BLK>, kBlock, 0,
                                                (long long)rows * (P_.W / VEC)));
-      mg_jacobi_kernel<T, CPLX, BLK><<<g, kBlock, 0, st_>>>(Q, rhs, out, md, kd, C_, (T)kMgOmega);
+      mg_jacobi_kernel<T, CPLX, BLK><<<g, kBlock, 0, st_>>>(Q, rhs, out, md, kd, C_, (T)(*mgl_)[l].omega);
     }
   }
   // One V-cycle on level l for the right-hand side rhs: two damped-Jacobi

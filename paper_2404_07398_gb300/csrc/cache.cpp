@@ -36,7 +36,7 @@ namespace ifilt {
 namespace {
 
 constexpr char kMagic[8] = {'I', 'F', 'I', 'L', 'T', 'M', 'C', 0};
-constexpr uint32_t kFormat = 2;
+constexpr uint32_t kFormat = 3;
 // Bumped whenever preparation or the multigrid construction changes what it
 // produces, so that files written by an older library are prepared again.
 constexpr uint32_t kPrepareRevision = 2;
@@ -243,7 +243,7 @@ void check_multigrid(const MgHost& g, const HostPrepared& h) {
   const int32_t nv = h.placement == IFILT_VERTEX_VECTOR ? 2 : 1;
   for (size_t l = 0; l < L; l++) {
     const MgHostLevel& Lv = g.levels[l];
-    if (Lv.n <= 0 || !std::isfinite(Lv.omega_p)) bad("multigrid level");
+    if (Lv.n <= 0 || !std::isfinite(Lv.omega_p) || !(Lv.omega_s > 0.0 && Lv.omega_s <= 1.0)) bad("multigrid level");
     if (l == 0) {
       if (!Lv.S.row_ptr.empty() || !Lv.S.col.empty()) bad("multigrid level 0");
     } else {
@@ -271,7 +271,7 @@ uint64_t mesh_key(const ifilt_mesh_desc& d) {
   h.update(rev, sizeof rev);
   const int32_t ints[7] = {d.n_vert, d.n_tri, d.geometry, d.placement, d.max_order, d.reorder, d.ell_slice};
   h.update(ints, sizeof ints);
-  const double dbl[4] = {d.period_x, d.period_y, d.radius, d.cell_A};
+  const double dbl[5] = {d.period_x, d.period_y, d.radius, d.cell_A, d.mg_strength};
   h.update(dbl, sizeof dbl);
   const int dim = d.geometry == IFILT_GEOM_SPHERE ? 3 : 2;
   h.update(d.coords, sizeof(double) * (size_t)d.n_vert * dim);
@@ -318,6 +318,7 @@ void save_mesh(ifilt_mesh_s* m, const char* path, int32_t flags) {
       const int32_t ints[9] = {h.placement, h.geometry, h.max_order, h.reorder, h.n_rows,
                                h.n_in,      h.n_out,    h.n_comp,    m->slice_h};
       w.raw(ints, sizeof ints);
+      w.scalar<double>(h.mg_strength);
       w.vec(h.perm);
       w.vec(h.mass);
       w.csr(h.K);
@@ -332,6 +333,7 @@ void save_mesh(ifilt_mesh_s* m, const char* path, int32_t flags) {
         for (const MgHostLevel& L : mg->levels) {
           w.scalar<int32_t>(L.n);
           w.scalar<double>(L.omega_p);
+          w.scalar<double>(L.omega_s);
           w.csr(L.S);
           w.csr(L.P);
           w.csr(L.R);
@@ -400,6 +402,8 @@ ifilt_mesh_s* load_mesh_host(const char* path, uint64_t expect_key) {
   h.n_out = ints[6];
   h.n_comp = ints[7];
   m->slice_h = ints[8];
+  h.mg_strength = r.scalar<double>();
+  if (!(h.mg_strength >= 0.0 && h.mg_strength < 1.0)) bad("multigrid strength");
   r.vec(h.perm);
   r.vec(h.mass);
   r.csr(h.K);
@@ -420,6 +424,7 @@ ifilt_mesh_s* load_mesh_host(const char* path, uint64_t expect_key) {
     for (MgHostLevel& L : mg->levels) {
       L.n = r.scalar<int32_t>();
       L.omega_p = r.scalar<double>();
+      L.omega_s = r.scalar<double>();
       r.csr(L.S);
       r.csr(L.P);
       r.csr(L.R);

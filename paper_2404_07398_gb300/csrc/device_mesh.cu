@@ -198,7 +198,11 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
 
 const MgHost& multigrid_host(ifilt_mesh_s* m) {
   std::lock_guard<std::mutex> lk(m->mg_mu);
-  if (!m->mg_host) m->mg_host = std::make_shared<MgHost>(build_multigrid(m->host, MgParams{}));
+  if (!m->mg_host) {
+    MgParams prm;
+    prm.strength = m->host.mg_strength;
+    m->mg_host = std::make_shared<MgHost>(build_multigrid(m->host, prm));
+  }
   return *m->mg_host;
 }
 
@@ -214,6 +218,7 @@ const std::vector<DevMgLevel>& multigrid_device(ifilt_mesh_s* m, cudaStream_t st
     const MgHostLevel& L = h.levels[l];
     DevMgLevel& D = dev[l];
     D.n = L.n;
+    D.omega = L.omega_s;
     if (l > 0) build_ell(m, L.S, kMgSlice, D.S, st);
     if (l + 1 < h.levels.size()) {
       build_ell(m, L.P, kMgSlice, D.P, st, h.levels[l + 1].n);

@@ -47,6 +47,7 @@ struct HostCSR {
 
 struct HostPrepared {
   uint64_t key = 0;               // ifilt_mesh_key of the descriptor it was prepared from
+  double mg_strength = 0.0;       // multigrid aggregation threshold (ifilt_mesh_desc)
   int32_t placement = 0, geometry = 0, max_order = 1, reorder = 1;
   int32_t n_rows = 0, n_in = 0, n_out = 0, n_comp = 1;
   std::vector<int32_t> perm;      // device row -> original index (vertex or triangle)
@@ -90,6 +91,7 @@ struct DevMgLevel {
   DevEll S, P, R;
   float* dk32 = nullptr;
   float* dm32 = nullptr;
+  double omega = 2.0 / 3.0;  // damped-Jacobi weight of the smoother on this level
 };
 struct MgHost;  // multigrid.h
 

@@ -184,30 +184,44 @@ Csr<V> transpose(const Csr<V>& P) {
   return R;
 }
 
-// greedy aggregation on the pattern of A (diagonal ignored)
+// Greedy aggregation on the pattern of A (diagonal ignored), following only strong
+// connections |a_ij| >= theta sqrt(|a_ii a_jj|) (theta = 0: every stored neighbour):
+// a node whose strong neighbours are all free roots an aggregate of itself and them;
+// left nodes join the aggregate of a strong neighbour; the rest form their own.
 template <typename V>
-std::vector<int32_t> aggregate(const Csr<V>& A, int32_t& n_agg) {
+std::vector<int32_t> aggregate(const Csr<V>& A, double theta, int32_t& n_agg) {
   const int32_t n = A.n;
+  std::vector<double> d((size_t)n, 0.0);
+  if (theta > 0.0)
+    for (int32_t i = 0; i < n; i++)
+      for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; e++)
+        if (A.col[e] == i) d[i] = mag(A.val[e]);
+  auto strong = [&](int32_t i, int64_t e) {
+    const int32_t j = A.col[e];
+    if (j == i) return false;
+    return theta <= 0.0 || mag(A.val[e]) >= theta * std::sqrt(d[i] * d[j]);
+  };
   std::vector<int32_t> agg((size_t)n, -1);
   int32_t na = 0;
   for (int32_t i = 0; i < n; i++) {
     if (agg[i] >= 0) continue;
     bool free_nb = true;
     for (int64_t e = A.ptr[i]; e < A.ptr[i + 1] && free_nb; e++)
-      if (agg[A.col[e]] >= 0) free_nb = false;
+      if (strong(i, e) && agg[A.col[e]] >= 0) free_nb = false;
     if (!free_nb) continue;
-    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; e++) agg[A.col[e]] = na;
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; e++)
+      if (strong(i, e)) agg[A.col[e]] = na;
     agg[i] = na++;
   }
   for (int32_t i = 0; i < n; i++) {
     if (agg[i] >= 0) continue;
     for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; e++)
-      if (A.col[e] != i && agg[A.col[e]] >= 0 && agg[A.col[e]] < na) {
+      if (strong(i, e) && agg[A.col[e]] >= 0 && agg[A.col[e]] < na) {
         agg[i] = agg[A.col[e]];
         break;
       }
   }
-  // nodes with no aggregated neighbour (e.g. isolated rows) form their own
+  // nodes with no aggregated strong neighbour (e.g. isolated rows) form their own
   for (int32_t i = 0; i < n; i++)
     if (agg[i] < 0) agg[i] = na++;
   n_agg = na;
@@ -350,6 +364,26 @@ MgHost build(const HostPrepared& hp, const MgParams& prm) {
           }
     });
     if (level > 0) L.S = to_host(S);
+    if (level > 0 && prm.strength > 0.0) {
+      // smoother weight scaled to this level's pair: the Galerkin mass is not diagonal
+      Csr<V> Kl, Ml;
+      Kl.n = Kl.m = Ml.n = Ml.m = S.n;
+      Kl.ptr = Ml.ptr = S.ptr;
+      Kl.col = Ml.col = S.col;
+      Kl.val.resize(S.val.size());
+      Ml.val.resize(S.val.size());
+      for (size_t q = 0; q < S.val.size(); q++) {
+        Kl.val[q] = S.val[q].k;
+        Ml.val[q] = S.val[q].m;
+      }
+      std::vector<double> ik((size_t)S.n), im((size_t)S.n);
+      for (int32_t i = 0; i < S.n; i++) {
+        ik[i] = L.dk[i] > 0.0 ? 1.0 / L.dk[i] : 0.0;
+        im[i] = L.dm[i] > 0.0 ? 1.0 / L.dm[i] : 0.0;
+      }
+      const double lam = std::max(lambda_max(Kl, ik), lambda_max(Ml, im));
+      L.omega_s = std::min(2.0 / 3.0, (4.0 / 3.0) / lam);
+    }
     const bool last = S.n <= prm.coarsest_rows || level + 1 >= prm.max_levels;
     if (!last) {
       // K_l alone, for the aggregation graph and the prolongator smoothing
@@ -362,7 +396,7 @@ MgHost build(const HostPrepared& hp, const MgParams& prm) {
         for (int64_t q = b; q < e; q++) K.val[q] = S.val[q].k;
       });
       int32_t na = 0;
-      const std::vector<int32_t> agg = aggregate(K, na);
+      const std::vector<int32_t> agg = aggregate(K, prm.strength, na);
       if (na > 0 && (double)na <= prm.min_ratio * (double)S.n) {
         std::vector<double> dinv((size_t)S.n, 0.0);
         for (int32_t i = 0; i < S.n; i++) dinv[i] = L.dk[i] > 0.0 ? 1.0 / L.dk[i] : 0.0;

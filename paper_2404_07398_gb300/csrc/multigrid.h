@@ -12,6 +12,11 @@ struct MgParams {
   int32_t coarsest_rows = 64;  // stop coarsening at or below this many rows
   int32_t max_levels = 16;
   double min_ratio = 0.8;      // stop when aggregation keeps more than this share of rows
+  // Aggregation follows only strong connections |k_ij| >= strength sqrt(|k_ii k_jj|) (0: every
+  // neighbour).  With strength > 0 the coarse levels also get damped-Jacobi weights scaled to
+  // their operators (Galerkin masses are far from diagonal): min(2/3, (4/3) / max(lambda_max(
+  // D_M^-1 M_l), lambda_max(D_K^-1 K_l))); the finest level keeps 2/3.
+  double strength = 0.0;
 };
 
 // One level.  S holds the pair (K_l, M_l) on one pattern: nval = 2 per entry
@@ -23,6 +28,7 @@ struct MgHostLevel {
   HostCSR S, P, R;
   std::vector<double> dk, dm;  // diagonals of K_l and M_l (real parts)
   double omega_p = 0.0;        // weight of the prolongator smoothing
+  double omega_s = 2.0 / 3.0;  // damped-Jacobi weight of the smoother on this level
 };
 
 struct MgHost {

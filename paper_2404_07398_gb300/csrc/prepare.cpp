@@ -320,6 +320,7 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
     fail(IFILT_EINVAL, "periodic geometry needs positive periods");
   if (d.geometry == IFILT_GEOM_SPHERE && !(d.radius > 0)) fail(IFILT_EINVAL, "sphere needs radius > 0");
   if (d.reorder < IFILT_REORDER_NONE || d.reorder > IFILT_REORDER_HILBERT) fail(IFILT_EINVAL, "unknown reorder %d", d.reorder);
+  if (!(d.mg_strength >= 0.0 && d.mg_strength < 1.0)) fail(IFILT_EINVAL, "mg_strength must be in [0, 1)");
 
   const int32_t V = d.n_vert, T = d.n_tri;
   const int32_t* tri = d.tri;
@@ -339,6 +340,7 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   hp.geometry = d.geometry;
   hp.max_order = d.max_order;
   hp.reorder = d.reorder;
+  hp.mg_strength = d.mg_strength;
 
   // ---- 1. ocean subset
   std::vector<int32_t> kept;  // original ids of kept triangles, ascending

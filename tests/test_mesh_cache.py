@@ -13,7 +13,7 @@ import synth
 
 PLACEMENTS = ["vertex_scalar", "vertex_vector", "cell", "vertex_voronoi", "cell_circumcenter"]
 EXPORTS = ["perm", "k_rowptr", "k_col", "k_val", "mass", "g2_rowptr", "g2_col", "g2_val"]
-MG_EXPORTS = ["s_rowptr", "s_col", "s_val", "p_rowptr", "p_col", "p_val", "dk", "dm"]
+MG_EXPORTS = ["s_rowptr", "s_col", "s_val", "p_rowptr", "p_col", "p_val", "dk", "dm", "omega"]
 HEADER = 8 + 4 + 4 + 8 + 8 + 8    # magic, format, revision, key, payload bytes, payload hash
 
 
@@ -194,7 +194,7 @@ def _offsets(b):
     """Byte offsets of the first arrays of a payload (see the file layout)."""
     o = HEADER
     ints = struct.unpack_from("<9i", b, o)
-    o += 36
+    o += 36 + 8                                             # header ints, multigrid strength
     n = ints[4]
     off = {}
     cnt = struct.unpack_from("<Q", b, o)[0]

@@ -53,9 +53,10 @@ def _level0(h):
     return rp, cl, K, h.export("mass"), n
 
 
+@pytest.mark.parametrize("strength", [0.0, 0.05])
 @pytest.mark.parametrize("placement", ["vertex_scalar", "cell", "vertex_vector"])
-def test_galerkin_products_and_constants(api, placement):
-    h = api.prepare_mesh_host(_mesh(4, 31), placement, max_order=1)
+def test_galerkin_products_and_constants(api, placement, strength):
+    h = api.prepare_mesh_host(_mesh(4, 31), placement, max_order=1, mg_strength=strength)
     g = h.multigrid()
     L = g["levels"]
     assert L >= 3
@@ -143,3 +144,47 @@ def test_host_threads_do_not_change_results(api, monkeypatch, placement):
         seen.append(b"".join(a.tobytes() for a in arrays))
         h.release()
     assert seen[0] == seen[1] == seen[2]
+
+
+@pytest.mark.parametrize("placement", ["cell", "vertex_vector"])
+def test_strength_filtered_aggregation(api, placement):
+    """mg_strength > 0: aggregates follow strong connections only, so the coarse
+    levels shrink more slowly (more, smaller aggregates),
+    and every coarse level gets a smoother weight in (0, 2/3] from the largest
+    eigenvalues of D^-1 M_l and D^-1 K_l, recomputed here with scipy; the finest
+    level keeps 2/3.  With strength 0 every weight is 2/3 (the default hierarchy)."""
+    import scipy.sparse.linalg as spla
+    m = _mesh(5, 39)
+    h0 = api.prepare_mesh_host(m, placement, max_order=1)
+    h1 = api.prepare_mesh_host(m, placement, max_order=1, mg_strength=0.05)
+    g0, g1 = h0.multigrid(), h1.multigrid()
+    assert g1["rows"][0] == g0["rows"][0] and g1["levels"] >= g0["levels"]
+    assert sum(g1["rows"][2:]) > sum(g0["rows"][2:])          # slower coarsening below level 1
+    for level in range(g0["levels"]):
+        assert h0.multigrid_export(level, "omega")[1] == 2.0 / 3.0
+    assert h1.multigrid_export(0, "omega")[1] == 2.0 / 3.0
+    blk = placement == "vertex_vector"
+    for level in range(1, g1["levels"]):
+        nc = g1["rows"][level]
+        rp, cl, sv = (h1.multigrid_export(level, w) for w in ("s_rowptr", "s_col", "s_val"))
+        if blk:
+            K = _blocks(rp, cl, np.stack([sv[0::4], sv[1::4]], 1).ravel(), (nc, nc))
+            M = _blocks(rp, cl, np.stack([sv[2::4], sv[3::4]], 1).ravel(), (nc, nc))
+        else:
+            K = _csr(rp, cl, sv[0::2], (nc, nc))
+            M = _csr(rp, cl, sv[1::2], (nc, nc))
+
+        def lam(A):
+            d = 1.0 / np.sqrt(A.diagonal())
+            B = (sp.diags(d) @ A @ sp.diags(d)).toarray() if A.shape[0] <= 600 else None
+            if B is not None:
+                return np.linalg.eigvalsh(B).max()
+            B = (sp.diags(d) @ A @ sp.diags(d)).tocsr()
+            return spla.eigsh(B, k=1, which="LA", return_eigenvectors=False, tol=1e-6)[0]
+
+        expect = min(2.0 / 3.0, (4.0 / 3.0) / max(lam(K), lam(M)))
+        got = h1.multigrid_export(level, "omega")[1]
+        # the library's 40-step power iteration approaches lambda_max from below
+        assert 0.0 < got <= 2.0 / 3.0 and abs(got - expect) <= 0.03 * expect, (level, got, expect)
+    h0.release()
+    h1.release()
