@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--err-tol", type=float, default=1e-7,
                     help="also stop each column only at a certified relative M-norm error bound (0: off)")
     ap.add_argument("--reorder", choices=["rcm", "hilbert"], default="rcm", help="device row order of the meshes")
+    ap.add_argument("--max-iter", type=int, default=2000,
+                    help="Krylov iteration cap per column (the hardest columns need well under 100)")
     ap.add_argument("--mg-strength", type=float, default=0.05,
                     help="multigrid aggregation threshold (0: every neighbour, the library default)")
     ap.add_argument("--cache-dir", default="", help="keep the synthetic workload and the prepared meshes "
@@ -245,7 +247,8 @@ class Ours:
         self.opts = dict(order=2, tol=args.tol, precision=prec, n2_solver=api.N2_COMPLEX,
                          precond={"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI,
                                   "mg": api.PRECOND_MG}[args.precond],
-                         check_every=args.check_every, inner_tol=args.inner_tol, err_tol=args.err_tol)
+                         check_every=args.check_every, inner_tol=args.inner_tol, err_tol=args.err_tol,
+                         max_iter=args.max_iter)
         K = self.k.size
         self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
         self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
