@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--err-tol", type=float, default=1e-7,
                     help="also stop each column only at a certified relative M-norm error bound (0: off)")
     ap.add_argument("--reorder", choices=["rcm", "hilbert"], default="rcm", help="device row order of the meshes")
+    ap.add_argument("--mg-cycle", choices=["v", "w12"], default="v",
+                    help="multigrid cycle (w12: coarse corrections of levels 1 and 2 twice)")
     ap.add_argument("--max-iter", type=int, default=2000,
                     help="Krylov iteration cap per column (the hardest columns need well under 100)")
     ap.add_argument("--mg-strength", type=float, default=0.05,
@@ -215,6 +217,7 @@ def workload_config(args, w, world):
             "columns_per_step": 4 * N_K, "order": 2, "n2_solver": "complex", "tol": args.tol,
             "precision": args.precision, "precond": getattr(args, "precond", "none"),
             "mg_strength": getattr(args, "mg_strength", 0.0) if getattr(args, "precond", "none") == "mg" else None,
+            "mg_cycle": getattr(args, "mg_cycle", "v") if getattr(args, "precond", "none") == "mg" else None,
             "err_tol": getattr(args, "err_tol", 0.0), "reorder": getattr(args, "reorder", "rcm"),
             "l2": "inputs larger than L2 (GBs per vector), no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
@@ -248,7 +251,7 @@ class Ours:
                          precond={"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI,
                                   "mg": api.PRECOND_MG}[args.precond],
                          check_every=args.check_every, inner_tol=args.inner_tol, err_tol=args.err_tol,
-                         max_iter=args.max_iter)
+                         max_iter=args.max_iter, mg_cycle={"v": api.MG_V, "w12": api.MG_W12}[args.mg_cycle])
         K = self.k.size
         self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
         self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")
@@ -408,15 +411,16 @@ def run_ours(args, world, rank, local):
             if bad:
                 raise RuntimeError(f"{bad} columns not converged")
     except (RuntimeError, api.IfiltError) as e:
-        if o.mg_strength == 0.0:
+        if o.mg_strength == 0.0 and args.mg_cycle == "v":
             raise
         # the strength-filtered hierarchy misbehaved during warm-up: rebuild with the default
         # hierarchy (untimed) and say so in the line
-        fallback = f"mg_strength {o.mg_strength} -> 0 after warm-up: {str(e)[:120]}"
+        fallback = f"mg_strength {o.mg_strength}, cycle {args.mg_cycle} -> 0, v after warm-up: {str(e)[:120]}"
         sys.stderr.write("bench: " + fallback + "\n")
         o.mv.release()
         o.mc.release()
         args.mg_strength = 0.0
+        args.mg_cycle = "v"
         o = Ours(args, w)
         for _ in range(args.warmup):
             o.step()

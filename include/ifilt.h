@@ -180,7 +180,12 @@ typedef struct {
                                 (x the filtered part: the real part in the complex n = 2 form), a
                                 bound on its relative error in the M-norm, because S >= M (and
                                 |e^H A e| >= e^H M e for A = M + i s K); 0 = the residual test only */
+  int32_t mg_cycle;          /* multigrid cycle: IFILT_MG_V (0) or IFILT_MG_W12 (1), which applies the
+                                coarse correction of levels 1 and 2 twice (more coarse work, fewer
+                                Krylov iterations on large meshes) */
 } ifilt_solve_opts;
+
+enum { IFILT_MG_V = 0, IFILT_MG_W12 = 1 };
 
 typedef struct {
   int32_t iters;             /* Krylov iterations (all rounds) */

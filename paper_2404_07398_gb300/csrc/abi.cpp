@@ -424,6 +424,7 @@ static void check_opts(ifilt_mesh m, const ifilt_solve_opts* o) {
   if (o->max_iter < 0 || o->check_every < 0 || o->max_lanes < 0 || o->inner_tol < 0)
     fail(IFILT_EINVAL, "negative option");
   if (!(o->err_tol >= 0.0) || !std::isfinite(o->err_tol)) fail(IFILT_EINVAL, "err_tol must be >= 0 and finite");
+  if (o->mg_cycle != IFILT_MG_V && o->mg_cycle != IFILT_MG_W12) fail(IFILT_EINVAL, "unknown mg_cycle %d", o->mg_cycle);
   if (o->method == IFILT_METHOD_PLAIN && o->err_tol > 0.0)
     fail(IFILT_EINVAL, "the plain method stops on the residual only (err_tol = 0)");
 }

@@ -2653,33 +2653,49 @@ class EngineT final : public Engine {
       }
       return x;
     }
-    const DevMgLevel& L = (*mgl_)[l];
     if (l == 0) mark(8);
     mg_smooth(l, B.a, B.b, rhs, nullptr);
     if (l == 0) mark(9);
-    mg_resid(l, B.b, B.a, rhs);
-    (void)L;
-    mg_transfer(l, true, B.a, mgb_[l + 1].r, nullptr);
-    const T* xc = vcycle(l + 1, mgb_[l + 1].r);
-    mg_transfer(l, false, xc, B.a, B.b);
-    mg_smooth(l, B.a, B.b, rhs, nullptr);
-    const int nb = mg_smooth(l, B.b, B.a, rhs, l == 0 ? partial2_ : nullptr);
+    // coarse correction(s): x <- x + P V_{l+1}(R (rhs - S x)), twice on levels 1 and 2 of a W12 cycle
+    T* x = B.b;
+    T* t = B.a;
+    for (int rep = 0; rep < mg_reps(l); rep++) {
+      mg_resid(l, x, t, rhs);
+      mg_transfer(l, true, t, mgb_[l + 1].r, nullptr);
+      const T* xc = vcycle(l + 1, mgb_[l + 1].r);
+      mg_transfer(l, false, xc, t, x);
+      std::swap(x, t);
+    }
+    mg_smooth(l, x, t, rhs, nullptr);
+    const int nb = mg_smooth(l, t, x, rhs, l == 0 ? partial2_ : nullptr);
     if (l == 0) nbz_ = nb;
-    return B.a;
+    return x;
+  }
+  int mg_reps(size_t l) const { return (o_.mg_cycle == IFILT_MG_W12 && (l == 1 || l == 2)) ? 2 : 1; }
+  // visits of each level in one cycle
+  std::vector<int> mg_visits() const {
+    std::vector<int> v(mgl_->size(), 0);
+    v[0] = 1;
+    for (size_t l = 0; l + 1 < v.size(); l++) v[l + 1] = v[l] * mg_reps(l);
+    return v;
   }
   void mark(int i) {
     if (prof_ && mg_sample_) IFILT_CUDA(cudaEventRecordWithFlags(ev_[i], st_, evf_));
   }
   int mg_launches() const {
     if (!mg_on_) return 0;
-    const int L = (int)mgl_->size();
-    return 7 * (L - 1) + kMgCoarseSweeps;
+    const std::vector<int> v = mg_visits();
+    int n = 0;
+    for (size_t l = 0; l < v.size(); l++)
+      n += v[l] * (l + 1 == v.size() ? kMgCoarseSweeps : 4 + 3 * mg_reps(l));
+    return n;
   }
   // algorithmic bytes of one V-cycle (vectors and operators, all levels)
   double mg_bytes_per_cycle() const {
     if (!mg_on_) return 0.0;
     double b = 0.0;
     const int W = P_.W;
+    const std::vector<int> visits = mg_visits();
     for (size_t l = 0; l < mgl_->size(); l++) {
       const DevMgLevel& L = (*mgl_)[l];
       const double rows = l == 0 ? (double)n_ : (double)L.n;
@@ -2687,11 +2703,13 @@ class EngineT final : public Engine {
       const DevEll& S = l == 0 ? m_->ell_k : L.S;
       const double sb = (double)S.entries * (4.0 + (l == 0 ? 1 : 2) * NVAL * sizeof(T));
       if (l + 1 == mgl_->size()) {
-        b += 2 * vb + (kMgCoarseSweeps - 1) * (3 * vb + sb);
+        b += visits[l] * (2 * vb + (kMgCoarseSweeps - 1) * (3 * vb + sb));
       } else {
+        // jacobi, one sweep, per coarse correction (residual, restriction, prolongation), two sweeps
         const double vc = (double)(*mgl_)[l + 1].n * NS * W * sizeof(T);
-        b += 2 * vb + 4 * (3 * vb + sb) + (vb + vc) + (2 * vb + vc) +
-             (double)(L.P.entries + L.R.entries) * (4.0 + NVAL * sizeof(T));
+        const double corr = (3 * vb + sb) + (vb + vc) + (2 * vb + vc) +
+                            (double)(L.P.entries + L.R.entries) * (4.0 + NVAL * sizeof(T));
+        b += visits[l] * (2 * vb + 3 * (3 * vb + sb) + mg_reps(l) * corr);
       }
     }
     return b;

@@ -3,6 +3,7 @@
  * link and answer from C.  Builds a doubly periodic n x n split-square mesh
  * (unit spacing, every square cut along the same diagonal), prepares it for
  * the scalar vertex placement, and prints what the test checks. */
+#include <stddef.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -92,6 +93,12 @@ int main(int argc, char** argv) {
   if (ifilt_mesh_multigrid(back, &mg) != IFILT_OK) return 10;
   printf("key_match %d wrong_key_status %d mg_levels %d\n", key == key2, (int)wrong, mg.n_levels);
   printf("version %s\n", ifilt_version());
+  printf("layout desc %zu %zu opts %zu %zu %zu info %zu stats %zu\n", sizeof(ifilt_mesh_desc),
+         offsetof(ifilt_mesh_desc, mg_strength), sizeof(ifilt_solve_opts), offsetof(ifilt_solve_opts, err_tol),
+         offsetof(ifilt_solve_opts, mg_cycle), sizeof(ifilt_mesh_info_t), sizeof(ifilt_col_stats));
+  printf("layout2 item %zu mg %zu server %zu request %zu profile %zu\n", sizeof(ifilt_solve_item),
+         sizeof(ifilt_multigrid_info), sizeof(ifilt_server_opts), sizeof(ifilt_request_info),
+         sizeof(ifilt_kernel_profile));
   ifilt_release_mesh(back);
   ifilt_release_mesh(mesh);
   ifilt_release_mesh(NULL);

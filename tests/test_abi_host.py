@@ -168,6 +168,15 @@ def test_plain_c_client(api, tmp_path):
     assert out["error"] == "message: yes"
     kv = out["key_match"].split()
     assert kv[0] == "1" and int(kv[2]) == api.ECACHE and int(kv[4]) >= 1
+    # the binding's ctypes structures have the C layout
+    import ctypes
+    lay = [int(x) for x in out["layout"].split()[1::1] if x.isdigit()]
+    assert lay == [ctypes.sizeof(api.MeshDesc), api.MeshDesc.mg_strength.offset, ctypes.sizeof(api.SolveOpts),
+                   api.SolveOpts.err_tol.offset, api.SolveOpts.mg_cycle.offset, ctypes.sizeof(api.MeshInfo),
+                   ctypes.sizeof(api.ColStats)], (out["layout"], lay)
+    lay2 = [int(x) for x in out["layout2"].split() if x.isdigit()]
+    assert lay2 == [ctypes.sizeof(c) for c in (api.SolveItem, api.MultigridInfo, api.ServerOpts, api.RequestInfo,
+                                               api.KernelProfile)], out["layout2"]
 
 
 def test_concurrent_preparation_is_deterministic(api):

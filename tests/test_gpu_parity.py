@@ -544,3 +544,28 @@ def test_multigrid_strength_needs_no_more_iterations(lib, placement):
         assert st == 0 and (stats["status"] == 0).all()
         its[strength] = stats["iters"].reshape(-1)
     assert its[0.05].max() <= its[0.0].max(), its
+
+
+@pytest.mark.parametrize("placement", ["vertex_vector", "cell"])
+def test_multigrid_w12_cycle(lib, placement):
+    """The W12 cycle (coarse corrections of levels 1 and 2 applied twice) keeps
+    the V-cycle's fields and needs no more iterations than it."""
+    import torch
+    m = _sphere(6, 71, polar=5.0)
+    P = oracle.build_problem(m, placement)
+    rng = np.random.default_rng(12)
+    f = rng.normal(size=(1, P.n_comp, P.n_in))
+    ks = synth.log_wavenumbers(4000.0, 300.0, 3)
+    h = lib.prepare_mesh(m, placement, max_order=2, mg_strength=0.05)
+    assert h.multigrid()["levels"] >= 4
+    res = {}
+    for cycle in (lib.MG_V, lib.MG_W12):
+        out, stats, st = lib.solve(h, torch.tensor(f, device="cuda"), ks, order=2, tol=1e-10,
+                                   precision=lib.PREC_FP32_IR, n2_solver=2, precond=lib.PRECOND_MG, mg_cycle=cycle)
+        assert st == 0, stats
+        res[cycle] = (out.cpu().numpy(), stats["iters"].reshape(-1))
+    h.release()
+    for c in range(res[lib.MG_V][0].shape[2]):
+        a, b = res[lib.MG_V][0][0, :, c], res[lib.MG_W12][0][0, :, c]
+        assert np.linalg.norm(a - b) <= 2e-6 * np.linalg.norm(b)
+    assert res[lib.MG_W12][1].max() <= res[lib.MG_V][1].max()
