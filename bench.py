@@ -62,7 +62,9 @@ def parse_args():
     ap.add_argument("--precision-study", action="store_true",
                     help="errors of FP32 / BF16 / FP64 per field and per spectrum bin (level-9 workload)")
     ap.add_argument("--precond", choices=["none", "jacobi", "mg"], default="mg", help="Krylov preconditioner")
-    ap.add_argument("--check-every", type=int, default=0, help="iterations per solver step (0: library default)")
+    ap.add_argument("--check-every", type=int, default=4,
+                    help="iterations per solver step (0: library default, 8 with multigrid); refinement rounds end "
+                         "on step boundaries, so short rounds favour short steps")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="FP32 inner reduction per round (0: default)")
     ap.add_argument("--err-tol", type=float, default=1e-7,
                     help="also stop each column only at a certified relative M-norm error bound (0: off)")
