@@ -220,6 +220,7 @@ def workload_config(args, w, world):
             "precision": args.precision, "precond": getattr(args, "precond", "none"),
             "mg_strength": getattr(args, "mg_strength", 0.0) if getattr(args, "precond", "none") == "mg" else None,
             "mg_cycle": getattr(args, "mg_cycle", "v") if getattr(args, "precond", "none") == "mg" else None,
+            "check_every": getattr(args, "check_every", 0), "max_iter": getattr(args, "max_iter", 0),
             "err_tol": getattr(args, "err_tol", 0.0), "reorder": getattr(args, "reorder", "rcm"),
             "l2": "inputs larger than L2 (GBs per vector), no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
