@@ -34,6 +34,8 @@
  *                       mesh (results then depend on nothing but the inputs)
  *   IFILT_NO_GRAPH=1    launch every kernel directly instead of through CUDA graphs
  *   IFILT_TRACE=1       print each batched-solver launch to stderr (read once)
+ *   IFILT_MG_COARSE_SWEEPS=k  damped-Jacobi sweeps before and after the coarse
+ *                       correction on multigrid levels >= 1 (1..6; default 2)
  */
 #ifndef IFILT_H
 #define IFILT_H

@@ -1761,6 +1761,8 @@ class EngineT final : public Engine {
     m_it_ = o.check_every > 0 ? o.check_every : (o.precond == IFILT_PRECOND_MG ? 8 : 32);
     const char* ng = getenv("IFILT_NO_GRAPH");
     use_graph_ = !(ng && ng[0] == '1');
+    // experiment knob: damped-Jacobi sweeps before and after the coarse correction on levels >= 1
+    if (const char* cs = getenv("IFILT_MG_COARSE_SWEEPS")) mg_nu_c_ = std::max(1, std::min(6, atoi(cs)));
     // double-float refinement residual on the FP32 engines, unless a tolerance asks for more than its
     // about 48 bits carry on hard columns; then FP64, as on the FP64 engine
     df_ = sizeof(T) == 4 && o.tol >= kDfMinTol && (!(o.err_tol > 0.0) || o.err_tol >= kDfMinErrTol);
@@ -2375,6 +2377,7 @@ class EngineT final : public Engine {
   cudaGraphExec_t exec_ = nullptr;
   int m_it_ = 32;
   bool use_graph_ = true, launched_ = false, prof_ = false;
+  int mg_nu_c_ = 2;  // smoothing sweeps before and after the coarse correction on levels >= 1
   // ------------------------------------------------------------ autotuning
   // Launch shape of the gather kernels (rows per tile, blocks per SM), chosen
   // per engine kind and tile-width bucket by timing the candidates on the live
@@ -2659,6 +2662,10 @@ class EngineT final : public Engine {
     // coarse correction(s): x <- x + P V_{l+1}(R (rhs - S x)), twice on levels 1 and 2 of a W12 cycle
     T* x = B.b;
     T* t = B.a;
+    for (int s = 2; s < mg_nu(l); s++) {  // further pre-smoothing sweeps (coarse levels, on request)
+      mg_smooth(l, x, t, rhs, nullptr);
+      std::swap(x, t);
+    }
     for (int rep = 0; rep < mg_reps(l); rep++) {
       mg_resid(l, x, t, rhs);
       mg_transfer(l, true, t, mgb_[l + 1].r, nullptr);
@@ -2666,11 +2673,16 @@ class EngineT final : public Engine {
       mg_transfer(l, false, xc, t, x);
       std::swap(x, t);
     }
+    for (int s = 2; s < mg_nu(l); s++) {
+      mg_smooth(l, x, t, rhs, nullptr);
+      std::swap(x, t);
+    }
     mg_smooth(l, x, t, rhs, nullptr);
     const int nb = mg_smooth(l, t, x, rhs, l == 0 ? partial2_ : nullptr);
     if (l == 0) nbz_ = nb;
     return x;
   }
+  int mg_nu(size_t l) const { return l == 0 ? 2 : mg_nu_c_; }
   int mg_reps(size_t l) const { return (o_.mg_cycle == IFILT_MG_W12 && (l == 1 || l == 2)) ? 2 : 1; }
   // visits of each level in one cycle
   std::vector<int> mg_visits() const {
@@ -2687,7 +2699,7 @@ class EngineT final : public Engine {
     const std::vector<int> v = mg_visits();
     int n = 0;
     for (size_t l = 0; l < v.size(); l++)
-      n += v[l] * (l + 1 == v.size() ? kMgCoarseSweeps : 4 + 3 * mg_reps(l));
+      n += v[l] * (l + 1 == v.size() ? kMgCoarseSweeps : 2 * mg_nu(l) + 3 * mg_reps(l));
     return n;
   }
   // algorithmic bytes of one V-cycle (vectors and operators, all levels)
@@ -2709,7 +2721,7 @@ class EngineT final : public Engine {
         const double vc = (double)(*mgl_)[l + 1].n * NS * W * sizeof(T);
         const double corr = (3 * vb + sb) + (vb + vc) + (2 * vb + vc) +
                             (double)(L.P.entries + L.R.entries) * (4.0 + NVAL * sizeof(T));
-        b += visits[l] * (2 * vb + 3 * (3 * vb + sb) + mg_reps(l) * corr);
+        b += visits[l] * (2 * vb + (2 * mg_nu(l) - 1) * (3 * vb + sb) + mg_reps(l) * corr);
       }
     }
     return b;
