@@ -548,8 +548,9 @@ def test_multigrid_strength_needs_no_more_iterations(lib, placement):
 
 @pytest.mark.parametrize("placement", ["vertex_vector", "cell"])
 def test_multigrid_w12_cycle(lib, monkeypatch, placement):
-    """The W12 cycle (coarse corrections of levels 1 and 2 applied twice) keeps
-    the V-cycle's fields and needs no more iterations than it (up to one)."""
+    """The W12 cycle (coarse corrections of levels 1 and 2 applied twice) and
+    three smoothing sweeps on the coarse levels each keep the V-cycle's fields
+    and need no more iterations than it (up to one)."""
     import torch
     m = _sphere(6, 71, polar=5.0)
     P = oracle.build_problem(m, placement)
