@@ -397,7 +397,9 @@ ifilt_status ifilt_spectrum(ifilt_mesh mesh, int32_t n_fields, int32_t n_k,
  * results and synchronisation.
  *   - n_fields * n_k must not exceed 512 (EINVAL otherwise).
  *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture on that device.
+ *     that first call before any stream capture on that device.  Later calls
+ *     outside a capture look it up again, so a device reset (which reloads
+ *     the library's device code) does not leave a stale address behind.
  *   - All calls share the one array: calls that overlap on the GPU (other
  *     streams, other host threads) race and must be serialised by the caller.
  *     Every scratch value a call reads is written earlier in the same call,

@@ -427,11 +427,25 @@ def solve_many(jobs, stream=None):
     return results, st
 
 
+def _check_filtered(mesh, filtered, K):
+    """The spectrum kernels read filtered[F][K][n_comp][n_out] as one block of
+    float64 on the device: refuse any other shape, type or layout up front."""
+    import torch
+    info = mesh.info
+    if not (isinstance(filtered, torch.Tensor) and filtered.is_cuda and filtered.dtype == torch.float64
+            and filtered.is_contiguous() and filtered.dim() == 4):
+        raise ValueError("filtered must be a contiguous CUDA float64 tensor [F][K][n_comp][n_out]")
+    want = (K, info["n_comp"], info["n_out"])
+    if tuple(filtered.shape[1:]) != want:
+        raise ValueError(f"filtered has shape {tuple(filtered.shape)}, expected [F]{list(want)}")
+
+
 def spectrum(mesh, filtered, k, stream=None):
     """filtered: CUDA float64 [F][K][n_comp][n_out] (as `solve` returns); k ascending.
     Returns (energy [F][K], spec [F][K-1], kmid [K-1]) as numpy arrays."""
     lib = load()
     kk = np.ascontiguousarray(k, dtype=np.float64).ravel()
+    _check_filtered(mesh, filtered, kk.size)
     F, K = filtered.shape[0], kk.size
     energy = np.zeros((F, K))
     spec = np.zeros((F, max(K - 1, 1)))
@@ -446,6 +460,7 @@ def spectrum_noalloc(mesh, filtered, k, stream=None):
     any allocator (its scratch is a fixed array inside the library)."""
     lib = load()
     kk = np.ascontiguousarray(k, dtype=np.float64).ravel()
+    _check_filtered(mesh, filtered, kk.size)
     F, K = filtered.shape[0], kk.size
     energy = np.zeros((F, K))
     spec = np.zeros((F, max(K - 1, 1)))

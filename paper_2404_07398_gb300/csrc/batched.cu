@@ -213,6 +213,8 @@ struct Params {
   int spt;          // ELL slices per SpMM tile
   int wmax;         // widest ELL slice
   int stage_e;      // ELL entries one SpMM stage buffer holds
+  int rn_slot;      // real columns: ||r||^2 has slots of its own in the update partials (Jacobi)
+  int pf;           // gather kernels: prefetch a tile's gathered and row operands into L2 at its start
 };
 
 // ------------------------------------------------------------------ kernels
@@ -397,6 +399,11 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Fire-and-forget prefetch of a 16-byte aligned block (a multiple of 16 bytes)
+// into L2 by the bulk-copy engine: no registers or shared memory are held.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 // Wait for phase `parity` of `bar` for at most ~1 s of SM clock; false on expiry.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   const long long t0 = clock64();
@@ -507,6 +514,20 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
     const MV* sval = stage_val(b);
     const int64_t r0 = (int64_t)tile * spt * H;
     const int rows = (int)min((int64_t)TR, (int64_t)P.n - r0);
+    if (P.pf) {
+      // every row the tile gathers (padding entries name their own row) and its row operands are
+      // requested from DRAM at once, so the rows a thread works through one after another find
+      // them in L2 instead of each waiting out a DRAM miss
+      const int s0 = tile * spt;
+      const int ne = (int)(A.slice_off[min(s0 + spt, n_slices)] - A.slice_off[s0]);
+      const uint32_t rb = (uint32_t)(rowW * sizeof(T));
+      for (int e = threadIdx.x; e < ne; e += kBlock) prefetch_l2(p + (int64_t)scol[e] * rowW, rb);
+      if (threadIdx.x == 0) {
+        const uint32_t tb = (uint32_t)rows * rb;
+        if constexpr (EPI == kEpiSmooth || EPI == kEpiResid) prefetch_l2(mg.rhs + r0 * rowW, tb);
+        if constexpr (EPI == kEpiProlong) prefetch_l2(mg.own + r0 * rowW, tb);
+      }
+    }
     if (on) {
       for (int lr = tr; lr < rows; lr += RPP) {
         const int64_t r = r0 + lr;
@@ -625,8 +646,10 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
   }
 }
 
-// x += alpha p ; r -= alpha q ; partial <r, r> (slots [0, W): lane-wise for real,
-// (re, im) pairs for complex) and ||r||^2 (complex only, slots W + column).
+// x += alpha p ; r -= alpha q ; partial <r, z> (slots [0, W): lane-wise for real,
+// (re, im) pairs for complex; z = r, or D^-1 r under Jacobi preconditioning)
+// and ||r||^2 (slots W + column) where <r, z> is not it: complex columns, and
+// real columns under Jacobi preconditioning.
 template <typename T, bool CPLX, bool BLK, bool PRE>
 __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T* __restrict__ x, const T* __restrict__ p,
                                                         T* __restrict__ r, const T* __restrict__ q, Cols C,
@@ -637,12 +660,13 @@ __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T
   constexpr int NS = BLK ? 2 : 1;
   extern __shared__ double sm[];
   const int W = P.W;
-  const int NSL = CPLX ? W + W / 2 : W;  // slots
+  const int NSL = CPLX ? W + W / 2 : (PRE ? 2 * W : W);  // slots
   const int TPR = W / VEC;
   const int RPP = kBlock / TPR;
   const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
   const int l0 = g * VEC;
-  DotAcc<T> d1[VEC], d2[VEC / 2 > 0 ? VEC / 2 : 1];
+  constexpr int ND2 = CPLX ? (VEC / 2 > 0 ? VEC / 2 : 1) : (PRE ? VEC : 1);
+  DotAcc<T> d1[VEC], d2[ND2];
   if (tr < RPP) {
     T a[VEC], sh[VEC];
 #pragma unroll
@@ -659,7 +683,7 @@ __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T
 #pragma unroll
         for (int v = 0; v < VEC; v++) d1[v].flush();
 #pragma unroll
-        for (int v = 0; v < (VEC / 2 > 0 ? VEC / 2 : 1); v++) d2[v].flush();
+        for (int v = 0; v < ND2; v++) d2[v].flush();
       }
       const T mr = PRE ? mass[row] : (T)0, gr = PRE ? gdiag[row] : (T)0;
 #pragma unroll
@@ -700,7 +724,10 @@ __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T
           }
         } else {
 #pragma unroll
-          for (int v = 0; v < VEC; v++) d1[v].add(rv.v[v], zv[v]);
+          for (int v = 0; v < VEC; v++) {
+            d1[v].add(rv.v[v], zv[v]);
+            if constexpr (PRE) d2[v].add(rv.v[v], rv.v[v]);
+          }
         }
         stp(x + off, xv);
         stp(r + off, rv);
@@ -711,6 +738,9 @@ __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T
     if constexpr (CPLX) {
 #pragma unroll
       for (int v = 0; v < VEC / 2; v++) sm[tr * NSL + W + l0 / 2 + v] = d2[v].get();
+    } else if constexpr (PRE) {
+#pragma unroll
+      for (int v = 0; v < VEC; v++) sm[tr * NSL + W + l0 + v] = d2[v].get();
     }
   }
   __syncthreads();
@@ -828,7 +858,8 @@ __global__ void finish_beta_kernel(Params P, int nb, const double* __restrict__ 
   const bool ok = col < P.ncols;
   const double rre = reduce_slot(partial, nb, P.pstride, ok ? (CPLX ? 2 * col : col) : -1, buf);
   const double rim = CPLX ? reduce_slot(partial, nb, P.pstride, ok ? 2 * col + 1 : -1, buf) : 0.0;
-  const double n2 = CPLX ? reduce_slot(partial, nb, P.pstride, ok ? P.W + col : -1, buf) : rre;
+  // ||r||^2: its own slot for complex columns and under Jacobi preconditioning, <r, r> otherwise
+  const double n2 = (CPLX || P.rn_slot) ? reduce_slot(partial, nb, P.pstride, ok ? P.W + col : -1, buf) : rre;
   if (threadIdx.y != 0 || !ok) return;
   double br = 0.0, bi = 0.0;
   if (C.active[col]) {
@@ -863,21 +894,70 @@ __global__ void finish_beta_kernel(Params P, int nb, const double* __restrict__ 
   C.beta[2 * col + 1] = bi;
 }
 
-// x64 = x0 on the lanes of newly admitted columns (real lanes; imaginary lanes 0)
-template <bool CPLX, bool BLK>
-__global__ void init_lanes_kernel(Params P, const double* const* __restrict__ xptr, const int* __restrict__ lane_src,
-                                  const int* __restrict__ fresh, double* __restrict__ x64) {
+// Residual form of the solve (Sect. 2.2.2): the unfiltered field x0 is kept
+// apart and the engines solve S delta = r0 = b - S x0, the filtered field being
+// x0 + delta.  The true residual of a refinement round is then r0 - S delta,
+// whose rounding error is relative to ||S delta|| ~ ||r0|| rather than to
+// ||b|| (at small scales ||r0|| is orders of magnitude below ||b||, and b - S x
+// could not be driven to the paper's relative tolerance in FP64).  Each source
+// (field, system) keeps, in one buffer of 3 [n][NS] FP64 blocks and one FP32
+// block:
+//   e0 = b - M x0   (exact up to one rounding; 0 up to rounding for b = M x0)
+//   x0
+//   g0 = G x0       (the operator without its shift, shared by all scales)
+//   x0 rounded to float (the double-float engines' norm of the solution)
+// so that r0 = e0 - shift g0 (real columns) or e0 - i shift g0 (complex ones).
+template <bool BLK>
+__global__ void __launch_bounds__(256) source_kernel(EllView<double> A, int32_t n, const double* __restrict__ mass,
+                                                     double* __restrict__ buf) {
   constexpr int NS = BLK ? 2 : 1;
-  const int64_t total = (int64_t)P.n * NS * P.W;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(i % P.W);
-    if (!fresh[CPLX ? l >> 1 : l]) continue;
-    const int64_t rs = i / P.W;  // row * NS + sub
-    x64[i] = (CPLX && (l & 1)) ? 0.0 : xptr[lane_src[l]][rs];
+  const int64_t bs = (int64_t)n * NS;
+  double* e0 = buf;
+  const double* x0 = buf + bs;
+  double* g0 = buf + 2 * bs;
+  float* x0f = reinterpret_cast<float*>(buf + 3 * bs);
+  for (int32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+    const int s = row / A.slice_h;
+    const int w = A.slice_w[s];
+    const int64_t base = A.slice_off[s] + (int64_t)(row - s * A.slice_h) * w;
+    double acc[NS];
+#pragma unroll
+    for (int b = 0; b < NS; b++) acc[b] = 0.0;
+    for (int e = 0; e < w; e++) {
+      const int64_t c = A.col[base + e];
+      if constexpr (BLK) {
+        const double a = A.val[(base + e) * 2], bb = A.val[(base + e) * 2 + 1];
+        const double xu = x0[c * 2], xw = x0[c * 2 + 1];
+        acc[0] = __fma_rn(a, xu, __fma_rn(bb, xw, acc[0]));
+        acc[1] = __fma_rn(a, xw, __fma_rn(-bb, xu, acc[1]));
+      } else {
+        acc[0] = __fma_rn(A.val[base + e], x0[c], acc[0]);
+      }
+    }
+    const double mr = mass[row];
+#pragma unroll
+    for (int b = 0; b < NS; b++) {
+      const int64_t i = (int64_t)row * NS + b;
+      g0[i] = acc[b];
+      x0f[i] = (float)x0[i];
+      e0[i] = __fma_rn(-mr, x0[i], e0[i]);
+    }
   }
 }
 
-// FP64 true residual r64 = b - S x64; starts an inner round: r = p = (T) r64, d = 0.
+// delta = 0 on the lanes of newly admitted columns (FP64 and double-float
+// lanes alike: both are 8 bytes of zeros)
+template <bool CPLX>
+__global__ void init_lanes_kernel(Params P, int NS, const int* __restrict__ fresh, double* __restrict__ x64) {
+  const int64_t total = (int64_t)P.n * NS * P.W;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i % P.W);
+    if (fresh[CPLX ? l >> 1 : l]) x64[i] = 0.0;
+  }
+}
+
+// FP64 true residual r64 = r0 - S delta (delta in x64); starts an inner round:
+// r = p = (T) r64, d = 0.
 // Slots: [0, W) <r, r> of the rounded residual (lane-wise / (re, im) pairs),
 //        [W, W + ncols) ||r64||^2.
 template <typename T, bool CPLX, bool BLK>
@@ -925,6 +1005,7 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
       src[v] = lane_src[l0 + v];
     }
     const int64_t rowW = (int64_t)NS * W;
+    const int64_t sstride = (int64_t)P.n * NS;  // blocks of a source buffer
     for (int64_t row = (int64_t)blockIdx.x * RPP + tr; row < P.n; row += (int64_t)gridDim.x * RPP) {
       const int s = (int)(row / A.slice_h);
       const int w = A.slice_w[s];
@@ -983,9 +1064,16 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
         if constexpr (CPLX) {
 #pragma unroll
           for (int v = 0; v < VEC; v += 2) {
-            const double bre = bptr[src[v]][row * NS + b];
-            const double r_re = bre - (mr * xo[v] - sh[v] * acc[b][v + 1]);
-            const double r_im = -(mr * xo[v + 1] + sh[v] * acc[b][v]);
+            double e0 = 0.0, g0 = 0.0, x0 = 0.0;
+            if (mine[v]) {  // a retired column's source may be gone
+              const double* sb = bptr[src[v]] + row * NS + b;
+              e0 = sb[0];
+              x0 = sb[sstride];
+              g0 = sb[2 * sstride];
+            }
+            // r0 = e0 - i shift g0, minus S delta = (m + i shift G) delta
+            const double r_re = e0 - (mr * xo[v] - sh[v] * acc[b][v + 1]);
+            const double r_im = -(sh[v] * g0) - (mr * xo[v + 1] + sh[v] * acc[b][v]);
             const T tre = (T)r_re, tim = (T)r_im;
             T zre = tre, zim = tim;
             if (gdiag) {
@@ -1002,13 +1090,20 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
             d1[v + 1] += (double)tre * zim + (double)tim * zre;
             d2[v / 2] += r_re * r_re + r_im * r_im;
             e2[v / 2] += (r_re * r_re + r_im * r_im) / mr;
-            x2[v / 2] += mr * xo[v] * xo[v];  // the filtered field is the real part
+            const double xr = x0 + xo[v];  // the filtered field is the real part
+            x2[v / 2] += mr * xr * xr;
           }
         } else {
 #pragma unroll
           for (int v = 0; v < VEC; v++) {
-            const double bv = bptr[src[v]][row * NS + b];
-            const double rv = bv - (mr * xo[v] + sh[v] * acc[b][v]);
+            double e0 = 0.0, g0 = 0.0, x0 = 0.0;
+            if (mine[v]) {
+              const double* sb = bptr[src[v]] + row * NS + b;
+              e0 = sb[0];
+              x0 = sb[sstride];
+              g0 = sb[2 * sstride];
+            }
+            const double rv = __fma_rn(-sh[v], g0, e0) - (mr * xo[v] + sh[v] * acc[b][v]);
             const T t = (T)rv;
             const T z = gdiag ? (T)(rv / (mr + sh[v] * gr)) : t;
             ro.v[v] = t;
@@ -1016,7 +1111,8 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(EllView<double> A, Par
             d1[v] += (double)t * z;
             d2[v] += rv * rv;
             e2[v] += rv * rv / mr;
-            x2[v] += mr * xo[v] * xo[v];
+            const double xr = x0 + xo[v];
+            x2[v] += mr * xr * xr;
           }
         }
         if (all) {
@@ -1082,6 +1178,7 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
     C.tol2[col] = P.tol2_rel * n2;
   }
   const double r0 = C.r0n2[col];
+  const double rel_prev = C.rel[col];  // at the end of the previous round (1 after the first residual)
   C.rel[col] = r0 > 0.0 ? sqrt(n2 / r0) : 0.0;
   C.err[col] = x2 > 0.0 ? sqrt(e2 / x2) : (e2 > 0.0 ? INFINITY : 0.0);
   // error test: ||r||^2_{M^-1} <= err_tol^2 ||x||^2_M; its equivalent in ||r||^2
@@ -1103,6 +1200,13 @@ __global__ void finish_residual_kernel(Params P, int nb, const double* __restric
     return;
   }
   if (C.iters[col] >= P.maxit) {
+    C.done[col] = 1;
+    C.status[col] = 1;
+    return;
+  }
+  if (C.rounds[col] >= 1 && !(C.rel[col] < rel_prev)) {
+    // a whole round left the true residual where it was: it sits at its
+    // rounding floor (or the inner solve diverges), and more rounds cannot help
     C.done[col] = 1;
     C.status[col] = 1;
     return;
@@ -1231,12 +1335,13 @@ __global__ void gather_lanes_kernel(int64_t rows, int Wold, int Wnew, const int*
   }
 }
 
-// The FP64 solution (real part) of every column flagged in `emit`, written to
-// its caller block out[comp][o] in original mesh order; land entries copy the
-// input (scalar, cell) or are zero (vector).
+// The filtered field x0 + delta (real part) of every column flagged in `emit`,
+// written to its caller block out[comp][o] in original mesh order; land
+// entries copy the input (scalar, cell) or are zero (vector).
 template <bool CPLX, bool BLK, bool DFX>
 __global__ void output_kernel(Params P, int32_t n_out, const int32_t* __restrict__ inv,
-                              const double* __restrict__ x64, double* const* __restrict__ col_out,
+                              const double* __restrict__ x64, const double* const* __restrict__ bptr,
+                              const int* __restrict__ lane_src, double* const* __restrict__ col_out,
                               const double* const* __restrict__ col_in, const int* __restrict__ emit) {
   constexpr int NS = BLK ? 2 : 1;
   const int col = blockIdx.y;
@@ -1244,6 +1349,7 @@ __global__ void output_kernel(Params P, int32_t n_out, const int32_t* __restrict
   double* out = col_out[col];
   const double* in = col_in[col];
   const int lane = CPLX ? 2 * col : col;
+  const double* x0 = bptr[lane_src[lane]] + (int64_t)P.n * NS;
   for (int32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
     const int32_t r = inv[o];
 #pragma unroll
@@ -1251,12 +1357,14 @@ __global__ void output_kernel(Params P, int32_t n_out, const int32_t* __restrict
       double v;
       if (r >= 0) {
         const int64_t i = ((int64_t)r * NS + b) * P.W + lane;
+        double dv;
         if constexpr (DFX) {  // double-float pair (FP32 engines)
           const float2 h = reinterpret_cast<const float2*>(x64)[i];
-          v = (double)h.x + (double)h.y;
+          dv = (double)h.x + (double)h.y;
         } else {
-          v = x64[i];
+          dv = x64[i];
         }
+        v = x0[(int64_t)r * NS + b] + dv;
       }
       else v = BLK ? 0.0 : in[o];
       out[(int64_t)b * n_out + o] = v;
@@ -1299,19 +1407,6 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
 }
 __device__ __forceinline__ DF df_add_f(DF a, float b) { return df_add(a, DF{b, 0.f}); }
 
-// x64 = x0 (refined-solution lanes of newly admitted columns) as double-float pairs
-template <bool CPLX, bool BLK>
-__global__ void init_lanes_df_kernel(Params P, const double* const* __restrict__ xptr, const int* __restrict__ lane_src,
-                                     const int* __restrict__ fresh, DF* __restrict__ x) {
-  constexpr int NS = BLK ? 2 : 1;
-  const int64_t total = (int64_t)P.n * NS * P.W;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(i % P.W);
-    if (!fresh[CPLX ? l >> 1 : l]) continue;
-    const int64_t rs = i / P.W;
-    x[i] = (CPLX && (l & 1)) ? DF{0.f, 0.f} : df_from(xptr[lane_src[l]][rs]);
-  }
-}
 template <bool CPLX>
 __global__ void accumulate_df_kernel(int64_t total, int W, const int* __restrict__ refresh, DF* __restrict__ x,
                                      const float* __restrict__ d, const int* __restrict__ live) {
@@ -1321,7 +1416,7 @@ __global__ void accumulate_df_kernel(int64_t total, int W, const int* __restrict
     if (refresh[CPLX ? l >> 1 : l]) x[i] = df_add_f(x[i], d[i]);
   }
 }
-// a right-hand side b (double) rewritten in place as double-float pairs
+// a block of a source buffer (double) rewritten in place as double-float pairs
 __global__ void to_df_kernel(int64_t n, double* __restrict__ v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const DF a = df_from(v[i]);
@@ -1330,9 +1425,10 @@ __global__ void to_df_kernel(int64_t n, double* __restrict__ v) {
 }
 
 // The refinement residual of the FP32 engines, as residual_kernel computes it
-// in FP64 but in double-float arithmetic: r = b - (M x + shift * (G x)) with the
-// operator values split hi + lo (val32 and val32lo), the lumped mass likewise,
-// x and b as pairs.  Writes r (rounded to float), the restarted p (= r, or
+// in FP64 but in double-float arithmetic: r = r0 - (M delta + shift * (G delta))
+// with r0 = e0 - shift g0 from the column's source, the operator values split
+// hi + lo (val32 and val32lo), the lumped mass likewise, delta, e0 and g0 as
+// pairs.  Writes r (rounded to float), the restarted p (= r, or
 // D^-1 r with Jacobi) and d = 0 on the refreshed lanes, and per-block partials
 // of <r, z>, ||r||^2, ||r||^2_{M^-1} and ||x||^2_M (compensated FP32 sums of
 // the rounded values, flushed to FP64).
@@ -1377,6 +1473,7 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
       src[v] = lane_src[l0 + v];
     }
     const int64_t rowW = (int64_t)NS * W;
+    const int64_t sstride = (int64_t)P.n * NS;  // blocks of a source buffer
     int chain = 0;
     for (int64_t row = (int64_t)blockIdx.x * RPP + tr; row < P.n; row += (int64_t)gridDim.x * RPP) {
       const int s = (int)(row / A.slice_h);
@@ -1435,12 +1532,19 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
         if constexpr (CPLX) {
 #pragma unroll
           for (int v = 0; v < VEC; v += 2) {
-            const DF bre = bptr[src[v]][row * NS + b];
-            // r_re = b - (m x_re - s acc_im),  r_im = -(m x_im + s acc_re)
+            DF e0{0.f, 0.f}, g0{0.f, 0.f};
+            float x0 = 0.f;
+            if (mine[v]) {  // a retired column's source may be gone
+              const DF* sb = bptr[src[v]] + row * NS + b;
+              e0 = sb[0];
+              g0 = sb[2 * sstride];
+              x0 = reinterpret_cast<const float*>(bptr[src[v]] + 3 * sstride)[row * NS + b];
+            }
+            // r_re = e0 - (m d_re - s acc_im),  r_im = -s g0 - (m d_im + s acc_re)
             const DF q_re = df_add(df_mul(mr, xo[v]), df_neg(df_mul(sh[v], acc[b][v + 1])));
             const DF q_im = df_add(df_mul(mr, xo[v + 1]), df_mul(sh[v], acc[b][v]));
-            const DF rre = df_add(bre, df_neg(q_re));
-            const DF rim = df_neg(q_im);
+            const DF rre = df_add(e0, df_neg(q_re));
+            const DF rim = df_neg(df_add(df_mul(sh[v], g0), q_im));
             const float tre = rre.hi + rre.lo, tim = rim.hi + rim.lo;
             float zre = tre, zim = tim;
             if (gdiag) {
@@ -1458,15 +1562,22 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
             const float nn = __fmaf_rn(tre, tre, tim * tim);
             d2[v / 2].add_sum(nn);
             e2[v / 2].add_sum(nn / mrf);
-            const float xr = xo[v].hi;
+            const float xr = x0 + xo[v].hi;
             x2[v / 2].add_sum(mrf * xr * xr);  // the filtered field is the real part
           }
         } else {
 #pragma unroll
           for (int v = 0; v < VEC; v++) {
-            const DF bv = bptr[src[v]][row * NS + b];
+            DF e0{0.f, 0.f}, g0{0.f, 0.f};
+            float x0 = 0.f;
+            if (mine[v]) {
+              const DF* sb = bptr[src[v]] + row * NS + b;
+              e0 = sb[0];
+              g0 = sb[2 * sstride];
+              x0 = reinterpret_cast<const float*>(bptr[src[v]] + 3 * sstride)[row * NS + b];
+            }
             const DF q = df_add(df_mul(mr, xo[v]), df_mul(sh[v], acc[b][v]));
-            const DF rv = df_add(bv, df_neg(q));
+            const DF rv = df_add(df_add(e0, df_neg(df_mul(sh[v], g0))), df_neg(q));
             const float t = rv.hi + rv.lo;
             const float z = gdiag ? t / __fmaf_rn(shf[v], gr, mrf) : t;
             ro.v[v] = t;
@@ -1474,7 +1585,8 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
             d1[v].add(t, z);
             d2[v].add(t, t);
             e2[v].add_sum(t * t / mrf);
-            x2[v].add_sum(mrf * xo[v].hi * xo[v].hi);
+            const float xr = x0 + xo[v].hi;
+            x2[v].add_sum(mrf * xr * xr);
           }
         }
         if (all) {
@@ -1664,7 +1776,7 @@ class EngineT final : public Engine {
   struct Source {
     const double* field = nullptr;
     int sys = 0;
-    double* buf = nullptr;  // b [n][NS] then x0 [n][NS]
+    double* buf = nullptr;  // e0, x0, g0 [n][NS] (FP64 or double-float pairs), x0 as float [n][NS]
     int refs = 0;
   };
   struct Slot {
@@ -1739,7 +1851,6 @@ class EngineT final : public Engine {
     lane_map_ = (int*)take(wcap_ * 4);
     flags_ = (int*)take(ncap_ * 4);
     bptr_ = (const double**)take(ncap_ * 8);
-    xptr_ = (const double**)take(ncap_ * 8);
     col_out_ = (double**)take(ncap_ * 8);
     col_in_ = (const double**)take(ncap_ * 8);
     IFILT_CUDA(cudaMemsetAsync(C_.live, 0, 16, st_));
@@ -1748,7 +1859,7 @@ class EngineT final : public Engine {
       IFILT_CUDA(cudaMemcpyAsync(tune_live_, one, sizeof one, cudaMemcpyHostToDevice, st_));
       IFILT_CUDA(cudaStreamSynchronize(st_));
     }
-    IFILT_CUDA(cudaMallocHost(&h_cnt_, 4 * sizeof(int)));
+    IFILT_CUDA(cudaMallocHost(&h_cnt_, 8 * sizeof(int)));
     P_.n = (int32_t)n_;
     P_.maxit = o.max_iter > 0 ? o.max_iter : 100000;
     P_.tol2_rel = o.tol * o.tol;
@@ -1766,11 +1877,11 @@ class EngineT final : public Engine {
     // double-float refinement residual on the FP32 engines, unless a tolerance asks for more than its
     // about 48 bits carry on hard columns; then FP64, as on the FP64 engine
     df_ = sizeof(T) == 4 && o.tol >= kDfMinTol && (!(o.err_tol > 0.0) || o.err_tol >= kDfMinErrTol);
+    pf_cg_ = pf_mg_ = std::max(0, prefetch_env());
     if (o.precond == IFILT_PRECOND_MG) mg_setup();
     P_.mg = mg_on_ ? 1 : 0;
+    P_.rn_slot = (!CPLX && o.precond == IFILT_PRECOND_JACOBI) ? 1 : 0;
     prof_ = profiling_on();
-    if (prof_)
-      for (auto& e : ev_) IFILT_CUDA(cudaEventCreate(&e));
   }
 
   ~EngineT() override {
@@ -1783,7 +1894,7 @@ class EngineT final : public Engine {
     if (mg_base_) scratch_free(mg_base_, st_);
     if (fixed_) scratch_free(fixed_, st_);
     if (h_cnt_) cudaFreeHost(h_cnt_);
-    for (auto& e : ev_)
+    for (auto& e : pev_)
       if (e) cudaEventDestroy(e);
     cudaStreamSynchronize(st_);
   }
@@ -1847,7 +1958,7 @@ class EngineT final : public Engine {
     if (bpsm_cg_ > 0) nb = std::min(nb, n_sms_ * bpsm_cg_);
     return nb;
   }
-  size_t src_bytes() const { return (size_t)2 * n_ * NS * sizeof(double); }
+  size_t src_bytes() const { return (size_t)n_ * NS * (3 * sizeof(double) + sizeof(float)); }
   const T* mass_t() const {
     if constexpr (sizeof(T) == 4) return m_->mass32;
     else return m_->mass;
@@ -1897,10 +2008,17 @@ class EngineT final : public Engine {
     q.buf = (double*)scratch_alloc(src_bytes(), st_);
     q.refs = 1;
     launch_rhs(m_, j.field, j.sys, q.buf, q.buf + (size_t)n_ * NS, st_);
-    if (df_) {  // b as double-float pairs for the double-float residual
+    {  // e0 = b - M x0, g0 = G x0 and x0 as float: the residual form's fixed part
+      const int g = grid_for((const void*)source_kernel<BLK>, 256, 0, n_);
+      source_kernel<BLK><<<g, 256, 0, st_>>>(A64_, (int32_t)n_, m_->mass, q.buf);
+      launch_check("source", g, 0, 0);
+      other_launches_++;
+    }
+    if (df_) {  // e0 and g0 as double-float pairs for the double-float residual
       const int g = grid_for((const void*)to_df_kernel, kBlock, 0, n_ * NS);
       to_df_kernel<<<g, kBlock, 0, st_>>>(n_ * NS, q.buf);
-      other_launches_++;
+      to_df_kernel<<<g, kBlock, 0, st_>>>(n_ * NS, q.buf + (size_t)2 * n_ * NS);
+      other_launches_ += 2;
     }
     other_launches_++;
     return s;
@@ -1917,25 +2035,30 @@ class EngineT final : public Engine {
   // one step: refinement prologue, m iterations, counters to the host
   void enqueue_step(bool check) {
     const int W = P_.W;
-    const size_t sm2 = spmm_smem(W), sm3 = smem_of(W, 3), sm4 = smem_of(W, 8);
+    const size_t sm2 = spmm_smem(W), sm3 = smem_of(W, 4), sm4 = smem_of(W, 8);
     const int fg = (P_.ncols + 31) / 32;
     const dim3 fb(32, 8);
-    const unsigned evf = check ? cudaEventRecordDefault : cudaEventRecordExternal;
-    evf_ = evf;
-    auto rec = [&](int i) {
-      if (prof_) IFILT_CUDA(cudaEventRecordWithFlags(ev_[i], st_, evf));
-    };
+    evf_ = check ? cudaEventRecordDefault : cudaEventRecordExternal;
     auto chk = [&](const char* what) {
       if (!check) return;
       cudaError_t e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
       if (e != cudaSuccess) fail(IFILT_ECUDA, "%s (W=%d, blocks=%d): %s", what, W, nb_, cudaGetErrorString(e));
     };
+    // algorithmic bytes: one tile vector, the operator's entries, one per-row scalar array
+    const double vb = (double)n_ * NS * W * sizeof(T);
+    const double ell_b = (double)E_->entries * (4.0 + E_->nval * sizeof(MV));
+    const double rows_t = (double)n_ * sizeof(T);
     const int ga = grid_for((const void*)accumulate_kernel<T, CPLX>, kBlock, 0, n_ * NS * W);
     const int nr = std::min(nb_max_, grid_for((const void*)residual_df_kernel<CPLX, BLK>, kBlock, sm4,
                                               (long long)n_ * (W / VEC)));
+    marks_.clear();
+    pmark_open();
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
     chk("scan");
+    pmark(kCatFinish, 0.0);
+    // refreshed-column count of this step, for the bytes of its refinement kernels
+    IFILT_CUDA(cudaMemcpyAsync(h_cnt_ + 4, C_.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st_));
     bool done_acc = false;
     if constexpr (sizeof(T) == 4) {
       if (df_) {
@@ -1947,7 +2070,7 @@ class EngineT final : public Engine {
     if (!done_acc)
       accumulate_kernel<T, CPLX><<<ga, kBlock, 0, st_>>>(n_ * NS * W, W, C_.refresh, tl_.x64, tl_.d, C_.live);
     chk("accumulate");
-    rec(10);
+    pmark(kCatAccumulate, 0.0);  // bytes follow the refreshed lanes (settle)
     int nbr = nb_;
     bool done_res = false;
     if constexpr (sizeof(T) == 4) {
@@ -1964,34 +2087,31 @@ class EngineT final : public Engine {
       residual_kernel<T, CPLX, BLK><<<nb_, kBlock, sm4, st_>>>(A64_, P_, tl_.x64, bptr_, lane_src_, m_->mass, C_,
                                                               tl_.r, tl_.d, tl_.p, partial_, gdiag64());
     chk("residual");
-    rec(11);
+    pmark(kCatResidual, 0.0);  // bytes follow the refreshed lanes (settle)
     finish_residual_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbr, partial_, C_);
     chk("finish_residual");
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
+    pmark(kCatFinish, 0.0);
+    const double pre_b = gdiag_t() ? 2.0 * rows_t : 0.0;
     for (int it = 0; it < m_it_; it++) {
       if (mg_on_) {
         // preconditioned order: z = V(r), beta from <r, z>, p = z + beta p, then q = S p ...
-        if (it == 0) rec(6);
-        mg_sample_ = it == 0;
         const T* z = vcycle(0, tl_.r);
-        mg_sample_ = false;
         chk("vcycle");
-        if (it == 0) rec(7);
         finish_rho_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbz_, partial2_, C_);
         chk("finish_rho");
-        if (it == 0) rec(4);
+        pmark(kCatFinish, 0.0);
         direction_kernel<T, CPLX, BLK, false><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, z, C_, mass_t(), nullptr);
         chk("direction");
-        if (it == 0) rec(5);
+        pmark(kCatDirection, 3.0 * vb);
       }
-      if (it == 0) rec(0);
       spmm_fn()<<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), C_, partial_,
                                             MgArgs<T>{});
       chk("spmm");
-      if (it == 0) rec(1);
+      pmark(kCatSpmm, 2.0 * vb + ell_b + rows_t);
       finish_alpha_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
       chk("finish_alpha");
-      if (it == 0) rec(2);
+      pmark(kCatFinish, 0.0);
       if (gdiag_t())
         update_kernel<T, CPLX, BLK, true><<<nbu_, kBlock, sm3, st_>>>(P_, tl_.d, tl_.p, tl_.r, tl_.q, C_, partial_,
                                                                     mass_t(), gdiag_t());
@@ -1999,19 +2119,21 @@ class EngineT final : public Engine {
         update_kernel<T, CPLX, BLK, false><<<nbu_, kBlock, sm3, st_>>>(P_, tl_.d, tl_.p, tl_.r, tl_.q, C_,
                                                                      partial_, mass_t(), nullptr);
       chk("update");
-      if (it == 0) rec(3);
+      pmark(kCatUpdate, 6.0 * vb + pre_b);
       finish_beta_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbu_, partial_, C_);
       chk("finish_beta");
+      pmark(kCatFinish, 0.0);
       if (mg_on_) continue;
-      if (it == 0) rec(4);
       if (gdiag_t())
         direction_kernel<T, CPLX, BLK, true><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_, mass_t(), gdiag_t());
       else
         direction_kernel<T, CPLX, BLK, false><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_, mass_t(), nullptr);
       chk("direction");
-      if (it == 0) rec(5);
+      pmark(kCatDirection, 3.0 * vb + pre_b);
     }
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
+    pmark(kCatFinish, 0.0);
+    marking_ = false;
     IFILT_CUDA(cudaMemcpyAsync(h_cnt_, C_.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st_));
   }
   int launches_per_step() const { return 7 + 5 * m_it_ + (mg_on_ ? m_it_ * (mg_launches() + 1) : 0); }
@@ -2028,7 +2150,7 @@ class EngineT final : public Engine {
     const bool pre = gdiag_t() != nullptr;
     nbu_ = std::min(nb_max_, grid_for(pre ? (const void*)update_kernel<T, CPLX, BLK, true>
                                           : (const void*)update_kernel<T, CPLX, BLK, false>,
-                                      kBlock, smem_of(P_.W, 3), rows_threads));
+                                      kBlock, smem_of(P_.W, 4), rows_threads));
     nbd_ = std::min(nb_max_, grid_for(pre ? (const void*)direction_kernel<T, CPLX, BLK, true>
                                           : (const void*)direction_kernel<T, CPLX, BLK, false>,
                                       kBlock, 0, rows_threads));
@@ -2044,6 +2166,7 @@ class EngineT final : public Engine {
 
   void set_width(int W) {
     P_.W = W;
+    P_.pf = pf_cg_;
     P_.ncols = W / LPC;
     P_.pstride = 4 * W;
     P_.spt = W > 0 ? spmm_spt(W) : 1;
@@ -2150,12 +2273,8 @@ class EngineT final : public Engine {
     upload_tables();
     cols_upload(C_, Hn, ncn, st_);
     IFILT_CUDA(cudaMemcpyAsync(flags_, fresh.data(), ncn * 4, cudaMemcpyHostToDevice, st_));
-    const int g = grid_for((const void*)init_lanes_kernel<CPLX, BLK>, kBlock, 0, rows * Wn);
-    if (df_)
-      init_lanes_df_kernel<CPLX, BLK><<<g, kBlock, 0, st_>>>(P_, xptr_, lane_src_, flags_,
-                                                             reinterpret_cast<DF*>(tl_.x64));
-    else
-      init_lanes_kernel<CPLX, BLK><<<g, kBlock, 0, st_>>>(P_, xptr_, lane_src_, flags_, tl_.x64);
+    const int g = grid_for((const void*)init_lanes_kernel<CPLX>, kBlock, 0, rows * Wn);
+    init_lanes_kernel<CPLX><<<g, kBlock, 0, st_>>>(P_, NS, flags_, tl_.x64);
     other_launches_++;
     launch_check("init lanes", g, 0, Wn);
     IFILT_CUDA(cudaStreamSynchronize(st_));
@@ -2166,20 +2285,15 @@ class EngineT final : public Engine {
     const HostPrepared& h = m_->host;
     const int W = P_.W, nc = P_.ncols;
     const double* any_b = nullptr;
-    const double* any_x = nullptr;
     for (auto& s : src_)
       if (s.buf) {
         any_b = s.buf;
-        any_x = s.buf + (size_t)n_ * NS;
         break;
       }
-    std::vector<const double*> bp(ncap_, any_b), xp(ncap_, any_x), ci(ncap_, nullptr);
+    std::vector<const double*> bp(ncap_, any_b), ci(ncap_, nullptr);
     std::vector<double*> co(ncap_, nullptr);
     for (int s = 0; s < (int)src_.size(); s++)
-      if (src_[s].buf) {
-        bp[s] = src_[s].buf;
-        xp[s] = src_[s].buf + (size_t)n_ * NS;
-      }
+      if (src_[s].buf) bp[s] = src_[s].buf;
     std::vector<int> ls(W, 0);
     for (int c = 0; c < nc; c++) {
       const Slot& sl = cur_[c];
@@ -2191,7 +2305,6 @@ class EngineT final : public Engine {
     }
     IFILT_CUDA(cudaMemcpyAsync(lane_src_, ls.data(), W * 4, cudaMemcpyHostToDevice, st_));
     IFILT_CUDA(cudaMemcpyAsync(bptr_, bp.data(), ncap_ * 8, cudaMemcpyHostToDevice, st_));
-    IFILT_CUDA(cudaMemcpyAsync(xptr_, xp.data(), ncap_ * 8, cudaMemcpyHostToDevice, st_));
     IFILT_CUDA(cudaMemcpyAsync(col_out_, co.data(), ncap_ * 8, cudaMemcpyHostToDevice, st_));
     IFILT_CUDA(cudaMemcpyAsync(col_in_, ci.data(), ncap_ * 8, cudaMemcpyHostToDevice, st_));
     IFILT_CUDA(cudaStreamSynchronize(st_));
@@ -2213,11 +2326,11 @@ class EngineT final : public Engine {
     IFILT_CUDA(cudaMemcpyAsync(flags_, emit.data(), nc * 4, cudaMemcpyHostToDevice, st_));
     dim3 og((unsigned)std::min<long long>((h.n_out + kBlock - 1) / kBlock, 1024), (unsigned)nc);
     if (df_)
-      output_kernel<CPLX, BLK, true><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, col_out_, col_in_,
-                                                             flags_);
+      output_kernel<CPLX, BLK, true><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, bptr_, lane_src_,
+                                                             col_out_, col_in_, flags_);
     else
-      output_kernel<CPLX, BLK, false><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, col_out_,
-                                                              col_in_, flags_);
+      output_kernel<CPLX, BLK, false><<<og, kBlock, 0, st_>>>(P_, h.n_out, m_->inv_perm, tl_.x64, bptr_, lane_src_,
+                                                              col_out_, col_in_, flags_);
     other_launches_++;
     launch_check("output", (int)og.x, 0, P_.W);
     IFILT_CUDA(cudaStreamSynchronize(st_));
@@ -2261,35 +2374,7 @@ class EngineT final : public Engine {
     const int live = h_cnt_[0], notdone = h_cnt_[2];
     (void)live;
     if (h_cnt_[3]) fail(IFILT_DEVICE_TIMEOUT, "SpMM stage copy did not complete within its wait limit");
-    if (prof_) {
-      float tr = 0;
-      IFILT_CUDA(cudaEventElapsedTime(&tr, ev_[10], ev_[11]));
-      t_res_ += tr;
-      float a = 0, b = 0, c = 0;
-      IFILT_CUDA(cudaEventElapsedTime(&a, ev_[0], ev_[1]));
-      IFILT_CUDA(cudaEventElapsedTime(&b, ev_[2], ev_[3]));
-      IFILT_CUDA(cudaEventElapsedTime(&c, ev_[4], ev_[5]));
-      if (a > 0.01f) {  // the first iteration did work (kernels exit early when no column runs)
-        const double vb = (double)n_ * NS * P_.W * sizeof(T);
-        const double mb = (double)E_->entries * (4.0 + E_->nval * sizeof(MV)) + (double)n_ * sizeof(T);
-        t_[0] += a;
-        t_[1] += b;
-        t_[2] += c;
-        by_[0] += 2.0 * vb + mb;
-        by_[1] += 6.0 * vb;
-        by_[2] += 3.0 * vb;
-        if (mg_on_ && mgl_->size() > 1) {
-          float d = 0, e = 0;
-          IFILT_CUDA(cudaEventElapsedTime(&d, ev_[6], ev_[7]));
-          IFILT_CUDA(cudaEventElapsedTime(&e, ev_[8], ev_[9]));
-          t_[3] += d;
-          t_[4] += e;
-          by_[3] += mg_bytes_per_cycle();
-          by_[4] += 3.0 * vb + (double)m_->ell_k.entries * (4.0 + NVAL * sizeof(T)) + 2.0 * n_ * sizeof(T);
-        }
-        samples_++;
-      }
-    }
+    if (prof_) account_step();
     const int lc = live_columns();
     if (notdone < lc) {
       HostCols H;
@@ -2311,37 +2396,25 @@ class EngineT final : public Engine {
   void report_profile() override {
     profile_count(other_launches_ + steps_ * launches_per_step());
     other_launches_ = 0;
-    if (prof_ && samples_ > 0) {
-      const int64_t launches = steps_ * m_it_;
-      const char* k1 = CPLX ? "c" : "r";
-      const char* k2 = BLK ? "b" : "s";
-      const char* k3 = sizeof(T) == 8 ? "f64" : "f32";
-      char nm[32];
-      snprintf(nm, sizeof nm, "spmm_%s%s_%s", k1, k2, k3);
-      profile_add(nm, launches, samples_, t_[0], by_[0] / samples_);
-      snprintf(nm, sizeof nm, "update_%s%s_%s", k1, k2, k3);
-      profile_add(nm, launches, samples_, t_[1], by_[1] / samples_);
-      snprintf(nm, sizeof nm, "direction_%s%s_%s", k1, k2, k3);
-      profile_add(nm, launches, samples_, t_[2], by_[2] / samples_);
-      if (t_[3] > 0.0) {  // the V-cycle as a whole (several kernels) and its first fine smoothing sweep
-        snprintf(nm, sizeof nm, "(vcycle)_%s%s_%s", k1, k2, k3);
-        profile_add(nm, launches, samples_, t_[3], by_[3] / samples_);
-        snprintf(nm, sizeof nm, "mgsmooth_%s%s_%s", k1, k2, k3);
-        profile_add(nm, launches, samples_, t_[4], by_[4] / samples_);
+    if (prof_) {
+      char eng[16];
+      snprintf(eng, sizeof eng, "%s%s_%s", CPLX ? "c" : "r", BLK ? "b" : "s", sizeof(T) == 8 ? "f64" : "f32");
+      for (int c = 0; c < kCatN; c++) {
+        if (cat_n_[c] == 0) continue;
+        char nm[48];
+        snprintf(nm, sizeof nm, "%s_%s", kCatName[c], eng);
+        profile_add(nm, cat_n_[c], cat_n_[c], cat_ms_[c], cat_bytes_[c] / (double)cat_n_[c]);
+      }
+      if (graph_n_ > 0) {  // every step's graph from its first to its last event (spans all categories)
+        char nm[48];
+        snprintf(nm, sizeof nm, "(steps)_%s", eng);
+        profile_add(nm, graph_n_, graph_n_, graph_ms_, 0.0);
       }
     }
-    if (prof_ && steps_ > 0) {  // every step's FP64 residual (work follows the refreshed columns)
-      const char* k1 = CPLX ? "c" : "r";
-      const char* k2 = BLK ? "b" : "s";
-      const char* k3 = sizeof(T) == 8 ? "f64" : "f32";
-      char nm[40];
-      snprintf(nm, sizeof nm, "(residual64)_%s%s_%s", k1, k2, k3);
-      profile_add(nm, steps_, steps_, t_res_, 0.0);
-    }
-    t_res_ = 0.0;
+    for (int c = 0; c < kCatN; c++) cat_ms_[c] = cat_bytes_[c] = 0.0, cat_n_[c] = 0;
+    graph_ms_ = 0.0;
+    graph_n_ = 0;
     steps_ = 0;
-    samples_ = 0;
-    for (int i = 0; i < 5; i++) t_[i] = by_[i] = 0;
   }
 
  private:
@@ -2365,7 +2438,6 @@ class EngineT final : public Engine {
   int* lane_map_ = nullptr;
   int* flags_ = nullptr;
   const double** bptr_ = nullptr;
-  const double** xptr_ = nullptr;
   double** col_out_ = nullptr;
   const double** col_in_ = nullptr;
   int* h_cnt_ = nullptr;
@@ -2385,6 +2457,12 @@ class EngineT final : public Engine {
   // The timed launches write only outputs the next iteration recomputes (q,
   // partial sums, multigrid scratch) and see a "live" flag forced to 1.
   int tp_cg_ = kTilePasses, bpsm_cg_ = 0, tp_mg_ = kTilePasses, bpsm_mg_ = 0;  // bpsm 0: occupancy
+  int pf_cg_ = 0, pf_mg_ = 0;  // L2 prefetch of each tile's operands (SpMM, multigrid gathers)
+  // IFILT_PREFETCH=0 / 1 fixes the prefetch choice instead of timing it
+  static int prefetch_env() {
+    const char* e = getenv("IFILT_PREFETCH");
+    return (e && (e[0] == '0' || e[0] == '1')) ? e[0] - '0' : -1;
+  }
   Cols mg_cols_{};
   int* tune_live_ = nullptr;
   std::string tune_key(int W) const {
@@ -2410,6 +2488,8 @@ class EngineT final : public Engine {
         bpsm_cg_ = it->second[1];
         tp_mg_ = it->second[2];
         bpsm_mg_ = it->second[3];
+        pf_cg_ = it->second[4];
+        pf_mg_ = it->second[5];
         set_width(W);
         return;
       }
@@ -2431,58 +2511,73 @@ class EngineT final : public Engine {
       return ms;
     };
     const int tps[3] = {4, 8, 16};
+    const int pfe = prefetch_env();
+    std::vector<int> pfs;
+    if (pfe >= 0) pfs = {pfe};
+    else pfs = {0, 1};
     int occ = 1;
     float best = 1e30f;
-    int btp = kTilePasses, bb = 0;
-    for (int tp : tps) {
-      tp_cg_ = tp;
-      bpsm_cg_ = 0;
-      set_width(W);
-      IFILT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)spmm_fn(), kBlock, spmm_smem(W)));
-      for (int bps : {0, occ - 1}) {  // all resident blocks, or one fewer per SM
-        if (bps == occ - 1 && bps < 1) continue;
-        bpsm_cg_ = bps;
-        const int nb = blocks_for(W);
-        const size_t sm = spmm_smem(W);
-        const float ms = timeit([&] {
-          spmm_fn()<<<nb, kBlock, sm, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), Ct, partial_,
-                                             MgArgs<T>{});
-        });
-        if (ms < best) {
-          best = ms;
-          btp = tp;
-          bb = bps;
+    int btp = kTilePasses, bb = 0, bpf = pfs[0];
+    for (int pf : pfs) {
+      for (int tp : tps) {
+        tp_cg_ = tp;
+        bpsm_cg_ = 0;
+        set_width(W);
+        P_.pf = pf;
+        IFILT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)spmm_fn(), kBlock, spmm_smem(W)));
+        for (int bps : {0, occ - 1}) {  // all resident blocks, or one fewer per SM
+          if (bps == occ - 1 && bps < 1) continue;
+          bpsm_cg_ = bps;
+          const int nb = blocks_for(W);
+          const size_t sm = spmm_smem(W);
+          const float ms = timeit([&] {
+            spmm_fn()<<<nb, kBlock, sm, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), Ct, partial_,
+                                               MgArgs<T>{});
+          });
+          if (ms < best) {
+            best = ms;
+            btp = tp;
+            bb = bps;
+            bpf = pf;
+          }
         }
       }
     }
     tp_cg_ = btp;
     bpsm_cg_ = bb;
+    pf_cg_ = bpf;
     if (mg_on_) {
       best = 1e30f;
       btp = kTilePasses;
       bb = 0;
+      bpf = pfs[0];
       mg_cols_ = Ct;
-      for (int tp : tps) {
-        for (int bps : {0, 2}) {
-          tp_mg_ = tp;
-          bpsm_mg_ = bps;
-          const float ms = timeit([&] { mg_smooth(0, mgb_[0].a, mgb_[0].b, tl_.r, nullptr); });
-          if (ms < best) {
-            best = ms;
-            btp = tp;
-            bb = bps;
+      for (int pf : pfs) {
+        for (int tp : tps) {
+          for (int bps : {0, 2}) {
+            tp_mg_ = tp;
+            bpsm_mg_ = bps;
+            pf_mg_ = pf;
+            const float ms = timeit([&] { mg_smooth(0, mgb_[0].a, mgb_[0].b, tl_.r, nullptr); });
+            if (ms < best) {
+              best = ms;
+              btp = tp;
+              bb = bps;
+              bpf = pf;
+            }
           }
         }
       }
       mg_cols_ = C_;
       tp_mg_ = btp;
       bpsm_mg_ = bb;
+      pf_mg_ = bpf;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     set_width(W);
     std::lock_guard<std::mutex> lk(m_->tune_mu);
-    m_->tune[key] = {tp_cg_, bpsm_cg_, tp_mg_, bpsm_mg_};
+    m_->tune[key] = {tp_cg_, bpsm_cg_, tp_mg_, bpsm_mg_, pf_cg_, pf_mg_};
   }
   // ------------------------------------------------------------ multigrid
   static constexpr int kMgMinB = 3;
@@ -2592,6 +2687,7 @@ class EngineT final : public Engine {
     Params Q = P_;
     Q.n = E.n;
     Q.spt = spt_of(E, W, vbytes, mg_minb<EPI>());
+    Q.pf = pf_mg_;
     Q.stage_e = (int)stage_entries_of(E, Q.spt);
     const size_t smem = smem_of(W, 2) + 2 * stage_bytes_of(E, Q.spt, vbytes);
     const long long ntiles = (E.n_slices + Q.spt - 1) / Q.spt;
@@ -2602,13 +2698,25 @@ class EngineT final : public Engine {
     return blocks;
   }
   // S_l-operations: level 0 uses the mesh's K and lumped mass, coarser levels their (K, M) pair
-  // (FP32 engines only: the FP64 engine refuses multigrid in mg_setup)
+  // (FP32 engines only: the FP64 engine refuses multigrid in mg_setup).  Each records its
+  // category and algorithmic bytes for the profile.
+  int64_t mg_rows(size_t l) const { return l == 0 ? n_ : (int64_t)(*mgl_)[l].n; }
+  double mg_vb(size_t l) const { return (double)mg_rows(l) * NS * P_.W * sizeof(T); }
+  double mg_ell_b(const DevEll& E, int nset) const {
+    return (double)E.entries * (4.0 + (double)nset * NVAL * sizeof(T));
+  }
   int mg_smooth(size_t l, const T* x, T* out, const T* rhs, double* partial) {
     if constexpr (sizeof(T) == 4) {
       const DevMgLevel& L = (*mgl_)[l];
+      int nb;
       if (l == 0)
-        return mg_gather<kEpiSmooth, 1>(m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial, L.omega);
-      return mg_gather<kEpiSmooth, 2>(L.S, x, out, L.dm32, L.dk32, rhs, nullptr, partial, L.omega);
+        nb = mg_gather<kEpiSmooth, 1>(m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial, L.omega);
+      else
+        nb = mg_gather<kEpiSmooth, 2>(L.S, x, out, L.dm32, L.dk32, rhs, nullptr, partial, L.omega);
+      const DevEll& S = l == 0 ? m_->ell_k : L.S;
+      pmark(l == 0 ? kCatMgSmooth0 : kCatMgSmoothC,
+            3.0 * mg_vb(l) + mg_ell_b(S, l == 0 ? 1 : 2) + 2.0 * mg_rows(l) * sizeof(T));
+      return nb;
     } else {
       return 0;
     }
@@ -2617,18 +2725,26 @@ class EngineT final : public Engine {
     if constexpr (sizeof(T) == 4) {
       if (l == 0) mg_gather<kEpiResid, 1>(m_->ell_k, x, out, mass_t(), nullptr, rhs, nullptr, nullptr);
       else mg_gather<kEpiResid, 2>((*mgl_)[l].S, x, out, (*mgl_)[l].dm32, nullptr, rhs, nullptr, nullptr);
+      const DevEll& S = l == 0 ? m_->ell_k : (*mgl_)[l].S;
+      pmark(l == 0 ? kCatMgResid0 : kCatMgResidC,
+            3.0 * mg_vb(l) + mg_ell_b(S, l == 0 ? 1 : 2) + (double)mg_rows(l) * sizeof(T));
     }
   }
   void mg_transfer(size_t l, bool restrict_, const T* src, T* out, const T* own) {
     if constexpr (sizeof(T) == 4) {
       const DevMgLevel& L = (*mgl_)[l];
-      if (restrict_) mg_gather<kEpiRestrict, 1>(L.R, src, out, nullptr, nullptr, nullptr, nullptr, nullptr);
-      else mg_gather<kEpiProlong, 1>(L.P, src, out, nullptr, nullptr, nullptr, own, nullptr);
+      if (restrict_) {
+        mg_gather<kEpiRestrict, 1>(L.R, src, out, nullptr, nullptr, nullptr, nullptr, nullptr);
+        pmark(l == 0 ? kCatMgRestrict0 : kCatMgRestrictC, mg_vb(l) + mg_vb(l + 1) + mg_ell_b(L.R, 1));
+      } else {
+        mg_gather<kEpiProlong, 1>(L.P, src, out, nullptr, nullptr, nullptr, own, nullptr);
+        pmark(l == 0 ? kCatMgProlong0 : kCatMgProlongC, 2.0 * mg_vb(l) + mg_vb(l + 1) + mg_ell_b(L.P, 1));
+      }
     }
   }
   void mg_jacobi(size_t l, const T* rhs, T* out) {
     if constexpr (sizeof(T) == 4) {
-      const int32_t rows = l == 0 ? (int32_t)n_ : (*mgl_)[l].n;
+      const int32_t rows = (int32_t)mg_rows(l);
       const T* md = l == 0 ? mass_t() : (*mgl_)[l].dm32;
       const T* kd = l == 0 ? m_->diag_k32 : (*mgl_)[l].dk32;
       Params Q = P_;
@@ -2636,6 +2752,7 @@ class EngineT final : public Engine {
       const int g = std::min(nb_max_, grid_for((const void*)mg_jacobi_kernel<T, CPLX, BLK>, kBlock, 0,
                                                (long long)rows * (P_.W / VEC)));
       mg_jacobi_kernel<T, CPLX, BLK><<<g, kBlock, 0, st_>>>(Q, rhs, out, md, kd, C_, (T)(*mgl_)[l].omega);
+      pmark(l == 0 ? kCatMgJacobi0 : kCatMgJacobiC, 2.0 * mg_vb(l) + 2.0 * rows * sizeof(T));
     }
   }
   // One V-cycle on level l for the right-hand side rhs: two damped-Jacobi
@@ -2656,9 +2773,7 @@ class EngineT final : public Engine {
       }
       return x;
     }
-    if (l == 0) mark(8);
     mg_smooth(l, B.a, B.b, rhs, nullptr);
-    if (l == 0) mark(9);
     // coarse correction(s): x <- x + P V_{l+1}(R (rhs - S x)), twice on levels 1 and 2 of a W12 cycle
     T* x = B.b;
     T* t = B.a;
@@ -2691,9 +2806,6 @@ class EngineT final : public Engine {
     for (size_t l = 0; l + 1 < v.size(); l++) v[l + 1] = v[l] * mg_reps(l);
     return v;
   }
-  void mark(int i) {
-    if (prof_ && mg_sample_) IFILT_CUDA(cudaEventRecordWithFlags(ev_[i], st_, evf_));
-  }
   int mg_launches() const {
     if (!mg_on_) return 0;
     const std::vector<int> v = mg_visits();
@@ -2702,38 +2814,83 @@ class EngineT final : public Engine {
       n += v[l] * (l + 1 == v.size() ? kMgCoarseSweeps : 2 * mg_nu(l) + 3 * mg_reps(l));
     return n;
   }
-  // algorithmic bytes of one V-cycle (vectors and operators, all levels)
-  double mg_bytes_per_cycle() const {
-    if (!mg_on_) return 0.0;
-    double b = 0.0;
-    const int W = P_.W;
-    const std::vector<int> visits = mg_visits();
-    for (size_t l = 0; l < mgl_->size(); l++) {
-      const DevMgLevel& L = (*mgl_)[l];
-      const double rows = l == 0 ? (double)n_ : (double)L.n;
-      const double vb = rows * NS * W * sizeof(T);
-      const DevEll& S = l == 0 ? m_->ell_k : L.S;
-      const double sb = (double)S.entries * (4.0 + (l == 0 ? 1 : 2) * NVAL * sizeof(T));
-      if (l + 1 == mgl_->size()) {
-        b += visits[l] * (2 * vb + (kMgCoarseSweeps - 1) * (3 * vb + sb));
-      } else {
-        // jacobi, one sweep, per coarse correction (residual, restriction, prolongation), two sweeps
-        const double vc = (double)(*mgl_)[l + 1].n * NS * W * sizeof(T);
-        const double corr = (3 * vb + sb) + (vb + vc) + (2 * vb + vc) +
-                            (double)(L.P.entries + L.R.entries) * (4.0 + NVAL * sizeof(T));
-        b += visits[l] * (2 * vb + (2 * mg_nu(l) - 1) * (3 * vb + sb) + mg_reps(l) * corr);
-      }
-    }
-    return b;
-  }
   static constexpr double kDfMinTol = 1e-10, kDfMinErrTol = 1e-8;
   bool df_ = false;  // refined solution, right-hand sides and true residual as double-float pairs
-  cudaEvent_t ev_[12] = {};
+  // ------------------------------------------------------------ profiling
+  // With profiling on, an event is recorded after every launch of a step (in
+  // the captured graph: external event-record nodes), so the device time of
+  // every launch is measured and the launches of a step account for all of its
+  // time from the first event to the last.  Each launch carries a category and
+  // its algorithmic bytes (every vector it reads or writes counted once, the
+  // operator entries and per-row scalars it reads).  A launch that found no
+  // work (its kernel returns at once when no column runs) counts its time but
+  // no bytes.
+  enum Cat {
+    kCatSpmm, kCatUpdate, kCatDirection, kCatFinish, kCatResidual, kCatAccumulate,
+    kCatMgJacobi0, kCatMgSmooth0, kCatMgResid0, kCatMgRestrict0, kCatMgProlong0,
+    kCatMgJacobiC, kCatMgSmoothC, kCatMgResidC, kCatMgRestrictC, kCatMgProlongC, kCatN
+  };
+  static constexpr const char* kCatName[kCatN] = {
+      "spmm", "update", "direction", "finish", "residual", "accumulate",
+      "mgjacobi0", "mgsmooth0", "mgresid0", "mgrestrict0", "mgprolong0",
+      "mgjacobic", "mgsmoothc", "mgresidc", "mgrestrictc", "mgprolongc"};
+  struct Mark {
+    int cat;
+    double bytes;
+  };
+  std::vector<Mark> marks_;
+  std::vector<cudaEvent_t> pev_;
   unsigned evf_ = cudaEventRecordDefault;
-  bool mg_sample_ = false;
-  double t_[5] = {0, 0, 0, 0, 0}, by_[5] = {0, 0, 0, 0, 0};
-  double t_res_ = 0.0;  // FP64 true-residual kernel, every step
-  int64_t samples_ = 0, steps_ = 0, other_launches_ = 0;
+  double cat_ms_[kCatN] = {}, cat_bytes_[kCatN] = {};
+  int64_t cat_n_[kCatN] = {};
+  double graph_ms_ = 0.0;
+  int64_t graph_n_ = 0, steps_ = 0, other_launches_ = 0;
+  cudaEvent_t pev(size_t i) {
+    while (pev_.size() <= i) {
+      cudaEvent_t e = nullptr;
+      IFILT_CUDA(cudaEventCreate(&e));
+      pev_.push_back(e);
+    }
+    return pev_[i];
+  }
+  bool marking_ = false;  // inside enqueue_step (autotuning launches are not marked)
+  void pmark_open() {
+    marking_ = prof_;
+    if (marking_) IFILT_CUDA(cudaEventRecordWithFlags(pev(0), st_, evf_));
+  }
+  void pmark(int cat, double bytes) {
+    if (!marking_) return;
+    IFILT_CUDA(cudaEventRecordWithFlags(pev(marks_.size() + 1), st_, evf_));
+    marks_.push_back({cat, bytes});
+  }
+  // after a step: the time of every launch into its category
+  void account_step() {
+    if (marks_.empty()) return;
+    // lanes of the columns refreshed this step (counts copied after the step's first scan)
+    const double wr = (double)h_cnt_[5] * LPC;
+    const double s = sizeof(T);
+    const double src_b = (double)n_ * NS * (3 * 8 + 4) * std::min<double>((double)src_.size(), h_cnt_[5]);
+    const double res_ell = df_ ? (double)E_->entries * (4.0 + 2 * 4.0 * E_->nval)
+                               : (double)E_->entries * (4.0 + 8.0 * E_->nval);
+    const double rows = (double)n_ * NS;
+    float total = 0.f;
+    IFILT_CUDA(cudaEventElapsedTime(&total, pev_[0], pev_[marks_.size()]));
+    graph_ms_ += total;
+    graph_n_++;
+    for (size_t i = 0; i < marks_.size(); i++) {
+      float ms = 0.f;
+      IFILT_CUDA(cudaEventElapsedTime(&ms, pev_[i], pev_[i + 1]));
+      const Mark& mk = marks_[i];
+      double b = mk.bytes;
+      if (mk.cat == kCatResidual) b = wr > 0 ? rows * wr * (8.0 + 3.0 * s) + res_ell + 8.0 * n_ + src_b : 0.0;
+      if (mk.cat == kCatAccumulate) b = rows * wr * (16.0 + s);
+      // a launch that returned at once (no column running) moves nothing
+      if (b > 0.0 && ms < 0.004f && b > 4e7) b = 0.0;
+      cat_ms_[mk.cat] += ms;
+      cat_bytes_[mk.cat] += b;
+      cat_n_[mk.cat]++;
+    }
+  }
 };
 
 template <typename T, typename MV>
@@ -2768,7 +2925,7 @@ size_t batched_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o, i
   const size_t tb = o.precision == IFILT_PREC_FP64 ? 8 : 4;
   const size_t n = (size_t)h.n_rows;
   const size_t cols = (size_t)W / (cplx ? 2 : 1);
-  const size_t srcs = std::min<size_t>((size_t)F * nsys, cols) * n * ns * 16;
+  const size_t srcs = std::min<size_t>((size_t)F * nsys, cols) * n * ns * (3 * 8 + 4);  // e0, x0, g0, x0 float
   // multigrid: two fine scratch vectors and three per coarser level (coarsening >= 1.25x per level)
   const size_t mg = o.precond == IFILT_PRECOND_MG ? n * ns * W * tb * (2 + 3 * 4) : 0;
   // tiles twice (old and new during a re-pack), sources, partial sums and tables

@@ -23,11 +23,20 @@ std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};  // device -> address of g_spectrum_scratch on that device
 
 // The array's name in host code is only a host-side handle; its device
-// address is looked up once per device, with that device current.
-double* scratch_address(int dev) {
+// address is looked up with that device current: on the first call on the
+// device, and again on every call made outside a stream capture, so that an
+// address cached before a device reset (which reloads the module) is never
+// used.  Inside a capture the address cached by an earlier call is used.
+double* scratch_address(int dev, cudaStream_t st) {
   if (dev < 0 || dev >= kMaxDevices) fail(IFILT_EINVAL, "device ordinal %d out of range", dev);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  IFILT_CUDA(cudaStreamIsCapturing(st, &cap));
   std::lock_guard<std::mutex> lk(g_mu);
-  if (g_addr[dev]) return g_addr[dev];
+  if (cap != cudaStreamCaptureStatusNone) {
+    if (!g_addr[dev])
+      fail(IFILT_EINVAL, "the first ifilt_spectrum_noalloc call on device %d must come before any stream capture", dev);
+    return g_addr[dev];
+  }
   void* p = nullptr;
   IFILT_CUDA(cudaGetSymbolAddress(&p, g_spectrum_scratch));
   g_addr[dev] = static_cast<double*>(p);
@@ -45,7 +54,7 @@ ifilt_status spectrum_noalloc(ifilt_mesh_s* m, int32_t F, int32_t K, const doubl
          (long long)F * K, kMaxCols);
   int dev = 0;
   IFILT_CUDA(cudaGetDevice(&dev));
-  double* base = scratch_address(dev);
+  double* base = scratch_address(dev, st);
   double* k_dev = base;
   double* e_dev = base + kMaxCols;
   double* s_dev = base + 2 * kMaxCols;

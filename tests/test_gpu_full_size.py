@@ -1,16 +1,20 @@
 """Full size: the 10.5 M-vertex velocity workload in the configuration the
-benchmark times (both placements, 40 scales x 2 components, n = 2 in the
-complex form, FP32 with FP64 refinement to 1e-9, multigrid preconditioning).
+benchmark times -- both placements, 40 scales x 2 components, n = 2 in the
+complex form, FP32 with FP64-accurate refinement to the paper's residual test
+1e-9 and a certified relative error bound of 1e-7, multigrid preconditioning
+on the strength-filtered hierarchy (mg_strength 0.05), 4 iterations per
+solver step, at most 2000 iterations per column.
 
-Every column is solved to the paper's residual test (1e-9 of ||b - S x0||)
-and, in addition, to a certified relative error bound of 1e-7: the library
-stops a column only once ||r||_{M^-1} <= 1e-7 ||x||_M for the system it
-solves (S >= M, or |e^H A e| >= e^H M e in the complex form), a test pinned
-against the oracle's exact solutions on smaller meshes.  Here the oracle
-cannot re-solve the large-scale columns, so it checks (1) the largest-
-wavenumber columns element by element against its own solve, and (2) for
-every column the real system's residual recomputed in FP64 from the returned
-field, bounded loosely (its ratio to the error grows like l^4).
+The oracle checks every column without trusting the library's own numbers:
+
+* its FP64 error certificate, recomputed from the returned field: S >= M for
+  the paper's real operator S = M + 1/2 l^4 K M^-1 K, so
+  ||x - x*||_M <= ||b - S x||_{M^-1}; every column must show a bound of at most
+  1e-6 ||x||_M (the target tolerance against the FP64 solution);
+* element by element against its own conjugate-gradient solve, for the
+  largest wavenumber and for a mid-range one (index 30 of 40, a 40 km
+  wavelength: about one mesh spacing for l, so the oracle's unpreconditioned
+  CG ends in minutes at 10.5 M vertices).
 """
 
 import numpy as np
@@ -22,6 +26,8 @@ import synth
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 TOL_MIXED = 1e-6
+BENCH_OPTS = dict(order=2, tol=1e-9, err_tol=1e-7, max_iter=2000, check_every=4)
+SAMPLED_K = (39, 30)
 
 
 @pytest.fixture(scope="module")
@@ -30,28 +36,29 @@ def workload():
 
 
 @pytest.mark.parametrize("placement", ["vertex_vector", "cell"])
-def test_uv_batch_level10_bound_and_sample(lib, workload, placement):
+def test_uv_batch_level10_certified_and_sampled(lib, workload, placement):
     import torch
     w = workload
-    h = lib.prepare_mesh(w["mesh"], placement, max_order=2)
+    h = lib.prepare_mesh(w["mesh"], placement, max_order=2, mg_strength=0.05)
     f = torch.tensor(w["fields"], device="cuda")
-    out, stats, st = lib.solve(h, f, w["k"], order=2, tol=1e-9, precision=lib.PREC_FP32_IR,
-                               n2_solver=lib.N2_COMPLEX, precond=lib.PRECOND_MG, err_tol=1e-7)
+    out, stats, st = lib.solve(h, f, w["k"], precision=lib.PREC_FP32_IR, n2_solver=lib.N2_COMPLEX,
+                               precond=lib.PRECOND_MG, **BENCH_OPTS)
     h.release()
     assert st == 0, stats
     assert (stats["status"] == 0).all()
+    assert (stats["err_bound"] <= 1e-7).all() and (stats["rel_residual"] <= 1e-9).all()
     res = out.cpu().numpy()
     del out
     P = oracle.build_problem(w["mesh"], placement)
     fld = w["fields"][0]
     K = w["k"].size
-    assert (stats["err_bound"] <= 1e-7).all() and (stats["rel_residual"] <= 1e-9).all()
     worst = 0.0
     for j in range(K):
-        for rel in oracle.relative_residual(P, fld, res[0, j], w["k"][j], 2):
-            worst = max(worst, rel)
-    assert worst <= 1e-3, worst
-    ref, _ = oracle.filter_field(P, fld, [w["k"][K - 1]], 2, rtol=1e-12)
-    for c in range(ref.shape[1]):
-        a, b = res[0, K - 1, c], ref[0, c]
-        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= TOL_MIXED
+        for bound, xnorm in oracle.residual_certificate(P, fld, res[0, j], w["k"][j], 2):
+            worst = max(worst, bound / xnorm)
+    assert worst <= TOL_MIXED, worst
+    ref, _ = oracle.filter_field(P, fld, [w["k"][j] for j in SAMPLED_K], 2, rtol=1e-12)
+    for i, j in enumerate(SAMPLED_K):
+        for c in range(ref.shape[1]):
+            a, b = res[0, j, c], ref[i, c]
+            assert np.linalg.norm(a - b) / np.linalg.norm(b) <= TOL_MIXED, (j, c)

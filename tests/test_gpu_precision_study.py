@@ -1,0 +1,110 @@
+"""Precision study against the FP64 oracle: the error of each arithmetic per
+filtered field and per spectrum bin.
+
+Workload: the level-9 scalar sphere (2,621,442 vertices, jittered, land-masked),
+filter order n = 2, 40 wavenumbers 2 pi / 4000 km ... 2 pi / 10 km, two seeded
+fields.  The library solves it in three arithmetics, each with the paper's
+residual test 1e-9:
+
+  fp32 : FP32 matrix values and Krylov vectors, FP64-accurate refinement,
+         multigrid, certified error bound 1e-7
+  bf16 : BF16-stored matrix values, otherwise as fp32
+  fp64 : FP64 throughout, no preconditioner
+
+The oracle then measures every case without the library's help:
+
+* per filtered field (all 2 x 40): a certified bound on the relative M-norm
+  error, ||b - S x||_{M^-1} / ||x||_M >= ||x - x*||_M / ||x||_M (S >= M for the
+  paper's real operator), computed in FP64 from the returned field;
+* per filtered field, exactly, on a subset where the oracle's own CG to 1e-12
+  is affordable at this size: field 0 at wavenumber indices 20, 37, 38, 39;
+* per spectrum bin: a certified bound on the relative error of every bin, from
+  the field bounds (|E(x) - E(x*)| <= (||x||_M + delta / 2) delta / sum w for
+  E = 1/2 ||x||_M^2 / sum w and delta the bound on ||x - x*||_M), and the exact
+  relative error of the bins whose two ends are in the oracle's subset
+  (37-38, 38-39).
+
+The numbers are printed as one JSON line (pytest -s) and written to the file
+named by IFILT_PRECISION_STUDY_OUT when that is set.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+SUBSET = (20, 37, 38, 39)
+
+
+def _cases(lib):
+    mg = dict(n2_solver=lib.N2_COMPLEX, precond=lib.PRECOND_MG, err_tol=1e-7, check_every=4)
+    return {"fp32": dict(precision=lib.PREC_FP32_IR, **mg),
+            "bf16": dict(precision=lib.PREC_BF16_IR, **mg),
+            "fp64": dict(precision=lib.PREC_FP64, n2_solver=lib.N2_COMPLEX)}
+
+
+def test_precision_study_against_oracle(lib):
+    import torch
+    w = synth.workload("precision", n_fields=2)
+    mesh, fields, k = w["mesh"], w["fields"], w["k"]
+    F, K = fields.shape[0], k.size
+    P = oracle.build_problem(mesh, "vertex_scalar")
+    wts = P.weights()
+    wsum = float(np.sum(wts))
+    # the oracle's own solutions on the subset (field 0)
+    ref, _ = oracle.filter_field(P, fields[0], [k[j] for j in SUBSET], 2, rtol=1e-12)
+    Eref = oracle.filtered_energy(ref, P.out_ids, wts)
+    h = lib.prepare_mesh(mesh, "vertex_scalar", max_order=2, mg_strength=0.05)
+    ft = torch.tensor(fields, device="cuda")
+    report = {"workload": f"level-9 scalar sphere, {mesh['coords'].shape[0]} vertices, n=2, {K} wavenumbers, "
+                          f"{F} fields, tol 1e-9", "oracle_subset": {"field": 0, "k_index": list(SUBSET)},
+              "cases": {}}
+    for name, opts in _cases(lib).items():
+        out, stats, st = lib.solve(h, ft, k, order=2, tol=1e-9, **opts)
+        assert st == 0, (name, stats)
+        x = out.cpu().numpy()
+        del out
+        # certified bounds on every field, and the energies they bound
+        rel_bound = np.zeros((F, K))
+        E = np.zeros((F, K))
+        dE = np.zeros((F, K))
+        for f in range(F):
+            for j in range(K):
+                (delta, xn), = oracle.residual_certificate(P, fields[f], x[f, j], k[j], 2)
+                rel_bound[f, j] = delta / xn
+                E[f, j] = 0.5 * xn * xn / wsum
+                dE[f, j] = (xn + 0.5 * delta) * delta / wsum
+        kmid, spec = oracle.spectrum(k, E)
+        dk = np.diff(np.sort(k))
+        bin_bound = (dE[:, 1:] + dE[:, :-1]) / dk / np.abs(spec)
+        # exact errors on the subset
+        exact = [float(np.linalg.norm(x[0, j] - ref[i]) / np.linalg.norm(ref[i])) for i, j in enumerate(SUBSET)]
+        _, spec_ref = oracle.spectrum(k[list(SUBSET[1:])], Eref[1:])
+        _, spec_got = oracle.spectrum(k[list(SUBSET[1:])], E[0, list(SUBSET[1:])])
+        bin_exact = np.abs(spec_got - spec_ref) / np.abs(spec_ref)
+        report["cases"][name] = {
+            "iters_max": int(stats["iters"].max()),
+            "field_rel_err_bound_max": float(rel_bound.max()),
+            "field_rel_err_bound_median": float(np.median(rel_bound)),
+            "field_rel_err_bound_per_k_max": [float(v) for v in rel_bound.max(axis=0)],
+            "field_rel_err_exact_subset": exact,
+            "bin_rel_err_bound_max": float(bin_bound.max()),
+            "bin_rel_err_bound_median": float(np.median(bin_bound)),
+            "bin_rel_err_exact_subset": [float(v) for v in bin_exact],
+        }
+        assert rel_bound.max() <= 1e-6, (name, rel_bound.max())
+        assert max(exact) <= 1e-6, (name, exact)
+        assert np.all(np.isfinite(bin_bound)) and bin_exact.max() <= 1e-5, (name, bin_exact)
+    h.release()
+    line = json.dumps(report)
+    print(line)
+    path = os.environ.get("IFILT_PRECISION_STUDY_OUT")
+    if path:
+        with open(path, "w") as fh:
+            fh.write(line + "\n")
