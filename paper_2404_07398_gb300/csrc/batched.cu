@@ -214,7 +214,6 @@ struct Params {
   int wmax;         // widest ELL slice
   int stage_e;      // ELL entries one SpMM stage buffer holds
   int rn_slot;      // real columns: ||r||^2 has slots of its own in the update partials (Jacobi)
-  int pf;           // gather kernels: prefetch a tile's gathered and row operands into L2 at its start
 };
 
 // ------------------------------------------------------------------ kernels
@@ -399,11 +398,6 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Fire-and-forget prefetch of a 16-byte aligned block (a multiple of 16 bytes)
-// into L2 by the bulk-copy engine: no registers or shared memory are held.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
 // Wait for phase `parity` of `bar` for at most ~1 s of SM clock; false on expiry.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   const long long t0 = clock64();
@@ -514,20 +508,7 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
     const MV* sval = stage_val(b);
     const int64_t r0 = (int64_t)tile * spt * H;
     const int rows = (int)min((int64_t)TR, (int64_t)P.n - r0);
-    if (P.pf) {
-      // every row the tile gathers (padding entries name their own row) and its row operands are
-      // requested from DRAM at once, so the rows a thread works through one after another find
-      // them in L2 instead of each waiting out a DRAM miss
-      const int s0 = tile * spt;
-      const int ne = (int)(A.slice_off[min(s0 + spt, n_slices)] - A.slice_off[s0]);
-      const uint32_t rb = (uint32_t)(rowW * sizeof(T));
-      for (int e = threadIdx.x; e < ne; e += kBlock) prefetch_l2(p + (int64_t)scol[e] * rowW, rb);
-      if (threadIdx.x == 0) {
-        const uint32_t tb = (uint32_t)rows * rb;
-        if constexpr (EPI == kEpiSmooth || EPI == kEpiResid) prefetch_l2(mg.rhs + r0 * rowW, tb);
-        if constexpr (EPI == kEpiProlong) prefetch_l2(mg.own + r0 * rowW, tb);
-      }
-    }
+
     if (on) {
       for (int lr = tr; lr < rows; lr += RPP) {
         const int64_t r = r0 + lr;
@@ -1441,6 +1422,7 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
                                                                float* __restrict__ p, double* __restrict__ partial,
                                                                const float* __restrict__ gdiag) {
   constexpr int VEC = Pack<float>::N;
+  static_assert(VEC == 4, "the double-float residual moves 4 lanes of (hi, lo) pairs per thread");
   constexpr int NS = BLK ? 2 : 1;
   constexpr int NV = BLK ? 2 : 1;
   if (C.live[1] == 0) return;
@@ -1484,27 +1466,56 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
       for (int b = 0; b < NS; b++)
 #pragma unroll
         for (int v = 0; v < VEC; v++) acc[b][v] = DF{0.f, 0.f};
-      for (int e = 0; e < w; e++) {
-        const int c = A.col[base + e];
-        const DF* xs = x + (int64_t)c * rowW + l0;
-        DF xu[VEC], xw[VEC];
-#pragma unroll
-        for (int v = 0; v < VEC; v++) {
-          xu[v] = xs[v];
-          if constexpr (BLK) xw[v] = xs[W + v];
-        }
-        if constexpr (BLK) {
-          const DF a{A.val[(base + e) * NV], vlo[(base + e) * NV]};
-          const DF bb{A.val[(base + e) * NV + 1], vlo[(base + e) * NV + 1]};
-#pragma unroll
-          for (int v = 0; v < VEC; v++) {
-            acc[0][v] = df_add(acc[0][v], df_add(df_mul(a, xu[v]), df_mul(bb, xw[v])));
-            acc[1][v] = df_add(acc[1][v], df_add(df_mul(a, xw[v]), df_neg(df_mul(bb, xu[v]))));
-          }
+      // EBR entries at a time: their column indices in one load, then all their
+      // gathered rows, then the arithmetic (one round of dependent loads per batch).
+      // Rows hold a multiple of 4 entries and start 4-aligned, so the index and
+      // value loads are aligned vector loads.
+      constexpr int EBR = BLK ? 2 : 4;
+      for (int e = 0; e < w; e += EBR) {
+        int cc[EBR];
+        if constexpr (EBR == 4) {
+          const int4 c4 = __ldg(reinterpret_cast<const int4*>(A.col + base + e));
+          cc[0] = c4.x, cc[1] = c4.y, cc[2] = c4.z, cc[3] = c4.w;
         } else {
-          const DF a{A.val[base + e], vlo[base + e]};
+          const int2 c2 = __ldg(reinterpret_cast<const int2*>(A.col + base + e));
+          cc[0] = c2.x, cc[1] = c2.y;
+        }
+        float4 xv[EBR][NS][2];  // 4 lanes of (hi, lo) pairs per entry and sub-row
 #pragma unroll
-          for (int v = 0; v < VEC; v++) acc[0][v] = df_add(acc[0][v], df_mul(a, xu[v]));
+        for (int t = 0; t < EBR; t++)
+#pragma unroll
+          for (int b = 0; b < NS; b++) {
+            const float4* xp = reinterpret_cast<const float4*>(x + (int64_t)cc[t] * rowW + (int64_t)b * W + l0);
+            xv[t][b][0] = __ldg(xp);
+            xv[t][b][1] = __ldg(xp + 1);
+          }
+        const float4 vh = __ldg(reinterpret_cast<const float4*>(A.val + (base + e) * NV));
+        const float4 vl = __ldg(reinterpret_cast<const float4*>(vlo + (base + e) * NV));
+        const float hv[4] = {vh.x, vh.y, vh.z, vh.w}, lv[4] = {vl.x, vl.y, vl.z, vl.w};
+#pragma unroll
+        for (int t = 0; t < EBR; t++) {
+          DF xu[VEC], xw[VEC];
+#pragma unroll
+          for (int b = 0; b < NS; b++) {
+            DF* d = b == 0 ? xu : xw;
+            d[0] = DF{xv[t][b][0].x, xv[t][b][0].y};
+            d[1] = DF{xv[t][b][0].z, xv[t][b][0].w};
+            d[2] = DF{xv[t][b][1].x, xv[t][b][1].y};
+            d[3] = DF{xv[t][b][1].z, xv[t][b][1].w};
+          }
+          if constexpr (BLK) {
+            const DF a{hv[2 * t], lv[2 * t]};
+            const DF bb{hv[2 * t + 1], lv[2 * t + 1]};
+#pragma unroll
+            for (int v = 0; v < VEC; v++) {
+              acc[0][v] = df_add(acc[0][v], df_add(df_mul(a, xu[v]), df_mul(bb, xw[v])));
+              acc[1][v] = df_add(acc[1][v], df_add(df_mul(a, xw[v]), df_neg(df_mul(bb, xu[v]))));
+            }
+          } else {
+            const DF a{hv[t], lv[t]};
+#pragma unroll
+            for (int v = 0; v < VEC; v++) acc[0][v] = df_add(acc[0][v], df_mul(a, xu[v]));
+          }
         }
       }
       const DF mr{mhi[row], mlo[row]};
@@ -1524,8 +1535,11 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
       for (int b = 0; b < NS; b++) {
         const int64_t off = row * rowW + (int64_t)b * W + l0;
         DF xo[VEC];
-#pragma unroll
-        for (int v = 0; v < VEC; v++) xo[v] = x[off + v];
+        {
+          const float4* xp = reinterpret_cast<const float4*>(x + off);
+          const float4 a = __ldg(xp), c = __ldg(xp + 1);
+          xo[0] = DF{a.x, a.y}, xo[1] = DF{a.z, a.w}, xo[2] = DF{c.x, c.y}, xo[3] = DF{c.z, c.w};
+        }
         Pack<float> ro, po, zo;
 #pragma unroll
         for (int v = 0; v < VEC; v++) zo.v[v] = 0.f;
@@ -1877,7 +1891,6 @@ class EngineT final : public Engine {
     // double-float refinement residual on the FP32 engines, unless a tolerance asks for more than its
     // about 48 bits carry on hard columns; then FP64, as on the FP64 engine
     df_ = sizeof(T) == 4 && o.tol >= kDfMinTol && (!(o.err_tol > 0.0) || o.err_tol >= kDfMinErrTol);
-    pf_cg_ = pf_mg_ = std::max(0, prefetch_env());
     if (o.precond == IFILT_PRECOND_MG) mg_setup();
     P_.mg = mg_on_ ? 1 : 0;
     P_.rn_slot = (!CPLX && o.precond == IFILT_PRECOND_JACOBI) ? 1 : 0;
@@ -2166,7 +2179,6 @@ class EngineT final : public Engine {
 
   void set_width(int W) {
     P_.W = W;
-    P_.pf = pf_cg_;
     P_.ncols = W / LPC;
     P_.pstride = 4 * W;
     P_.spt = W > 0 ? spmm_spt(W) : 1;
@@ -2457,12 +2469,7 @@ class EngineT final : public Engine {
   // The timed launches write only outputs the next iteration recomputes (q,
   // partial sums, multigrid scratch) and see a "live" flag forced to 1.
   int tp_cg_ = kTilePasses, bpsm_cg_ = 0, tp_mg_ = kTilePasses, bpsm_mg_ = 0;  // bpsm 0: occupancy
-  int pf_cg_ = 0, pf_mg_ = 0;  // L2 prefetch of each tile's operands (SpMM, multigrid gathers)
-  // IFILT_PREFETCH=0 / 1 fixes the prefetch choice instead of timing it
-  static int prefetch_env() {
-    const char* e = getenv("IFILT_PREFETCH");
-    return (e && (e[0] == '0' || e[0] == '1')) ? e[0] - '0' : -1;
-  }
+
   Cols mg_cols_{};
   int* tune_live_ = nullptr;
   std::string tune_key(int W) const {
@@ -2488,8 +2495,6 @@ class EngineT final : public Engine {
         bpsm_cg_ = it->second[1];
         tp_mg_ = it->second[2];
         bpsm_mg_ = it->second[3];
-        pf_cg_ = it->second[4];
-        pf_mg_ = it->second[5];
         set_width(W);
         return;
       }
@@ -2511,73 +2516,58 @@ class EngineT final : public Engine {
       return ms;
     };
     const int tps[3] = {4, 8, 16};
-    const int pfe = prefetch_env();
-    std::vector<int> pfs;
-    if (pfe >= 0) pfs = {pfe};
-    else pfs = {0, 1};
     int occ = 1;
     float best = 1e30f;
-    int btp = kTilePasses, bb = 0, bpf = pfs[0];
-    for (int pf : pfs) {
-      for (int tp : tps) {
-        tp_cg_ = tp;
-        bpsm_cg_ = 0;
-        set_width(W);
-        P_.pf = pf;
-        IFILT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)spmm_fn(), kBlock, spmm_smem(W)));
-        for (int bps : {0, occ - 1}) {  // all resident blocks, or one fewer per SM
-          if (bps == occ - 1 && bps < 1) continue;
-          bpsm_cg_ = bps;
-          const int nb = blocks_for(W);
-          const size_t sm = spmm_smem(W);
-          const float ms = timeit([&] {
-            spmm_fn()<<<nb, kBlock, sm, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), Ct, partial_,
-                                               MgArgs<T>{});
-          });
-          if (ms < best) {
-            best = ms;
-            btp = tp;
-            bb = bps;
-            bpf = pf;
-          }
+    int btp = kTilePasses, bb = 0;
+    for (int tp : tps) {
+      tp_cg_ = tp;
+      bpsm_cg_ = 0;
+      set_width(W);
+      IFILT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)spmm_fn(), kBlock, spmm_smem(W)));
+      for (int bps : {0, occ - 1}) {  // all resident blocks, or one fewer per SM
+        if (bps == occ - 1 && bps < 1) continue;
+        bpsm_cg_ = bps;
+        const int nb = blocks_for(W);
+        const size_t sm = spmm_smem(W);
+        const float ms = timeit([&] {
+          spmm_fn()<<<nb, kBlock, sm, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), Ct, partial_,
+                                             MgArgs<T>{});
+        });
+        if (ms < best) {
+          best = ms;
+          btp = tp;
+          bb = bps;
         }
       }
     }
     tp_cg_ = btp;
     bpsm_cg_ = bb;
-    pf_cg_ = bpf;
     if (mg_on_) {
       best = 1e30f;
       btp = kTilePasses;
       bb = 0;
-      bpf = pfs[0];
       mg_cols_ = Ct;
-      for (int pf : pfs) {
-        for (int tp : tps) {
-          for (int bps : {0, 2}) {
-            tp_mg_ = tp;
-            bpsm_mg_ = bps;
-            pf_mg_ = pf;
-            const float ms = timeit([&] { mg_smooth(0, mgb_[0].a, mgb_[0].b, tl_.r, nullptr); });
-            if (ms < best) {
-              best = ms;
-              btp = tp;
-              bb = bps;
-              bpf = pf;
-            }
+      for (int tp : tps) {
+        for (int bps : {0, 2}) {
+          tp_mg_ = tp;
+          bpsm_mg_ = bps;
+          const float ms = timeit([&] { mg_smooth(0, mgb_[0].a, mgb_[0].b, tl_.r, nullptr); });
+          if (ms < best) {
+            best = ms;
+            btp = tp;
+            bb = bps;
           }
         }
       }
       mg_cols_ = C_;
       tp_mg_ = btp;
       bpsm_mg_ = bb;
-      pf_mg_ = bpf;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     set_width(W);
     std::lock_guard<std::mutex> lk(m_->tune_mu);
-    m_->tune[key] = {tp_cg_, bpsm_cg_, tp_mg_, bpsm_mg_, pf_cg_, pf_mg_};
+    m_->tune[key] = {tp_cg_, bpsm_cg_, tp_mg_, bpsm_mg_};
   }
   // ------------------------------------------------------------ multigrid
   static constexpr int kMgMinB = 3;
@@ -2687,7 +2677,6 @@ class EngineT final : public Engine {
     Params Q = P_;
     Q.n = E.n;
     Q.spt = spt_of(E, W, vbytes, mg_minb<EPI>());
-    Q.pf = pf_mg_;
     Q.stage_e = (int)stage_entries_of(E, Q.spt);
     const size_t smem = smem_of(W, 2) + 2 * stage_bytes_of(E, Q.spt, vbytes);
     const long long ntiles = (E.n_slices + Q.spt - 1) / Q.spt;

@@ -150,6 +150,7 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
   const HostPrepared& h = m->host;
   if (slice_h <= 0) slice_h = 64;
   if (slice_h < 4 || slice_h > 1024) fail(IFILT_EINVAL, "ell_slice must be between 4 and 1024 rows");
+  PhaseClock clock("upload");
   m->perm = dev_copy(m, h.perm.data(), h.perm.size(), st);
   m->mass = dev_copy(m, h.mass.data(), h.mass.size(), st);
   std::vector<float> m32(h.mass.begin(), h.mass.end()), m32lo(h.mass.size());
@@ -162,6 +163,7 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
   m->diag_k32 = dev_copy(m, dk32.data(), dk32.size(), st);
   build_ell(m, h.K, slice_h, m->ell_k, st);
   build_csr(m, h.K, m->csr_k, st);
+  clock.lap("K");
   if (h.max_order >= 2) {
     std::vector<double> dg = diagonal(h.G2);
     m->diag_g2 = dev_copy(m, dg.data(), dg.size(), st);
@@ -170,6 +172,7 @@ void upload_mesh(ifilt_mesh_s* m, int32_t slice_h, cudaStream_t st) {
     build_ell(m, h.G2, slice_h, m->ell_g2, st);
     build_csr(m, h.G2, m->csr_g2, st);
   }
+  clock.lap("G2");
   m->ell_gn.assign(h.Gn.size(), DevEll{});
   m->csr_gn.assign(h.Gn.size(), DevCSR{});
   m->diag_gn.assign(h.Gn.size(), nullptr);

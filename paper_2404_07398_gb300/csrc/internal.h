@@ -33,6 +33,15 @@ void set_last_error(const std::string& msg);
                     __FILE__, __LINE__);                                          \
   } while (0)
 
+// Wall-clock phases of preparation, printed to stderr when IFILT_TRACE_PREPARE=1.
+struct PhaseClock {
+  explicit PhaseClock(const char* what);
+  void lap(const char* phase);
+  const char* what;
+  bool on;
+  double t0;
+};
+
 // ---------------------------------------------------------------- host side
 // Compressed sparse rows; `nval` doubles per entry (1 = scalar, 2 = block
 // [[a, b], [-b, a]] stored as (a, b)).
@@ -138,7 +147,7 @@ struct ifilt_mesh_s {
   std::vector<ifilt::DevMgLevel> mg_dev;
   // autotuned launch shapes of the batched solver, per engine kind and tile width
   std::mutex tune_mu;
-  std::map<std::string, std::array<int, 6>> tune;
+  std::map<std::string, std::array<int, 4>> tune;
 };
 
 namespace ifilt {

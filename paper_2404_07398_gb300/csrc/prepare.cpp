@@ -19,8 +19,11 @@
 //   4. G2 = K M^-1 K for order n = 2 (Sect. 2.1.1).
 // Everything is FP64 here; device copies are cast once at upload.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
@@ -309,6 +312,20 @@ HostCSR product_amk(const HostCSR& A, const HostCSR& K, const std::vector<double
 
 }  // namespace
 
+static double wall_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+PhaseClock::PhaseClock(const char* w) : what(w), t0(wall_ms()) {
+  const char* e = getenv("IFILT_TRACE_PREPARE");
+  on = e && e[0] == '1';
+}
+void PhaseClock::lap(const char* phase) {
+  if (!on) return;
+  const double t = wall_ms();
+  fprintf(stderr, "ifilt %s: %-24s %9.1f ms\n", what, phase, t - t0);
+  t0 = t;
+}
+
 HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   if (d.n_vert <= 0 || d.n_tri <= 0 || !d.coords || !d.tri)
     fail(IFILT_EINVAL, "mesh needs n_vert > 0, n_tri > 0, coords and tri");
@@ -334,6 +351,7 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
     if (a == b || b == c || a == c) fail(IFILT_EMESH, "triangle %d repeats a vertex", t);
   }
   Geometry geo{d.coords, d.geometry, d.period_x, d.period_y, d.radius};
+  PhaseClock clock("prepare");
 
   HostPrepared hp;
   hp.placement = d.placement;
@@ -379,6 +397,7 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   bucket(Nv, inc_key, inc_ptr, inc_idx);
   auto corner_v = [&](int32_t c, int q) { return vid[tri[3 * (int64_t)kept[c] + q]]; };
 
+  clock.lap("ocean subset");
   // ---- graph of the n = 1 operator (compact ids)
   Graph g;
   const bool cells = d.placement == IFILT_CELL || d.placement == IFILT_CELL_CIRCUMCENTER;
@@ -431,6 +450,7 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   }
   const int32_t N = g.n;
 
+  clock.lap("graph");
   // ---- 2. device order
   std::vector<int32_t> order(N), rank(N);
   if (d.reorder == IFILT_REORDER_RCM) {
@@ -479,6 +499,7 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
   hp.n_in = (d.placement == IFILT_VERTEX_SCALAR || d.placement == IFILT_VERTEX_VORONOI) ? V : T;
   hp.n_out = cells ? T : V;
 
+  clock.lap("device order");
   // ---- 3. operator and mass in device order
   const int nval = d.placement == IFILT_VERTEX_VECTOR ? 2 : 1;
   hp.K = pattern_from_graph(g, order, rank, nval);
@@ -679,10 +700,12 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
       }
     }
   }
+  clock.lap("operator and mass");
   // ---- 4. order-2 product
   if (d.max_order >= 2) hp.G2 = product_amk(K, K, hp.mass);
   for (int n = 3; n <= d.max_order; n++)
     hp.Gn.push_back(product_amk(n == 3 ? hp.G2 : hp.Gn.back(), K, hp.mass));
+  clock.lap("higher-order products");
   return hp;
 }
 

@@ -361,6 +361,41 @@ def test_certificate_bounds_error():
     assert err <= bound * (1 + 1e-9)
 
 
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector"])
+def test_refined_certificate_is_a_bound_and_tighter(placement):
+    """The refined certificate ||e~||_M + ||r - S e~||_{M^-1} bounds the exact
+    M-norm error of a candidate from above, for a rough perturbation (a large
+    residual hiding a small error: the plain bound overstates it many times)
+    and for a smooth one (the error sits in the correction e~); with 0 steps it
+    is the plain bound."""
+    m = synth.icosphere(4, radius=6371.0, jitter=0.2, seed=25)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=26, polar_cap_deg=10.0)
+    P = oracle.build_problem(m, placement)
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=(P.n_comp, P.n_in))
+    k = 2 * np.pi / 4000.0
+    exact = oracle.filter_dense(P, f, [k], 2)[0]
+    ids = P.out_ids
+    xs = oracle.solve._candidates(P, f, exact)[0]
+    smooth = np.cos(np.arange(xs.size) * 2 * np.pi / xs.size)
+    for pert in (rng.normal(size=xs.size), smooth):
+        x = xs + 1e-6 * np.linalg.norm(xs) / np.linalg.norm(pert) * pert
+        cand = exact.copy()
+        if placement == "vertex_vector":
+            n = ids.size
+            cand[0][ids], cand[1][ids] = x[:n], x[n:]
+        else:
+            cand[0][ids] = x
+        err = np.sqrt(np.sum(P.A * (x - xs) ** 2))
+        (plain, xn), = oracle.residual_certificate(P, f, cand, k, 2)
+        (zero, xn0), = oracle.refined_certificate(P, f, cand, k, 2, iters=0)
+        (ref, _), = oracle.refined_certificate(P, f, cand, k, 2, iters=30)
+        assert abs(zero - plain) <= 1e-12 * plain and xn0 == xn
+        assert err <= ref * (1 + 1e-9) and ref <= plain * (1 + 1e-9)
+        # here the plain bound is about 45 times the error, the refined one within a few percent
+        assert plain > 10.0 * err and ref <= 1.1 * err, (ref / err, plain / err)
+
+
 @pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
 def test_relative_residual_of_x0_exact_and_perturbed(placement):
     """||b - S x|| / ||b - S x0||: exactly 1 at x0 (the paper's initial guess),
