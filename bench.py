@@ -66,13 +66,15 @@ def parse_args():
                     help="iterations per solver step (0: library default, 8 with multigrid); refinement rounds end "
                          "on step boundaries, so short rounds favour short steps")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="FP32 inner reduction per round (0: default)")
-    ap.add_argument("--err-tol", type=float, default=1e-7,
+    ap.add_argument("--err-tol", type=float, default=1e-8,
                     help="also stop each column only at a certified relative M-norm error bound (0: off)")
     ap.add_argument("--reorder", choices=["rcm", "hilbert"], default="rcm", help="device row order of the meshes")
     ap.add_argument("--mg-cycle", choices=["v", "w12"], default="v",
                     help="multigrid cycle (w12: coarse corrections of levels 1 and 2 twice)")
     ap.add_argument("--max-iter", type=int, default=2000,
                     help="Krylov iteration cap per column (the hardest columns need well under 100)")
+    ap.add_argument("--mg-vectors", choices=["fp32", "bf16"], default="fp32",
+                    help="storage of the multigrid preconditioner's work vectors (FP32 arithmetic either way)")
     ap.add_argument("--mg-strength", type=float, default=0.05,
                     help="multigrid aggregation threshold (0: every neighbour, the library default)")
     ap.add_argument("--cache-dir", default="", help="keep the synthetic workload and the prepared meshes "
@@ -220,6 +222,7 @@ def workload_config(args, w, world):
             "precision": args.precision, "precond": getattr(args, "precond", "none"),
             "mg_strength": getattr(args, "mg_strength", 0.0) if getattr(args, "precond", "none") == "mg" else None,
             "mg_cycle": getattr(args, "mg_cycle", "v") if getattr(args, "precond", "none") == "mg" else None,
+            "mg_vectors": getattr(args, "mg_vectors", "fp32") if getattr(args, "precond", "none") == "mg" else None,
             "check_every": getattr(args, "check_every", 0), "max_iter": getattr(args, "max_iter", 0),
             "err_tol": getattr(args, "err_tol", 0.0), "reorder": getattr(args, "reorder", "rcm"),
             "l2": "inputs larger than L2 (GBs per vector), no flush",
@@ -254,7 +257,8 @@ class Ours:
                          precond={"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI,
                                   "mg": api.PRECOND_MG}[args.precond],
                          check_every=args.check_every, inner_tol=args.inner_tol, err_tol=args.err_tol,
-                         max_iter=args.max_iter, mg_cycle={"v": api.MG_V, "w12": api.MG_W12}[args.mg_cycle])
+                         max_iter=args.max_iter, mg_cycle={"v": api.MG_V, "w12": api.MG_W12}[args.mg_cycle],
+                         mg_vectors={"bf16": api.MG_VEC_BF16, "fp32": api.MG_VEC_FP32}[args.mg_vectors])
         K = self.k.size
         self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
         self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")

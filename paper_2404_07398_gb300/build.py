@@ -28,7 +28,9 @@ def nvcc():
 
 
 def _flags(ptxas_verbose=False):
-    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
+    # host code without contracted multiply-adds: the same host results on x86 and Arm, and the
+    # same bits as the device kernels that restate host arithmetic with IEEE operations
+    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-ffp-contract=off",
                 "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", SRC]
     if ptxas_verbose:
         f += ["-Xptxas", "-v"]

@@ -172,7 +172,7 @@ ifilt_status ifilt_prepare_mesh(const ifilt_mesh_desc* desc, void* stream, ifilt
   ifilt_mesh_s* m = new ifilt_mesh_s();
   try {
     IFILT_CUDA(cudaGetDevice(&m->device));
-    m->host = prepare_host(*desc);
+    m->host = prepare_host(*desc, /*products=*/false);  // the upload forms G2 and G_n on the device
     m->host.key = mesh_key(*desc);
     m->slice_h = desc->ell_slice;
     upload_mesh(m, desc->ell_slice, st);
@@ -425,6 +425,8 @@ static void check_opts(ifilt_mesh m, const ifilt_solve_opts* o) {
     fail(IFILT_EINVAL, "negative option");
   if (!(o->err_tol >= 0.0) || !std::isfinite(o->err_tol)) fail(IFILT_EINVAL, "err_tol must be >= 0 and finite");
   if (o->mg_cycle != IFILT_MG_V && o->mg_cycle != IFILT_MG_W12) fail(IFILT_EINVAL, "unknown mg_cycle %d", o->mg_cycle);
+  if (o->mg_vectors != IFILT_MG_VEC_BF16 && o->mg_vectors != IFILT_MG_VEC_FP32)
+    fail(IFILT_EINVAL, "unknown mg_vectors %d", o->mg_vectors);
   if (o->method == IFILT_METHOD_PLAIN && o->err_tol > 0.0)
     fail(IFILT_EINVAL, "the plain method stops on the residual only (err_tol = 0)");
 }

@@ -28,6 +28,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -233,22 +234,100 @@ __device__ __forceinline__ T cvt(MV v) {
 //   PROLONG   out = y + P x_c                (gather of the coarser level)
 constexpr int kEpiCG = 0, kEpiSmooth = 1, kEpiResid = 2, kEpiRestrict = 3, kEpiProlong = 4;
 
-template <typename T>
+template <typename T, typename TR, typename TS>
 struct MgArgs {
   const T* dk;    // diagonal of K_l (SMOOTH)
-  const T* rhs;   // right-hand side of the level (SMOOTH, RESID)
-  const T* own;   // y of PROLONG
+  const TR* rhs;  // right-hand side of the level (SMOOTH, RESID)
+  const TS* own;  // y of PROLONG
   T omega;        // Jacobi weight (SMOOTH)
 };
+
+// VEC lanes of a vector stored as TS (FP64, FP32 or BF16), moved as one load or
+// store of VEC * sizeof(TS) bytes (8, 16 or 32) and converted to or from the
+// arithmetic type T.  BF16 lanes 2i and 2i+1 are the low and high halves of
+// 32-bit word i; a BF16 value widens to FP32 exactly, FP32 narrows to BF16 by
+// round-to-nearest-even.
+template <typename TS, int VEC>
+struct Lanes {
+  static constexpr int B = VEC * (int)sizeof(TS);
+  static_assert(B == 8 || B == 16 || B == 32, "a lane group moves 8, 16 or 32 bytes");
+  uint32_t w[B / 4];
+};
+template <bool NC, typename TS, int VEC>
+__device__ __forceinline__ Lanes<TS, VEC> lanes_ld(const TS* p) {
+  Lanes<TS, VEC> r;
+  if constexpr (Lanes<TS, VEC>::B == 8) {
+    const uint2 u = NC ? __ldg(reinterpret_cast<const uint2*>(p)) : *reinterpret_cast<const uint2*>(p);
+    r.w[0] = u.x, r.w[1] = u.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < Lanes<TS, VEC>::B / 16; c++) {
+      const uint4 u = NC ? __ldg(reinterpret_cast<const uint4*>(p) + c) : reinterpret_cast<const uint4*>(p)[c];
+      r.w[4 * c] = u.x, r.w[4 * c + 1] = u.y, r.w[4 * c + 2] = u.z, r.w[4 * c + 3] = u.w;
+    }
+  }
+  return r;
+}
+template <typename TS, int VEC>
+__device__ __forceinline__ void lanes_st(TS* p, const Lanes<TS, VEC>& r) {
+  if constexpr (Lanes<TS, VEC>::B == 8) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(r.w[0], r.w[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < Lanes<TS, VEC>::B / 16; c++)
+      reinterpret_cast<uint4*>(p)[c] = make_uint4(r.w[4 * c], r.w[4 * c + 1], r.w[4 * c + 2], r.w[4 * c + 3]);
+  }
+}
+template <typename T, typename TS, int VEC>
+__device__ __forceinline__ void lanes_get(const Lanes<TS, VEC>& r, T* v) {
+  if constexpr (sizeof(TS) == 2) {
+#pragma unroll
+    for (int i = 0; i < VEC / 2; i++) {
+      v[2 * i] = (T)__uint_as_float(r.w[i] << 16);
+      v[2 * i + 1] = (T)__uint_as_float(r.w[i] & 0xffff0000u);
+    }
+  } else if constexpr (sizeof(TS) == 4) {
+#pragma unroll
+    for (int i = 0; i < VEC; i++) v[i] = (T)__uint_as_float(r.w[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < VEC; i++) v[i] = (T)__hiloint2double((int)r.w[2 * i + 1], (int)r.w[2 * i]);
+  }
+}
+template <typename T, typename TS, int VEC>
+__device__ __forceinline__ Lanes<TS, VEC> lanes_put(const T* v) {
+  Lanes<TS, VEC> r;
+  if constexpr (sizeof(TS) == 2) {
+#pragma unroll
+    for (int i = 0; i < VEC / 2; i++) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn((float)v[2 * i], (float)v[2 * i + 1]);
+      r.w[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  } else if constexpr (sizeof(TS) == 4) {
+#pragma unroll
+    for (int i = 0; i < VEC; i++) r.w[i] = __float_as_uint((float)v[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < VEC; i++) {
+      r.w[2 * i] = (uint32_t)__double2loint((double)v[i]);
+      r.w[2 * i + 1] = (uint32_t)__double2hiint((double)v[i]);
+    }
+  }
+  return r;
+}
+// the values of v as they read back once stored as TS
+template <typename T, typename TS, int VEC>
+__device__ __forceinline__ void lanes_round(T* v) {
+  if constexpr (sizeof(TS) < sizeof(T)) lanes_get<T, TS, VEC>(lanes_put<T, TS, VEC>(v), v);
+}
 
 // q = M p + shift * acc for one row (all sub-rows), and the row's share of
 // <p, q>: the row's few terms are summed in FP32, then added to the
 // compensated per-thread accumulator.
-template <typename T, bool CPLX, bool BLK>
+template <typename T, typename TS, int VEC, bool CPLX, bool BLK>
 __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, int l0, const T mr,
-                                              const T* sh, T (*acc)[Pack<T>::N], const Pack<T>* own,
-                                              T* __restrict__ q, DotAcc<T>* dacc) {
-  constexpr int VEC = Pack<T>::N;
+                                              const T* sh, T (*acc)[VEC], T (*pr)[VEC],
+                                              TS* __restrict__ q, DotAcc<T>* dacc) {
   constexpr int NS = BLK ? 2 : 1;
   T rowdot[VEC];
 #pragma unroll
@@ -256,29 +335,28 @@ __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, in
 #pragma unroll
   for (int b = 0; b < NS; b++) {
     const int64_t off = r * rowW + (int64_t)b * W + l0;
-    const Pack<T>& pr = own[b];
-    Pack<T> qo;
+    T qo[VEC];
     if constexpr (CPLX) {
 #pragma unroll
       for (int v = 0; v < VEC; v += 2) {
-        const T pre = pr.v[v], pim = pr.v[v + 1];
+        const T pre = pr[b][v], pim = pr[b][v + 1];
         const T qre = mr * pre - sh[v] * acc[b][v + 1];
         const T qim = mr * pim + sh[v] * acc[b][v];
-        qo.v[v] = qre;
-        qo.v[v + 1] = qim;
+        qo[v] = qre;
+        qo[v + 1] = qim;
         rowdot[v] = madd(pre, qre, madd(-pim, qim, rowdot[v]));
         rowdot[v + 1] = madd(pre, qim, madd(pim, qre, rowdot[v + 1]));
       }
     } else {
 #pragma unroll
       for (int v = 0; v < VEC; v++) {
-        const T qv = mr * pr.v[v] + sh[v] * acc[b][v];
-        qo.v[v] = qv;
-        if constexpr (NS == 1) dacc[v].add(pr.v[v], qv);  // a single exact product
-        else rowdot[v] = madd(pr.v[v], qv, rowdot[v]);
+        const T qv = mr * pr[b][v] + sh[v] * acc[b][v];
+        qo[v] = qv;
+        if constexpr (NS == 1) dacc[v].add(pr[b][v], qv);  // a single exact product
+        else rowdot[v] = madd(pr[b][v], qv, rowdot[v]);
       }
     }
-    stp(q + off, qo);
+    lanes_st<TS, VEC>(q + off, lanes_put<T, TS, VEC>(qo));
   }
   if constexpr (CPLX || NS > 1) {
 #pragma unroll
@@ -289,13 +367,13 @@ __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, in
 // Multigrid epilogue for one row: acc holds the K part of the gather (or the
 // whole gather for RESTRICT / PROLONG), accm the M part on coarse levels
 // (NSET = 2); own is x_r (SMOOTH, RESID) or y_r (PROLONG); mdiag is the
-// diagonal of M_l (the lumped mass on the finest level).
-template <typename T, bool CPLX, bool BLK, int EPI, int NSET>
+// diagonal of M_l (the lumped mass on the finest level).  The output is stored
+// as TS; the partial <rhs, out> of a smoothing sweep uses the stored values.
+template <typename T, typename TS, int VEC, bool CPLX, bool BLK, int EPI, int NSET>
 __device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int l0, const T mr, const T gr,
-                                            const Pack<T>* rhs, const T* sh, T (*acc)[Pack<T>::N],
-                                            T (*accm)[Pack<T>::N], const Pack<T>* own, const MgArgs<T>& g,
-                                            T* __restrict__ out, DotAcc<T>* dacc, bool dot) {
-  constexpr int VEC = Pack<T>::N;
+                                            T (*rh)[VEC], const T* sh, T (*acc)[VEC], T (*accm)[VEC],
+                                            T (*own)[VEC], const T omega, TS* __restrict__ out, DotAcc<T>* dacc,
+                                            bool dot) {
   constexpr int NS = BLK ? 2 : 1;
   T rowdot[VEC];
 #pragma unroll
@@ -303,47 +381,47 @@ __device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int 
 #pragma unroll
   for (int b = 0; b < NS; b++) {
     const int64_t off = r * rowW + (int64_t)b * W + l0;
-    Pack<T> o;
+    T o[VEC];
     if constexpr (EPI == kEpiRestrict) {
 #pragma unroll
-      for (int v = 0; v < VEC; v++) o.v[v] = acc[b][v];
+      for (int v = 0; v < VEC; v++) o[v] = acc[b][v];
     } else if constexpr (EPI == kEpiProlong) {
 #pragma unroll
-      for (int v = 0; v < VEC; v++) o.v[v] = own[b].v[v] + acc[b][v];
+      for (int v = 0; v < VEC; v++) o[v] = own[b][v] + acc[b][v];
     } else {
-      const Pack<T>& rh = rhs[b];
       T res[VEC];
 #pragma unroll
       for (int v = 0; v < VEC; v++) {
-        const T mx = NSET == 2 ? accm[b][v] : mr * own[b].v[v];
+        const T mx = NSET == 2 ? accm[b][v] : mr * own[b][v];
         T sx;
         if constexpr (CPLX) sx = (v & 1) ? mx + sh[v] * acc[b][v - 1] : mx - sh[v] * acc[b][v + 1];
         else sx = madd(sh[v], acc[b][v], mx);
-        res[v] = rh.v[v] - sx;
+        res[v] = rh[b][v] - sx;
       }
       if constexpr (EPI == kEpiResid) {
 #pragma unroll
-        for (int v = 0; v < VEC; v++) o.v[v] = res[v];
+        for (int v = 0; v < VEC; v++) o[v] = res[v];
       } else {
         T z[VEC];
         jacobi<T, CPLX, VEC>(mr, gr, sh, res, z);
 #pragma unroll
-        for (int v = 0; v < VEC; v++) o.v[v] = madd(g.omega, z[v], own[b].v[v]);
+        for (int v = 0; v < VEC; v++) o[v] = madd(omega, z[v], own[b][v]);
         if (dot) {
+          lanes_round<T, TS, VEC>(o);
           if constexpr (CPLX) {
 #pragma unroll
             for (int v = 0; v < VEC; v += 2) {
-              rowdot[v] = madd(rh.v[v], o.v[v], madd(-rh.v[v + 1], o.v[v + 1], rowdot[v]));
-              rowdot[v + 1] = madd(rh.v[v], o.v[v + 1], madd(rh.v[v + 1], o.v[v], rowdot[v + 1]));
+              rowdot[v] = madd(rh[b][v], o[v], madd(-rh[b][v + 1], o[v + 1], rowdot[v]));
+              rowdot[v + 1] = madd(rh[b][v], o[v + 1], madd(rh[b][v + 1], o[v], rowdot[v + 1]));
             }
           } else {
 #pragma unroll
-            for (int v = 0; v < VEC; v++) rowdot[v] = madd(rh.v[v], o.v[v], rowdot[v]);
+            for (int v = 0; v < VEC; v++) rowdot[v] = madd(rh[b][v], o[v], rowdot[v]);
           }
         }
       }
     }
-    stp(out + off, o);
+    lanes_st<TS, VEC>(out + off, lanes_put<T, TS, VEC>(o));
   }
   if constexpr (EPI == kEpiSmooth) {
     if (dot) {
@@ -406,18 +484,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// q = M p + shift * (G p) for every lane, with the per-block partials of <p, q>.
-// Work is cut into tiles of `spt` ELL slices.  A tile's column indices and
-// values are bulk-copied into one of two shared-memory buffers while the block
-// works on the previous tile, so a row waits on one round of global loads: its
-// own row of p and all gathered neighbour rows (EB entries at a time) are
-// issued before any of them is used.
-template <typename T, typename MV, bool CPLX, bool BLK, int EB, int MINB, int EPI = kEpiCG, int NSET = 1>
-__global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Params P, int n_slices, const T* __restrict__ p,
-                                                         T* __restrict__ q, const T* __restrict__ mass,
-                                                         Cols C, double* __restrict__ partial, MgArgs<T> mg) {
+// q = M p + shift * (G p) for every lane, with the per-block partials of <p, q>
+// (or a multigrid operation, EPI).  Work is cut into tiles of `spt` ELL slices.
+// A tile's column indices and values are bulk-copied into one of two
+// shared-memory buffers while the block works on the previous tile, so a row
+// waits on one round of global loads: its own row of p and all gathered
+// neighbour rows (EB entries at a time) are issued before any of them is used.
+// Vectors are stored as TS (the right-hand side of a multigrid level as TRS,
+// the output as TO) and computed in T; a thread owns VEC consecutive lanes of
+// a row.
+template <typename T, typename MV, typename TS, typename TRS, typename TO, int VEC, bool CPLX, bool BLK, int EB,
+          int MINB, int EPI = kEpiCG, int NSET = 1>
+__global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Params P, int n_slices, const TS* __restrict__ p,
+                                                         TO* __restrict__ q, const T* __restrict__ mass,
+                                                         Cols C, double* __restrict__ partial, MgArgs<T, TRS, TS> mg) {
   if (*C.live == 0) return;
-  constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
   constexpr int NV = (BLK ? 2 : 1) * NSET;  // values per ELL entry
   constexpr int NB = BLK ? 2 : 1;           // values of one operator per entry
@@ -515,39 +596,48 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
         const int sl = lr / H;
         const int w = s_w[b][sl];
         const int eb = s_o[b][sl] + (lr - sl * H) * w;
-        Pack<T> pr[NS];
+        Lanes<TS, VEC> pr[NS];
         if constexpr (EPI == kEpiProlong) {
 #pragma unroll
-          for (int s = 0; s < NS; s++) pr[s] = ldv(mg.own + r * rowW + (int64_t)s * W + l0);
+          for (int s = 0; s < NS; s++) pr[s] = lanes_ld<false, TS, VEC>(mg.own + r * rowW + (int64_t)s * W + l0);
         } else if constexpr (EPI != kEpiRestrict) {
 #pragma unroll
-          for (int s = 0; s < NS; s++) pr[s] = ldp(p + r * rowW + (int64_t)s * W + l0);
+          for (int s = 0; s < NS; s++) pr[s] = lanes_ld<true, TS, VEC>(p + r * rowW + (int64_t)s * W + l0);
         }
         // the row's own operands are loaded with its gathers: one round of global loads per row
         T mrow = (T)0, grow = (T)0;
-        Pack<T> rrow[NS];
+        Lanes<TRS, VEC> rrow[NS];
         if constexpr (EPI == kEpiCG || EPI == kEpiSmooth || EPI == kEpiResid) mrow = mass[r];
         if constexpr (EPI == kEpiSmooth) grow = mg.dk[r];
         if constexpr (EPI == kEpiSmooth || EPI == kEpiResid) {
 #pragma unroll
-          for (int s = 0; s < NS; s++) rrow[s] = ldv(mg.rhs + r * rowW + (int64_t)s * W + l0);
+          for (int s = 0; s < NS; s++) rrow[s] = lanes_ld<false, TRS, VEC>(mg.rhs + r * rowW + (int64_t)s * W + l0);
         }
         T acc[NS][VEC], accm[NS][VEC];
 #pragma unroll
         for (int s = 0; s < NS; s++)
 #pragma unroll
           for (int v = 0; v < VEC; v++) acc[s][v] = accm[s][v] = (T)0;
+        // EB entries at a time (a multiple of 4 entries, or 2 for a 2-entry batch:
+        // rows hold a multiple of 4 entries, so a batch never runs past the row)
         for (int e = 0; e < w; e += EB) {
-          Pack<T> nb[EB][NS];
+          Lanes<TS, VEC> nb[EB][NS];
 #pragma unroll
           for (int h = 0; h < EB; h += 4) {
             if (h == 0 || e + h < w) {
-              const int4 c4 = *reinterpret_cast<const int4*>(scol + eb + e + h);
-              const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+              int cc[4];
+              if constexpr (EB >= 4) {
+                const int4 c4 = *reinterpret_cast<const int4*>(scol + eb + e + h);
+                cc[0] = c4.x, cc[1] = c4.y, cc[2] = c4.z, cc[3] = c4.w;
+              } else {
+                const int2 c2 = *reinterpret_cast<const int2*>(scol + eb + e);
+                cc[0] = c2.x, cc[1] = c2.y, cc[2] = cc[3] = 0;
+              }
 #pragma unroll
-              for (int t = 0; t < 4; t++)
+              for (int t = 0; t < (EB >= 4 ? 4 : EB); t++)
 #pragma unroll
-                for (int s = 0; s < NS; s++) nb[h + t][s] = ldp(p + (int64_t)cc[t] * rowW + (int64_t)s * W + l0);
+                for (int s = 0; s < NS; s++)
+                  nb[h + t][s] = lanes_ld<true, TS, VEC>(p + (int64_t)cc[t] * rowW + (int64_t)s * W + l0);
             }
           }
 #pragma unroll
@@ -555,30 +645,33 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
             if (h == 0 || e + h < w) {
               const MV* vv = sval + (size_t)(eb + e + h) * NV;
 #pragma unroll
-              for (int t = 0; t < 4; t++) {
+              for (int t = 0; t < (EB >= 4 ? 4 : EB); t++) {
+                T xu[VEC], xw[VEC];
+                lanes_get<T, TS, VEC>(nb[h + t][0], xu);
                 if constexpr (BLK) {
+                  lanes_get<T, TS, VEC>(nb[h + t][1], xw);
                   const T a = cvt<T>(vv[NV * t]), bb = cvt<T>(vv[NV * t + 1]);
 #pragma unroll
                   for (int v = 0; v < VEC; v++) {
-                    acc[0][v] = madd(a, nb[h + t][0].v[v], madd(bb, nb[h + t][1].v[v], acc[0][v]));
-                    acc[1][v] = madd(a, nb[h + t][1].v[v], madd(-bb, nb[h + t][0].v[v], acc[1][v]));
+                    acc[0][v] = madd(a, xu[v], madd(bb, xw[v], acc[0][v]));
+                    acc[1][v] = madd(a, xw[v], madd(-bb, xu[v], acc[1][v]));
                   }
                   if constexpr (NSET == 2) {
                     const T am = cvt<T>(vv[NV * t + NB]), bm = cvt<T>(vv[NV * t + NB + 1]);
 #pragma unroll
                     for (int v = 0; v < VEC; v++) {
-                      accm[0][v] = madd(am, nb[h + t][0].v[v], madd(bm, nb[h + t][1].v[v], accm[0][v]));
-                      accm[1][v] = madd(am, nb[h + t][1].v[v], madd(-bm, nb[h + t][0].v[v], accm[1][v]));
+                      accm[0][v] = madd(am, xu[v], madd(bm, xw[v], accm[0][v]));
+                      accm[1][v] = madd(am, xw[v], madd(-bm, xu[v], accm[1][v]));
                     }
                   }
                 } else {
                   const T a = cvt<T>(vv[NV * t]);
 #pragma unroll
-                  for (int v = 0; v < VEC; v++) acc[0][v] = madd(a, nb[h + t][0].v[v], acc[0][v]);
+                  for (int v = 0; v < VEC; v++) acc[0][v] = madd(a, xu[v], acc[0][v]);
                   if constexpr (NSET == 2) {
                     const T am = cvt<T>(vv[NV * t + NB]);
 #pragma unroll
-                    for (int v = 0; v < VEC; v++) accm[0][v] = madd(am, nb[h + t][0].v[v], accm[0][v]);
+                    for (int v = 0; v < VEC; v++) accm[0][v] = madd(am, xu[v], accm[0][v]);
                   }
                 }
               }
@@ -592,9 +685,19 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
             for (int v = 0; v < VEC; v++) dacc[v].spill(sred[tr * W + l0 + v]);
           }
         }
-        if constexpr (EPI == kEpiCG) spmm_epilogue<T, CPLX, BLK>(r, rowW, W, l0, mrow, sh, acc, pr, q, dacc);
+        T own[NS][VEC], rh[NS][VEC];
+        if constexpr (EPI != kEpiRestrict) {
+#pragma unroll
+          for (int s = 0; s < NS; s++) lanes_get<T, TS, VEC>(pr[s], own[s]);
+        }
+        if constexpr (EPI == kEpiSmooth || EPI == kEpiResid) {
+#pragma unroll
+          for (int s = 0; s < NS; s++) lanes_get<T, TRS, VEC>(rrow[s], rh[s]);
+        }
+        if constexpr (EPI == kEpiCG) spmm_epilogue<T, TO, VEC, CPLX, BLK>(r, rowW, W, l0, mrow, sh, acc, own, q, dacc);
         else
-          mg_epilogue<T, CPLX, BLK, EPI, NSET>(r, rowW, W, l0, mrow, grow, rrow, sh, acc, accm, pr, mg, q, dacc, dot);
+          mg_epilogue<T, TO, VEC, CPLX, BLK, EPI, NSET>(r, rowW, W, l0, mrow, grow, rh, sh, acc, accm, own, mg.omega,
+                                                         q, dacc, dot);
       }
     }
     if ((int)threadIdx.x < ncnt) {
@@ -732,9 +835,9 @@ __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T
   }
 }
 
-// p = r + beta p
-template <typename T, bool CPLX, bool BLK, bool PRE>
-__global__ void __launch_bounds__(kBlock) direction_kernel(Params P, T* __restrict__ p, const T* __restrict__ r,
+// p = r + beta p (r: the residual, or the preconditioned z stored as TZ)
+template <typename T, typename TZ, bool CPLX, bool BLK, bool PRE>
+__global__ void __launch_bounds__(kBlock) direction_kernel(Params P, T* __restrict__ p, const TZ* __restrict__ r,
                                                            Cols C, const T* __restrict__ mass,
                                                            const T* __restrict__ gdiag) {
   if (*C.live == 0) return;
@@ -760,7 +863,8 @@ __global__ void __launch_bounds__(kBlock) direction_kernel(Params P, T* __restri
     for (int b = 0; b < NS; b++) {
       const int64_t off = row * rowW + (int64_t)b * W + l0;
       Pack<T> pv = ldv(p + off);
-      Pack<T> rv = ldv(r + off);
+      Pack<T> rv;
+      lanes_get<T, TZ, VEC>(lanes_ld<false, TZ, VEC>(r + off), rv.v);
       if constexpr (PRE) {  // p = D^-1 r + beta p
         T zv[VEC];
         jacobi<T, CPLX, VEC>(mr, gr, sh, rv.v, zv);
@@ -1239,13 +1343,13 @@ __global__ void finish_rho_kernel(Params P, int nb, const double* __restrict__ p
   C.beta[2 * col + 1] = bi;
 }
 
-// x = w D^-1 rhs on a multigrid level (the first smoothing sweep from zero)
-template <typename T, bool CPLX, bool BLK>
-__global__ void __launch_bounds__(kBlock) mg_jacobi_kernel(Params P, const T* __restrict__ rhs, T* __restrict__ x,
+// x = w D^-1 rhs on a multigrid level (the first smoothing sweep from zero);
+// rhs stored as TR, x as TS, VEC lanes per thread
+template <typename T, typename TR, typename TS, int VEC, bool CPLX, bool BLK>
+__global__ void __launch_bounds__(kBlock) mg_jacobi_kernel(Params P, const TR* __restrict__ rhs, TS* __restrict__ x,
                                                            const T* __restrict__ mdiag, const T* __restrict__ kdiag,
                                                            Cols C, T omega) {
   if (*C.live == 0) return;
-  constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
   const int W = P.W;
   const int TPR = W / VEC;
@@ -1262,13 +1366,13 @@ __global__ void __launch_bounds__(kBlock) mg_jacobi_kernel(Params P, const T* __
 #pragma unroll
     for (int b = 0; b < NS; b++) {
       const int64_t off = row * rowW + (int64_t)b * W + l0;
-      const Pack<T> rv = ldv(rhs + off);
+      T rv[VEC];
+      lanes_get<T, TR, VEC>(lanes_ld<false, TR, VEC>(rhs + off), rv);
       T z[VEC];
-      jacobi<T, CPLX, VEC>(mr, kr, sh, rv.v, z);
-      Pack<T> o;
+      jacobi<T, CPLX, VEC>(mr, kr, sh, rv, z);
 #pragma unroll
-      for (int v = 0; v < VEC; v++) o.v[v] = omega * z[v];
-      stp(x + off, o);
+      for (int v = 0; v < VEC; v++) z[v] *= omega;
+      lanes_st<TS, VEC>(x + off, lanes_put<T, TS, VEC>(z));
     }
   }
 }
@@ -1466,6 +1570,30 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
       for (int b = 0; b < NS; b++)
 #pragma unroll
         for (int v = 0; v < VEC; v++) acc[b][v] = DF{0.f, 0.f};
+      // The row's source values (e0, g0, x0 of each refreshed column): loaded
+      // before its gathers, so that both wait out one memory latency together,
+      // where the registers allow it (scalar rows); after them for 2x2 blocks.
+      constexpr int SV = CPLX ? VEC / 2 : VEC;  // source values per sub-row: one per column
+      constexpr bool HOIST = !BLK;
+      DF se0[NS][SV], sg0[NS][SV];
+      float sx0[NS][SV];
+      auto load_sources = [&]() {
+#pragma unroll
+        for (int b = 0; b < NS; b++)
+#pragma unroll
+          for (int c = 0; c < SV; c++) {
+            const int v = CPLX ? 2 * c : c;
+            se0[b][c] = sg0[b][c] = DF{0.f, 0.f};
+            sx0[b][c] = 0.f;
+            if (mine[v]) {  // a retired column's source may be gone
+              const DF* sb = bptr[src[v]] + row * NS + b;
+              se0[b][c] = sb[0];
+              sg0[b][c] = sb[2 * sstride];
+              sx0[b][c] = reinterpret_cast<const float*>(bptr[src[v]] + 3 * sstride)[row * NS + b];
+            }
+          }
+      };
+      if constexpr (HOIST) load_sources();
       // EBR entries at a time: their column indices in one load, then all their
       // gathered rows, then the arithmetic (one round of dependent loads per batch).
       // Rows hold a multiple of 4 entries and start 4-aligned, so the index and
@@ -1518,6 +1646,7 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
           }
         }
       }
+      if constexpr (!HOIST) load_sources();
       const DF mr{mhi[row], mlo[row]};
       const float mrf = mhi[row];
       const float gr = gdiag ? gdiag[row] : 0.f;
@@ -1546,14 +1675,8 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
         if constexpr (CPLX) {
 #pragma unroll
           for (int v = 0; v < VEC; v += 2) {
-            DF e0{0.f, 0.f}, g0{0.f, 0.f};
-            float x0 = 0.f;
-            if (mine[v]) {  // a retired column's source may be gone
-              const DF* sb = bptr[src[v]] + row * NS + b;
-              e0 = sb[0];
-              g0 = sb[2 * sstride];
-              x0 = reinterpret_cast<const float*>(bptr[src[v]] + 3 * sstride)[row * NS + b];
-            }
+            const DF e0 = se0[b][v / 2], g0 = sg0[b][v / 2];
+            const float x0 = sx0[b][v / 2];
             // r_re = e0 - (m d_re - s acc_im),  r_im = -s g0 - (m d_im + s acc_re)
             const DF q_re = df_add(df_mul(mr, xo[v]), df_neg(df_mul(sh[v], acc[b][v + 1])));
             const DF q_im = df_add(df_mul(mr, xo[v + 1]), df_mul(sh[v], acc[b][v]));
@@ -1582,14 +1705,8 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
         } else {
 #pragma unroll
           for (int v = 0; v < VEC; v++) {
-            DF e0{0.f, 0.f}, g0{0.f, 0.f};
-            float x0 = 0.f;
-            if (mine[v]) {
-              const DF* sb = bptr[src[v]] + row * NS + b;
-              e0 = sb[0];
-              g0 = sb[2 * sstride];
-              x0 = reinterpret_cast<const float*>(bptr[src[v]] + 3 * sstride)[row * NS + b];
-            }
+            const DF e0 = se0[b][v], g0 = sg0[b][v];
+            const float x0 = sx0[b][v];
             const DF q = df_add(df_mul(mr, xo[v]), df_mul(sh[v], acc[b][v]));
             const DF rv = df_add(df_add(e0, df_neg(df_mul(sh[v], g0))), df_neg(q));
             const float t = rv.hi + rv.lo;
@@ -1780,9 +1897,17 @@ void cols_upload(const Cols& C, const HostCols& H, int n, cudaStream_t st) {
   IFILT_CUDA(cudaStreamSynchronize(st));  // the host vectors must outlive the copies
 }
 
-template <typename T, typename MV, bool CPLX, bool BLK>
+// T: arithmetic and Krylov-vector type; MV: stored operator values; TM: stored
+// multigrid vectors (the preconditioner's work vectors, computed in T; the
+// Krylov vectors, the refinement and the certificates never see them).
+template <typename T, typename MV, typename TM, bool CPLX, bool BLK>
 class EngineT final : public Engine {
   static constexpr int VEC = Pack<T>::N;
+#ifdef IFILT_MG_LANES
+  static constexpr int VM = IFILT_MG_LANES;  // experiment: lanes per thread in the multigrid kernels
+#else
+  static constexpr int VM = 16 / (int)sizeof(TM);  // lanes per thread in the multigrid kernels (16-byte loads)
+#endif
   static constexpr int NS = BLK ? 2 : 1;
   static constexpr int LPC = CPLX ? 2 : 1;  // lanes per column
   static constexpr int NVAL = BLK ? 2 : 1;
@@ -1934,19 +2059,25 @@ class EngineT final : public Engine {
       if (s.src >= 0 && !s.retired) c++;
     return c;
   }
-  int lanes_for(int ncol) const { return (ncol * LPC + 3) / 4 * 4; }
-  size_t smem_of(int W, int slots2) const {
-    return (size_t)(kBlock / (W / VEC)) * (size_t)W * slots2 / 2 * sizeof(double);
+  // lanes of a tile: a multiple of the lanes one thread moves (4, or VM in the multigrid kernels)
+  int lanes_for(int ncol) const {
+    const int g = mg_on_ ? std::max(4, VM) : 4;
+    return (ncol * LPC + g - 1) / g * g;
+  }
+  size_t smem_of(int W, int slots2, int vec = VEC) const {
+    return (size_t)(kBlock / (W / vec)) * (size_t)W * slots2 / 2 * sizeof(double);
   }
   // SpMM instance: gathers issued EB entries at a time (4 when no row holds
   // more, as for the cell operator); FP32 2x2 blocks trade occupancy for more
   // loads in flight per thread.
-  using SpmmFn = void (*)(EllView<MV>, Params, int, const T*, T*, const T*, Cols, double*, MgArgs<T>);
+  using SpmmFn = void (*)(EllView<MV>, Params, int, const T*, T*, const T*, Cols, double*, MgArgs<T, T, T>);
   static constexpr int kMinB = (BLK && sizeof(T) == 4) ? IFILT_SPMM_MINB_BLK : IFILT_SPMM_MINB;
   SpmmFn spmm_fn() const {
-    if constexpr (sizeof(T) == 8) return spmm_kernel<T, MV, CPLX, BLK, 4, kMinB>;
-    else if constexpr (BLK) return spmm_kernel<T, MV, CPLX, BLK, IFILT_SPMM_EB_BLK, kMinB>;
-    else return E_->max_width <= 4 ? spmm_kernel<T, MV, CPLX, BLK, 4, kMinB> : spmm_kernel<T, MV, CPLX, BLK, 8, kMinB>;
+    if constexpr (sizeof(T) == 8) return spmm_kernel<T, MV, T, T, T, VEC, CPLX, BLK, 4, kMinB>;
+    else if constexpr (BLK) return spmm_kernel<T, MV, T, T, T, VEC, CPLX, BLK, IFILT_SPMM_EB_BLK, kMinB>;
+    else
+      return E_->max_width <= 4 ? spmm_kernel<T, MV, T, T, T, VEC, CPLX, BLK, 4, kMinB>
+                                : spmm_kernel<T, MV, T, T, T, VEC, CPLX, BLK, 8, kMinB>;
   }
   // ELL entries of a stage buffer holding `spt` slices (each slice starts on an
   // 8-entry boundary, so a slice spans at most 7 entries more than it holds)
@@ -2109,17 +2240,18 @@ class EngineT final : public Engine {
     for (int it = 0; it < m_it_; it++) {
       if (mg_on_) {
         // preconditioned order: z = V(r), beta from <r, z>, p = z + beta p, then q = S p ...
-        const T* z = vcycle(0, tl_.r);
+        vcycle(0, tl_.r, tl_.q);  // z = V(r) into q (free until the SpMM below)
+        const T* z = tl_.q;
         chk("vcycle");
         finish_rho_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbz_, partial2_, C_);
         chk("finish_rho");
         pmark(kCatFinish, 0.0);
-        direction_kernel<T, CPLX, BLK, false><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, z, C_, mass_t(), nullptr);
+        direction_kernel<T, T, CPLX, BLK, false><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, z, C_, mass_t(), nullptr);
         chk("direction");
         pmark(kCatDirection, 3.0 * vb);
       }
       spmm_fn()<<<nb_, kBlock, sm2, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), C_, partial_,
-                                            MgArgs<T>{});
+                                            MgArgs<T, T, T>{});
       chk("spmm");
       pmark(kCatSpmm, 2.0 * vb + ell_b + rows_t);
       finish_alpha_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
@@ -2138,9 +2270,9 @@ class EngineT final : public Engine {
       pmark(kCatFinish, 0.0);
       if (mg_on_) continue;
       if (gdiag_t())
-        direction_kernel<T, CPLX, BLK, true><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_, mass_t(), gdiag_t());
+        direction_kernel<T, T, CPLX, BLK, true><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_, mass_t(), gdiag_t());
       else
-        direction_kernel<T, CPLX, BLK, false><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_, mass_t(), nullptr);
+        direction_kernel<T, T, CPLX, BLK, false><<<nbd_, kBlock, 0, st_>>>(P_, tl_.p, tl_.r, C_, mass_t(), nullptr);
       chk("direction");
       pmark(kCatDirection, 3.0 * vb + pre_b);
     }
@@ -2164,8 +2296,8 @@ class EngineT final : public Engine {
     nbu_ = std::min(nb_max_, grid_for(pre ? (const void*)update_kernel<T, CPLX, BLK, true>
                                           : (const void*)update_kernel<T, CPLX, BLK, false>,
                                       kBlock, smem_of(P_.W, 4), rows_threads));
-    nbd_ = std::min(nb_max_, grid_for(pre ? (const void*)direction_kernel<T, CPLX, BLK, true>
-                                          : (const void*)direction_kernel<T, CPLX, BLK, false>,
+    nbd_ = std::min(nb_max_, grid_for(pre ? (const void*)direction_kernel<T, T, CPLX, BLK, true>
+                                          : (const void*)direction_kernel<T, T, CPLX, BLK, false>,
                                       kBlock, 0, rows_threads));
     launch_check("before capture", nb_, 0, P_.W);
     if (!use_graph_) return;
@@ -2531,7 +2663,7 @@ class EngineT final : public Engine {
         const size_t sm = spmm_smem(W);
         const float ms = timeit([&] {
           spmm_fn()<<<nb, kBlock, sm, st_>>>(A_, P_, E_->n_slices, tl_.p, tl_.q, mass_t(), Ct, partial_,
-                                             MgArgs<T>{});
+                                             MgArgs<T, T, T>{});
         });
         if (ms < best) {
           best = ms;
@@ -2574,9 +2706,9 @@ class EngineT final : public Engine {
   static constexpr int kMgCoarseSweeps = 4;  // Jacobi sweeps on the coarsest level
   static constexpr double kMgOmega = 2.0 / 3.0;
   struct MgBuf {
-    T* r = nullptr;  // right-hand side of the level (levels >= 1)
-    T* a = nullptr;
-    T* b = nullptr;
+    TM* r = nullptr;  // right-hand side of the level (levels >= 1)
+    TM* a = nullptr;
+    TM* b = nullptr;
   };
   bool mg_on_ = false;
   const std::vector<DevMgLevel>* mgl_ = nullptr;
@@ -2591,9 +2723,23 @@ class EngineT final : public Engine {
   static constexpr int mg_minb() {
     return (BLK && (EPI == kEpiSmooth || EPI == kEpiResid)) ? IFILT_MG_MINB_BLK : kMgMinB;
   }
+  // right-hand side type of a gather: the Krylov residual (T) for the sweeps and
+  // residuals of the finest level (NSET = 1), a multigrid vector (TM) otherwise
   template <int EPI, int NSET>
+  using MgTR = std::conditional_t<NSET == 1 && (EPI == kEpiSmooth || EPI == kEpiResid), T, TM>;
+  // entries gathered per batch: 2x2 blocks of two sub-rows take 2 at a time when a thread moves 8
+  // lanes (register room), else 4
+  static constexpr int kMgEB = (BLK && VM > 4) ? 2 : 4;
+  // output type of a gather: TM, or T for the last sweep of the finest level, whose
+  // result z = V(r) enters the Krylov recursion (<r, z> and p = z + beta p): it is
+  // kept unrounded so that the preconditioner stays the same symmetric operator
+  // from one iteration to the next
+  template <int EPI, int NSET, bool FINAL>
+  using MgTO = std::conditional_t<FINAL, T, TM>;
+  template <int EPI, int NSET, bool FINAL = false>
   static const void* mg_fn() {
-    return (const void*)spmm_kernel<T, T, CPLX, BLK, 4, mg_minb<EPI>(), EPI, NSET>;
+    return (const void*)spmm_kernel<T, T, TM, MgTR<EPI, NSET>, MgTO<EPI, NSET, FINAL>, VM, CPLX, BLK, kMgEB,
+                                    mg_minb<EPI>(), EPI, NSET>;
   }
   static int64_t stage_entries_of(const DevEll& E, int spt) {
     return (int64_t)spt * ((int64_t)E.slice_h * E.max_width + 8);
@@ -2603,7 +2749,7 @@ class EngineT final : public Engine {
     return (size_t)((e * 4 + 15) / 16 * 16 + (e * vbytes + 15) / 16 * 16);
   }
   int spt_of(const DevEll& E, int W, int vbytes, int minb) const {
-    const int RPP = kBlock / (W / VEC);
+    const int RPP = kBlock / (W / VM);
     int spt = std::max(1, (RPP * tp_mg_ + E.slice_h - 1) / E.slice_h);
     while (spt > 1 && stage_bytes_of(E, spt, vbytes) > (size_t)kStageBytes) spt--;
     const long long want = (long long)n_sms_ * minb * 8;
@@ -2624,9 +2770,10 @@ class EngineT final : public Engine {
           fail(IFILT_EINVAL, "multigrid level %zu: ELL slice exceeds the shared-memory stage", l);
     }
     if constexpr (sizeof(T) == 4) {
-      const int smax = (int)(kBlock * VEC * sizeof(double) + 2 * kStageMax);
+      const int smax = (int)(kBlock * VM * sizeof(double) + 2 * kStageMax);
       const void* fns[] = {mg_fn<kEpiSmooth, 1>(), mg_fn<kEpiSmooth, 2>(), mg_fn<kEpiResid, 1>(),
-                           mg_fn<kEpiResid, 2>(), mg_fn<kEpiRestrict, 1>(), mg_fn<kEpiProlong, 1>()};
+                           mg_fn<kEpiResid, 2>(), mg_fn<kEpiRestrict, 1>(), mg_fn<kEpiProlong, 1>(),
+                           mg_fn<kEpiSmooth, 1, true>()};
       for (const void* f : fns)
         IFILT_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
       mg_on_ = true;
@@ -2637,7 +2784,7 @@ class EngineT final : public Engine {
     int64_t b = 0;
     for (size_t l = 0; l < mgl_->size(); l++) {
       const int64_t rows = l == 0 ? n_ : (*mgl_)[l].n;
-      const int64_t vb = (rows * NS * W * (int64_t)sizeof(T) + 255) / 256 * 256;
+      const int64_t vb = (rows * NS * W * (int64_t)sizeof(TM) + 255) / 256 * 256;
       b += (l == 0 ? 2 : 3) * vb;
     }
     return b;
@@ -2656,70 +2803,79 @@ class EngineT final : public Engine {
     mgb_.resize(mgl_->size());
     for (size_t l = 0; l < mgl_->size(); l++) {
       const int64_t rows = l == 0 ? n_ : (*mgl_)[l].n;
-      const int64_t vb = (rows * NS * W * (int64_t)sizeof(T) + 255) / 256 * 256;
+      const int64_t vb = (rows * NS * W * (int64_t)sizeof(TM) + 255) / 256 * 256;
       if (l > 0) {
-        mgb_[l].r = (T*)p;
+        mgb_[l].r = (TM*)p;
         p += vb;
       }
-      mgb_[l].a = (T*)p;
+      mgb_[l].a = (TM*)p;
       p += vb;
-      mgb_[l].b = (T*)p;
+      mgb_[l].b = (TM*)p;
       p += vb;
     }
   }
 
   // one gather-kernel launch on a multigrid operator; returns its block count
-  template <int EPI, int NSET>
-  int mg_gather(const DevEll& E, const T* src, T* out, const T* mdiag, const T* kd, const T* rhs, const T* own,
-                double* partial, double omega = kMgOmega) {
+  template <int EPI, int NSET, bool FINAL = false>
+  int mg_gather(const DevEll& E, const TM* src, void* out, const T* mdiag, const T* kd, const void* rhs,
+                const TM* own, double* partial, double omega = kMgOmega) {
     const int W = P_.W;
     const int vbytes = NVAL * NSET * (int)sizeof(T);
     Params Q = P_;
     Q.n = E.n;
     Q.spt = spt_of(E, W, vbytes, mg_minb<EPI>());
     Q.stage_e = (int)stage_entries_of(E, Q.spt);
-    const size_t smem = smem_of(W, 2) + 2 * stage_bytes_of(E, Q.spt, vbytes);
+    const size_t smem = smem_of(W, 2, VM) + 2 * stage_bytes_of(E, Q.spt, vbytes);
     const long long ntiles = (E.n_slices + Q.spt - 1) / Q.spt;
-    int blocks = std::min(nb_max_, grid_for(mg_fn<EPI, NSET>(), kBlock, smem, ntiles * kBlock));
+    int blocks = std::min(nb_max_, grid_for(mg_fn<EPI, NSET, FINAL>(), kBlock, smem, ntiles * kBlock));
     if (bpsm_mg_ > 0) blocks = std::min(blocks, n_sms_ * bpsm_mg_);
-    spmm_kernel<T, T, CPLX, BLK, 4, mg_minb<EPI>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
-        ell_view<T>(E), Q, E.n_slices, src, out, mdiag, mg_cols_, partial, MgArgs<T>{kd, rhs, own, (T)omega});
+    using TR = MgTR<EPI, NSET>;
+    using TO = MgTO<EPI, NSET, FINAL>;
+    spmm_kernel<T, T, TM, TR, TO, VM, CPLX, BLK, kMgEB, mg_minb<EPI>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
+        ell_view<T>(E), Q, E.n_slices, src, static_cast<TO*>(out), mdiag, mg_cols_, partial,
+        MgArgs<T, TR, TM>{kd, static_cast<const TR*>(rhs), own, (T)omega});
     return blocks;
   }
   // S_l-operations: level 0 uses the mesh's K and lumped mass, coarser levels their (K, M) pair
   // (FP32 engines only: the FP64 engine refuses multigrid in mg_setup).  Each records its
   // category and algorithmic bytes for the profile.
   int64_t mg_rows(size_t l) const { return l == 0 ? n_ : (int64_t)(*mgl_)[l].n; }
-  double mg_vb(size_t l) const { return (double)mg_rows(l) * NS * P_.W * sizeof(T); }
+  double mg_vb(size_t l) const { return (double)mg_rows(l) * NS * P_.W * sizeof(TM); }
+  // a level's right-hand side: the Krylov residual on level 0, a multigrid vector below
+  double mg_vb_rhs(size_t l) const { return l == 0 ? (double)n_ * NS * P_.W * sizeof(T) : mg_vb(l); }
   double mg_ell_b(const DevEll& E, int nset) const {
     return (double)E.entries * (4.0 + (double)nset * NVAL * sizeof(T));
   }
-  int mg_smooth(size_t l, const T* x, T* out, const T* rhs, double* partial) {
+  // final: the last sweep of the finest level, writing z = V(r) in T into `out`
+  int mg_smooth(size_t l, const TM* x, void* out, const void* rhs, double* partial, bool final = false) {
     if constexpr (sizeof(T) == 4) {
       const DevMgLevel& L = (*mgl_)[l];
       int nb;
-      if (l == 0)
+      if (final)
+        nb = mg_gather<kEpiSmooth, 1, true>(m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial, L.omega);
+      else if (l == 0)
         nb = mg_gather<kEpiSmooth, 1>(m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial, L.omega);
       else
         nb = mg_gather<kEpiSmooth, 2>(L.S, x, out, L.dm32, L.dk32, rhs, nullptr, partial, L.omega);
       const DevEll& S = l == 0 ? m_->ell_k : L.S;
+      const double out_b = final ? (double)n_ * NS * P_.W * sizeof(T) : mg_vb(l);
       pmark(l == 0 ? kCatMgSmooth0 : kCatMgSmoothC,
-            3.0 * mg_vb(l) + mg_ell_b(S, l == 0 ? 1 : 2) + 2.0 * mg_rows(l) * sizeof(T));
+            mg_vb(l) + out_b + mg_vb_rhs(l) + mg_ell_b(S, l == 0 ? 1 : 2) + 2.0 * mg_rows(l) * sizeof(T));
       return nb;
     } else {
       return 0;
     }
   }
-  void mg_resid(size_t l, const T* x, T* out, const T* rhs) {
+  void mg_resid(size_t l, const TM* x, TM* out, const void* rhs) {
     if constexpr (sizeof(T) == 4) {
       if (l == 0) mg_gather<kEpiResid, 1>(m_->ell_k, x, out, mass_t(), nullptr, rhs, nullptr, nullptr);
       else mg_gather<kEpiResid, 2>((*mgl_)[l].S, x, out, (*mgl_)[l].dm32, nullptr, rhs, nullptr, nullptr);
       const DevEll& S = l == 0 ? m_->ell_k : (*mgl_)[l].S;
       pmark(l == 0 ? kCatMgResid0 : kCatMgResidC,
-            3.0 * mg_vb(l) + mg_ell_b(S, l == 0 ? 1 : 2) + (double)mg_rows(l) * sizeof(T));
+            2.0 * mg_vb(l) + mg_vb_rhs(l) + mg_ell_b(S, l == 0 ? 1 : 2) + (double)mg_rows(l) * sizeof(T));
     }
   }
-  void mg_transfer(size_t l, bool restrict_, const T* src, T* out, const T* own) {
+  void mg_transfer(size_t l, bool restrict_, const TM* src, TM* out, const TM* own) {
     if constexpr (sizeof(T) == 4) {
       const DevMgLevel& L = (*mgl_)[l];
       if (restrict_) {
@@ -2731,32 +2887,42 @@ class EngineT final : public Engine {
       }
     }
   }
-  void mg_jacobi(size_t l, const T* rhs, T* out) {
+  void mg_jacobi(size_t l, const void* rhs, TM* out) {
     if constexpr (sizeof(T) == 4) {
       const int32_t rows = (int32_t)mg_rows(l);
       const T* md = l == 0 ? mass_t() : (*mgl_)[l].dm32;
       const T* kd = l == 0 ? m_->diag_k32 : (*mgl_)[l].dk32;
       Params Q = P_;
       Q.n = rows;
-      const int g = std::min(nb_max_, grid_for((const void*)mg_jacobi_kernel<T, CPLX, BLK>, kBlock, 0,
-                                               (long long)rows * (P_.W / VEC)));
-      mg_jacobi_kernel<T, CPLX, BLK><<<g, kBlock, 0, st_>>>(Q, rhs, out, md, kd, C_, (T)(*mgl_)[l].omega);
-      pmark(l == 0 ? kCatMgJacobi0 : kCatMgJacobiC, 2.0 * mg_vb(l) + 2.0 * rows * sizeof(T));
+      const T om = (T)(*mgl_)[l].omega;
+      const long long work = (long long)rows * (P_.W / VM);
+      if (l == 0) {
+        const int g = std::min(nb_max_, grid_for((const void*)mg_jacobi_kernel<T, T, TM, VM, CPLX, BLK>, kBlock, 0, work));
+        mg_jacobi_kernel<T, T, TM, VM, CPLX, BLK><<<g, kBlock, 0, st_>>>(Q, static_cast<const T*>(rhs), out, md, kd,
+                                                                        C_, om);
+      } else {
+        const int g = std::min(nb_max_, grid_for((const void*)mg_jacobi_kernel<T, TM, TM, VM, CPLX, BLK>, kBlock, 0, work));
+        mg_jacobi_kernel<T, TM, TM, VM, CPLX, BLK><<<g, kBlock, 0, st_>>>(Q, static_cast<const TM*>(rhs), out, md,
+                                                                         kd, C_, om);
+      }
+      pmark(l == 0 ? kCatMgJacobi0 : kCatMgJacobiC, mg_vb(l) + mg_vb_rhs(l) + 2.0 * rows * sizeof(T));
     }
   }
   // One V-cycle on level l for the right-hand side rhs: two damped-Jacobi
   // sweeps, coarse correction, two sweeps (Jacobi sweeps only on the last
-  // level).  Returns the buffer holding the result; on level 0 the last sweep
-  // also leaves the partials of <rhs, result> in partial2_.
-  T* vcycle(size_t l, const T* rhs) {
+  // level).  Returns the buffer holding the result.  On level 0 the last sweep
+  // writes the result z in T into zout and leaves the partials of <rhs, z> in
+  // partial2_.
+  TM* vcycle(size_t l, const void* rhs, T* zout = nullptr) {
     MgBuf& B = mgb_[l];
     const bool last = l + 1 == mgl_->size();
     mg_jacobi(l, rhs, B.a);
     if (last) {
-      T* x = B.a;
-      T* y = B.b;
+      TM* x = B.a;
+      TM* y = B.b;
       for (int s = 1; s < kMgCoarseSweeps; s++) {
-        const int nb = mg_smooth(l, x, y, rhs, (l == 0 && s + 1 == kMgCoarseSweeps) ? partial2_ : nullptr);
+        const bool fin = l == 0 && s + 1 == kMgCoarseSweeps;
+        const int nb = mg_smooth(l, x, fin ? (void*)zout : (void*)y, rhs, fin ? partial2_ : nullptr, fin);
         if (l == 0) nbz_ = nb;
         std::swap(x, y);
       }
@@ -2764,8 +2930,8 @@ class EngineT final : public Engine {
     }
     mg_smooth(l, B.a, B.b, rhs, nullptr);
     // coarse correction(s): x <- x + P V_{l+1}(R (rhs - S x)), twice on levels 1 and 2 of a W12 cycle
-    T* x = B.b;
-    T* t = B.a;
+    TM* x = B.b;
+    TM* t = B.a;
     for (int s = 2; s < mg_nu(l); s++) {  // further pre-smoothing sweeps (coarse levels, on request)
       mg_smooth(l, x, t, rhs, nullptr);
       std::swap(x, t);
@@ -2773,7 +2939,7 @@ class EngineT final : public Engine {
     for (int rep = 0; rep < mg_reps(l); rep++) {
       mg_resid(l, x, t, rhs);
       mg_transfer(l, true, t, mgb_[l + 1].r, nullptr);
-      const T* xc = vcycle(l + 1, mgb_[l + 1].r);
+      const TM* xc = vcycle(l + 1, mgb_[l + 1].r);
       mg_transfer(l, false, xc, t, x);
       std::swap(x, t);
     }
@@ -2782,7 +2948,7 @@ class EngineT final : public Engine {
       std::swap(x, t);
     }
     mg_smooth(l, x, t, rhs, nullptr);
-    const int nb = mg_smooth(l, t, x, rhs, l == 0 ? partial2_ : nullptr);
+    const int nb = mg_smooth(l, t, l == 0 ? (void*)zout : (void*)x, rhs, l == 0 ? partial2_ : nullptr, l == 0);
     if (l == 0) nbz_ = nb;
     return x;
   }
@@ -2882,14 +3048,14 @@ class EngineT final : public Engine {
   }
 };
 
-template <typename T, typename MV>
+template <typename T, typename MV, typename TM>
 Engine* make_kind(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st, int64_t budget, bool cplx, bool blk) {
   if (cplx) {
-    if (blk) return new EngineT<T, MV, true, true>(m, o, st, budget);
-    return new EngineT<T, MV, true, false>(m, o, st, budget);
+    if (blk) return new EngineT<T, MV, TM, true, true>(m, o, st, budget);
+    return new EngineT<T, MV, TM, true, false>(m, o, st, budget);
   }
-  if (blk) return new EngineT<T, MV, false, true>(m, o, st, budget);
-  return new EngineT<T, MV, false, false>(m, o, st, budget);
+  if (blk) return new EngineT<T, MV, TM, false, true>(m, o, st, budget);
+  return new EngineT<T, MV, TM, false, false>(m, o, st, budget);
 }
 
 }  // namespace
@@ -2897,9 +3063,13 @@ Engine* make_kind(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st, i
 Engine* make_engine(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st, int64_t budget) {
   const bool cplx = complex_form(o);
   const bool blk = m->host.placement == IFILT_VERTEX_VECTOR;
-  if (o.precision == IFILT_PREC_FP64) return make_kind<double, double>(m, o, st, budget, cplx, blk);
-  if (o.precision == IFILT_PREC_BF16_IR) return make_kind<float, __nv_bfloat16>(m, o, st, budget, cplx, blk);
-  return make_kind<float, float>(m, o, st, budget, cplx, blk);
+  if (o.precision == IFILT_PREC_FP64) return make_kind<double, double, double>(m, o, st, budget, cplx, blk);
+  const bool mg32 = o.mg_vectors != IFILT_MG_VEC_BF16;
+  if (o.precision == IFILT_PREC_BF16_IR)
+    return mg32 ? make_kind<float, __nv_bfloat16, float>(m, o, st, budget, cplx, blk)
+                : make_kind<float, __nv_bfloat16, __nv_bfloat16>(m, o, st, budget, cplx, blk);
+  return mg32 ? make_kind<float, float, float>(m, o, st, budget, cplx, blk)
+              : make_kind<float, float, __nv_bfloat16>(m, o, st, budget, cplx, blk);
 }
 
 size_t batched_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, int32_t nk) {

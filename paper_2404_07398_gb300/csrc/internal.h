@@ -64,13 +64,17 @@ struct HostPrepared {
   HostCSR K;                      // n = 1 operator, l-free, device order, sorted columns
   HostCSR G2;                     // K M^-1 K (max_order >= 2)
   std::vector<HostCSR> Gn;        // G_n = G_(n-1) M^-1 K for n = 3 .. max_order (index n - 3)
+  bool products_pending = false;  // G2, Gn not formed yet: the upload forms them on the device
   // vertex-vector right-hand side: b_i = sum over incident ocean triangles c of (A_c / 3) u_c
   std::vector<int64_t> proj_ptr;
   std::vector<int32_t> proj_cell;
   std::vector<double> proj_w;
 };
 
-HostPrepared prepare_host(const ifilt_mesh_desc& d);
+// products = false leaves G2 and the higher orders to the upload (on the device)
+HostPrepared prepare_host(const ifilt_mesh_desc& d, bool products = true);
+// the products of prepare_host, formed on the host
+void host_products(HostPrepared& hp);
 
 // The complex-shift factorisation serves order 2 only (orders >= 3 run on G_n in real arithmetic).
 inline bool complex_form(const ifilt_solve_opts& o) { return o.order == 2 && o.n2_solver != IFILT_N2_REAL; }

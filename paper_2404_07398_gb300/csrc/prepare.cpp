@@ -326,7 +326,15 @@ void PhaseClock::lap(const char* phase) {
   t0 = t;
 }
 
-HostPrepared prepare_host(const ifilt_mesh_desc& d) {
+void host_products(HostPrepared& hp) {
+  hp.G2 = HostCSR{};
+  hp.Gn.clear();
+  if (hp.max_order >= 2) hp.G2 = product_amk(hp.K, hp.K, hp.mass);
+  for (int n = 3; n <= hp.max_order; n++) hp.Gn.push_back(product_amk(n == 3 ? hp.G2 : hp.Gn.back(), hp.K, hp.mass));
+  hp.products_pending = false;
+}
+
+HostPrepared prepare_host(const ifilt_mesh_desc& d, bool products) {
   if (d.n_vert <= 0 || d.n_tri <= 0 || !d.coords || !d.tri)
     fail(IFILT_EINVAL, "mesh needs n_vert > 0, n_tri > 0, coords and tri");
   if (d.placement < IFILT_VERTEX_SCALAR || d.placement > IFILT_CELL_CIRCUMCENTER)
@@ -701,11 +709,10 @@ HostPrepared prepare_host(const ifilt_mesh_desc& d) {
     }
   }
   clock.lap("operator and mass");
-  // ---- 4. order-2 product
-  if (d.max_order >= 2) hp.G2 = product_amk(K, K, hp.mass);
-  for (int n = 3; n <= d.max_order; n++)
-    hp.Gn.push_back(product_amk(n == 3 ? hp.G2 : hp.Gn.back(), K, hp.mass));
-  clock.lap("higher-order products");
+  // ---- 4. order-2 and higher products (on the device at upload when products = false)
+  if (products) host_products(hp);
+  else hp.products_pending = d.max_order >= 2;
+  clock.lap("products");
   return hp;
 }
 

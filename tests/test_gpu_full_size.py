@@ -1,7 +1,7 @@
 """Full size: the 10.5 M-vertex velocity workload in the configuration the
 benchmark times -- both placements, 40 scales x 2 components, n = 2 in the
 complex form, FP32 with FP64-accurate refinement to the paper's residual test
-1e-9 and a certified relative error bound of 1e-7, multigrid preconditioning
+1e-9 and a certified relative error bound of 1e-8, multigrid preconditioning
 on the strength-filtered hierarchy (mg_strength 0.05), 4 iterations per
 solver step, at most 2000 iterations per column.
 
@@ -10,7 +10,11 @@ The oracle checks every column without trusting the library's own numbers:
 * its FP64 error certificate, recomputed from the returned field: S >= M for
   the paper's real operator S = M + 1/2 l^4 K M^-1 K, so
   ||x - x*||_M <= ||b - S x||_{M^-1}; every column must show a bound of at most
-  1e-6 ||x||_M (the target tolerance against the FP64 solution);
+  1e-6 ||x||_M (the target tolerance against the FP64 solution).  At the
+  largest scales that bound overstates the error (S is far above M on the
+  short scales of the residual), and where it misses 1e-6 the oracle sharpens
+  it with a few of its own CG steps on the residual equation
+  (`oracle.refined_certificate`), still an upper bound;
 * element by element against its own conjugate-gradient solve, for the
   largest wavenumber and for a mid-range one (index 30 of 40, a 40 km
   wavelength: about one mesh spacing for l, so the oracle's unpreconditioned
@@ -26,8 +30,22 @@ import synth
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 TOL_MIXED = 1e-6
-BENCH_OPTS = dict(order=2, tol=1e-9, err_tol=1e-7, max_iter=2000, check_every=4)
+BENCH_OPTS = dict(order=2, tol=1e-9, err_tol=1e-8, max_iter=2000, check_every=4)
 SAMPLED_K = (39, 30)
+
+
+def certified(P, fld, filtered, k, target=TOL_MIXED):
+    """(largest certified relative M-norm error over the column's systems, oracle
+    CG steps the bound needed): the plain certificate, sharpened by 20 and then
+    60 of the oracle's steps where it is above the target."""
+    steps = 0
+    rel = max(b / xn for b, xn in oracle.residual_certificate(P, fld, filtered, k, 2))
+    for it in (20, 60):
+        if rel <= target:
+            break
+        steps = it
+        rel = max(b / xn for b, xn in oracle.refined_certificate(P, fld, filtered, k, 2, iters=it))
+    return rel, steps
 
 
 @pytest.fixture(scope="module")
@@ -46,16 +64,19 @@ def test_uv_batch_level10_certified_and_sampled(lib, workload, placement):
     h.release()
     assert st == 0, stats
     assert (stats["status"] == 0).all()
-    assert (stats["err_bound"] <= 1e-7).all() and (stats["rel_residual"] <= 1e-9).all()
+    assert (stats["err_bound"] <= 1e-8).all() and (stats["rel_residual"] <= 1e-9).all()
     res = out.cpu().numpy()
     del out
     P = oracle.build_problem(w["mesh"], placement)
     fld = w["fields"][0]
     K = w["k"].size
-    worst = 0.0
+    worst, refined = 0.0, []
     for j in range(K):
-        for bound, xnorm in oracle.residual_certificate(P, fld, res[0, j], w["k"][j], 2):
-            worst = max(worst, bound / xnorm)
+        rel = certified(P, fld, res[0, j], w["k"][j])
+        if rel[1]:
+            refined.append((j, rel[1]))
+        worst = max(worst, rel[0])
+    print(f"{placement}: worst certified relative error {worst:.3e}; refined columns (k index, steps) {refined}")
     assert worst <= TOL_MIXED, worst
     ref, _ = oracle.filter_field(P, fld, [w["k"][j] for j in SAMPLED_K], 2, rtol=1e-12)
     for i, j in enumerate(SAMPLED_K):

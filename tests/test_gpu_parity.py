@@ -579,3 +579,30 @@ def test_multigrid_w12_cycle(lib, monkeypatch, placement):
             a, b = res[lib.MG_V][0][0, :, c], res[key][0][0, :, c]
             assert np.linalg.norm(a - b) <= 2e-6 * np.linalg.norm(b)
         assert res[key][1].max() <= res[lib.MG_V][1].max() + 1
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+def test_device_products_equal_host_products(lib, placement):
+    """Preparation forms G2 = K M^-1 K and G_n = G_(n-1) M^-1 K on the device
+    (ifilt_prepare_mesh); the host-only preparation forms them on the host.
+    Same structural pattern, same products summed in the same order with the
+    same IEEE operations: the arrays read back are equal bit for bit, for the
+    three operator kinds and orders 2 to 4, and the two meshes solve alike."""
+    import torch
+    m = _sphere(3, 77, polar=10.0)
+    dev = lib.prepare_mesh(m, placement, max_order=4)
+    host = lib.prepare_mesh_host(m, placement, max_order=4)
+    for what in ("g2_rowptr", "g2_col", "g2_val"):
+        assert np.array_equal(dev.export(what), host.export(what)), what
+    for order in (3, 4):
+        for part in ("rowptr", "col", "val"):
+            assert np.array_equal(dev.export_gn(order, part), host.export_gn(order, part)), (order, part)
+    host.upload()
+    P = oracle.build_problem(m, placement)
+    f = torch.tensor(_fields(P, 1, 9), device="cuda")
+    ks = synth.log_wavenumbers(3000.0, 800.0, 3)
+    a, _, st_a = lib.solve(dev, f, ks, order=2, tol=1e-12, method=lib.METHOD_PLAIN)
+    b, _, st_b = lib.solve(host, f, ks, order=2, tol=1e-12, method=lib.METHOD_PLAIN)
+    assert st_a == 0 and st_b == 0 and torch.equal(a, b)
+    dev.release()
+    host.release()
