@@ -73,8 +73,6 @@ def parse_args():
                     help="multigrid cycle (w12: coarse corrections of levels 1 and 2 twice)")
     ap.add_argument("--max-iter", type=int, default=2000,
                     help="Krylov iteration cap per column (the hardest columns need well under 100)")
-    ap.add_argument("--mg-vectors", choices=["fp32", "bf16"], default="fp32",
-                    help="storage of the multigrid preconditioner's work vectors (FP32 arithmetic either way)")
     ap.add_argument("--mg-strength", type=float, default=0.05,
                     help="multigrid aggregation threshold (0: every neighbour, the library default)")
     ap.add_argument("--cache-dir", default="", help="keep the synthetic workload and the prepared meshes "
@@ -222,7 +220,6 @@ def workload_config(args, w, world):
             "precision": args.precision, "precond": getattr(args, "precond", "none"),
             "mg_strength": getattr(args, "mg_strength", 0.0) if getattr(args, "precond", "none") == "mg" else None,
             "mg_cycle": getattr(args, "mg_cycle", "v") if getattr(args, "precond", "none") == "mg" else None,
-            "mg_vectors": getattr(args, "mg_vectors", "fp32") if getattr(args, "precond", "none") == "mg" else None,
             "check_every": getattr(args, "check_every", 0), "max_iter": getattr(args, "max_iter", 0),
             "err_tol": getattr(args, "err_tol", 0.0), "reorder": getattr(args, "reorder", "rcm"),
             "l2": "inputs larger than L2 (GBs per vector), no flush",
@@ -257,8 +254,7 @@ class Ours:
                          precond={"none": api.PRECOND_NONE, "jacobi": api.PRECOND_JACOBI,
                                   "mg": api.PRECOND_MG}[args.precond],
                          check_every=args.check_every, inner_tol=args.inner_tol, err_tol=args.err_tol,
-                         max_iter=args.max_iter, mg_cycle={"v": api.MG_V, "w12": api.MG_W12}[args.mg_cycle],
-                         mg_vectors={"bf16": api.MG_VEC_BF16, "fp32": api.MG_VEC_FP32}[args.mg_vectors])
+                         max_iter=args.max_iter, mg_cycle={"v": api.MG_V, "w12": api.MG_W12}[args.mg_cycle])
         K = self.k.size
         self.out_v = torch.empty((1, K, 2, self.mv.info["n_out"]), dtype=torch.float64, device="cuda")
         self.out_c = torch.empty((1, K, 2, self.mc.info["n_out"]), dtype=torch.float64, device="cuda")

@@ -185,20 +185,9 @@ typedef struct {
   int32_t mg_cycle;          /* multigrid cycle: IFILT_MG_V (0) or IFILT_MG_W12 (1), which applies the
                                 coarse correction of levels 1 and 2 twice (more coarse work, fewer
                                 Krylov iterations on large meshes) */
-  int32_t mg_vectors;        /* storage of the multigrid preconditioner's work vectors:
-                                IFILT_MG_VEC_FP32 (0, default) or IFILT_MG_VEC_BF16 (1).  The V-cycle
-                                computes in FP32 either way, and its result z enters the Krylov
-                                recursion in FP32.  BF16 storage halves the V-cycle's vector
-                                traffic but perturbs the preconditioner by about 2^-9 per stored
-                                value; on the 10.5 M-vertex sphere the hardest columns then need
-                                several times the iterations or do not converge, so it suits small
-                                meshes only.  The solution's accuracy is unaffected either way: the
-                                Krylov vectors, the FP64-accurate refinement and the stopping tests
-                                never use these vectors. */
 } ifilt_solve_opts;
 
 enum { IFILT_MG_V = 0, IFILT_MG_W12 = 1 };
-enum { IFILT_MG_VEC_FP32 = 0, IFILT_MG_VEC_BF16 = 1 };
 
 typedef struct {
   int32_t iters;             /* Krylov iterations (all rounds) */

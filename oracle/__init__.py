@@ -31,6 +31,7 @@ from .operators import (  # noqa: F401
 from .reorder import rcm_order, check_rcm_order, hilbert_index, curve_keys, curve_order  # noqa: F401
 from .solve import (  # noqa: F401
     cg, filter_field, filter_dense, residual_certificate, refined_certificate, relative_residual, Problem,
+    lambda_max_minv_k,
     build_problem,
     shifted_factors, filter_shifted,
 )

@@ -277,6 +277,25 @@ def refined_certificate(problem, fld, filtered_k, k, order, iters=50):
     return res
 
 
+def lambda_max_minv_k(problem, iters=60, seed=0):
+    """Power iteration for the largest eigenvalue of M^-1 K (the l-free
+    operator's spectrum in the M inner product).  Power iteration approaches it
+    from below, so the result never overstates it.  The condition number of S
+    in the M-norm is then kappa(l) = 1 + 1/2 (l^2 lambda)^n for K symmetric
+    positive semidefinite."""
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=problem.A.size)
+    lam = 0.0
+    for _ in range(iters):
+        y = (problem.K @ x) / problem.A
+        nrm = np.sqrt(np.sum(problem.A * y * y))
+        if nrm == 0.0:
+            return 0.0
+        lam = np.sum(problem.A * x * y) / np.sum(problem.A * x * x)  # Rayleigh quotient in the M inner product
+        x = y / nrm
+    return float(lam)
+
+
 def residual_certificate(problem, fld, filtered_k, k, order):
     """For one wavenumber: per system (||b - S x||_{M^-1}, ||x||_M) where x is the
     candidate solution read back from `filtered_k` [n_comp][n_out].  The first

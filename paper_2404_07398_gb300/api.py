@@ -22,7 +22,6 @@ N2_AUTO, N2_REAL, N2_COMPLEX = 0, 1, 2
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG = 0, 1, 2
 REORDER_NONE, REORDER_RCM, REORDER_HILBERT = 0, 1, 2
 MG_V, MG_W12 = 0, 1
-MG_VEC_FP32, MG_VEC_BF16 = 0, 1
 MG_MAX_LEVELS = 16
 MAX_ORDER = 4
 OK, NOT_CONVERGED = 0, 1
@@ -52,7 +51,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("order", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("method", C.c_int32), ("n2_solver", C.c_int32), ("precond", C.c_int32),
                 ("check_every", C.c_int32), ("inner_tol", C.c_double), ("max_lanes", C.c_int32),
-                ("err_tol", C.c_double), ("mg_cycle", C.c_int32), ("mg_vectors", C.c_int32)]
+                ("err_tol", C.c_double), ("mg_cycle", C.c_int32)]
 
 
 class SolveItem(C.Structure):
@@ -367,10 +366,10 @@ def prepare_mesh_cached(mesh, placement, cache_dir, max_order=2, reorder=1, cell
 
 
 def solve_opts(order=1, tol=1e-9, precision=PREC_FP64, method=METHOD_BATCHED, n2_solver=N2_AUTO, max_iter=0,
-               precond=0, check_every=0, inner_tol=0.0, max_lanes=0, err_tol=0.0, mg_cycle=0, mg_vectors=0):
+               precond=0, check_every=0, inner_tol=0.0, max_lanes=0, err_tol=0.0, mg_cycle=0):
     return SolveOpts(order=order, tol=tol, max_iter=max_iter, precision=precision, method=method,
                      n2_solver=n2_solver, precond=precond, check_every=check_every, inner_tol=inner_tol,
-                     max_lanes=max_lanes, err_tol=err_tol, mg_cycle=mg_cycle, mg_vectors=mg_vectors)
+                     max_lanes=max_lanes, err_tol=err_tol, mg_cycle=mg_cycle)
 
 
 def solve(mesh, fields, k, out=None, stream=None, **opts):

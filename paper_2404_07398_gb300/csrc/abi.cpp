@@ -425,8 +425,6 @@ static void check_opts(ifilt_mesh m, const ifilt_solve_opts* o) {
     fail(IFILT_EINVAL, "negative option");
   if (!(o->err_tol >= 0.0) || !std::isfinite(o->err_tol)) fail(IFILT_EINVAL, "err_tol must be >= 0 and finite");
   if (o->mg_cycle != IFILT_MG_V && o->mg_cycle != IFILT_MG_W12) fail(IFILT_EINVAL, "unknown mg_cycle %d", o->mg_cycle);
-  if (o->mg_vectors != IFILT_MG_VEC_BF16 && o->mg_vectors != IFILT_MG_VEC_FP32)
-    fail(IFILT_EINVAL, "unknown mg_vectors %d", o->mg_vectors);
   if (o->method == IFILT_METHOD_PLAIN && o->err_tol > 0.0)
     fail(IFILT_EINVAL, "the plain method stops on the residual only (err_tol = 0)");
 }

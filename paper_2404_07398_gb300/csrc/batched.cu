@@ -242,51 +242,36 @@ struct MgArgs {
   T omega;        // Jacobi weight (SMOOTH)
 };
 
-// VEC lanes of a vector stored as TS (FP64, FP32 or BF16), moved as one load or
-// store of VEC * sizeof(TS) bytes (8, 16 or 32) and converted to or from the
-// arithmetic type T.  BF16 lanes 2i and 2i+1 are the low and high halves of
-// 32-bit word i; a BF16 value widens to FP32 exactly, FP32 narrows to BF16 by
-// round-to-nearest-even.
+
+
+// VEC lanes of a vector stored as TS (FP64 or FP32), moved as one load or store
+// of VEC * sizeof(TS) bytes (16 or 32) and converted to or from the arithmetic
+// type T.
 template <typename TS, int VEC>
 struct Lanes {
   static constexpr int B = VEC * (int)sizeof(TS);
-  static_assert(B == 8 || B == 16 || B == 32, "a lane group moves 8, 16 or 32 bytes");
+  static_assert(B == 16 || B == 32, "a lane group moves 16 or 32 bytes");
   uint32_t w[B / 4];
 };
 template <bool NC, typename TS, int VEC>
 __device__ __forceinline__ Lanes<TS, VEC> lanes_ld(const TS* p) {
   Lanes<TS, VEC> r;
-  if constexpr (Lanes<TS, VEC>::B == 8) {
-    const uint2 u = NC ? __ldg(reinterpret_cast<const uint2*>(p)) : *reinterpret_cast<const uint2*>(p);
-    r.w[0] = u.x, r.w[1] = u.y;
-  } else {
 #pragma unroll
-    for (int c = 0; c < Lanes<TS, VEC>::B / 16; c++) {
-      const uint4 u = NC ? __ldg(reinterpret_cast<const uint4*>(p) + c) : reinterpret_cast<const uint4*>(p)[c];
-      r.w[4 * c] = u.x, r.w[4 * c + 1] = u.y, r.w[4 * c + 2] = u.z, r.w[4 * c + 3] = u.w;
-    }
+  for (int c = 0; c < Lanes<TS, VEC>::B / 16; c++) {
+    const uint4 u = NC ? __ldg(reinterpret_cast<const uint4*>(p) + c) : reinterpret_cast<const uint4*>(p)[c];
+    r.w[4 * c] = u.x, r.w[4 * c + 1] = u.y, r.w[4 * c + 2] = u.z, r.w[4 * c + 3] = u.w;
   }
   return r;
 }
 template <typename TS, int VEC>
 __device__ __forceinline__ void lanes_st(TS* p, const Lanes<TS, VEC>& r) {
-  if constexpr (Lanes<TS, VEC>::B == 8) {
-    *reinterpret_cast<uint2*>(p) = make_uint2(r.w[0], r.w[1]);
-  } else {
 #pragma unroll
-    for (int c = 0; c < Lanes<TS, VEC>::B / 16; c++)
-      reinterpret_cast<uint4*>(p)[c] = make_uint4(r.w[4 * c], r.w[4 * c + 1], r.w[4 * c + 2], r.w[4 * c + 3]);
-  }
+  for (int c = 0; c < Lanes<TS, VEC>::B / 16; c++)
+    reinterpret_cast<uint4*>(p)[c] = make_uint4(r.w[4 * c], r.w[4 * c + 1], r.w[4 * c + 2], r.w[4 * c + 3]);
 }
 template <typename T, typename TS, int VEC>
 __device__ __forceinline__ void lanes_get(const Lanes<TS, VEC>& r, T* v) {
-  if constexpr (sizeof(TS) == 2) {
-#pragma unroll
-    for (int i = 0; i < VEC / 2; i++) {
-      v[2 * i] = (T)__uint_as_float(r.w[i] << 16);
-      v[2 * i + 1] = (T)__uint_as_float(r.w[i] & 0xffff0000u);
-    }
-  } else if constexpr (sizeof(TS) == 4) {
+  if constexpr (sizeof(TS) == 4) {
 #pragma unroll
     for (int i = 0; i < VEC; i++) v[i] = (T)__uint_as_float(r.w[i]);
   } else {
@@ -297,13 +282,7 @@ __device__ __forceinline__ void lanes_get(const Lanes<TS, VEC>& r, T* v) {
 template <typename T, typename TS, int VEC>
 __device__ __forceinline__ Lanes<TS, VEC> lanes_put(const T* v) {
   Lanes<TS, VEC> r;
-  if constexpr (sizeof(TS) == 2) {
-#pragma unroll
-    for (int i = 0; i < VEC / 2; i++) {
-      const __nv_bfloat162 h = __floats2bfloat162_rn((float)v[2 * i], (float)v[2 * i + 1]);
-      r.w[i] = *reinterpret_cast<const uint32_t*>(&h);
-    }
-  } else if constexpr (sizeof(TS) == 4) {
+  if constexpr (sizeof(TS) == 4) {
 #pragma unroll
     for (int i = 0; i < VEC; i++) r.w[i] = __float_as_uint((float)v[i]);
   } else {
@@ -314,11 +293,6 @@ __device__ __forceinline__ Lanes<TS, VEC> lanes_put(const T* v) {
     }
   }
   return r;
-}
-// the values of v as they read back once stored as TS
-template <typename T, typename TS, int VEC>
-__device__ __forceinline__ void lanes_round(T* v) {
-  if constexpr (sizeof(TS) < sizeof(T)) lanes_get<T, TS, VEC>(lanes_put<T, TS, VEC>(v), v);
 }
 
 // q = M p + shift * acc for one row (all sub-rows), and the row's share of
@@ -367,8 +341,7 @@ __device__ __forceinline__ void spmm_epilogue(int64_t r, int64_t rowW, int W, in
 // Multigrid epilogue for one row: acc holds the K part of the gather (or the
 // whole gather for RESTRICT / PROLONG), accm the M part on coarse levels
 // (NSET = 2); own is x_r (SMOOTH, RESID) or y_r (PROLONG); mdiag is the
-// diagonal of M_l (the lumped mass on the finest level).  The output is stored
-// as TS; the partial <rhs, out> of a smoothing sweep uses the stored values.
+// diagonal of M_l (the lumped mass on the finest level).
 template <typename T, typename TS, int VEC, bool CPLX, bool BLK, int EPI, int NSET>
 __device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int l0, const T mr, const T gr,
                                             T (*rh)[VEC], const T* sh, T (*acc)[VEC], T (*accm)[VEC],
@@ -407,7 +380,6 @@ __device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int 
 #pragma unroll
         for (int v = 0; v < VEC; v++) o[v] = madd(omega, z[v], own[b][v]);
         if (dot) {
-          lanes_round<T, TS, VEC>(o);
           if constexpr (CPLX) {
 #pragma unroll
             for (int v = 0; v < VEC; v += 2) {
@@ -1898,16 +1870,12 @@ void cols_upload(const Cols& C, const HostCols& H, int n, cudaStream_t st) {
 }
 
 // T: arithmetic and Krylov-vector type; MV: stored operator values; TM: stored
-// multigrid vectors (the preconditioner's work vectors, computed in T; the
-// Krylov vectors, the refinement and the certificates never see them).
+// multigrid work vectors (T in every engine the library builds; FP16 and BF16
+// storage were measured and dropped).
 template <typename T, typename MV, typename TM, bool CPLX, bool BLK>
 class EngineT final : public Engine {
   static constexpr int VEC = Pack<T>::N;
-#ifdef IFILT_MG_LANES
-  static constexpr int VM = IFILT_MG_LANES;  // experiment: lanes per thread in the multigrid kernels
-#else
   static constexpr int VM = 16 / (int)sizeof(TM);  // lanes per thread in the multigrid kernels (16-byte loads)
-#endif
   static constexpr int NS = BLK ? 2 : 1;
   static constexpr int LPC = CPLX ? 2 : 1;  // lanes per column
   static constexpr int NVAL = BLK ? 2 : 1;
@@ -2816,8 +2784,9 @@ class EngineT final : public Engine {
   }
 
   // one gather-kernel launch on a multigrid operator; returns its block count
+  // level l: the level whose rows the operation writes (restriction and prolongation: the finer one)
   template <int EPI, int NSET, bool FINAL = false>
-  int mg_gather(const DevEll& E, const TM* src, void* out, const T* mdiag, const T* kd, const void* rhs,
+  int mg_gather(size_t l, const DevEll& E, const TM* src, void* out, const T* mdiag, const T* kd, const void* rhs,
                 const TM* own, double* partial, double omega = kMgOmega) {
     const int W = P_.W;
     const int vbytes = NVAL * NSET * (int)sizeof(T);
@@ -2831,9 +2800,10 @@ class EngineT final : public Engine {
     if (bpsm_mg_ > 0) blocks = std::min(blocks, n_sms_ * bpsm_mg_);
     using TR = MgTR<EPI, NSET>;
     using TO = MgTO<EPI, NSET, FINAL>;
+    (void)l;
+    MgArgs<T, TR, TM> args{kd, static_cast<const TR*>(rhs), own, (T)omega};
     spmm_kernel<T, T, TM, TR, TO, VM, CPLX, BLK, kMgEB, mg_minb<EPI>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
-        ell_view<T>(E), Q, E.n_slices, src, static_cast<TO*>(out), mdiag, mg_cols_, partial,
-        MgArgs<T, TR, TM>{kd, static_cast<const TR*>(rhs), own, (T)omega});
+        ell_view<T>(E), Q, E.n_slices, src, static_cast<TO*>(out), mdiag, mg_cols_, partial, args);
     return blocks;
   }
   // S_l-operations: level 0 uses the mesh's K and lumped mass, coarser levels their (K, M) pair
@@ -2852,11 +2822,12 @@ class EngineT final : public Engine {
       const DevMgLevel& L = (*mgl_)[l];
       int nb;
       if (final)
-        nb = mg_gather<kEpiSmooth, 1, true>(m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial, L.omega);
+        nb = mg_gather<kEpiSmooth, 1, true>(l, m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial,
+                                            L.omega);
       else if (l == 0)
-        nb = mg_gather<kEpiSmooth, 1>(m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial, L.omega);
+        nb = mg_gather<kEpiSmooth, 1>(l, m_->ell_k, x, out, mass_t(), m_->diag_k32, rhs, nullptr, partial, L.omega);
       else
-        nb = mg_gather<kEpiSmooth, 2>(L.S, x, out, L.dm32, L.dk32, rhs, nullptr, partial, L.omega);
+        nb = mg_gather<kEpiSmooth, 2>(l, L.S, x, out, L.dm32, L.dk32, rhs, nullptr, partial, L.omega);
       const DevEll& S = l == 0 ? m_->ell_k : L.S;
       const double out_b = final ? (double)n_ * NS * P_.W * sizeof(T) : mg_vb(l);
       pmark(l == 0 ? kCatMgSmooth0 : kCatMgSmoothC,
@@ -2868,8 +2839,8 @@ class EngineT final : public Engine {
   }
   void mg_resid(size_t l, const TM* x, TM* out, const void* rhs) {
     if constexpr (sizeof(T) == 4) {
-      if (l == 0) mg_gather<kEpiResid, 1>(m_->ell_k, x, out, mass_t(), nullptr, rhs, nullptr, nullptr);
-      else mg_gather<kEpiResid, 2>((*mgl_)[l].S, x, out, (*mgl_)[l].dm32, nullptr, rhs, nullptr, nullptr);
+      if (l == 0) mg_gather<kEpiResid, 1>(l, m_->ell_k, x, out, mass_t(), nullptr, rhs, nullptr, nullptr);
+      else mg_gather<kEpiResid, 2>(l, (*mgl_)[l].S, x, out, (*mgl_)[l].dm32, nullptr, rhs, nullptr, nullptr);
       const DevEll& S = l == 0 ? m_->ell_k : (*mgl_)[l].S;
       pmark(l == 0 ? kCatMgResid0 : kCatMgResidC,
             2.0 * mg_vb(l) + mg_vb_rhs(l) + mg_ell_b(S, l == 0 ? 1 : 2) + (double)mg_rows(l) * sizeof(T));
@@ -2879,10 +2850,10 @@ class EngineT final : public Engine {
     if constexpr (sizeof(T) == 4) {
       const DevMgLevel& L = (*mgl_)[l];
       if (restrict_) {
-        mg_gather<kEpiRestrict, 1>(L.R, src, out, nullptr, nullptr, nullptr, nullptr, nullptr);
+        mg_gather<kEpiRestrict, 1>(l, L.R, src, out, nullptr, nullptr, nullptr, nullptr, nullptr);
         pmark(l == 0 ? kCatMgRestrict0 : kCatMgRestrictC, mg_vb(l) + mg_vb(l + 1) + mg_ell_b(L.R, 1));
       } else {
-        mg_gather<kEpiProlong, 1>(L.P, src, out, nullptr, nullptr, nullptr, own, nullptr);
+        mg_gather<kEpiProlong, 1>(l, L.P, src, out, nullptr, nullptr, nullptr, own, nullptr);
         pmark(l == 0 ? kCatMgProlong0 : kCatMgProlongC, 2.0 * mg_vb(l) + mg_vb(l + 1) + mg_ell_b(L.P, 1));
       }
     }
@@ -3064,12 +3035,8 @@ Engine* make_engine(ifilt_mesh_s* m, const ifilt_solve_opts& o, cudaStream_t st,
   const bool cplx = complex_form(o);
   const bool blk = m->host.placement == IFILT_VERTEX_VECTOR;
   if (o.precision == IFILT_PREC_FP64) return make_kind<double, double, double>(m, o, st, budget, cplx, blk);
-  const bool mg32 = o.mg_vectors != IFILT_MG_VEC_BF16;
-  if (o.precision == IFILT_PREC_BF16_IR)
-    return mg32 ? make_kind<float, __nv_bfloat16, float>(m, o, st, budget, cplx, blk)
-                : make_kind<float, __nv_bfloat16, __nv_bfloat16>(m, o, st, budget, cplx, blk);
-  return mg32 ? make_kind<float, float, float>(m, o, st, budget, cplx, blk)
-              : make_kind<float, float, __nv_bfloat16>(m, o, st, budget, cplx, blk);
+  if (o.precision == IFILT_PREC_BF16_IR) return make_kind<float, __nv_bfloat16, float>(m, o, st, budget, cplx, blk);
+  return make_kind<float, float, float>(m, o, st, budget, cplx, blk);
 }
 
 size_t batched_scratch_bytes(const ifilt_mesh_s* m, const ifilt_solve_opts& o, int32_t F, int32_t nk) {

@@ -38,8 +38,8 @@ struct Request {
   double t_submit = 0, t_start = 0, t_done = 0;
 };
 
-// mesh, order, precision, n = 2 form, preconditioner, error tolerance, cycle, multigrid vector storage
-using Key = std::tuple<ifilt_mesh, int, int, int, int, double, int, int>;
+// mesh, order, precision, n = 2 form, preconditioner, error tolerance, cycle
+using Key = std::tuple<ifilt_mesh, int, int, int, int, double, int>;
 
 struct EngineSlot {
   std::unique_ptr<ifilt::Engine> engine;
@@ -81,8 +81,7 @@ struct ifilt_server_s {
       o.max_lanes = opts.max_lanes;
       o.check_every = opts.check_every;
       const bool cplx = ifilt::complex_form(o);
-      Key key{r->mesh, o.order, o.precision, o.order >= 2 ? (cplx ? 2 : 1) : 0, o.precond, o.err_tol, o.mg_cycle,
-              o.mg_vectors};
+      Key key{r->mesh, o.order, o.precision, o.order >= 2 ? (cplx ? 2 : 1) : 0, o.precond, o.err_tol, o.mg_cycle};
       auto it = engines.find(key);
       if (it == engines.end()) {
         EngineSlot slot;
@@ -259,7 +258,6 @@ ifilt_status ifilt_server_submit(ifilt_server s, ifilt_mesh mesh, const ifilt_so
     if (o->order >= 3 && o->n2_solver == IFILT_N2_COMPLEX)
       fail(IFILT_EINVAL, "the complex factorisation serves order 2 only");
     if (o->mg_cycle != IFILT_MG_V && o->mg_cycle != IFILT_MG_W12) fail(IFILT_EINVAL, "unknown mg_cycle");
-    if (o->mg_vectors != IFILT_MG_VEC_BF16 && o->mg_vectors != IFILT_MG_VEC_FP32) fail(IFILT_EINVAL, "unknown mg_vectors");
     if (o->precond == IFILT_PRECOND_MG &&
         (o->precision == IFILT_PREC_FP64 || !(o->order == 1 || ifilt::complex_form(*o))))
       fail(IFILT_EINVAL, "multigrid preconditioning needs FP32/BF16 and order 1 or the complex n = 2 form");

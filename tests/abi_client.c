@@ -93,10 +93,9 @@ int main(int argc, char** argv) {
   if (ifilt_mesh_multigrid(back, &mg) != IFILT_OK) return 10;
   printf("key_match %d wrong_key_status %d mg_levels %d\n", key == key2, (int)wrong, mg.n_levels);
   printf("version %s\n", ifilt_version());
-  printf("layout desc %zu %zu opts %zu %zu %zu %zu info %zu stats %zu\n", sizeof(ifilt_mesh_desc),
+  printf("layout desc %zu %zu opts %zu %zu %zu info %zu stats %zu\n", sizeof(ifilt_mesh_desc),
          offsetof(ifilt_mesh_desc, mg_strength), sizeof(ifilt_solve_opts), offsetof(ifilt_solve_opts, err_tol),
-         offsetof(ifilt_solve_opts, mg_cycle), offsetof(ifilt_solve_opts, mg_vectors), sizeof(ifilt_mesh_info_t),
-         sizeof(ifilt_col_stats));
+         offsetof(ifilt_solve_opts, mg_cycle), sizeof(ifilt_mesh_info_t), sizeof(ifilt_col_stats));
   printf("layout2 item %zu mg %zu server %zu request %zu profile %zu\n", sizeof(ifilt_solve_item),
          sizeof(ifilt_multigrid_info), sizeof(ifilt_server_opts), sizeof(ifilt_request_info),
          sizeof(ifilt_kernel_profile));

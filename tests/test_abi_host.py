@@ -172,8 +172,7 @@ def test_plain_c_client(api, tmp_path):
     import ctypes
     lay = [int(x) for x in out["layout"].split()[1::1] if x.isdigit()]
     assert lay == [ctypes.sizeof(api.MeshDesc), api.MeshDesc.mg_strength.offset, ctypes.sizeof(api.SolveOpts),
-                   api.SolveOpts.err_tol.offset, api.SolveOpts.mg_cycle.offset, api.SolveOpts.mg_vectors.offset,
-                   ctypes.sizeof(api.MeshInfo),
+                   api.SolveOpts.err_tol.offset, api.SolveOpts.mg_cycle.offset, ctypes.sizeof(api.MeshInfo),
                    ctypes.sizeof(api.ColStats)], (out["layout"], lay)
     lay2 = [int(x) for x in out["layout2"].split() if x.isdigit()]
     assert lay2 == [ctypes.sizeof(c) for c in (api.SolveItem, api.MultigridInfo, api.ServerOpts, api.RequestInfo,

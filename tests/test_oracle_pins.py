@@ -397,6 +397,22 @@ def test_refined_certificate_is_a_bound_and_tighter(placement):
 
 
 @pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
+def test_lambda_max_power_iteration(placement):
+    """The power-iteration estimate of the largest eigenvalue of M^-1 K stays at
+    or below the dense generalized eigenvalue (scipy eigh of (K, M)) and within
+    a few percent of it."""
+    import scipy.linalg
+    m = synth.icosphere(3, radius=6371.0, jitter=0.2, seed=27)
+    m["ocean"] = synth.land_mask(m["coords"], 0.3, seed=28, polar_cap_deg=10.0)
+    P = oracle.build_problem(m, placement)
+    lam = oracle.lambda_max_minv_k(P, iters=200)
+    K = P.K.toarray()
+    K = 0.5 * (K + K.T)
+    ref = scipy.linalg.eigh(K, np.diag(P.A), eigvals_only=True)[-1]
+    assert lam <= ref * (1 + 1e-12) and lam >= 0.95 * ref, (lam, ref)
+
+
+@pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
 def test_relative_residual_of_x0_exact_and_perturbed(placement):
     """||b - S x|| / ||b - S x0||: exactly 1 at x0 (the paper's initial guess),
     at rounding level for the dense solve, and equal to ||S e|| / ||r0|| for
