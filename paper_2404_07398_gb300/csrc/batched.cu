@@ -154,6 +154,33 @@ __device__ __forceinline__ void jacobi(T m, T g, const T* sh, const T* rv, T* z)
   }
 }
 
+// The multigrid smoother's damped-Jacobi step: the same z = D^-1 r, with the
+// reciprocal of each diagonal entry taken by the fast hardware approximation
+// in single precision (a relative error of a few ulp).  The smoother only has
+// to be one fixed diagonal operator, applied alike before and after the coarse
+// correction (which keeps the V-cycle symmetric); an IEEE division per lane was
+// a large share of the sweep's instructions.  The Jacobi preconditioner of the
+// Krylov solve keeps the exact division (jacobi above).
+template <typename T, bool CPLX, int VEC>
+__device__ __forceinline__ void smooth_jacobi(T m, T g, const T* sh, const T* rv, T* z) {
+  if constexpr (sizeof(T) == 4) {
+    if constexpr (CPLX) {
+#pragma unroll
+      for (int v = 0; v < VEC; v += 2) {
+        const T bg = sh[v] * g;
+        const T inv = __fdividef(1.0f, madd(m, m, bg * bg));
+        z[v] = madd(rv[v], m, rv[v + 1] * bg) * inv;
+        z[v + 1] = madd(rv[v + 1], m, -(rv[v] * bg)) * inv;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < VEC; v++) z[v] = rv[v] * __fdividef(1.0f, madd(sh[v], g, m));
+    }
+  } else {
+    jacobi<T, CPLX, VEC>(m, g, sh, rv, z);
+  }
+}
+
 // 4 consecutive ELL entries' values (NV per entry) converted to AT.
 template <typename MV, int NV, typename AT>
 __device__ __forceinline__ void load_vals(const MV* __restrict__ p, AT* out) {
@@ -376,7 +403,7 @@ __device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int 
         for (int v = 0; v < VEC; v++) o[v] = res[v];
       } else {
         T z[VEC];
-        jacobi<T, CPLX, VEC>(mr, gr, sh, res, z);
+        smooth_jacobi<T, CPLX, VEC>(mr, gr, sh, res, z);
 #pragma unroll
         for (int v = 0; v < VEC; v++) o[v] = madd(omega, z[v], own[b][v]);
         if (dot) {
@@ -1341,7 +1368,7 @@ __global__ void __launch_bounds__(kBlock) mg_jacobi_kernel(Params P, const TR* _
       T rv[VEC];
       lanes_get<T, TR, VEC>(lanes_ld<false, TR, VEC>(rhs + off), rv);
       T z[VEC];
-      jacobi<T, CPLX, VEC>(mr, kr, sh, rv, z);
+      smooth_jacobi<T, CPLX, VEC>(mr, kr, sh, rv, z);
 #pragma unroll
       for (int v = 0; v < VEC; v++) z[v] *= omega;
       lanes_st<TS, VEC>(x + off, lanes_put<T, TS, VEC>(z));
@@ -1621,6 +1648,7 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
       if constexpr (!HOIST) load_sources();
       const DF mr{mhi[row], mlo[row]};
       const float mrf = mhi[row];
+      const float imrf = 1.0f / mrf;  // once per row: the M^-1-norm terms of its lanes
       const float gr = gdiag ? gdiag[row] : 0.f;
       if (++chain == kFlushRows) {
         chain = 0;
@@ -1670,7 +1698,7 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
             d1[v + 1].add_sum(__fmaf_rn(tre, zim, tim * zre));
             const float nn = __fmaf_rn(tre, tre, tim * tim);
             d2[v / 2].add_sum(nn);
-            e2[v / 2].add_sum(nn / mrf);
+            e2[v / 2].add_sum(nn * imrf);
             const float xr = x0 + xo[v].hi;
             x2[v / 2].add_sum(mrf * xr * xr);  // the filtered field is the real part
           }
@@ -1687,7 +1715,7 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
             po.v[v] = z;
             d1[v].add(t, z);
             d2[v].add(t, t);
-            e2[v].add_sum(t * t / mrf);
+            e2[v].add_sum(t * t * imrf);
             const float xr = x0 + xo[v].hi;
             x2[v].add_sum(mrf * xr * xr);
           }
@@ -2615,7 +2643,7 @@ class EngineT final : public Engine {
       launch_check("autotune", 0, 0, W);
       return ms;
     };
-    const int tps[3] = {4, 8, 16};
+    const int tps[4] = {4, 8, 16, 32};
     int occ = 1;
     float best = 1e30f;
     int btp = kTilePasses, bb = 0;
