@@ -69,8 +69,9 @@ def parse_args():
     ap.add_argument("--err-tol", type=float, default=1e-8,
                     help="also stop each column only at a certified relative M-norm error bound (0: off)")
     ap.add_argument("--reorder", choices=["rcm", "hilbert"], default="rcm", help="device row order of the meshes")
-    ap.add_argument("--mg-cycle", choices=["v", "w12"], default="v",
-                    help="multigrid cycle (w12: coarse corrections of levels 1 and 2 twice)")
+    ap.add_argument("--mg-cycle", choices=["v", "w12"], default="w12",
+                    help="multigrid cycle (w12: coarse corrections of levels 1 and 2 twice, fewer Krylov "
+                         "iterations for more coarse work; v: one coarse correction per level)")
     ap.add_argument("--max-iter", type=int, default=2000,
                     help="Krylov iteration cap per column (the hardest columns need well under 100)")
     ap.add_argument("--mg-strength", type=float, default=0.05,

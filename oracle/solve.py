@@ -240,7 +240,7 @@ def relative_residual(problem, fld, filtered_k, k, order):
     return out
 
 
-def refined_certificate(problem, fld, filtered_k, k, order, iters=50):
+def refined_certificate(problem, fld, filtered_k, k, order, iters=50, stop=0.0):
     """As `residual_certificate`, sharpened by a correction the oracle computes
     itself.  For a candidate x with residual r = b - S x, let e~ be the result of
     `iters` conjugate-gradient steps on S e = r from e = 0.  Since
@@ -250,19 +250,23 @@ def refined_certificate(problem, fld, filtered_k, k, order, iters=50):
     residual the steps did not resolve.  Where S is far above M (the short
     scales of a large-l system) the plain bound ||r||_{M^-1} overstates the
     error by up to the ratio of the two, and a few steps remove that part of r.
-    iters = 0 gives the plain bound.  Returns per system (bound, ||x||_M)."""
+    iters = 0 gives the plain bound.  With stop > 0 the steps end early, once
+    the recurrence's residual r - S e~ is at most stop ||x||_M in the M^-1 norm
+    (the bound itself is always formed from r - S e~ recomputed).  Returns per
+    system (bound, ||x||_M)."""
     ell = 1.0 / k
     apply = lambda v: problem.apply_S(v, ell, order)
     res = []
     syst = problem.systems(fld)
     for (b, _), x in zip(syst, _candidates(problem, fld, filtered_k)):
         r = b - apply(x)
+        xn = np.sqrt(np.sum(problem.A * x * x))
         e = np.zeros_like(r)
         rr = r.copy()
         p = rr.copy()
         rho = rr @ rr
         for _ in range(iters):
-            if rho == 0.0:
+            if rho == 0.0 or np.sqrt(np.sum(rr * rr / problem.A)) <= stop * xn:
                 break
             q = apply(p)
             alpha = rho / (p @ q)
@@ -273,7 +277,7 @@ def refined_certificate(problem, fld, filtered_k, k, order, iters=50):
             rho = rho_new
         left = r - apply(e)  # the unresolved residual, recomputed
         bound = np.sqrt(np.sum(problem.A * e * e)) + np.sqrt(np.sum(left * left / problem.A))
-        res.append((bound, np.sqrt(np.sum(problem.A * x * x))))
+        res.append((bound, xn))
     return res
 
 

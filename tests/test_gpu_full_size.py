@@ -2,27 +2,34 @@
 benchmark times -- both placements, 40 scales x 2 components, n = 2 in the
 complex form, FP32 with FP64-accurate refinement to the paper's residual test
 1e-9 and a certified relative error bound of 1e-8, multigrid preconditioning
-on the strength-filtered hierarchy (mg_strength 0.05), 4 iterations per
-solver step, at most 2000 iterations per column.
+on the strength-filtered hierarchy (mg_strength 0.05) with the W(1,2) cycle,
+4 iterations per solver step, at most 2000 iterations per column.
 
 The oracle checks every column without trusting the library's own numbers:
 
-* its FP64 error certificate, recomputed from the returned field: S >= M for
-  the paper's real operator S = M + 1/2 l^4 K M^-1 K, so
-  ||x - x*||_M <= ||b - S x||_{M^-1}; every column must show a bound of at most
-  1e-6 ||x||_M (the target tolerance against the FP64 solution) wherever the
-  oracle's FP64 evaluation of b - S x can resolve it.  Its rounding noise grows
-  like eps kappa(S) ||x||_M with kappa(S) = 1 + 1/2 (l^2 lambda_max(M^-1 K))^2,
-  which reaches 1e9 - 1e10 at the largest scales on this mesh.  Columns with
-  1000 eps kappa(S) > 1e-7 are "limited by conditioning": their certificate is
-  reported and only checked to be below 1e-3 (the library's own bound, computed
-  in the complex form whose condition is the square root, is 1e-8 for every
-  column);
+* a bound on its relative M-norm error, computed in FP64 from the returned
+  field.  S >= M for the paper's real operator S = M + 1/2 l^4 K M^-1 K, so
+  ||x - x*||_M <= ||b - S x||_{M^-1} (the plain certificate).  At the largest
+  scales kappa(S) = 1 + 1/2 (l^2 lambda_max(M^-1 K))^2 reaches 1e9 - 4e10 on
+  this mesh, and there the plain certificate of any FP64 vector sits near
+  eps kappa(S) ||x||_M: rounding x alone leaves a residual that S amplifies by
+  up to kappa.  Where the plain certificate is above the target the oracle
+  sharpens it with its own conjugate-gradient correction on the residual
+  equation (`oracle.refined_certificate`: ||e~||_M + ||r - S e~||_{M^-1}, still
+  a bound).  Every column must reach 1e-6 ||x||_M, the target tolerance
+  against the FP64 solution;
 * element by element against its own conjugate-gradient solve, for the
   largest wavenumber and for a mid-range one (index 30 of 40, a 40 km
   wavelength: about one mesh spacing for l, so the oracle's unpreconditioned
   CG ends in minutes at 10.5 M vertices).
+
+The certificates of the 40 columns are independent and run on a thread pool
+(the sparse products release the interpreter lock).
 """
+
+import os
+import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -33,17 +40,25 @@ import synth
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 TOL_MIXED = 1e-6
-BENCH_OPTS = dict(order=2, tol=1e-9, err_tol=1e-8, max_iter=2000, check_every=4)
 SAMPLED_K = (39, 30)
+REFINE_ITERS = 800
 
 
-EPS = np.finfo(np.float64).eps
-RESOLVED = 1e-7 / (1000.0 * EPS)  # kappa(S) up to which the oracle's FP64 certificate resolves 1e-6
+def bench_opts(lib):
+    return dict(order=2, tol=1e-9, err_tol=1e-8, max_iter=2000, check_every=4, mg_cycle=lib.MG_W12)
 
 
-def certified(P, fld, filtered, k):
-    """Largest certified relative M-norm error over the column's systems."""
-    return max(b / xn for b, xn in oracle.residual_certificate(P, fld, filtered, k, 2))
+def column_certificate(P, fld, filtered, k, lam):
+    """(kappa(S), plain bound, refined bound or None, seconds) of one column,
+    each bound relative to ||x||_M and the largest over the column's systems."""
+    t = time.time()
+    kappa = 1.0 + 0.5 * (lam / k ** 2) ** 2
+    plain = max(b / xn for b, xn in oracle.residual_certificate(P, fld, filtered, k, 2))
+    refined = None
+    if plain > 0.5 * TOL_MIXED:
+        refined = max(b / xn for b, xn in oracle.refined_certificate(
+            P, fld, filtered, k, 2, iters=REFINE_ITERS, stop=0.6 * TOL_MIXED))
+    return kappa, plain, refined, time.time() - t
 
 
 @pytest.fixture(scope="module")
@@ -58,7 +73,7 @@ def test_uv_batch_level10_certified_and_sampled(lib, workload, placement):
     h = lib.prepare_mesh(w["mesh"], placement, max_order=2, mg_strength=0.05)
     f = torch.tensor(w["fields"], device="cuda")
     out, stats, st = lib.solve(h, f, w["k"], precision=lib.PREC_FP32_IR, n2_solver=lib.N2_COMPLEX,
-                               precond=lib.PRECOND_MG, **BENCH_OPTS)
+                               precond=lib.PRECOND_MG, **bench_opts(lib))
     h.release()
     assert st == 0, stats
     assert (stats["status"] == 0).all()
@@ -69,18 +84,16 @@ def test_uv_batch_level10_certified_and_sampled(lib, workload, placement):
     fld = w["fields"][0]
     K = w["k"].size
     lam = oracle.lambda_max_minv_k(P)
-    limited, worst = [], 0.0
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        cert = list(ex.map(lambda j: column_certificate(P, fld, res[0, j], w["k"][j], lam), range(K)))
+    final = [c[2] if c[2] is not None else c[1] for c in cert]
+    refined = [(j, f"{c[0]:.3g}", f"{c[1]:.3g}", f"{c[2]:.3g}", round(c[3])) for j, c in enumerate(cert)
+               if c[2] is not None]
+    print(f"{placement}: lambda_max(M^-1 K) {lam:.4g}; worst certificate {max(final):.3g}; "
+          f"refined columns (k index, kappa, plain, refined, s): {refined}")
     for j in range(K):
-        kappa = 1.0 + 0.5 * (lam / w["k"][j] ** 2) ** 2
-        rel = certified(P, fld, res[0, j], w["k"][j])
-        if kappa <= RESOLVED:
-            assert rel <= TOL_MIXED, (j, rel, kappa)
-            worst = max(worst, rel)
-        else:
-            assert rel <= 1e-3, (j, rel, kappa)
-            limited.append((j, float(f"{rel:.3g}"), float(f"{kappa:.3g}")))
-    print(f"{placement}: lambda_max(M^-1 K) {lam:.4g}; worst certificate where resolved {worst:.3g}; "
-          f"limited by conditioning (k index, certificate, kappa): {limited}")
+        assert final[j] <= TOL_MIXED, (j, cert[j])
     ref, _ = oracle.filter_field(P, fld, [w["k"][j] for j in SAMPLED_K], 2, rtol=1e-12)
     for i, j in enumerate(SAMPLED_K):
         for c in range(ref.shape[1]):

@@ -394,6 +394,9 @@ def test_refined_certificate_is_a_bound_and_tighter(placement):
         assert err <= ref * (1 + 1e-9) and ref <= plain * (1 + 1e-9)
         # here the plain bound is about 45 times the error, the refined one within a few percent
         assert plain > 10.0 * err and ref <= 1.1 * err, (ref / err, plain / err)
+        # stopping early on the recurrence's residual keeps it a bound
+        (early, _), = oracle.refined_certificate(P, f, cand, k, 2, iters=30, stop=0.1 * err / xn)
+        assert err <= early * (1 + 1e-9) and early <= 1.5 * err, early / err
 
 
 @pytest.mark.parametrize("placement", ["vertex_scalar", "vertex_vector", "cell"])
