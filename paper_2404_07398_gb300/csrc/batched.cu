@@ -2858,7 +2858,7 @@ class EngineT final : public Engine {
         nb = mg_gather<kEpiSmooth, 2>(l, L.S, x, out, L.dm32, L.dk32, rhs, nullptr, partial, L.omega);
       const DevEll& S = l == 0 ? m_->ell_k : L.S;
       const double out_b = final ? (double)n_ * NS * P_.W * sizeof(T) : mg_vb(l);
-      pmark(l == 0 ? kCatMgSmooth0 : kCatMgSmoothC,
+      pmark(lcat(l, kCatMgSmooth0),
             mg_vb(l) + out_b + mg_vb_rhs(l) + mg_ell_b(S, l == 0 ? 1 : 2) + 2.0 * mg_rows(l) * sizeof(T));
       return nb;
     } else {
@@ -2870,7 +2870,7 @@ class EngineT final : public Engine {
       if (l == 0) mg_gather<kEpiResid, 1>(l, m_->ell_k, x, out, mass_t(), nullptr, rhs, nullptr, nullptr);
       else mg_gather<kEpiResid, 2>(l, (*mgl_)[l].S, x, out, (*mgl_)[l].dm32, nullptr, rhs, nullptr, nullptr);
       const DevEll& S = l == 0 ? m_->ell_k : (*mgl_)[l].S;
-      pmark(l == 0 ? kCatMgResid0 : kCatMgResidC,
+      pmark(lcat(l, kCatMgResid0),
             2.0 * mg_vb(l) + mg_vb_rhs(l) + mg_ell_b(S, l == 0 ? 1 : 2) + (double)mg_rows(l) * sizeof(T));
     }
   }
@@ -2879,10 +2879,10 @@ class EngineT final : public Engine {
       const DevMgLevel& L = (*mgl_)[l];
       if (restrict_) {
         mg_gather<kEpiRestrict, 1>(l, L.R, src, out, nullptr, nullptr, nullptr, nullptr, nullptr);
-        pmark(l == 0 ? kCatMgRestrict0 : kCatMgRestrictC, mg_vb(l) + mg_vb(l + 1) + mg_ell_b(L.R, 1));
+        pmark(lcat(l, kCatMgRestrict0), mg_vb(l) + mg_vb(l + 1) + mg_ell_b(L.R, 1));
       } else {
         mg_gather<kEpiProlong, 1>(l, L.P, src, out, nullptr, nullptr, nullptr, own, nullptr);
-        pmark(l == 0 ? kCatMgProlong0 : kCatMgProlongC, 2.0 * mg_vb(l) + mg_vb(l + 1) + mg_ell_b(L.P, 1));
+        pmark(lcat(l, kCatMgProlong0), 2.0 * mg_vb(l) + mg_vb(l + 1) + mg_ell_b(L.P, 1));
       }
     }
   }
@@ -2904,7 +2904,7 @@ class EngineT final : public Engine {
         mg_jacobi_kernel<T, TM, TM, VM, CPLX, BLK><<<g, kBlock, 0, st_>>>(Q, static_cast<const TM*>(rhs), out, md,
                                                                          kd, C_, om);
       }
-      pmark(l == 0 ? kCatMgJacobi0 : kCatMgJacobiC, mg_vb(l) + mg_vb_rhs(l) + 2.0 * rows * sizeof(T));
+      pmark(lcat(l, kCatMgJacobi0), mg_vb(l) + mg_vb_rhs(l) + 2.0 * rows * sizeof(T));
     }
   }
   // One V-cycle on level l for the right-hand side rhs: two damped-Jacobi
@@ -2982,11 +2982,17 @@ class EngineT final : public Engine {
   enum Cat {
     kCatSpmm, kCatUpdate, kCatDirection, kCatFinish, kCatResidual, kCatAccumulate,
     kCatMgJacobi0, kCatMgSmooth0, kCatMgResid0, kCatMgRestrict0, kCatMgProlong0,
+    kCatMgJacobi1, kCatMgSmooth1, kCatMgResid1, kCatMgRestrict1, kCatMgProlong1,
     kCatMgJacobiC, kCatMgSmoothC, kCatMgResidC, kCatMgRestrictC, kCatMgProlongC, kCatN
   };
+  static constexpr int kCatMgKinds = kCatMgJacobi1 - kCatMgJacobi0;
+  // a multigrid launch's category on level l: the finest level, the first
+  // coarse level (the largest), or the coarser ones together
+  static Cat lcat(size_t l, Cat fine) { return (Cat)(fine + kCatMgKinds * (int)(l < 2 ? l : 2)); }
   static constexpr const char* kCatName[kCatN] = {
       "spmm", "update", "direction", "finish", "residual", "accumulate",
       "mgjacobi0", "mgsmooth0", "mgresid0", "mgrestrict0", "mgprolong0",
+      "mgjacobi1", "mgsmooth1", "mgresid1", "mgrestrict1", "mgprolong1",
       "mgjacobic", "mgsmoothc", "mgresidc", "mgrestrictc", "mgprolongc"};
   struct Mark {
     int cat;
