@@ -40,8 +40,9 @@ N_K = 40
 # roofline's `traffic` is this ratio times the bytes of an average timed launch.
 # A kernel that changed since its capture has no entry.
 TRAFFIC_RATIO = {
-    # update, cell placement: 3.458 GB read + written vs 3.502 GB algorithmic (911,865 rows x 160 lanes)
-    "update_cs_f32": 3.457877 / 3.501562,
+    # first fine Jacobi sweep, cell placement: 1.8086 GB read + written vs 1.7872 GB algorithmic
+    # (911,865 rows x 160 lanes: iterate, right-hand side and output, ELL, mass and K diagonal)
+    "mgsmooth0_cs_f32": 1.808603 / 1.787200,
 }
 
 
