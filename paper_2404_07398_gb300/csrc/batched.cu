@@ -514,9 +514,14 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
   double* sred = reinterpret_cast<double*>(smraw);
   const size_t colb = ((size_t)P.stage_e * 4 + 15) / 16 * 16;
   const size_t valb = ((size_t)P.stage_e * NV * sizeof(MV) + 15) / 16 * 16;
+  // row lengths (A.rowq) only where rows are uneven: the Galerkin levels' (K, M) pairs and
+  // the restrictions; the other instances run every row to its slice's width
+  constexpr bool kRowq = NSET == 2 || EPI == kEpiRestrict;
+  const size_t qb = kRowq ? ((size_t)P.spt * A.slice_h + 15) / 16 * 16 : 0;
   unsigned char* const sbase = smraw + (size_t)RPP * W * sizeof(double);
-  auto stage_col = [&](int b) { return reinterpret_cast<int*>(sbase + b * (colb + valb)); };
-  auto stage_val = [&](int b) { return reinterpret_cast<MV*>(sbase + b * (colb + valb) + colb); };
+  auto stage_col = [&](int b) { return reinterpret_cast<int*>(sbase + b * (colb + valb + qb)); };
+  auto stage_val = [&](int b) { return reinterpret_cast<MV*>(sbase + b * (colb + valb + qb) + colb); };
+  auto stage_q = [&](int b) { return reinterpret_cast<const uint8_t*>(sbase + b * (colb + valb + qb) + colb + valb); };
   const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
   const int l0 = g * VEC;
   const bool on = tr < RPP && tr < TR;
@@ -531,12 +536,16 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
     const int64_t ob = A.slice_off[s0], oe = A.slice_off[s1];
     const uint32_t ne = (uint32_t)(oe - ob);
     const uint32_t bc = ne * 4u, bv = ne * (uint32_t)(NV * sizeof(MV));
+    // row lengths: whole slices of the per-row array (allocated for every slice's rows,
+    // so a multiple of 64 bytes from a 64-byte boundary)
+    const uint32_t bq = kRowq && A.rowq ? (uint32_t)((s1 - s0) * A.slice_h) : 0u;
     async_proxy_fence();  // earlier generic reads of the buffer come first
-    mbar_expect(&bar[b], bc + bv);  // with no bytes the phase completes here
+    mbar_expect(&bar[b], bc + bv + bq);  // with no bytes the phase completes here
     if (ne > 0) {
       bulk_to_smem(stage_col(b), A.col + ob, bc, &bar[b]);
       bulk_to_smem(stage_val(b), A.val + ob * NV, bv, &bar[b]);
     }
+    if (bq > 0) bulk_to_smem(const_cast<uint8_t*>(stage_q(b)), A.rowq + (int64_t)s0 * A.slice_h, bq, &bar[b]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar[0]);
@@ -595,6 +604,13 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
         const int sl = lr / H;
         const int w = s_w[b][sl];
         const int eb = s_o[b][sl] + (lr - sl * H) * w;
+        // the row's own length (a multiple of 4 entries, at most the slice's width), staged
+        // with the tile: the slice's padding past it is skipped
+        int rq = 255;
+        if constexpr (kRowq) {
+          if (A.rowq) rq = (int)stage_q(b)[lr];
+        }
+        const int wr = (kRowq && rq != 255) ? min(w, 4 * rq) : w;
         Lanes<TS, VEC> pr[NS];
         if constexpr (EPI == kEpiProlong) {
 #pragma unroll
@@ -620,10 +636,13 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
         // EB entries at a time (a multiple of 4 entries, or 2 for a 2-entry batch:
         // rows hold a multiple of 4 entries, so a batch never runs past the row)
         for (int e = 0; e < w; e += EB) {
+          if constexpr (kRowq) {
+            if (e > 0 && e >= wr) break;
+          }
           Lanes<TS, VEC> nb[EB][NS];
 #pragma unroll
           for (int h = 0; h < EB; h += 4) {
-            if (h == 0 || e + h < w) {
+            if (h == 0 || e + h < wr) {
               int cc[4];
               if constexpr (EB >= 4) {
                 const int4 c4 = *reinterpret_cast<const int4*>(scol + eb + e + h);
@@ -641,7 +660,7 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
           }
 #pragma unroll
           for (int h = 0; h < EB; h += 4) {
-            if (h == 0 || e + h < w) {
+            if (h == 0 || e + h < wr) {
               const MV* vv = sval + (size_t)(eb + e + h) * NV;
 #pragma unroll
               for (int t = 0; t < (EB >= 4 ? 4 : EB); t++) {
@@ -1932,6 +1951,7 @@ class EngineT final : public Engine {
     E_ = op_ == 1 ? &m->ell_k : (op_ == 2 ? &m->ell_g2 : &m->ell_gn[(size_t)op_ - 3]);
     A_ = ell_view<MV>(*E_);
     A64_ = ell_view<double>(*E_);
+    A_.rowq = A64_.rowq = nullptr;  // the Krylov product runs every row to its slice's width
     int lanes = o.max_lanes > 0 ? o.max_lanes : 256;
     lanes = std::min(lanes, kBlock * VEC) / 4 * 4;
     if (lanes < 4) fail(IFILT_EINVAL, "max_lanes must allow at least 4 lanes");
@@ -2009,6 +2029,7 @@ class EngineT final : public Engine {
     use_graph_ = !(ng && ng[0] == '1');
     // experiment knob: damped-Jacobi sweeps before and after the coarse correction on levels >= 1
     if (const char* cs = getenv("IFILT_MG_COARSE_SWEEPS")) mg_nu_c_ = std::max(1, std::min(6, atoi(cs)));
+    if (const char* fs = getenv("IFILT_MG_FINE_SWEEPS")) mg_nu_f_ = std::max(1, std::min(6, atoi(fs)));
     // double-float refinement residual on the FP32 engines, unless a tolerance asks for more than its
     // about 48 bits carry on hard columns; then FP64, as on the FP64 engine
     df_ = sizeof(T) == 4 && o.tol >= kDfMinTol && (!(o.err_tol > 0.0) || o.err_tol >= kDfMinErrTol);
@@ -2080,7 +2101,8 @@ class EngineT final : public Engine {
   int64_t stage_entries(int spt) const { return (int64_t)spt * ((int64_t)E_->slice_h * E_->max_width + 8); }
   size_t stage_bytes(int spt) const {
     const int64_t e = stage_entries(spt);
-    return (size_t)((e * 4 + 15) / 16 * 16 + (e * NVAL * (int64_t)sizeof(MV) + 15) / 16 * 16);
+    return (size_t)((e * 4 + 15) / 16 * 16 + (e * NVAL * (int64_t)sizeof(MV) + 15) / 16 * 16 +
+                    ((int64_t)spt * E_->slice_h + 15) / 16 * 16);
   }
   int spmm_spt(int W) const {
     const int RPP = kBlock / (W / VEC);
@@ -2590,6 +2612,7 @@ class EngineT final : public Engine {
   int m_it_ = 32;
   bool use_graph_ = true, launched_ = false, prof_ = false;
   int mg_nu_c_ = 2;  // smoothing sweeps before and after the coarse correction on levels >= 1
+  int mg_nu_f_ = 1;  // the same on the finest level: one sweep each side (more iterations, cheaper cycles)
   // ------------------------------------------------------------ autotuning
   // Launch shape of the gather kernels (rows per tile, blocks per SM), chosen
   // per engine kind and tile-width bucket by timing the candidates on the live
@@ -2742,7 +2765,7 @@ class EngineT final : public Engine {
   }
   static size_t stage_bytes_of(const DevEll& E, int spt, int vbytes) {
     const int64_t e = stage_entries_of(E, spt);
-    return (size_t)((e * 4 + 15) / 16 * 16 + (e * vbytes + 15) / 16 * 16);
+    return (size_t)((e * 4 + 15) / 16 * 16 + (e * vbytes + 15) / 16 * 16 + ((int64_t)spt * E.slice_h + 15) / 16 * 16);
   }
   int spt_of(const DevEll& E, int W, int vbytes, int minb) const {
     const int RPP = kBlock / (W / VM);
@@ -2830,8 +2853,12 @@ class EngineT final : public Engine {
     using TO = MgTO<EPI, NSET, FINAL>;
     (void)l;
     MgArgs<T, TR, TM> args{kd, static_cast<const TR*>(rhs), own, (T)omega};
+    // row lengths only where rows are uneven (Galerkin levels, transfers): the finest
+    // level's rows fill their slices almost exactly
+    EllView<T> V = ell_view<T>(E);
+    if (&E == &m_->ell_k) V.rowq = nullptr;
     spmm_kernel<T, T, TM, TR, TO, VM, CPLX, BLK, kMgEB, mg_minb<EPI>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
-        ell_view<T>(E), Q, E.n_slices, src, static_cast<TO*>(out), mdiag, mg_cols_, partial, args);
+        V, Q, E.n_slices, src, static_cast<TO*>(out), mdiag, mg_cols_, partial, args);
     return blocks;
   }
   // S_l-operations: level 0 uses the mesh's K and lumped mass, coarser levels their (K, M) pair
@@ -2907,9 +2934,10 @@ class EngineT final : public Engine {
       pmark(lcat(l, kCatMgJacobi0), mg_vb(l) + mg_vb_rhs(l) + 2.0 * rows * sizeof(T));
     }
   }
-  // One V-cycle on level l for the right-hand side rhs: two damped-Jacobi
-  // sweeps, coarse correction, two sweeps (Jacobi sweeps only on the last
-  // level).  Returns the buffer holding the result.  On level 0 the last sweep
+  // One V-cycle on level l for the right-hand side rhs: nu damped-Jacobi
+  // sweeps (1 on the finest level, 2 below it, unless IFILT_MG_FINE_SWEEPS /
+  // IFILT_MG_COARSE_SWEEPS say otherwise), coarse correction, nu sweeps (Jacobi
+  // sweeps only on the last level).  Returns the buffer holding the result.  On level 0 the last sweep
   // writes the result z in T into zout and leaves the partials of <rhs, z> in
   // partial2_.
   TM* vcycle(size_t l, const void* rhs, T* zout = nullptr) {
@@ -2927,14 +2955,14 @@ class EngineT final : public Engine {
       }
       return x;
     }
-    mg_smooth(l, B.a, B.b, rhs, nullptr);
-    // coarse correction(s): x <- x + P V_{l+1}(R (rhs - S x)), twice on levels 1 and 2 of a W12 cycle
-    TM* x = B.b;
-    TM* t = B.a;
-    for (int s = 2; s < mg_nu(l); s++) {  // further pre-smoothing sweeps (coarse levels, on request)
+    // the first pre-smoothing sweep is the Jacobi step above (from x = 0); then nu - 1 more
+    TM* x = B.a;
+    TM* t = B.b;
+    for (int s = 1; s < mg_nu(l); s++) {
       mg_smooth(l, x, t, rhs, nullptr);
       std::swap(x, t);
     }
+    // coarse correction(s): x <- x + P V_{l+1}(R (rhs - S x)), twice on levels 1 and 2 of a W12 cycle
     for (int rep = 0; rep < mg_reps(l); rep++) {
       mg_resid(l, x, t, rhs);
       mg_transfer(l, true, t, mgb_[l + 1].r, nullptr);
@@ -2942,16 +2970,17 @@ class EngineT final : public Engine {
       mg_transfer(l, false, xc, t, x);
       std::swap(x, t);
     }
-    for (int s = 2; s < mg_nu(l); s++) {
+    // nu post-smoothing sweeps with the same damped Jacobi operator (a symmetric cycle); the last
+    // writes the result (on level 0: z in T, with the partials of <rhs, z>)
+    for (int s = 1; s < mg_nu(l); s++) {
       mg_smooth(l, x, t, rhs, nullptr);
       std::swap(x, t);
     }
-    mg_smooth(l, x, t, rhs, nullptr);
-    const int nb = mg_smooth(l, t, l == 0 ? (void*)zout : (void*)x, rhs, l == 0 ? partial2_ : nullptr, l == 0);
+    const int nb = mg_smooth(l, x, l == 0 ? (void*)zout : (void*)t, rhs, l == 0 ? partial2_ : nullptr, l == 0);
     if (l == 0) nbz_ = nb;
-    return x;
+    return t;
   }
-  int mg_nu(size_t l) const { return l == 0 ? 2 : mg_nu_c_; }
+  int mg_nu(size_t l) const { return l == 0 ? mg_nu_f_ : mg_nu_c_; }
   int mg_reps(size_t l) const { return (o_.mg_cycle == IFILT_MG_W12 && (l == 1 || l == 2)) ? 2 : 1; }
   // visits of each level in one cycle
   std::vector<int> mg_visits() const {

@@ -28,16 +28,17 @@ struct EllView {
   const int32_t* __restrict__ col;
   const MV* __restrict__ val;
   int32_t slice_h;
+  const uint8_t* __restrict__ rowq;  // per-row length in fours (see DevEll), or null
 };
 
 template <typename MV>
 inline EllView<MV> ell_view(const DevEll& e);
 template <>
-inline EllView<double> ell_view<double>(const DevEll& e) { return {e.slice_off, e.slice_w, e.col, e.val64, e.slice_h}; }
+inline EllView<double> ell_view<double>(const DevEll& e) { return {e.slice_off, e.slice_w, e.col, e.val64, e.slice_h, e.rowq}; }
 template <>
-inline EllView<float> ell_view<float>(const DevEll& e) { return {e.slice_off, e.slice_w, e.col, e.val32, e.slice_h}; }
+inline EllView<float> ell_view<float>(const DevEll& e) { return {e.slice_off, e.slice_w, e.col, e.val32, e.slice_h, e.rowq}; }
 template <>
-inline EllView<__nv_bfloat16> ell_view<__nv_bfloat16>(const DevEll& e) { return {e.slice_off, e.slice_w, e.col, e.val16, e.slice_h}; }
+inline EllView<__nv_bfloat16> ell_view<__nv_bfloat16>(const DevEll& e) { return {e.slice_off, e.slice_w, e.col, e.val16, e.slice_h, e.rowq}; }
 
 // Grid size for a bandwidth-bound kernel: whole waves of resident CTAs.
 int grid_for(const void* kernel, int block, size_t smem, long long work_items);

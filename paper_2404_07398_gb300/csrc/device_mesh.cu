@@ -86,19 +86,22 @@ __global__ void ell_width_kernel(int32_t n, int32_t slice_h, int32_t ns, const i
 // One row of the sliced ELL per thread: its entries, then padding that points at
 // the row itself with value 0 (square operators) or repeats the row's last
 // column (rectangular ones, ncols >= 0: 0 for an empty row), with the FP64
-// values' FP32, FP32-remainder and BF16 copies.  A column outside the source
-// vector raises *bad.
+// values' FP32, FP32-remainder and BF16 copies, and the row's length in fours
+// (entries rounded up to 4; 255 for rows longer than 1020 entries, which then
+// run to the slice's width).  A column outside the source vector raises *bad.
 __global__ void ell_fill_kernel(int32_t n, int32_t slice_h, int nv, int32_t ncols, const int64_t* __restrict__ rp,
                                 const int32_t* __restrict__ col, const double* __restrict__ val,
                                 const int64_t* __restrict__ off, const int32_t* __restrict__ width,
                                 int32_t* __restrict__ ecol, double* __restrict__ v64, float* __restrict__ v32,
-                                float* __restrict__ v32lo, __nv_bfloat16* __restrict__ v16, int* __restrict__ bad) {
+                                float* __restrict__ v32lo, __nv_bfloat16* __restrict__ v16,
+                                uint8_t* __restrict__ rowq, int* __restrict__ bad) {
   const int32_t limit = ncols < 0 ? n : ncols;
   for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const int32_t s = r / slice_h;
     const int32_t w = width[s];
     const int64_t base = off[s] + (int64_t)(r - s * slice_h) * w;
     const int64_t b0 = rp[r], len = rp[r + 1] - b0;
+    rowq[r] = len > 4 * 254 ? (uint8_t)255 : (uint8_t)((len + 3) / 4);
     for (int64_t e = 0; e < w; e++) {
       int32_t c;
       if (e < len) c = col[b0 + e];
@@ -171,13 +174,14 @@ void pack_ell(ifilt_mesh_s* m, const RawCSR& a, int32_t slice_h, DevEll& out, cu
   out.val32 = dev_alloc<float>(m, (size_t)E * nv, st);
   out.val32lo = dev_alloc<float>(m, (size_t)E * nv, st);
   out.val16 = dev_alloc<__nv_bfloat16>(m, (size_t)E * nv, st);
+  out.rowq = dev_alloc<uint8_t>(m, (size_t)ns * slice_h, st);  // whole slices: bulk-copied per tile
   int* bad = nullptr;
   IFILT_CUDA(cudaMalloc(&bad, sizeof(int)));
   IFILT_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
   if (n > 0) {
     const int g = (int)std::min<int64_t>(((int64_t)n + block - 1) / block, 152LL * 32);
     ell_fill_kernel<<<g, block, 0, st>>>(n, slice_h, nv, ncols, a.rp, a.col, a.val, out.slice_off, dwidth, out.col,
-                                         out.val64, out.val32, out.val32lo, out.val16, bad);
+                                         out.val64, out.val32, out.val32lo, out.val16, out.rowq, bad);
     IFILT_CUDA(cudaGetLastError());
   }
   int hbad = 0;

@@ -93,6 +93,9 @@ struct DevEll {
   float* val32 = nullptr;
   float* val32lo = nullptr;  // val64 - val32 rounded to float (double-float residual)
   __nv_bfloat16* val16 = nullptr;
+  // per row: its entries rounded up to a multiple of 4, counted in fours (255: the
+  // slice's full width); a gather stops there instead of at the slice's width
+  uint8_t* rowq = nullptr;
 };
 
 // One level of the multigrid preconditioner on the device: the pair
