@@ -4,6 +4,9 @@
 
 Every translation unit is compiled in parallel into _build/, then linked into
 paper_2404_07398_gb300/libifilt.so (static CUDA runtime, no torch dependency).
+IFILT_NVCC_FLAGS adds nvcc flags (e.g. -DIFILT_MG_MINB_XFER=3 to change a kernel's
+resident-block target); objects are not rebuilt when only these flags change, so
+build with force=True (or remove _build/) after changing them.
 """
 
 import os
@@ -34,7 +37,7 @@ def _flags(ptxas_verbose=False):
                 "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", SRC]
     if ptxas_verbose:
         f += ["-Xptxas", "-v"]
-    return f
+    return f + os.environ.get("IFILT_NVCC_FLAGS", "").split()
 
 
 def sources():

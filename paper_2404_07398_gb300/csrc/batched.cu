@@ -439,6 +439,15 @@ __device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int 
 #ifndef IFILT_MG_MINB_BLK
 #define IFILT_MG_MINB_BLK 2    // resident blocks per SM asked for the 2x2-block multigrid sweeps and residuals
 #endif
+#ifndef IFILT_MG_MINB_XFER
+#define IFILT_MG_MINB_XFER 4     // resident blocks per SM asked for the scalar-row restrictions and prolongations
+#endif
+#ifndef IFILT_MG_MINB_CRESID
+#define IFILT_MG_MINB_CRESID 3   // ... for the coarse levels' residuals (scalar rows; 4 was slower)
+#endif
+#ifndef IFILT_MG_MINB_CSMOOTH
+#define IFILT_MG_MINB_CSMOOTH 3  // ... for the coarse levels' sweeps (scalar rows; 4 spills and was slower)
+#endif
 #ifndef IFILT_SPMM_EB_BLK
 #define IFILT_SPMM_EB_BLK 4    // gathered entries in flight per row for 2x2-block FP32 SpMM
 #endif
@@ -2619,7 +2628,9 @@ class EngineT final : public Engine {
   // tiles at the first capture, and kept with the mesh for later engines.
   // The timed launches write only outputs the next iteration recomputes (q,
   // partial sums, multigrid scratch) and see a "live" flag forced to 1.
-  int tp_cg_ = kTilePasses, bpsm_cg_ = 0, tp_mg_ = kTilePasses, bpsm_mg_ = 0;  // bpsm 0: occupancy
+  int tp_cg_ = kTilePasses, bpsm_cg_ = 0;  // bpsm 0: occupancy
+  // multigrid gathers: [0] the finest level (and its transfers), [1] the coarser levels
+  int tp_mg_[2] = {kTilePasses, kTilePasses}, bpsm_mg_[2] = {0, 0};
 
   Cols mg_cols_{};
   int* tune_live_ = nullptr;
@@ -2644,8 +2655,10 @@ class EngineT final : public Engine {
       if (it != m_->tune.end()) {
         tp_cg_ = it->second[0];
         bpsm_cg_ = it->second[1];
-        tp_mg_ = it->second[2];
-        bpsm_mg_ = it->second[3];
+        tp_mg_[0] = it->second[2];
+        bpsm_mg_[0] = it->second[3];
+        tp_mg_[1] = it->second[4];
+        bpsm_mg_[1] = it->second[5];
         set_width(W);
         return;
       }
@@ -2694,31 +2707,38 @@ class EngineT final : public Engine {
     tp_cg_ = btp;
     bpsm_cg_ = bb;
     if (mg_on_) {
-      best = 1e30f;
-      btp = kTilePasses;
-      bb = 0;
+      // the finest level's sweep sets the shape of the finest level's gathers; the first coarse
+      // level's sweep (a wider, uneven operator with a (K, M) pair per entry) that of the coarser ones
       mg_cols_ = Ct;
-      for (int tp : tps) {
-        for (int bps : {0, 2}) {
-          tp_mg_ = tp;
-          bpsm_mg_ = bps;
-          const float ms = timeit([&] { mg_smooth(0, mgb_[0].a, mgb_[0].b, tl_.r, nullptr); });
-          if (ms < best) {
-            best = ms;
-            btp = tp;
-            bb = bps;
+      const int groups = mgl_->size() > 1 ? 2 : 1;
+      for (int grp = 0; grp < groups; grp++) {
+        best = 1e30f;
+        btp = kTilePasses;
+        bb = 0;
+        const void* rhs = grp == 0 ? (const void*)tl_.r : (const void*)mgb_[1].r;
+        for (int tp : tps) {
+          for (int bps : {0, 2}) {
+            tp_mg_[grp] = tp;
+            bpsm_mg_[grp] = bps;
+            const float ms = timeit([&] { mg_smooth((size_t)grp, mgb_[grp].a, mgb_[grp].b, rhs, nullptr); });
+            if (ms < best) {
+              best = ms;
+              btp = tp;
+              bb = bps;
+            }
           }
         }
+        tp_mg_[grp] = btp;
+        bpsm_mg_[grp] = bb;
       }
+      if (groups == 1) tp_mg_[1] = tp_mg_[0], bpsm_mg_[1] = bpsm_mg_[0];
       mg_cols_ = C_;
-      tp_mg_ = btp;
-      bpsm_mg_ = bb;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     set_width(W);
     std::lock_guard<std::mutex> lk(m_->tune_mu);
-    m_->tune[key] = {tp_cg_, bpsm_cg_, tp_mg_, bpsm_mg_};
+    m_->tune[key] = {tp_cg_, bpsm_cg_, tp_mg_[0], bpsm_mg_[0], tp_mg_[1], bpsm_mg_[1]};
   }
   // ------------------------------------------------------------ multigrid
   static constexpr int kMgMinB = 3;
@@ -2737,10 +2757,17 @@ class EngineT final : public Engine {
   double* partial2_ = nullptr;
   int nbz_ = 1;  // blocks of the last level-0 smoothing sweep (partials of <r, z>)
 
-  // 2x2-block sweeps and residuals hold the row's right-hand side too: fewer blocks, no spills
-  template <int EPI>
+  // Resident blocks per SM asked of the compiler, per gather kind: the scalar-row transfers fit
+  // 64 registers without spills (4 blocks: prolongation 4.6 -> 3.8 ms, restriction from the
+  // finest level 2.6 -> 2.1 ms at level 10); the 2x2-block sweeps and residuals hold the row's
+  // right-hand side too (fewer blocks, no spills)
+  template <int EPI, int NSET>
   static constexpr int mg_minb() {
-    return (BLK && (EPI == kEpiSmooth || EPI == kEpiResid)) ? IFILT_MG_MINB_BLK : kMgMinB;
+    if constexpr (!BLK && (EPI == kEpiRestrict || EPI == kEpiProlong)) return IFILT_MG_MINB_XFER;
+    if constexpr (BLK && (EPI == kEpiSmooth || EPI == kEpiResid)) return IFILT_MG_MINB_BLK;
+    if constexpr (NSET == 2 && EPI == kEpiResid) return IFILT_MG_MINB_CRESID;
+    if constexpr (NSET == 2 && EPI == kEpiSmooth) return IFILT_MG_MINB_CSMOOTH;
+    return kMgMinB;
   }
   // right-hand side type of a gather: the Krylov residual (T) for the sweeps and
   // residuals of the finest level (NSET = 1), a multigrid vector (TM) otherwise
@@ -2758,7 +2785,7 @@ class EngineT final : public Engine {
   template <int EPI, int NSET, bool FINAL = false>
   static const void* mg_fn() {
     return (const void*)spmm_kernel<T, T, TM, MgTR<EPI, NSET>, MgTO<EPI, NSET, FINAL>, VM, CPLX, BLK, kMgEB,
-                                    mg_minb<EPI>(), EPI, NSET>;
+                                    mg_minb<EPI, NSET>(), EPI, NSET>;
   }
   static int64_t stage_entries_of(const DevEll& E, int spt) {
     return (int64_t)spt * ((int64_t)E.slice_h * E.max_width + 8);
@@ -2767,10 +2794,13 @@ class EngineT final : public Engine {
     const int64_t e = stage_entries_of(E, spt);
     return (size_t)((e * 4 + 15) / 16 * 16 + (e * vbytes + 15) / 16 * 16 + ((int64_t)spt * E.slice_h + 15) / 16 * 16);
   }
-  int spt_of(const DevEll& E, int W, int vbytes, int minb) const {
+  int spt_of(const DevEll& E, int W, int vbytes, int minb, int tp) const {
     const int RPP = kBlock / (W / VM);
-    int spt = std::max(1, (RPP * tp_mg_ + E.slice_h - 1) / E.slice_h);
-    while (spt > 1 && stage_bytes_of(E, spt, vbytes) > (size_t)kStageBytes) spt--;
+    int spt = std::max(1, (RPP * tp + E.slice_h - 1) / E.slice_h);
+    // two stage buffers per block, small enough that `minb` blocks fit an SM's shared memory
+    const size_t cap = std::min<size_t>((size_t)kStageBytes,
+                                        ((size_t)227 * 1024 / (size_t)minb - smem_of(W, 2, VM) - 2048) / 2);
+    while (spt > 1 && stage_bytes_of(E, spt, vbytes) > cap) spt--;
     const long long want = (long long)n_sms_ * minb * 8;
     while (spt > 1 && (E.n_slices + spt - 1) / spt < want) spt--;
     return std::min(spt, kMaxSpt);
@@ -2843,21 +2873,21 @@ class EngineT final : public Engine {
     const int vbytes = NVAL * NSET * (int)sizeof(T);
     Params Q = P_;
     Q.n = E.n;
-    Q.spt = spt_of(E, W, vbytes, mg_minb<EPI>());
+    const int grp = l == 0 ? 0 : 1;
+    Q.spt = spt_of(E, W, vbytes, mg_minb<EPI, NSET>(), tp_mg_[grp]);
     Q.stage_e = (int)stage_entries_of(E, Q.spt);
     const size_t smem = smem_of(W, 2, VM) + 2 * stage_bytes_of(E, Q.spt, vbytes);
     const long long ntiles = (E.n_slices + Q.spt - 1) / Q.spt;
     int blocks = std::min(nb_max_, grid_for(mg_fn<EPI, NSET, FINAL>(), kBlock, smem, ntiles * kBlock));
-    if (bpsm_mg_ > 0) blocks = std::min(blocks, n_sms_ * bpsm_mg_);
+    if (bpsm_mg_[grp] > 0) blocks = std::min(blocks, n_sms_ * bpsm_mg_[grp]);
     using TR = MgTR<EPI, NSET>;
     using TO = MgTO<EPI, NSET, FINAL>;
-    (void)l;
     MgArgs<T, TR, TM> args{kd, static_cast<const TR*>(rhs), own, (T)omega};
     // row lengths only where rows are uneven (Galerkin levels, transfers): the finest
     // level's rows fill their slices almost exactly
     EllView<T> V = ell_view<T>(E);
     if (&E == &m_->ell_k) V.rowq = nullptr;
-    spmm_kernel<T, T, TM, TR, TO, VM, CPLX, BLK, kMgEB, mg_minb<EPI>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
+    spmm_kernel<T, T, TM, TR, TO, VM, CPLX, BLK, kMgEB, mg_minb<EPI, NSET>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
         V, Q, E.n_slices, src, static_cast<TO*>(out), mdiag, mg_cols_, partial, args);
     return blocks;
   }

@@ -154,7 +154,7 @@ struct ifilt_mesh_s {
   std::vector<ifilt::DevMgLevel> mg_dev;
   // autotuned launch shapes of the batched solver, per engine kind and tile width
   std::mutex tune_mu;
-  std::map<std::string, std::array<int, 4>> tune;
+  std::map<std::string, std::array<int, 6>> tune;
 };
 
 namespace ifilt {
