@@ -36,6 +36,7 @@
  *   IFILT_TRACE=1       print each batched-solver launch to stderr (read once)
  *   IFILT_MG_COARSE_SWEEPS=k  damped-Jacobi sweeps before and after the coarse
  *                       correction on multigrid levels >= 1 (1..6; default 2)
+ *   IFILT_MG_FINE_SWEEPS=k    the same on the finest level (1..6; default 1)
  */
 #ifndef IFILT_H
 #define IFILT_H
