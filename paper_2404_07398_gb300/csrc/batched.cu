@@ -1557,7 +1557,9 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
   constexpr int NS = BLK ? 2 : 1;
   constexpr int NV = BLK ? 2 : 1;
   if (C.live[1] == 0) return;
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int s_w[2][kMaxSpt], s_o[2][kMaxSpt];
+  __shared__ __align__(8) uint64_t bar[2];
   const int W = P.W;
   const int ncolsW = CPLX ? W / 2 : W;
   const int NSL = W + 3 * ncolsW;
@@ -1565,204 +1567,294 @@ __global__ void __launch_bounds__(kBlock, 2) residual_df_kernel(EllView<float> A
   const int RPP = kBlock / TPR;
   const int tr = threadIdx.x / TPR, g = threadIdx.x - tr * TPR;
   const int l0 = g * VEC;
+  // Tiles of `spt` ELL slices: their column indices and the operator's hi and lo values are
+  // bulk-copied into one of two shared-memory buffers while the block works on the previous
+  // tile, as in spmm_kernel, so a row waits only on its gathered rows and its own operands.
+  const int H = A.slice_h;
+  const int spt = P.spt;
+  const int TR = spt * H;
+  const int n_slices = (int)((P.n + H - 1) / H);
+  const int ntiles = (n_slices + spt - 1) / spt;
+  unsigned char* const sbase =
+      reinterpret_cast<unsigned char*>(sm) + ((size_t)RPP * NSL * sizeof(double) + 15) / 16 * 16;
+  const size_t colb = ((size_t)P.stage_e * 4 + 15) / 16 * 16;
+  const size_t valb = ((size_t)P.stage_e * NV * sizeof(float) + 15) / 16 * 16;
+  auto stage_col = [&](int b) { return reinterpret_cast<int*>(sbase + b * (colb + 2 * valb)); };
+  auto stage_hi = [&](int b) { return reinterpret_cast<float*>(sbase + b * (colb + 2 * valb) + colb); };
+  auto stage_lo = [&](int b) { return reinterpret_cast<float*>(sbase + b * (colb + 2 * valb) + colb + valb); };
+  auto issue = [&](int tile, int b) {  // one thread
+    const int s0 = tile * spt, s1 = min(s0 + spt, n_slices);
+    const int64_t ob = A.slice_off[s0], oe = A.slice_off[s1];
+    const uint32_t ne = (uint32_t)(oe - ob);
+    const uint32_t bc = ne * 4u, bv = ne * (uint32_t)(NV * sizeof(float));
+    async_proxy_fence();  // earlier generic reads of the buffer come first
+    mbar_expect(&bar[b], bc + 2 * bv);
+    if (ne > 0) {
+      bulk_to_smem(stage_col(b), A.col + ob, bc, &bar[b]);
+      bulk_to_smem(stage_hi(b), A.val + ob * NV, bv, &bar[b]);
+      bulk_to_smem(stage_lo(b), vlo + ob * NV, bv, &bar[b]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    async_proxy_fence();
+  }
+  __syncthreads();
+  if ((int)blockIdx.x < ntiles) {
+    const int s0 = blockIdx.x * spt, cnt = min(s0 + spt, n_slices) - s0;
+    if (threadIdx.x == 0) issue(blockIdx.x, 0);
+    if ((int)threadIdx.x < cnt) {
+      s_w[0][threadIdx.x] = A.slice_w[s0 + threadIdx.x];
+      s_o[0][threadIdx.x] = (int)(A.slice_off[s0 + threadIdx.x] - A.slice_off[s0]);
+    }
+  }
+  __syncthreads();
   DotAcc<float> d1[VEC], d2[VEC], e2[VEC], x2[VEC];
   bool mine[VEC];
   bool any = false, all = true;
 #pragma unroll
   for (int v = 0; v < VEC; v++) {
-    mine[v] = C.refresh[CPLX ? (l0 + v) >> 1 : l0 + v] != 0;
+    mine[v] = tr < RPP && C.refresh[CPLX ? (l0 + v) >> 1 : l0 + v] != 0;
     any |= mine[v];
     all &= mine[v];
   }
-  if (tr < RPP && any) {
-    DF sh[VEC];
-    int src[VEC];
-    float shf[VEC];
+  const bool work = tr < RPP && any;
+  DF sh[VEC];
+  int src[VEC];
+  float shf[VEC];
 #pragma unroll
-    for (int v = 0; v < VEC; v++) {
-      const double s = C.shift[CPLX ? (l0 + v) >> 1 : l0 + v];
-      sh[v] = df_from(s);
-      shf[v] = (float)s;
-      src[v] = lane_src[l0 + v];
+  for (int v = 0; v < VEC; v++) {
+    const double s = work ? C.shift[CPLX ? (l0 + v) >> 1 : l0 + v] : 0.0;
+    sh[v] = df_from(s);
+    shf[v] = (float)s;
+    src[v] = work ? lane_src[l0 + v] : 0;
+  }
+  const int64_t rowW = (int64_t)NS * W;
+  const int64_t sstride = (int64_t)P.n * NS;  // blocks of a source buffer
+  int chain = 0;
+  unsigned inflight = (int)blockIdx.x < ntiles ? 1u : 0u;  // bit b: a copy into buffer b is outstanding
+  int it = 0;
+  bool failed = false;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+    const int buf = it & 1;
+    const int next = tile + gridDim.x;
+    int nw = 0, no = 0, ncnt = 0;
+    if (next < ntiles) {
+      if (threadIdx.x == 0) issue(next, buf ^ 1);
+      inflight |= 1u << (buf ^ 1);
+      const int s0 = next * spt;
+      ncnt = min(s0 + spt, n_slices) - s0;
+      if ((int)threadIdx.x < ncnt) {  // consumed after this tile's rows
+        nw = A.slice_w[s0 + threadIdx.x];
+        no = (int)(A.slice_off[s0 + threadIdx.x] - A.slice_off[s0]);
+      }
     }
-    const int64_t rowW = (int64_t)NS * W;
-    const int64_t sstride = (int64_t)P.n * NS;  // blocks of a source buffer
-    int chain = 0;
-    for (int64_t row = (int64_t)blockIdx.x * RPP + tr; row < P.n; row += (int64_t)gridDim.x * RPP) {
-      const int s = (int)(row / A.slice_h);
-      const int w = A.slice_w[s];
-      const int64_t base = A.slice_off[s] + (row - (int64_t)s * A.slice_h) * w;
-      DF acc[NS][VEC];
-#pragma unroll
-      for (int b = 0; b < NS; b++)
-#pragma unroll
-        for (int v = 0; v < VEC; v++) acc[b][v] = DF{0.f, 0.f};
-      // The row's source values (e0, g0, x0 of each refreshed column): loaded
-      // before its gathers, so that both wait out one memory latency together,
-      // where the registers allow it (scalar rows); after them for 2x2 blocks.
-      constexpr int SV = CPLX ? VEC / 2 : VEC;  // source values per sub-row: one per column
-      constexpr bool HOIST = !BLK;
-      DF se0[NS][SV], sg0[NS][SV];
-      float sx0[NS][SV];
-      auto load_sources = [&]() {
-#pragma unroll
+    bool late = false;
+    if (threadIdx.x == 0) late = !mbar_wait_bounded(&bar[buf], (uint32_t)((it >> 1) & 1));
+    if (__syncthreads_or(late)) {
+      failed = true;
+      break;
+    }
+    inflight &= ~(1u << buf);
+    const int* scol = stage_col(buf);
+    const float* shi = stage_hi(buf);
+    const float* slo = stage_lo(buf);
+    const int64_t r0 = (int64_t)tile * TR;
+    const int rows = (int)min((int64_t)TR, P.n - r0);
+    if (work) {
+      for (int lr = tr; lr < rows; lr += RPP) {
+        const int64_t row = r0 + lr;
+        const int sl = lr / H;
+        const int w = s_w[buf][sl];
+        const int eb = s_o[buf][sl] + (lr - sl * H) * w;
+        DF acc[NS][VEC];
+  #pragma unroll
         for (int b = 0; b < NS; b++)
-#pragma unroll
-          for (int c = 0; c < SV; c++) {
-            const int v = CPLX ? 2 * c : c;
-            se0[b][c] = sg0[b][c] = DF{0.f, 0.f};
-            sx0[b][c] = 0.f;
-            if (mine[v]) {  // a retired column's source may be gone
-              const DF* sb = bptr[src[v]] + row * NS + b;
-              se0[b][c] = sb[0];
-              sg0[b][c] = sb[2 * sstride];
-              sx0[b][c] = reinterpret_cast<const float*>(bptr[src[v]] + 3 * sstride)[row * NS + b];
+  #pragma unroll
+          for (int v = 0; v < VEC; v++) acc[b][v] = DF{0.f, 0.f};
+        // The row's source values (e0, g0, x0 of each refreshed column): loaded
+        // before its gathers, so that both wait out one memory latency together,
+        // where the registers allow it (scalar rows); after them for 2x2 blocks.
+        constexpr int SV = CPLX ? VEC / 2 : VEC;  // source values per sub-row: one per column
+        constexpr bool HOIST = !BLK;
+        DF se0[NS][SV], sg0[NS][SV];
+        float sx0[NS][SV];
+        auto load_sources = [&]() {
+  #pragma unroll
+          for (int b = 0; b < NS; b++)
+  #pragma unroll
+            for (int c = 0; c < SV; c++) {
+              const int v = CPLX ? 2 * c : c;
+              se0[b][c] = sg0[b][c] = DF{0.f, 0.f};
+              sx0[b][c] = 0.f;
+              if (mine[v]) {  // a retired column's source may be gone
+                const DF* sb = bptr[src[v]] + row * NS + b;
+                se0[b][c] = sb[0];
+                sg0[b][c] = sb[2 * sstride];
+                sx0[b][c] = reinterpret_cast<const float*>(bptr[src[v]] + 3 * sstride)[row * NS + b];
+              }
+            }
+        };
+        if constexpr (HOIST) load_sources();
+        // EBR entries at a time: their column indices in one load, then all their
+        // gathered rows, then the arithmetic (one round of dependent loads per batch).
+        // Rows hold a multiple of 4 entries and start 4-aligned, so the index and
+        // value loads are aligned vector loads.
+        constexpr int EBR = BLK ? 2 : 4;
+        for (int e = 0; e < w; e += EBR) {
+          int cc[EBR];
+          if constexpr (EBR == 4) {
+            const int4 c4 = *reinterpret_cast<const int4*>(scol + eb + e);
+            cc[0] = c4.x, cc[1] = c4.y, cc[2] = c4.z, cc[3] = c4.w;
+          } else {
+            const int2 c2 = *reinterpret_cast<const int2*>(scol + eb + e);
+            cc[0] = c2.x, cc[1] = c2.y;
+          }
+          float4 xv[EBR][NS][2];  // 4 lanes of (hi, lo) pairs per entry and sub-row
+  #pragma unroll
+          for (int t = 0; t < EBR; t++)
+  #pragma unroll
+            for (int b = 0; b < NS; b++) {
+              const float4* xp = reinterpret_cast<const float4*>(x + (int64_t)cc[t] * rowW + (int64_t)b * W + l0);
+              xv[t][b][0] = __ldg(xp);
+              xv[t][b][1] = __ldg(xp + 1);
+            }
+          const float4 vh = *reinterpret_cast<const float4*>(shi + (eb + e) * NV);
+          const float4 vl = *reinterpret_cast<const float4*>(slo + (eb + e) * NV);
+          const float hv[4] = {vh.x, vh.y, vh.z, vh.w}, lv[4] = {vl.x, vl.y, vl.z, vl.w};
+  #pragma unroll
+          for (int t = 0; t < EBR; t++) {
+            DF xu[VEC], xw[VEC];
+  #pragma unroll
+            for (int b = 0; b < NS; b++) {
+              DF* d = b == 0 ? xu : xw;
+              d[0] = DF{xv[t][b][0].x, xv[t][b][0].y};
+              d[1] = DF{xv[t][b][0].z, xv[t][b][0].w};
+              d[2] = DF{xv[t][b][1].x, xv[t][b][1].y};
+              d[3] = DF{xv[t][b][1].z, xv[t][b][1].w};
+            }
+            if constexpr (BLK) {
+              const DF a{hv[2 * t], lv[2 * t]};
+              const DF bb{hv[2 * t + 1], lv[2 * t + 1]};
+  #pragma unroll
+              for (int v = 0; v < VEC; v++) {
+                acc[0][v] = df_add(acc[0][v], df_add(df_mul(a, xu[v]), df_mul(bb, xw[v])));
+                acc[1][v] = df_add(acc[1][v], df_add(df_mul(a, xw[v]), df_neg(df_mul(bb, xu[v]))));
+              }
+            } else {
+              const DF a{hv[t], lv[t]};
+  #pragma unroll
+              for (int v = 0; v < VEC; v++) acc[0][v] = df_add(acc[0][v], df_mul(a, xu[v]));
             }
           }
-      };
-      if constexpr (HOIST) load_sources();
-      // EBR entries at a time: their column indices in one load, then all their
-      // gathered rows, then the arithmetic (one round of dependent loads per batch).
-      // Rows hold a multiple of 4 entries and start 4-aligned, so the index and
-      // value loads are aligned vector loads.
-      constexpr int EBR = BLK ? 2 : 4;
-      for (int e = 0; e < w; e += EBR) {
-        int cc[EBR];
-        if constexpr (EBR == 4) {
-          const int4 c4 = __ldg(reinterpret_cast<const int4*>(A.col + base + e));
-          cc[0] = c4.x, cc[1] = c4.y, cc[2] = c4.z, cc[3] = c4.w;
-        } else {
-          const int2 c2 = __ldg(reinterpret_cast<const int2*>(A.col + base + e));
-          cc[0] = c2.x, cc[1] = c2.y;
         }
-        float4 xv[EBR][NS][2];  // 4 lanes of (hi, lo) pairs per entry and sub-row
-#pragma unroll
-        for (int t = 0; t < EBR; t++)
-#pragma unroll
-          for (int b = 0; b < NS; b++) {
-            const float4* xp = reinterpret_cast<const float4*>(x + (int64_t)cc[t] * rowW + (int64_t)b * W + l0);
-            xv[t][b][0] = __ldg(xp);
-            xv[t][b][1] = __ldg(xp + 1);
+        if constexpr (!HOIST) load_sources();
+        const DF mr{mhi[row], mlo[row]};
+        const float mrf = mhi[row];
+        const float imrf = 1.0f / mrf;  // once per row: the M^-1-norm terms of its lanes
+        const float gr = gdiag ? gdiag[row] : 0.f;
+        if (++chain == kFlushRows) {
+          chain = 0;
+  #pragma unroll
+          for (int v = 0; v < VEC; v++) {
+            d1[v].flush();
+            d2[v].flush();
+            e2[v].flush();
+            x2[v].flush();
           }
-        const float4 vh = __ldg(reinterpret_cast<const float4*>(A.val + (base + e) * NV));
-        const float4 vl = __ldg(reinterpret_cast<const float4*>(vlo + (base + e) * NV));
-        const float hv[4] = {vh.x, vh.y, vh.z, vh.w}, lv[4] = {vl.x, vl.y, vl.z, vl.w};
-#pragma unroll
-        for (int t = 0; t < EBR; t++) {
-          DF xu[VEC], xw[VEC];
-#pragma unroll
-          for (int b = 0; b < NS; b++) {
-            DF* d = b == 0 ? xu : xw;
-            d[0] = DF{xv[t][b][0].x, xv[t][b][0].y};
-            d[1] = DF{xv[t][b][0].z, xv[t][b][0].w};
-            d[2] = DF{xv[t][b][1].x, xv[t][b][1].y};
-            d[3] = DF{xv[t][b][1].z, xv[t][b][1].w};
+        }
+  #pragma unroll
+        for (int b = 0; b < NS; b++) {
+          const int64_t off = row * rowW + (int64_t)b * W + l0;
+          DF xo[VEC];
+          {
+            const float4* xp = reinterpret_cast<const float4*>(x + off);
+            const float4 a = __ldg(xp), c = __ldg(xp + 1);
+            xo[0] = DF{a.x, a.y}, xo[1] = DF{a.z, a.w}, xo[2] = DF{c.x, c.y}, xo[3] = DF{c.z, c.w};
           }
-          if constexpr (BLK) {
-            const DF a{hv[2 * t], lv[2 * t]};
-            const DF bb{hv[2 * t + 1], lv[2 * t + 1]};
-#pragma unroll
-            for (int v = 0; v < VEC; v++) {
-              acc[0][v] = df_add(acc[0][v], df_add(df_mul(a, xu[v]), df_mul(bb, xw[v])));
-              acc[1][v] = df_add(acc[1][v], df_add(df_mul(a, xw[v]), df_neg(df_mul(bb, xu[v]))));
+          Pack<float> ro, po, zo;
+  #pragma unroll
+          for (int v = 0; v < VEC; v++) zo.v[v] = 0.f;
+          if constexpr (CPLX) {
+  #pragma unroll
+            for (int v = 0; v < VEC; v += 2) {
+              const DF e0 = se0[b][v / 2], g0 = sg0[b][v / 2];
+              const float x0 = sx0[b][v / 2];
+              // r_re = e0 - (m d_re - s acc_im),  r_im = -s g0 - (m d_im + s acc_re)
+              const DF q_re = df_add(df_mul(mr, xo[v]), df_neg(df_mul(sh[v], acc[b][v + 1])));
+              const DF q_im = df_add(df_mul(mr, xo[v + 1]), df_mul(sh[v], acc[b][v]));
+              const DF rre = df_add(e0, df_neg(q_re));
+              const DF rim = df_neg(df_add(df_mul(sh[v], g0), q_im));
+              const float tre = rre.hi + rre.lo, tim = rim.hi + rim.lo;
+              float zre = tre, zim = tim;
+              if (gdiag) {
+                const float bg = shf[v] * gr;
+                const float inv = 1.f / __fmaf_rn(mrf, mrf, bg * bg);
+                zre = __fmaf_rn(tre, mrf, tim * bg) * inv;
+                zim = __fmaf_rn(tim, mrf, -(tre * bg)) * inv;
+              }
+              ro.v[v] = tre;
+              ro.v[v + 1] = tim;
+              po.v[v] = zre;
+              po.v[v + 1] = zim;
+              d1[v].add_sum(__fmaf_rn(tre, zre, -(tim * zim)));
+              d1[v + 1].add_sum(__fmaf_rn(tre, zim, tim * zre));
+              const float nn = __fmaf_rn(tre, tre, tim * tim);
+              d2[v / 2].add_sum(nn);
+              e2[v / 2].add_sum(nn * imrf);
+              const float xr = x0 + xo[v].hi;
+              x2[v / 2].add_sum(mrf * xr * xr);  // the filtered field is the real part
             }
           } else {
-            const DF a{hv[t], lv[t]};
-#pragma unroll
-            for (int v = 0; v < VEC; v++) acc[0][v] = df_add(acc[0][v], df_mul(a, xu[v]));
-          }
-        }
-      }
-      if constexpr (!HOIST) load_sources();
-      const DF mr{mhi[row], mlo[row]};
-      const float mrf = mhi[row];
-      const float imrf = 1.0f / mrf;  // once per row: the M^-1-norm terms of its lanes
-      const float gr = gdiag ? gdiag[row] : 0.f;
-      if (++chain == kFlushRows) {
-        chain = 0;
-#pragma unroll
-        for (int v = 0; v < VEC; v++) {
-          d1[v].flush();
-          d2[v].flush();
-          e2[v].flush();
-          x2[v].flush();
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < NS; b++) {
-        const int64_t off = row * rowW + (int64_t)b * W + l0;
-        DF xo[VEC];
-        {
-          const float4* xp = reinterpret_cast<const float4*>(x + off);
-          const float4 a = __ldg(xp), c = __ldg(xp + 1);
-          xo[0] = DF{a.x, a.y}, xo[1] = DF{a.z, a.w}, xo[2] = DF{c.x, c.y}, xo[3] = DF{c.z, c.w};
-        }
-        Pack<float> ro, po, zo;
-#pragma unroll
-        for (int v = 0; v < VEC; v++) zo.v[v] = 0.f;
-        if constexpr (CPLX) {
-#pragma unroll
-          for (int v = 0; v < VEC; v += 2) {
-            const DF e0 = se0[b][v / 2], g0 = sg0[b][v / 2];
-            const float x0 = sx0[b][v / 2];
-            // r_re = e0 - (m d_re - s acc_im),  r_im = -s g0 - (m d_im + s acc_re)
-            const DF q_re = df_add(df_mul(mr, xo[v]), df_neg(df_mul(sh[v], acc[b][v + 1])));
-            const DF q_im = df_add(df_mul(mr, xo[v + 1]), df_mul(sh[v], acc[b][v]));
-            const DF rre = df_add(e0, df_neg(q_re));
-            const DF rim = df_neg(df_add(df_mul(sh[v], g0), q_im));
-            const float tre = rre.hi + rre.lo, tim = rim.hi + rim.lo;
-            float zre = tre, zim = tim;
-            if (gdiag) {
-              const float bg = shf[v] * gr;
-              const float inv = 1.f / __fmaf_rn(mrf, mrf, bg * bg);
-              zre = __fmaf_rn(tre, mrf, tim * bg) * inv;
-              zim = __fmaf_rn(tim, mrf, -(tre * bg)) * inv;
+  #pragma unroll
+            for (int v = 0; v < VEC; v++) {
+              const DF e0 = se0[b][v], g0 = sg0[b][v];
+              const float x0 = sx0[b][v];
+              const DF q = df_add(df_mul(mr, xo[v]), df_mul(sh[v], acc[b][v]));
+              const DF rv = df_add(df_add(e0, df_neg(df_mul(sh[v], g0))), df_neg(q));
+              const float t = rv.hi + rv.lo;
+              const float z = gdiag ? t / __fmaf_rn(shf[v], gr, mrf) : t;
+              ro.v[v] = t;
+              po.v[v] = z;
+              d1[v].add(t, z);
+              d2[v].add(t, t);
+              e2[v].add_sum(t * t * imrf);
+              const float xr = x0 + xo[v].hi;
+              x2[v].add_sum(mrf * xr * xr);
             }
-            ro.v[v] = tre;
-            ro.v[v + 1] = tim;
-            po.v[v] = zre;
-            po.v[v + 1] = zim;
-            d1[v].add_sum(__fmaf_rn(tre, zre, -(tim * zim)));
-            d1[v + 1].add_sum(__fmaf_rn(tre, zim, tim * zre));
-            const float nn = __fmaf_rn(tre, tre, tim * tim);
-            d2[v / 2].add_sum(nn);
-            e2[v / 2].add_sum(nn * imrf);
-            const float xr = x0 + xo[v].hi;
-            x2[v / 2].add_sum(mrf * xr * xr);  // the filtered field is the real part
           }
-        } else {
-#pragma unroll
-          for (int v = 0; v < VEC; v++) {
-            const DF e0 = se0[b][v], g0 = sg0[b][v];
-            const float x0 = sx0[b][v];
-            const DF q = df_add(df_mul(mr, xo[v]), df_mul(sh[v], acc[b][v]));
-            const DF rv = df_add(df_add(e0, df_neg(df_mul(sh[v], g0))), df_neg(q));
-            const float t = rv.hi + rv.lo;
-            const float z = gdiag ? t / __fmaf_rn(shf[v], gr, mrf) : t;
-            ro.v[v] = t;
-            po.v[v] = z;
-            d1[v].add(t, z);
-            d2[v].add(t, t);
-            e2[v].add_sum(t * t * imrf);
-            const float xr = x0 + xo[v].hi;
-            x2[v].add_sum(mrf * xr * xr);
+          if (all) {
+            stp(r + off, ro);
+            stp(p + off, po);
+            stp(d + off, zo);
+          } else {
+  #pragma unroll
+            for (int v = 0; v < VEC; v++)
+              if (mine[v]) {
+                r[off + v] = ro.v[v];
+                p[off + v] = po.v[v];
+                d[off + v] = 0.f;
+              }
           }
-        }
-        if (all) {
-          stp(r + off, ro);
-          stp(p + off, po);
-          stp(d + off, zo);
-        } else {
-#pragma unroll
-          for (int v = 0; v < VEC; v++)
-            if (mine[v]) {
-              r[off + v] = ro.v[v];
-              p[off + v] = po.v[v];
-              d[off + v] = 0.f;
-            }
         }
       }
     }
+    if ((int)threadIdx.x < ncnt) {
+      s_w[buf ^ 1][threadIdx.x] = nw;
+      s_o[buf ^ 1][threadIdx.x] = no;
+    }
+    __syncthreads();  // the buffer is free for the tile after next; the next tile's layout is visible
+  }
+  if (failed) {
+    // leave no bulk copy writing into this block's shared memory after it exits
+    if (threadIdx.x == 0) {
+      const int b0 = it & 1, b1 = b0 ^ 1;
+      if (inflight & (1u << b0)) (void)mbar_wait_bounded(&bar[b0], (uint32_t)((it >> 1) & 1));
+      if (inflight & (1u << b1)) (void)mbar_wait_bounded(&bar[b1], (uint32_t)(((it + 1) >> 1) & 1));
+      atomicExch(C.live + 3, 1);
+    }
+    return;
   }
   if (tr < RPP) {
 #pragma unroll
@@ -1977,6 +2069,11 @@ class EngineT final : public Engine {
     IFILT_CUDA(cudaFuncSetAttribute((const void*)spmm_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(kBlock * VEC * sizeof(double) +
                                           2 * std::max(stage_bytes(1), (size_t)kStageBytes))));
+    if constexpr (sizeof(T) == 4)
+      IFILT_CUDA(cudaFuncSetAttribute((const void*)residual_df_kernel<CPLX, BLK>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(smem_of(wcap_ > 0 ? wcap_ : 4, 8, 4) + 16 +
+                                            2 * std::max(res_stage_bytes(1), (size_t)kStageBytes))));
     // fixed part: partial sums, column state, tables
     size_t total = (size_t)nb_max_ * 8 * wcap_ * 8 + (size_t)ncap_ * (8 * 18 + 4 * 12 + 4 * 8) +
                    (size_t)wcap_ * 8 + 64 * 256;
@@ -2123,6 +2220,19 @@ class EngineT final : public Engine {
     return std::min(spt, kMaxSpt);
   }
   size_t spmm_smem(int W) const { return smem_of(W, 2) + 2 * stage_bytes(spmm_spt(W)); }
+  // the double-float residual's stage: column indices and the operator's hi and lo values
+  size_t res_stage_bytes(int spt) const {
+    const int64_t e = stage_entries(spt);
+    return (size_t)((e * 4 + 15) / 16 * 16 + 2 * ((e * NVAL * 4 + 15) / 16 * 16));
+  }
+  int res_spt(int W) const {
+    const int RPP = kBlock / (W / 4);
+    int spt = std::max(1, (RPP * kTilePasses + E_->slice_h - 1) / E_->slice_h);
+    while (spt > 1 && res_stage_bytes(spt) > (size_t)kStageBytes) spt--;
+    const long long want = (long long)n_sms_ * 2 * 8;  // several tiles per resident block
+    while (spt > 1 && (E_->n_slices + spt - 1) / spt < want) spt--;
+    return std::min(spt, kMaxSpt);
+  }
   int blocks_for(int W) const {
     const long long ntiles = (E_->n_slices + spmm_spt(W) - 1) / spmm_spt(W);
     int nb = std::min(nb_max_, grid_for((const void*)spmm_fn(), kBlock, spmm_smem(W), ntiles * kBlock));
@@ -2221,8 +2331,6 @@ class EngineT final : public Engine {
     const double ell_b = (double)E_->entries * (4.0 + E_->nval * sizeof(MV));
     const double rows_t = (double)n_ * sizeof(T);
     const int ga = grid_for((const void*)accumulate_kernel<T, CPLX>, kBlock, 0, n_ * NS * W);
-    const int nr = std::min(nb_max_, grid_for((const void*)residual_df_kernel<CPLX, BLK>, kBlock, sm4,
-                                              (long long)n_ * (W / VEC)));
     marks_.clear();
     pmark_open();
     scan_kernel<<<1, 256, 0, st_>>>(P_.ncols, C_);
@@ -2246,10 +2354,17 @@ class EngineT final : public Engine {
     bool done_res = false;
     if constexpr (sizeof(T) == 4) {
       if (df_) {
+        Params Qr = P_;
+        Qr.spt = res_spt(W);
+        Qr.stage_e = (int)stage_entries(Qr.spt);
+        const size_t smr = sm4 + 16 + 2 * res_stage_bytes(Qr.spt);
+        const long long rtiles = (E_->n_slices + Qr.spt - 1) / Qr.spt;
+        const int nr = std::min(nb_max_, grid_for((const void*)residual_df_kernel<CPLX, BLK>, kBlock, smr,
+                                                  rtiles * kBlock));
         nbr = nr;
         done_res = true;
-        residual_df_kernel<CPLX, BLK><<<nr, kBlock, sm4, st_>>>(
-            ell_view<float>(*E_), E_->val32lo, P_, reinterpret_cast<const DF*>(tl_.x64),
+        residual_df_kernel<CPLX, BLK><<<nr, kBlock, smr, st_>>>(
+            ell_view<float>(*E_), E_->val32lo, Qr, reinterpret_cast<const DF*>(tl_.x64),
             reinterpret_cast<const DF* const*>(bptr_), lane_src_, m_->mass32, m_->mass32lo, C_, tl_.r, tl_.d, tl_.p,
             partial_, gdiag_t());
       }
