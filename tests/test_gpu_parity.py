@@ -525,6 +525,30 @@ def test_multigrid_strength_hierarchy(lib, placement, order):
     _check(out.cpu().numpy(), ref, TOL_MIXED)
 
 
+@pytest.mark.parametrize("fine,coarse,cycle", [(2, 2, 0), (1, 1, 1), (3, 3, 1), (1, 2, 1)])
+@pytest.mark.parametrize("placement", ["vertex_vector", "cell"])
+def test_multigrid_sweep_counts(lib, monkeypatch, placement, fine, coarse, cycle):
+    """Any damped-Jacobi sweep count before and after the coarse correction
+    (finest level / coarser levels, IFILT_MG_FINE_SWEEPS / IFILT_MG_COARSE_SWEEPS)
+    and either cycle keep the V-cycle a symmetric preconditioner of the same
+    operator: each reaches the oracle's fields."""
+    import torch
+    monkeypatch.setenv("IFILT_MG_FINE_SWEEPS", str(fine))
+    monkeypatch.setenv("IFILT_MG_COARSE_SWEEPS", str(coarse))
+    m = _sphere(4, 61, polar=10.0, placement=placement)
+    P = oracle.build_problem(m, placement)
+    f = _fields(P, 2, 7)
+    ks = synth.log_wavenumbers(6000.0, 200.0, 5)
+    h = lib.prepare_mesh(m, placement, max_order=2, mg_strength=0.05)
+    assert h.multigrid()["levels"] >= 3
+    out, stats, st = lib.solve(h, torch.tensor(f, device="cuda"), ks, order=2, tol=1e-10,
+                               precision=lib.PREC_FP32_IR, n2_solver=2, precond=lib.PRECOND_MG, mg_cycle=cycle)
+    h.release()
+    assert st == 0, stats
+    _, ref = _oracle(m, placement, f, ks, 2)
+    _check(out.cpu().numpy(), ref, TOL_MIXED)
+
+
 @pytest.mark.parametrize("placement", ["vertex_vector", "cell"])
 def test_multigrid_strength_needs_no_more_iterations(lib, placement):
     """On a level-7 sphere with the benchmark's field and scales, the
