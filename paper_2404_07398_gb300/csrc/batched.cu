@@ -439,6 +439,9 @@ __device__ __forceinline__ void mg_epilogue(int64_t r, int64_t rowW, int W, int 
 #ifndef IFILT_MG_MINB_BLK
 #define IFILT_MG_MINB_BLK 2    // resident blocks per SM asked for the 2x2-block multigrid sweeps and residuals
 #endif
+#ifndef IFILT_MG_EB_COARSE
+#define IFILT_MG_EB_COARSE 4     // gathered entries in flight per row on the Galerkin levels (scalar rows)
+#endif
 #ifndef IFILT_MG_MINB_XFER
 #define IFILT_MG_MINB_XFER 4     // resident blocks per SM asked for the scalar-row restrictions and prolongations
 #endif
@@ -2891,6 +2894,9 @@ class EngineT final : public Engine {
   // entries gathered per batch: 2x2 blocks of two sub-rows take 2 at a time when a thread moves 8
   // lanes (register room), else 4
   static constexpr int kMgEB = (BLK && VM > 4) ? 2 : 4;
+  // ... and on the Galerkin levels of scalar rows (a (K, M) pair per entry, 12-16 entries a row)
+  template <int NSET>
+  static constexpr int mg_eb() { return (NSET == 2 && !BLK && VM == 4) ? IFILT_MG_EB_COARSE : kMgEB; }
   // output type of a gather: TM, or T for the last sweep of the finest level, whose
   // result z = V(r) enters the Krylov recursion (<r, z> and p = z + beta p): it is
   // kept unrounded so that the preconditioner stays the same symmetric operator
@@ -2899,7 +2905,7 @@ class EngineT final : public Engine {
   using MgTO = std::conditional_t<FINAL, T, TM>;
   template <int EPI, int NSET, bool FINAL = false>
   static const void* mg_fn() {
-    return (const void*)spmm_kernel<T, T, TM, MgTR<EPI, NSET>, MgTO<EPI, NSET, FINAL>, VM, CPLX, BLK, kMgEB,
+    return (const void*)spmm_kernel<T, T, TM, MgTR<EPI, NSET>, MgTO<EPI, NSET, FINAL>, VM, CPLX, BLK, mg_eb<NSET>(),
                                     mg_minb<EPI, NSET>(), EPI, NSET>;
   }
   static int64_t stage_entries_of(const DevEll& E, int spt) {
@@ -3002,7 +3008,7 @@ class EngineT final : public Engine {
     // level's rows fill their slices almost exactly
     EllView<T> V = ell_view<T>(E);
     if (&E == &m_->ell_k) V.rowq = nullptr;
-    spmm_kernel<T, T, TM, TR, TO, VM, CPLX, BLK, kMgEB, mg_minb<EPI, NSET>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
+    spmm_kernel<T, T, TM, TR, TO, VM, CPLX, BLK, mg_eb<NSET>(), mg_minb<EPI, NSET>(), EPI, NSET><<<blocks, kBlock, smem, st_>>>(
         V, Q, E.n_slices, src, static_cast<TO*>(out), mdiag, mg_cols_, partial, args);
     return blocks;
   }
