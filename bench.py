@@ -63,8 +63,6 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain-sample", type=int, default=3, help="scales (1-3) timed on the plain FP64 path")
     ap.add_argument("--serving", action="store_true", help="run the request-serving workload instead")
-    ap.add_argument("--precision-study", action="store_true",
-                    help="errors of FP32 / BF16 / FP64 per field and per spectrum bin (level-9 workload)")
     ap.add_argument("--precond", choices=["none", "jacobi", "mg"], default="mg", help="Krylov preconditioner")
     ap.add_argument("--check-every", type=int, default=4,
                     help="iterations per solver step (0: library default, 8 with multigrid); refinement rounds end "
@@ -648,63 +646,6 @@ def run_serving(args, world, rank):
         print(json.dumps(line), flush=True)
 
 
-def run_precision_study(args, world, rank):
-    """Error of each arithmetic, per filtered field-scale and per spectrum bin.
-
-    Level-9 scalar workload (2.6 M vertices, n = 2, 40 scales), two fields.
-    The reference is an FP32 + FP64-refinement multigrid solve stopped only at a
-    certified relative error bound of 1e-10 (||r||_{M^-1} <= 1e-10 ||x||_M);
-    each case is then solved as a user would (the paper's residual test at
-    1e-9, plus the bench's error bound where the case supports it) and compared
-    with it: relative L2 error of every filtered column, and relative error of
-    every spectrum bin."""
-    if rank != 0:
-        return
-    import torch
-    import synth
-    from paper_2404_07398_gb300 import api
-    api.load()
-    w = synth.workload("precision", n_fields=2)
-    h = api.prepare_mesh(w["mesh"], "vertex_scalar", max_order=2)
-    f = torch.tensor(w["fields"], device="cuda")
-    k = w["k"]
-    ocean = h.export("perm")
-
-    def run(**o):
-        torch.cuda.synchronize()
-        t0 = time.time()
-        out, st, status = api.solve(h, f, k, order=2, n2_solver=api.N2_COMPLEX, **o)
-        torch.cuda.synchronize()
-        e, sp, _ = api.spectrum(h, out, k)
-        x = out[:, :, 0, :].cpu().numpy()[:, :, ocean]
-        return x, sp, st.reshape(-1), status, time.time() - t0
-
-    xr, sr, str_, _, tr = run(tol=1e-12, precision=api.PREC_FP32_IR, precond=api.PRECOND_MG, err_tol=1e-10)
-    cases = {"fp32": dict(tol=args.tol, precision=api.PREC_FP32_IR, precond=api.PRECOND_MG, err_tol=args.err_tol),
-             "bf16": dict(tol=args.tol, precision=api.PREC_BF16_IR, precond=api.PRECOND_MG, err_tol=args.err_tol),
-             "fp64": dict(tol=args.tol, precision=api.PREC_FP64)}
-    res = {}
-    for name, o in cases.items():
-        x, sp, st, status, t = run(**o)
-        ef = np.linalg.norm(x - xr, axis=2) / np.linalg.norm(xr, axis=2)     # [F][K]
-        eb = np.abs(sp - sr) / np.abs(sr)                                     # [F][K-1]
-        res[name] = {"status": int(status), "seconds": round(t, 2),
-                     "field_err_max": float(ef.max()), "field_err_median": float(np.median(ef)),
-                     "field_err_per_scale_max": [float(v) for v in ef.max(axis=0)],
-                     "bin_err_max": float(eb.max()), "bin_err_median": float(np.median(eb)),
-                     "bin_err_per_bin_max": [float(v) for v in eb.max(axis=0)],
-                     "iters_max": int(st["iters"].max()), "err_bound_max": float(st["err_bound"].max())}
-    line = {"metric": "precision study: error per filtered field and per spectrum bin",
-            "config": {"workload": f"precision: icosahedral level 9 sphere, {w['mesh']['coords'].shape[0]} "
-                                   f"vertices, scalar at vertices, n=2, {k.size} wavenumbers, 2 fields",
-                       "reference": "FP32+FP64-IR multigrid solve to certified relative M-norm error 1e-10",
-                       "cases_tol": args.tol, "cases_err_tol": args.err_tol},
-            "reference": {"seconds": round(tr, 2), "err_bound_max": float(str_["err_bound"].max()),
-                          "iters_max": int(str_["iters"].max())},
-            "cases": res}
-    print(json.dumps(line), flush=True)
-
-
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
@@ -712,8 +653,6 @@ def main():
         run_reference(args, world, rank)
     elif args.serving:
         run_serving(args, world, rank)
-    elif args.precision_study:
-        run_precision_study(args, world, rank)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
