@@ -40,9 +40,6 @@ N_K = 40
 # roofline's `traffic` is this ratio times the bytes of an average timed launch.
 # A kernel that changed since its capture has no entry.
 TRAFFIC_RATIO = {
-    # update, cell placement: 3.4583 GB read + written vs 3.5016 GB algorithmic
-    # (911,865 rows x 160 lanes x 4 B x 6 vectors)
-    "update_cs_f32": 3.458295 / 3.501562,
     # fine Jacobi sweep, cell placement: 1.8114 GB read + written vs 1.7872 GB algorithmic
     # (iterate, right-hand side and output, ELL, mass and K diagonal)
     "mgsmooth0_cs_f32": 1.811418 / 1.787200,

@@ -763,12 +763,15 @@ __global__ void __launch_bounds__(kBlock, MINB) spmm_kernel(EllView<MV> A, Param
 // x += alpha p ; r -= alpha q ; partial <r, z> (slots [0, W): lane-wise for real,
 // (re, im) pairs for complex; z = r, or D^-1 r under Jacobi preconditioning)
 // and ||r||^2 (slots W + column) where <r, z> is not it: complex columns, and
-// real columns under Jacobi preconditioning.
-template <typename T, bool CPLX, bool BLK, bool PRE>
+// real columns under Jacobi preconditioning.  With MGJ it also writes the
+// multigrid's first fine-level sweep for the next iteration, zj = omega D^-1 r
+// (D = mass + shift * K diagonal, gdiag), as mg_jacobi_kernel would from the
+// stored r: one pass over r fewer per iteration.
+template <typename T, bool CPLX, bool BLK, bool PRE, bool MGJ = false>
 __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T* __restrict__ x, const T* __restrict__ p,
                                                         T* __restrict__ r, const T* __restrict__ q, Cols C,
                                                         double* __restrict__ partial, const T* __restrict__ mass,
-                                                        const T* __restrict__ gdiag) {
+                                                        const T* __restrict__ gdiag, T* __restrict__ zj, T omega) {
   if (*C.live == 0) return;
   constexpr int VEC = Pack<T>::N;
   constexpr int NS = BLK ? 2 : 1;
@@ -787,7 +790,7 @@ __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T
     for (int v = 0; v < VEC; v++) {
       if constexpr (CPLX) a[v] = (T)C.alpha[(l0 & ~1) + v];  // lanes (re, im) of one column
       else a[v] = (T)C.alpha[2 * (l0 + v)];
-      sh[v] = PRE ? (T)C.shift[CPLX ? (l0 + v) >> 1 : l0 + v] : (T)0;
+      sh[v] = (PRE || MGJ) ? (T)C.shift[CPLX ? (l0 + v) >> 1 : l0 + v] : (T)0;
     }
     const int64_t rowW = (int64_t)NS * W;
     int chain = 0;
@@ -799,7 +802,7 @@ __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T
 #pragma unroll
         for (int v = 0; v < ND2; v++) d2[v].flush();
       }
-      const T mr = PRE ? mass[row] : (T)0, gr = PRE ? gdiag[row] : (T)0;
+      const T mr = (PRE || MGJ) ? mass[row] : (T)0, gr = (PRE || MGJ) ? gdiag[row] : (T)0;
 #pragma unroll
       for (int b = 0; b < NS; b++) {
         const int64_t off = row * rowW + (int64_t)b * W + l0;
@@ -845,6 +848,13 @@ __global__ void __launch_bounds__(kBlock, BLK ? 3 : 4) update_kernel(Params P, T
         }
         stp(x + off, xv);
         stp(r + off, rv);
+        if constexpr (MGJ) {
+          Pack<T> zo;
+          smooth_jacobi<T, CPLX, VEC>(mr, gr, sh, rv.v, zo.v);
+#pragma unroll
+          for (int v = 0; v < VEC; v++) zo.v[v] *= omega;
+          stp(zj + off, zo);
+        }
       }
     }
 #pragma unroll
@@ -2385,7 +2395,9 @@ class EngineT final : public Engine {
     for (int it = 0; it < m_it_; it++) {
       if (mg_on_) {
         // preconditioned order: z = V(r), beta from <r, z>, p = z + beta p, then q = S p ...
-        vcycle(0, tl_.r, tl_.q);  // z = V(r) into q (free until the SpMM below)
+        // z = V(r) into q (free until the SpMM below); after the first iteration of the step the
+        // update kernel has already written the finest level's first sweep
+        vcycle(0, tl_.r, tl_.q, it > 0);
         const T* z = tl_.q;
         chk("vcycle");
         finish_rho_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbz_, partial2_, C_);
@@ -2402,14 +2414,20 @@ class EngineT final : public Engine {
       finish_alpha_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nb_, partial_, C_);
       chk("finish_alpha");
       pmark(kCatFinish, 0.0);
+      bool mgj = false;  // this update also writes the next iteration's first fine sweep
+      if constexpr (sizeof(T) == 4) mgj = mg_on_ && it + 1 < m_it_;
       if (gdiag_t())
         update_kernel<T, CPLX, BLK, true><<<nbu_, kBlock, sm3, st_>>>(P_, tl_.d, tl_.p, tl_.r, tl_.q, C_, partial_,
-                                                                    mass_t(), gdiag_t());
-      else
+                                                                    mass_t(), gdiag_t(), nullptr, (T)0);
+      else if (mgj) {
+        if constexpr (sizeof(T) == 4)
+          update_kernel<T, CPLX, BLK, false, true><<<nbu_, kBlock, sm3, st_>>>(
+              P_, tl_.d, tl_.p, tl_.r, tl_.q, C_, partial_, mass_t(), m_->diag_k32, mgb_[0].a, (T)(*mgl_)[0].omega);
+      } else
         update_kernel<T, CPLX, BLK, false><<<nbu_, kBlock, sm3, st_>>>(P_, tl_.d, tl_.p, tl_.r, tl_.q, C_,
-                                                                     partial_, mass_t(), nullptr);
+                                                                     partial_, mass_t(), nullptr, nullptr, (T)0);
       chk("update");
-      pmark(kCatUpdate, 6.0 * vb + pre_b);
+      pmark(kCatUpdate, 6.0 * vb + pre_b + (mgj ? vb + 2.0 * rows_t : 0.0));
       finish_beta_kernel<CPLX><<<fg, fb, 0, st_>>>(P_, nbu_, partial_, C_);
       chk("finish_beta");
       pmark(kCatFinish, 0.0);
@@ -2426,7 +2444,10 @@ class EngineT final : public Engine {
     marking_ = false;
     IFILT_CUDA(cudaMemcpyAsync(h_cnt_, C_.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st_));
   }
-  int launches_per_step() const { return 7 + 5 * m_it_ + (mg_on_ ? m_it_ * (mg_launches() + 1) : 0); }
+  // (with multigrid the updates of all but the last iteration replace the next cycle's first fine sweep)
+  int launches_per_step() const {
+    return 7 + 5 * m_it_ + (mg_on_ ? m_it_ * (mg_launches() + 1) - (m_it_ - 1) : 0);
+  }
 
   void capture() {
     if (exec_) cudaGraphExecDestroy(exec_);
@@ -3091,10 +3112,10 @@ class EngineT final : public Engine {
   // sweeps only on the last level).  Returns the buffer holding the result.  On level 0 the last sweep
   // writes the result z in T into zout and leaves the partials of <rhs, z> in
   // partial2_.
-  TM* vcycle(size_t l, const void* rhs, T* zout = nullptr) {
+  TM* vcycle(size_t l, const void* rhs, T* zout = nullptr, bool first_done = false) {
     MgBuf& B = mgb_[l];
     const bool last = l + 1 == mgl_->size();
-    mg_jacobi(l, rhs, B.a);
+    if (!first_done) mg_jacobi(l, rhs, B.a);  // else B.a holds it already (level 0, from the update)
     if (last) {
       TM* x = B.a;
       TM* y = B.b;
