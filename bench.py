@@ -40,6 +40,10 @@ N_K = 40
 # roofline's `traffic` is this ratio times the bytes of an average timed launch.
 # A kernel that changed since its capture has no entry.
 TRAFFIC_RATIO = {
+    # update with the fused first fine sweep, cell placement: 4.0458 GB read + written vs 4.0925 GB
+    # algorithmic (911,865 rows x 160 lanes x 4 B x 7 vectors, mass and K diagonal); the update
+    # without it (a step's last iteration) measured 0.988 as well
+    "update_cs_f32": 4.045815 / 4.092500,
     # fine Jacobi sweep, cell placement: 1.8114 GB read + written vs 1.7872 GB algorithmic
     # (iterate, right-hand side and output, ELL, mass and K diagonal)
     "mgsmooth0_cs_f32": 1.811418 / 1.787200,
