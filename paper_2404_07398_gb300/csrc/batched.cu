@@ -2683,7 +2683,9 @@ class EngineT final : public Engine {
     launched_ = false;
     const int live = h_cnt_[0], notdone = h_cnt_[2];
     (void)live;
-    if (h_cnt_[3]) fail(IFILT_DEVICE_TIMEOUT, "SpMM stage copy did not complete within its wait limit");
+    if (h_cnt_[3])
+      fail(IFILT_DEVICE_TIMEOUT,
+           "a stage copy of the SpMM, a multigrid gather or the refinement residual did not complete in its wait limit");
     if (prof_) account_step();
     const int lc = live_columns();
     if (notdone < lc) {
